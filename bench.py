@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 HiCR communication path.
+
+Headline (one JSON line on stdout): batched memcpy between memory slots --
+256 HBM slots totalling 16 GiB (log-uniform 1-256 MiB, seeded bytes),
+100,000 ops per batch, sizes log-uniform 16 B - 4 MiB, 10% unaligned
+offsets, destinations disjoint within each of the fence epochs; one step =
+one CUDA-graph replay of every epoch's batch (validate + plan + persistent
+copy kernel) followed by fence(tag 0). value = algorithmic bytes (2n per op:
+n read + n written) / device time, GB/s.
+
+Side results in the same line: the large-segment case (1-4 MiB aligned ops),
+the per-op cudaMemcpyAsync plain form, the end-to-end API call with host op
+tables, SPSC/MPSC channel rates, and the CPU oracle baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import configs, splitmix  # noqa: E402
+
+METRIC = "HiCR memcpy GB/s vs HBM peak; channel msgs/s; p99 latency vs per-op plain"
+GiB = 1 << 30
+FENCE_TIMEOUT = 120_000_000_000
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--no-side", action="store_true", help="headline only (no plain/large/e2e/channels/CPU)")
+    p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU work for the oracle baseline")
+    return p.parse_args(argv)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Workload set-up on the device (through the C ABI).
+# ---------------------------------------------------------------------------
+def remap(ops, ids):
+    o = ops.copy()
+    m = np.asarray(ids, dtype=np.uint32)
+    o["dst"] = m[ops["dst"]]
+    o["src"] = m[ops["src"]]
+    return o
+
+
+def setup_slots(h, inst, w, seed):
+    ids = []
+    for s, sz in enumerate(w.slot_sizes):
+        sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, int(sz), 0), "hicr_mem_alloc")
+        h.check(h.hicr_util_fill(inst, sid, 0, int(sz), splitmix.fill_key_base(seed, s)), "fill")
+        ids.append(sid)
+    return ids
+
+
+def device_ops(ops):
+    import torch
+    return torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+
+
+def capture_epochs(h, inst, dops, epochs):
+    """One CUDA graph holding every epoch's device-validated batch in order."""
+    h.check(h.hicr_batch_reserve(inst, max(b - a for a, b in epochs)), "reserve")
+    h.check(h.hicr_graph_begin(inst), "graph_begin")
+    for a, b in epochs:
+        h.check(h.hicr_memcpy_batch_device(inst, dops.data_ptr() + 32 * a, b - a), "batch_device")
+    return h.check(h.hicr_graph_end(inst), "graph_end")
+
+
+def autotune(h, inst, dops, epochs, reps=3):
+    a, b = max(epochs, key=lambda e: e[1] - e[0])
+    st, cfg, ms = h.hicr_batch_autotune(inst, dops.data_ptr() + 32 * a, b - a, reps)
+    h.check(st, "autotune")
+    return cfg.as_dict(), ms
+
+
+def time_graph(h, inst, stream, g, steps, warmup, prof=False, dist=None):
+    """Device time of `steps` graph replays, each followed by fence(0)."""
+    import torch
+    for _ in range(warmup):
+        h.check(h.hicr_graph_launch(inst, g), "graph_launch")
+        h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+    copy_ms, launches = 0.0, 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0.record(stream)
+    for _ in range(steps):
+        h.check(h.hicr_graph_launch(inst, g), "graph_launch")
+        h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+        if prof:
+            ms, n = h.check(h.hicr_profile_read(inst), "profile_read")
+            copy_ms += ms
+            launches += n
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    return e0.elapsed_time(e1), copy_ms, launches
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle baseline: the oracle as it stands on a bounded sample.
+# ---------------------------------------------------------------------------
+CPU_SAMPLE = dict(n_slots=32, total_bytes=2 * GiB, slot_lo=1 << 20, slot_hi=256 << 20, n_ops=12_500)
+CPU_SAMPLE_TEXT = ("config-2 distribution at 1/8 scale: 32 slots, 2 GiB, 12,500 ops log-uniform 16 B-4 MiB, "
+                   "10% unaligned, all epochs; slot bytes set to a constant (the copy cost does not depend on values)")
+
+
+def oracle_sample(seed):
+    from oracle import memcpy as om
+    w = configs.batched(seed, **CPU_SAMPLE, name="cpu_sample")
+    cm = om.CommManager()
+    for sz in w.slot_sizes:
+        cm.register(om.SPACE_HBM, np.ones(int(sz), dtype=np.uint8))
+    return cm, w
+
+
+def oracle_pass(cm, w):
+    from oracle import memcpy as om
+    for a, b in w.epochs:
+        st, _ = cm.memcpy_batch(w.ops[a:b])
+        assert st == om.OK
+        cm.fence(0)
+    return 2 * w.total_bytes
+
+
+def cpu_baseline(seed, target_s):
+    cm, w = oracle_sample(seed)
+    oracle_pass(cm, w)  # first touch of every page
+    t0 = time.perf_counter()
+    nbytes, passes = 0, 0
+    while True:
+        nbytes += oracle_pass(cm, w)
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or passes >= 200:
+            break
+    return {"value": nbytes / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{CPU_SAMPLE_TEXT}; {passes} passes in {el:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle (the parity authority) timed on the host
+    cores on the same metric, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cm, w = oracle_sample(args.seed)
+    for _ in range(args.warmup):
+        oracle_pass(cm, w)
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(args.steps):
+        nbytes += oracle_pass(cm, w)
+    el = time.perf_counter() - t0
+    v = nbytes / el / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": "batched memcpy (CPU oracle sample)",
+                                            "sample": CPU_SAMPLE_TEXT},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE_TEXT},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm.
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2509_01425_gb300 import build
+    build.build()
+    from paper_2509_01425_gb300 import hicr as h
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    inst = h.check(h.hicr_init(dev), "hicr_init")
+    stream_ptr = h.check(h.hicr_pu_stream(inst, 0), "pu_stream")
+    stream = torch.cuda.ExternalStream(stream_ptr)
+    peak, peak_src = peaks()
+
+    w = configs.batched(args.seed)
+    ids = setup_slots(h, inst, w, args.seed)
+    lops = remap(w.ops, ids)
+    dops = device_ops(lops)
+    torch.cuda.synchronize()
+    tuned, tuned_ms = autotune(h, inst, dops, w.epochs)
+    h.check(h.hicr_profile_enable(inst, 1), "profile")
+    g = capture_epochs(h, inst, dops, w.epochs)
+    bytes_step = 2 * w.total_bytes
+
+    clocks = Clocks(dev)
+    clocks.start()
+    ms, copy_ms, launches = time_graph(h, inst, stream, g, args.steps, args.warmup, prof=True, dist=dist)
+    clk = clocks.stop()
+    h.check(h.hicr_profile_enable(inst, 0), "profile")
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
+    achieved = bytes_step * args.steps / (copy_ms * 1e-3) / 1e9 if copy_ms > 0 else None
+    n_epochs = len(w.epochs)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "batched memcpy: 256 HBM slots totalling 16 GiB (log-uniform 1-256 MiB), "
+                               "100,000 ops log-uniform 16 B-4 MiB, 10% unaligned, "
+                               f"{n_epochs} fence epochs, one CUDA graph per step + fence(0)",
+                   "ops_per_step": int(len(w.ops)), "bytes_moved_per_step": int(w.total_bytes),
+                   "algorithmic_bytes_per_step": int(bytes_step), "epochs": n_epochs,
+                   "l2": "no flush: 16 GiB of slots >> 126 MB L2", "batch_config": tuned,
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "kernel": "k_copy", "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "launches_timed": launches},
+        "gpu_launches": args.steps * 3 * n_epochs,
+        "clocks": clk,
+    }
+
+    if not args.no_side:
+        side = {}
+        # large-segment case (1-4 MiB aligned): the >= 80% of peak gate
+        wl = configs.batched_large(args.seed)
+        assert (wl.slot_sizes == w.slot_sizes).all()
+        dl = device_ops(remap(wl.ops, ids))
+        h.check(h.hicr_profile_enable(inst, 1), "profile")
+        h.check(h.hicr_profile_reset(inst), "profile")
+        gl = capture_epochs(h, inst, dl, wl.epochs)
+        lsteps = max(3, args.steps // 2)
+        lms, lcopy, ln = time_graph(h, inst, stream, gl, lsteps, 2, prof=True)
+        h.check(h.hicr_profile_enable(inst, 0), "profile")
+        lb = 2 * wl.total_bytes
+        side["large_segments"] = {"workload": "1-4 MiB aligned ops, same slots", "ops": int(len(wl.ops)),
+                                  "GB_per_s": lb * lsteps / (lms * 1e-3) / 1e9,
+                                  "copy_kernel_GB_per_s": lb * lsteps / (lcopy * 1e-3) / 1e9,
+                                  "frac_of_peak": lb * lsteps / (lms * 1e-3) / 1e9 / peak}
+        h.check(h.hicr_graph_destroy(inst, gl), "graph_destroy")
+        del dl
+
+        # plain form: one cudaMemcpyAsync per op, same op table, same epochs + fences
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for a, b in w.epochs:
+            h.check(h.hicr_memcpy_batch_plain(inst, lops[a:b]), "plain")
+            h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+        pl = time.perf_counter() - t0
+        side["plain_form"] = {"GB_per_s": bytes_step / pl / 1e9, "ms_per_step": pl * 1e3,
+                              "speedup_of_batched": (bytes_step / pl / 1e9) and value / world / (bytes_step / pl / 1e9)}
+
+        # end to end through the public API with host op tables
+        esteps = max(3, args.steps // 4)
+        for _ in range(2):
+            for a, b in w.epochs:
+                h.check(h.hicr_memcpy_batch(inst, lops[a:b]), "batch")
+                h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(esteps):
+            for a, b in w.epochs:
+                h.check(h.hicr_memcpy_batch(inst, lops[a:b]), "batch")
+                h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+            h.check(h.hicr_slot_counters_range(inst, ids[0], len(ids)), "counters")
+        el = time.perf_counter() - t0
+        line["e2e"] = {"value": bytes_step * esteps / el / 1e9, "unit": "GB/s",
+                       "h2d_bytes_per_step": int(32 * len(w.ops)), "d2h_bytes_per_step": int(16 * len(ids)),
+                       "steps": esteps, "call": "hicr_memcpy_batch (host ops) + hicr_fence per epoch, "
+                                                "hicr_slot_counters_range per step"}
+        line["side"] = side
+        if world == 1 and rank == 0:
+            line["cpu_baseline"] = cpu_baseline(args.seed, args.cpu_seconds)
+
+    h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")
+    h.check(h.hicr_finalize(inst), "finalize")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

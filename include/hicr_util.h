@@ -1,0 +1,40 @@
+/*
+ * hicr_util.h -- workload and checking utilities of libhicr_gb300.so.
+ *
+ * The HiCR paper has no counterpart to these calls: they produce synthetic
+ * slot contents on the device and digest slot bytes so that large results can
+ * be compared without copying them back. Conventions as in hicr.h.
+ */
+#ifndef HICR_UTIL_H
+#define HICR_UTIL_H
+
+#include <stdint.h>
+
+#include "hicr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Fill bytes [off, off+n) of `slot` so that byte i of the slot (counted from
+ * the slot start) is byte (i mod 8), little endian, of SplitMix64's first
+ * output for state key_base + floor(i/8), i.e. finalise(key_base + i/8 +
+ * 0x9E3779B97F4A7C15) with the published SplitMix64 finaliser (Steele, Lea
+ * and Flood, OOPSLA 2014). Runs on the communication stream (asynchronous).
+ * Errors: INVALID (dead slot), BOUNDS (off + n > size), UNSUPPORTED (host
+ * slot), DEVICE. */
+hicr_status hicr_util_fill(hicr_instance_t inst, hicr_slot_t slot, uint64_t off, uint64_t n,
+                           uint64_t key_base);
+
+/* Word digest of bytes [off, off+n) of `slot`: with w_j the little-endian
+ * 8-byte words of that range (last word zero-padded), D = sum_j w_j * (2j+1)
+ * mod 2^64. Synchronous (waits for the communication stream first).
+ * Errors: INVALID, BOUNDS, DEVICE. */
+hicr_status hicr_util_digest(hicr_instance_t inst, hicr_slot_t slot, uint64_t off, uint64_t n,
+                             uint64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HICR_UTIL_H */

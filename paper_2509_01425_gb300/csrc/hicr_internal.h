@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libhicr_gb300.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <chrono>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hicr.h"
+#include "../../include/hicr_util.h"
+
+namespace hicr {
+
+// -------------------------------------------------------------------------
+// Device-resident tables. Slot metadata word: bit 0 live, bits 1..3 memory
+// space, bits 8..31 tag.
+// -------------------------------------------------------------------------
+struct DevTables {
+  uint64_t* slot_base;             // [HICR_MAX_SLOTS] device-usable address
+  uint64_t* slot_size;             // [HICR_MAX_SLOTS]
+  uint32_t* slot_meta;             // [HICR_MAX_SLOTS]
+  unsigned long long* sent;        // [HICR_MAX_SLOTS]
+  unsigned long long* recv;        // [HICR_MAX_SLOTS]
+  unsigned long long* tag_ops;     // [HICR_MAX_TAGS]
+  unsigned long long* sticky;      // [2]: packed (first_bad << 8 | -status), 0 = none
+};
+
+__host__ __device__ inline uint32_t meta_pack(uint32_t live, uint32_t space, uint32_t tag) {
+  return (live & 1u) | ((space & 7u) << 1) | (tag << 8);
+}
+__host__ __device__ inline uint32_t meta_live(uint32_t m) { return m & 1u; }
+__host__ __device__ inline uint32_t meta_space(uint32_t m) { return (m >> 1) & 7u; }
+__host__ __device__ inline uint32_t meta_tag(uint32_t m) { return m >> 8; }
+
+// Supported (dst space, src space) pairs as a bit mask: bit (dst * 8 + src).
+__host__ __device__ inline bool pair_supported(uint32_t mask, uint32_t dsp, uint32_t ssp) {
+  return (mask >> (dsp * 8u + ssp)) & 1u;
+}
+
+// Control block of one batch (device memory).
+struct BatchCtrl {
+  unsigned long long claim;      // next chunk to hand out
+  unsigned long long nchunks;    // chunks in this batch (0 when invalid)
+  unsigned long long total;      // summed cost
+  unsigned long long bad;        // packed (index << 8 | -status) of the first bad op; ~0 = none
+};
+
+// Per-batch scratch, sized for `cap` ops.
+struct Scratch {
+  uint64_t cap = 0;
+  unsigned long long* cost = nullptr;    // [cap]
+  unsigned long long* cstart = nullptr;  // [cap + 1]
+  unsigned int* done = nullptr;          // [cap]
+  BatchCtrl* ctrl = nullptr;
+};
+
+struct BatchArgs {
+  const hicr_op_t* ops;
+  unsigned long long count;
+  DevTables dt;
+  unsigned long long* cost;
+  unsigned long long* cstart;
+  unsigned int* done;
+  BatchCtrl* ctrl;
+  unsigned int chunk;
+  unsigned int op_cost;
+  unsigned int support;
+  unsigned int engine;
+  unsigned int tma_min;
+  unsigned int tma_stage;
+};
+
+struct HostSlot {
+  uint64_t base = 0;     // device-usable address
+  void* host_ptr = nullptr;
+  uint64_t size = 0;
+  uint32_t space = 0;
+  uint32_t tag = 0;
+  bool live = false;
+  bool owned = false;    // allocated by hicr_mem_alloc
+};
+
+struct Pu {
+  cudaStream_t stream = nullptr;
+  bool owned = false;
+  bool live = false;
+};
+
+struct GraphRec {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool live = false;
+};
+
+struct Channel;  // channels.cu
+
+struct Instance {
+  int device = 0;
+  cudaDeviceProp prop{};
+  int sm_count = 0;
+  std::vector<HostSlot> slots;
+  std::vector<uint32_t> free_ids;
+  DevTables dt{};
+  uint32_t support = 0;
+  std::vector<Pu> pus;
+  uint32_t comm_pu = 0;
+
+  // hicr_memcpy queue and host-batch upload
+  std::vector<hicr_op_t> queue;
+  hicr_op_t* pinned[2] = {nullptr, nullptr};
+  uint64_t pinned_cap[2] = {0, 0};
+  cudaEvent_t pinned_ev[2] = {nullptr, nullptr};
+  int pinned_idx = 0;
+  hicr_op_t* d_ops = nullptr;
+  uint64_t d_ops_cap = 0;
+
+  Scratch scratch;
+  hicr_batch_config_t cfg{};
+  int checked = 0;
+
+  cudaEvent_t done_ev = nullptr;  // recorded after the last issued work
+  bool capturing = false;
+  std::vector<GraphRec> graphs;
+
+  std::unordered_map<uint64_t, cudaEvent_t> execs;
+  uint64_t next_exec = 1;
+
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs
+  size_t prof_used = 0;
+
+  std::vector<Channel*> channels;
+  std::string last_err;
+
+  cudaStream_t comm() const { return pus[comm_pu].stream; }
+};
+
+// Record a CUDA error on the instance and return HICR_ERR_DEVICE.
+hicr_status cuda_fail(Instance* in, cudaError_t e, const char* what);
+
+#define HICR_CUDA(in, call)                                   \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::hicr::cuda_fail((in), _e, #call); \
+  } while (0)
+
+// Validation shared by the host entry points (same rules the device plan
+// kernel applies).
+hicr_status validate_op(const Instance* in, const hicr_op_t& op);
+hicr_status first_hazard(const Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* bad);
+
+// memcpy.cu
+hicr_status ensure_scratch(Instance* in, uint64_t count);
+hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st);
+hicr_status record_done(Instance* in);
+hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns);
+void default_config(Instance* in, hicr_batch_config_t* c);
+hicr_status check_config(const Instance* in, const hicr_batch_config_t* c);
+
+// channels.cu
+void destroy_channels(Instance* in);
+
+inline uint64_t now_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+}  // namespace hicr
+
+struct hicr_instance_s {
+  hicr::Instance impl;
+};

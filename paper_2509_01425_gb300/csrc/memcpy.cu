@@ -1,0 +1,701 @@
+// Batched local-to-local memcpy between memory slots (HiCR paper Sec. 3.1.4,
+// "memcpy" and "fence"; Fig. 5). One batch = three kernels on the
+// communication stream:
+//
+//   k_plan  (grid over ops)  validate each op against the device slot table
+//                            with the same rules as the host, charge it
+//                            cost = n + op_cost, zero its piece counter;
+//   k_scan  (one CTA)        exclusive prefix sum of the costs, chunk count,
+//                            first bad op -> the batch copies nothing and the
+//                            error is left for the next fence;
+//   k_copy  (persistent)     every warp repeatedly claims a chunk of
+//                            `chunk` cost units, finds the op holding its
+//                            first unit by a 32-ary search of the prefix sums,
+//                            and copies the byte pieces of every op the chunk
+//                            overlaps. The warp that finishes an op's last
+//                            piece bumps sent[src], recv[dst] and the tag
+//                            counters (the message counters fence reads).
+//
+// The cost model (bytes + a fixed per-op charge) is the size binning: large
+// ops are cut into many chunks that different warps copy in parallel, runs of
+// small ops are packed into one chunk, and the per-op charge keeps a warp
+// from being handed too many tiny ops at once.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "hicr_internal.h"
+
+namespace hicr {
+
+static constexpr unsigned FULL = 0xffffffffu;
+static constexpr unsigned long long NO_BAD = ~0ull;
+
+// ---------------------------------------------------------------------------
+// Validation on the device: the rules of validate_op() in runtime.cu.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dev_validate(const DevTables& dt, unsigned support, const hicr_op_t& op) {
+  if (op.dst >= HICR_MAX_SLOTS || op.src >= HICR_MAX_SLOTS) return HICR_ERR_INVALID;
+  const uint32_t md = dt.slot_meta[op.dst], ms = dt.slot_meta[op.src];
+  if (!meta_live(md) || !meta_live(ms)) return HICR_ERR_INVALID;
+  if (!pair_supported(support, meta_space(md), meta_space(ms))) return HICR_ERR_UNSUPPORTED;
+  const uint64_t ds = dt.slot_size[op.dst], ss = dt.slot_size[op.src];
+  if (op.src_off > ss || op.n > ss - op.src_off) return HICR_ERR_BOUNDS;
+  if (op.dst_off > ds || op.n > ds - op.dst_off) return HICR_ERR_BOUNDS;
+  if (op.dst == op.src && op.n > 0 && op.dst_off < op.src_off + op.n && op.src_off < op.dst_off + op.n)
+    return HICR_ERR_OVERLAP;
+  return HICR_OK;
+}
+
+__global__ void k_plan(BatchArgs a) {
+  const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.count) return;
+  const hicr_op_t op = a.ops[i];
+  const int st = dev_validate(a.dt, a.support, op);
+  if (st != HICR_OK) atomicMin(&a.ctrl->bad, (i << 8) | (unsigned long long)(-st));
+  a.cost[i] = op.n + a.op_cost;
+  a.done[i] = 0;
+}
+
+// Single-CTA exclusive scan (1024 threads): thread t sums a contiguous run
+// of ceil(count / 1024) costs, the 1024 run totals are scanned with warp
+// shuffles, then every run is written out.
+__global__ void __launch_bounds__(1024) k_scan(BatchArgs a) {
+  __shared__ unsigned long long warp_tot[32];
+  const unsigned t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned long long n = a.count;
+  const unsigned long long per = (n + 1023) / 1024;
+  const unsigned long long b = per * t, e = min(n, b + per);
+  unsigned long long s = 0;
+  for (unsigned long long i = b; i < e; ++i) s += a.cost[i];
+  // inclusive scan within the warp
+  unsigned long long x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(FULL, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long v = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(FULL, v, o);
+      if (lane >= (unsigned)o) v += y;
+    }
+    warp_tot[lane] = v;  // inclusive over warps
+  }
+  __syncthreads();
+  unsigned long long run = x - s + (w ? warp_tot[w - 1] : 0ull);  // exclusive start of this run
+  for (unsigned long long i = b; i < e; ++i) {
+    a.cstart[i] = run;
+    run += a.cost[i];
+  }
+  if (t == 1023) {
+    const unsigned long long total = warp_tot[31];
+    a.cstart[n] = total;
+    const unsigned long long bad = a.ctrl->bad;
+    a.ctrl->total = total;
+    a.ctrl->claim = 0;
+    if (bad != NO_BAD) {
+      a.ctrl->nchunks = 0;
+      // keep the first failure until a fence reads it
+      atomicCAS(a.dt.sticky, 0ull, bad);
+    } else {
+      a.ctrl->nchunks = (total + a.chunk - 1) / a.chunk;
+    }
+    a.ctrl->bad = NO_BAD;  // ready for the next batch
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative byte copy.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ld16(const uint4* p) { return __ldcs(p); }
+__device__ __forceinline__ void st16(uint4* p, const uint4& v) { __stcs(p, v); }
+
+// Destination is 16-byte aligned, source is k = 4*Q + r/8 bytes past the
+// aligned word sa[0] (k in 1..15). Word j of the output is bytes
+// [k + 16j, k + 16j + 16) of the aligned source stream, assembled from the
+// two aligned words sa[j] and sa[j+1] with funnel shifts. Every aligned
+// source word loaded holds at least one byte of the requested range, so the
+// loads never leave the 16-byte blocks of the source range.
+template <int Q>
+__device__ __forceinline__ uint4 shift_pair(const uint4& a, const uint4& b, unsigned r) {
+  const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  uint4 o;
+  o.x = __funnelshift_r(w[Q + 0], w[Q + 1], r);
+  o.y = __funnelshift_r(w[Q + 1], w[Q + 2], r);
+  o.z = __funnelshift_r(w[Q + 2], w[Q + 3], r);
+  o.w = __funnelshift_r(w[Q + 3], w[Q + 4], r);
+  return o;
+}
+
+template <int Q>
+__device__ __forceinline__ void copy_shifted(uint4* __restrict__ dw, const uint4* __restrict__ sa,
+                                             unsigned long long nw, unsigned r, unsigned lane) {
+  unsigned long long j = lane;
+  for (; j + 96 < nw; j += 128) {
+    uint4 a0 = ld16(sa + j), b0 = ld16(sa + j + 1);
+    uint4 a1 = ld16(sa + j + 32), b1 = ld16(sa + j + 33);
+    uint4 a2 = ld16(sa + j + 64), b2 = ld16(sa + j + 65);
+    uint4 a3 = ld16(sa + j + 96), b3 = ld16(sa + j + 97);
+    st16(dw + j, shift_pair<Q>(a0, b0, r));
+    st16(dw + j + 32, shift_pair<Q>(a1, b1, r));
+    st16(dw + j + 64, shift_pair<Q>(a2, b2, r));
+    st16(dw + j + 96, shift_pair<Q>(a3, b3, r));
+  }
+  for (; j < nw; j += 32) st16(dw + j, shift_pair<Q>(ld16(sa + j), ld16(sa + j + 1), r));
+}
+
+__device__ __forceinline__ void copy_aligned(uint4* __restrict__ dw, const uint4* __restrict__ sw,
+                                             unsigned long long nw, unsigned lane) {
+  unsigned long long j = lane;
+  for (; j + 224 < nw; j += 256) {
+    uint4 v0 = ld16(sw + j), v1 = ld16(sw + j + 32), v2 = ld16(sw + j + 64), v3 = ld16(sw + j + 96);
+    uint4 v4 = ld16(sw + j + 128), v5 = ld16(sw + j + 160), v6 = ld16(sw + j + 192), v7 = ld16(sw + j + 224);
+    st16(dw + j, v0);
+    st16(dw + j + 32, v1);
+    st16(dw + j + 64, v2);
+    st16(dw + j + 96, v3);
+    st16(dw + j + 128, v4);
+    st16(dw + j + 160, v5);
+    st16(dw + j + 192, v6);
+    st16(dw + j + 224, v7);
+  }
+  for (; j < nw; j += 32) st16(dw + j, ld16(sw + j));
+}
+
+// Copy n bytes from s to d with all 32 lanes of the warp.
+__device__ __forceinline__ void warp_copy(uint8_t* __restrict__ d, const uint8_t* __restrict__ s,
+                                          unsigned long long n, unsigned lane) {
+  if (n < 64) {
+    for (unsigned long long k = lane; k < n; k += 32) d[k] = s[k];
+    return;
+  }
+  const unsigned head = (unsigned)((16u - ((uintptr_t)d & 15u)) & 15u);
+  if (lane < head) d[lane] = s[lane];
+  d += head;
+  s += head;
+  n -= head;
+  const unsigned long long nw = n >> 4;
+  const unsigned tail = (unsigned)(n & 15u);
+  uint4* dw = reinterpret_cast<uint4*>(d);
+  const unsigned k = (unsigned)((uintptr_t)s & 15u);
+  if (k == 0) {
+    copy_aligned(dw, reinterpret_cast<const uint4*>(s), nw, lane);
+  } else {
+    const uint4* sa = reinterpret_cast<const uint4*>(s - k);
+    const unsigned r = (k & 3u) * 8u;
+    switch (k >> 2) {
+      case 0: copy_shifted<0>(dw, sa, nw, r, lane); break;
+      case 1: copy_shifted<1>(dw, sa, nw, r, lane); break;
+      case 2: copy_shifted<2>(dw, sa, nw, r, lane); break;
+      default: copy_shifted<3>(dw, sa, nw, r, lane); break;
+    }
+  }
+  if (lane < tail) d[nw * 16 + lane] = s[nw * 16 + lane];
+}
+
+// Largest i < count with cstart[i] <= key (cstart[0] = 0 <= key), found by
+// the whole warp: each round the lanes probe 32 evenly spaced positions.
+__device__ __forceinline__ unsigned long long find_op(const unsigned long long* __restrict__ cstart,
+                                                      unsigned long long count, unsigned long long key,
+                                                      unsigned lane) {
+  unsigned long long L = 0, R = count;
+  while (R - L > 32) {
+    const unsigned long long step = (R - L + 31) / 32;
+    const unsigned long long pos = L + lane * step;
+    const bool le = pos < R && cstart[pos] <= key;
+    const unsigned m = __ballot_sync(FULL, le);
+    const unsigned k = 31u - __clz(m);
+    const unsigned long long nL = L + k * step;
+    R = min(R, nL + step);
+    L = nL;
+  }
+  const unsigned long long pos = L + lane;
+  const bool le = pos < R && cstart[pos] <= key;
+  const unsigned m = __ballot_sync(FULL, le);
+  return L + (31u - __clz(m));
+}
+
+__device__ __forceinline__ void op_complete(const BatchArgs& a, const hicr_op_t& op) {
+  __threadfence();
+  atomicAdd(&a.dt.sent[op.src], 1ull);
+  atomicAdd(&a.dt.recv[op.dst], 1ull);
+  const uint32_t ts = meta_tag(a.dt.slot_meta[op.src]);
+  const uint32_t td = meta_tag(a.dt.slot_meta[op.dst]);
+  atomicAdd(&a.dt.tag_ops[ts], 1ull);
+  if (td != ts) atomicAdd(&a.dt.tag_ops[td], 1ull);
+}
+
+__global__ void __launch_bounds__(1024) k_copy(BatchArgs a) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long nchunks = *(volatile unsigned long long*)&a.ctrl->nchunks;
+  const unsigned long long total = *(volatile unsigned long long*)&a.ctrl->total;
+  const unsigned long long chunk = a.chunk;
+  for (;;) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(&a.ctrl->claim, 1ull);
+    c = __shfl_sync(FULL, c, 0);
+    if (c >= nchunks) break;
+    const unsigned long long lo = c * chunk;
+    const unsigned long long hi = min(lo + chunk, total);
+    for (unsigned long long i = find_op(a.cstart, a.count, lo, lane); i < a.count; ++i) {
+      const unsigned long long cs = a.cstart[i];
+      if (cs >= hi) break;
+      const hicr_op_t op = a.ops[i];
+      const unsigned long long bs = cs + a.op_cost;  // cost coordinate of byte 0
+      const unsigned long long be = bs + op.n;       // == cstart[i + 1]
+      const unsigned long long b0 = lo > bs ? lo - bs : 0ull;
+      const unsigned long long b1 = (hi < be ? hi : be) > bs ? (hi < be ? hi : be) - bs : 0ull;
+      if (b1 > b0) {
+        uint8_t* d = reinterpret_cast<uint8_t*>(a.dt.slot_base[op.dst]) + op.dst_off + b0;
+        const uint8_t* s = reinterpret_cast<const uint8_t*>(a.dt.slot_base[op.src]) + op.src_off + b0;
+        warp_copy(d, s, b1 - b0, lane);
+      }
+      // this chunk's piece of op i is done
+      const unsigned pieces = (unsigned)((be - 1) / chunk - cs / chunk + 1);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned prev = atomicAdd(&a.done[i], 1u);
+        if (prev + 1 == pieces) op_complete(a, op);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+
+void default_config(Instance* in, hicr_batch_config_t* c) {
+  memset(c, 0, sizeof(*c));
+  c->chunk_bytes = 64 * 1024;
+  c->op_cost_bytes = 2048;
+  c->blocks_per_sm = 2;
+  c->threads = 512;
+  c->engine = 0;
+  c->tma_min_bytes = 32 * 1024;
+  (void)in;
+}
+
+hicr_status check_config(const Instance* in, const hicr_batch_config_t* c) {
+  (void)in;
+  if (c->chunk_bytes < 1024 || c->chunk_bytes % 1024 || c->chunk_bytes > (64u << 20)) return HICR_ERR_INVALID;
+  if (c->op_cost_bytes < 1 || c->op_cost_bytes > (1u << 20)) return HICR_ERR_INVALID;
+  if (c->blocks_per_sm < 1 || c->blocks_per_sm > 32) return HICR_ERR_INVALID;
+  if (c->threads < 32 || c->threads > 1024 || c->threads % 32) return HICR_ERR_INVALID;
+  if (c->engine > 1) return HICR_ERR_INVALID;
+  if (c->tma_min_bytes < 1024) return HICR_ERR_INVALID;
+  return HICR_OK;
+}
+
+hicr_status ensure_scratch(Instance* in, uint64_t count) {
+  if (count <= in->scratch.cap && in->scratch.cost) return HICR_OK;
+  if (in->capturing) return HICR_ERR_INVALID;
+  uint64_t cap = std::max<uint64_t>(count, 1024);
+  cap = std::max<uint64_t>(cap, in->scratch.cap * 2 > cap ? std::min<uint64_t>(in->scratch.cap * 2, cap * 2) : cap);
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  if (in->scratch.cost) cudaFree(in->scratch.cost);
+  in->scratch = Scratch();
+  const size_t bytes = cap * 8 + (cap + 1) * 8 + cap * 4 + 64 + sizeof(BatchCtrl);
+  char* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    return HICR_ERR_NOMEM;
+  }
+  HICR_CUDA(in, e);
+  in->scratch.cap = cap;
+  in->scratch.cost = (unsigned long long*)p;
+  in->scratch.cstart = (unsigned long long*)(p + cap * 8);
+  in->scratch.done = (unsigned int*)(p + cap * 8 + (cap + 1) * 8);
+  in->scratch.ctrl = (BatchCtrl*)(p + ((cap * 8 + (cap + 1) * 8 + cap * 4 + 63) / 64) * 64);
+  BatchCtrl init;
+  init.claim = 0;
+  init.nchunks = 0;
+  init.total = 0;
+  init.bad = NO_BAD;
+  HICR_CUDA(in, cudaMemcpy(in->scratch.ctrl, &init, sizeof(init), cudaMemcpyHostToDevice));
+  return HICR_OK;
+}
+
+static BatchArgs make_args(Instance* in, const hicr_op_t* d_ops, uint64_t count) {
+  BatchArgs a;
+  a.ops = d_ops;
+  a.count = count;
+  a.dt = in->dt;
+  a.cost = in->scratch.cost;
+  a.cstart = in->scratch.cstart;
+  a.done = in->scratch.done;
+  a.ctrl = in->scratch.ctrl;
+  a.chunk = in->cfg.chunk_bytes;
+  a.op_cost = in->cfg.op_cost_bytes;
+  a.support = in->support;
+  a.engine = in->cfg.engine;
+  a.tma_min = in->cfg.tma_min_bytes;
+  a.tma_stage = 0;
+  return a;
+}
+
+static hicr_status prof_event(Instance* in, cudaEvent_t* ev) {
+  if (in->prof_used >= in->prof_ev.size()) {
+    cudaEvent_t e;
+    HICR_CUDA(in, cudaEventCreate(&e));
+    in->prof_ev.push_back(e);
+  }
+  *ev = in->prof_ev[in->prof_used++];
+  return HICR_OK;
+}
+
+static hicr_status record_prof(Instance* in, cudaEvent_t ev, cudaStream_t st) {
+  if (in->capturing) HICR_CUDA(in, cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+  else HICR_CUDA(in, cudaEventRecord(ev, st));
+  return HICR_OK;
+}
+
+hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st) {
+  if (count == 0) return HICR_OK;
+  hicr_status s = ensure_scratch(in, count);
+  if (s != HICR_OK) return s;
+  BatchArgs a = make_args(in, d_ops, count);
+  const unsigned pb = (unsigned)((count + 255) / 256);
+  k_plan<<<pb, 256, 0, st>>>(a);
+  k_scan<<<1, 1024, 0, st>>>(a);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (in->prof) {
+    if ((s = prof_event(in, &e0)) != HICR_OK) return s;
+    if ((s = prof_event(in, &e1)) != HICR_OK) return s;
+    if ((s = record_prof(in, e0, st)) != HICR_OK) return s;
+  }
+  const unsigned grid = (unsigned)in->sm_count * in->cfg.blocks_per_sm;
+  k_copy<<<grid, in->cfg.threads, 0, st>>>(a);
+  if (in->prof && (s = record_prof(in, e1, st)) != HICR_OK) return s;
+  HICR_CUDA(in, cudaGetLastError());
+  return HICR_OK;
+}
+
+// Copy a host op table to the device through a double-buffered pinned
+// staging area and launch it.
+static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
+  const int k = in->pinned_idx;
+  in->pinned_idx ^= 1;
+  // the staging buffer may still feed an earlier upload
+  HICR_CUDA(in, cudaEventSynchronize(in->pinned_ev[k]));
+  if (in->pinned_cap[k] < count) {
+    if (in->pinned[k]) cudaFreeHost(in->pinned[k]);
+    in->pinned[k] = nullptr;
+    in->pinned_cap[k] = 0;
+    uint64_t cap = std::max<uint64_t>(count, 4096);
+    HICR_CUDA(in, cudaHostAlloc((void**)&in->pinned[k], cap * sizeof(hicr_op_t), cudaHostAllocDefault));
+    in->pinned_cap[k] = cap;
+  }
+  if (in->d_ops_cap < count) {
+    HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+    if (in->d_ops) cudaFree(in->d_ops);
+    in->d_ops = nullptr;
+    in->d_ops_cap = 0;
+    uint64_t cap = std::max<uint64_t>(count, 4096);
+    cudaError_t e = cudaMalloc(&in->d_ops, cap * sizeof(hicr_op_t));
+    if (e == cudaErrorMemoryAllocation) {
+      (void)cudaGetLastError();
+      return HICR_ERR_NOMEM;
+    }
+    HICR_CUDA(in, e);
+    in->d_ops_cap = cap;
+  }
+  memcpy(in->pinned[k], ops, count * sizeof(hicr_op_t));
+  cudaStream_t st = in->comm();
+  HICR_CUDA(in, cudaMemcpyAsync(in->d_ops, in->pinned[k], count * sizeof(hicr_op_t), cudaMemcpyHostToDevice, st));
+  HICR_CUDA(in, cudaEventRecord(in->pinned_ev[k], st));
+  hicr_status s = launch_batch(in, in->d_ops, count, st);
+  if (s != HICR_OK) return s;
+  return record_done(in);
+}
+
+static hicr_status validate_all(Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
+  for (uint64_t i = 0; i < count; ++i) {
+    hicr_status s = validate_op(in, ops[i]);
+    if (s != HICR_OK) {
+      if (first_bad) *first_bad = i;
+      return s;
+    }
+  }
+  if (in->checked) {
+    uint64_t bad = 0;
+    hicr_status s = first_hazard(in, ops, count, &bad);
+    if (s != HICR_OK) {
+      if (first_bad) *first_bad = bad;
+      return s;
+    }
+  }
+  return HICR_OK;
+}
+
+}  // namespace hicr
+
+using namespace hicr;
+
+static Instance* I(hicr_instance_t h) { return h ? &h->impl : nullptr; }
+
+static const uint64_t QUEUE_MAX = 1u << 16;
+
+extern "C" {
+
+hicr_status hicr_memcpy(hicr_instance_t h, hicr_slot_t dst, uint64_t dst_off, hicr_slot_t src, uint64_t src_off,
+                        uint64_t n) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  hicr_op_t op;
+  op.dst = dst;
+  op.src = src;
+  op.dst_off = dst_off;
+  op.src_off = src_off;
+  op.n = n;
+  hicr_status s = validate_op(in, op);
+  if (s != HICR_OK) return s;
+  if (in->checked) {
+    in->queue.push_back(op);
+    uint64_t bad = 0;
+    s = first_hazard(in, in->queue.data(), in->queue.size(), &bad);
+    if (s != HICR_OK) {
+      in->queue.pop_back();
+      return s;
+    }
+  } else {
+    in->queue.push_back(op);
+  }
+  if (in->queue.size() >= QUEUE_MAX) return hicr_flush(h);
+  return HICR_OK;
+}
+
+hicr_status hicr_flush(hicr_instance_t h) {
+  Instance* in = I(h);
+  if (!in) return HICR_ERR_INVALID;
+  if (in->queue.empty()) return HICR_OK;
+  if (in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = upload_and_launch(in, in->queue.data(), in->queue.size());
+  in->queue.clear();
+  return s;
+}
+
+hicr_status hicr_memcpy_batch(hicr_instance_t h, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
+  Instance* in = I(h);
+  if (!in || (count && !ops) || in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = validate_all(in, ops, count, first_bad);
+  if (s != HICR_OK) return s;
+  if (count == 0) return HICR_OK;
+  // queued single ops belong to the same epoch and go first
+  if ((s = hicr_flush(h)) != HICR_OK) return s;
+  return upload_and_launch(in, ops, count);
+}
+
+hicr_status hicr_memcpy_batch_device(hicr_instance_t h, const hicr_op_t* d_ops, uint64_t count) {
+  Instance* in = I(h);
+  if (!in || (count && !d_ops) || ((uintptr_t)d_ops & 7u)) return HICR_ERR_INVALID;
+  if (count == 0) return HICR_OK;
+  if (in->capturing && count > in->scratch.cap) return HICR_ERR_INVALID;
+  hicr_status s = hicr_flush(h);
+  if (s != HICR_OK) return s;
+  s = launch_batch(in, d_ops, count, in->comm());
+  if (s != HICR_OK) return s;
+  return record_done(in);
+}
+
+hicr_status hicr_batch_reserve(hicr_instance_t h, uint64_t max_ops) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  return ensure_scratch(in, max_ops);
+}
+
+hicr_status hicr_memcpy_batch_plain(hicr_instance_t h, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
+  Instance* in = I(h);
+  if (!in || (count && !ops) || in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = validate_all(in, ops, count, first_bad);
+  if (s != HICR_OK) return s;
+  if ((s = hicr_flush(h)) != HICR_OK) return s;
+  cudaStream_t st = in->comm();
+  for (uint64_t i = 0; i < count; ++i) {
+    const hicr_op_t& o = ops[i];
+    if (o.n == 0) continue;
+    void* d = (void*)(in->slots[o.dst].base + o.dst_off);
+    const void* sp = (const void*)(in->slots[o.src].base + o.src_off);
+    HICR_CUDA(in, cudaMemcpyAsync(d, sp, o.n, cudaMemcpyDefault, st));
+  }
+  return record_done(in);
+}
+
+hicr_status hicr_batch_get_config(hicr_instance_t h, hicr_batch_config_t* out) {
+  Instance* in = I(h);
+  if (!in || !out) return HICR_ERR_INVALID;
+  *out = in->cfg;
+  return HICR_OK;
+}
+
+hicr_status hicr_batch_set_config(hicr_instance_t h, const hicr_batch_config_t* cfg) {
+  Instance* in = I(h);
+  if (!in || !cfg || in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = check_config(in, cfg);
+  if (s != HICR_OK) return s;
+  in->cfg = *cfg;
+  return HICR_OK;
+}
+
+hicr_status hicr_graph_begin(hicr_instance_t h) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = hicr_flush(h);
+  if (s != HICR_OK) return s;
+  HICR_CUDA(in, cudaStreamBeginCapture(in->comm(), cudaStreamCaptureModeThreadLocal));
+  in->capturing = true;
+  return HICR_OK;
+}
+
+hicr_status hicr_graph_end(hicr_instance_t h, hicr_graph_t* out) {
+  Instance* in = I(h);
+  if (!in || !in->capturing || !out) return HICR_ERR_INVALID;
+  in->capturing = false;
+  GraphRec g;
+  HICR_CUDA(in, cudaStreamEndCapture(in->comm(), &g.graph));
+  cudaError_t e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g.graph);
+    return cuda_fail(in, e, "cudaGraphInstantiate");
+  }
+  g.live = true;
+  for (size_t i = 0; i < in->graphs.size(); ++i) {
+    if (!in->graphs[i].live) {
+      in->graphs[i] = g;
+      *out = (hicr_graph_t)(i + 1);
+      return HICR_OK;
+    }
+  }
+  in->graphs.push_back(g);
+  *out = (hicr_graph_t)in->graphs.size();
+  return HICR_OK;
+}
+
+hicr_status hicr_graph_launch(hicr_instance_t h, hicr_graph_t g) {
+  Instance* in = I(h);
+  if (!in || in->capturing || g == 0 || g > in->graphs.size() || !in->graphs[g - 1].live) return HICR_ERR_INVALID;
+  hicr_status s = hicr_flush(h);
+  if (s != HICR_OK) return s;
+  HICR_CUDA(in, cudaGraphLaunch(in->graphs[g - 1].exec, in->comm()));
+  return record_done(in);
+}
+
+hicr_status hicr_graph_destroy(hicr_instance_t h, hicr_graph_t g) {
+  Instance* in = I(h);
+  if (!in || g == 0 || g > in->graphs.size() || !in->graphs[g - 1].live) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  cudaGraphExecDestroy(in->graphs[g - 1].exec);
+  cudaGraphDestroy(in->graphs[g - 1].graph);
+  in->graphs[g - 1] = GraphRec();
+  return HICR_OK;
+}
+
+hicr_status hicr_profile_enable(hicr_instance_t h, int32_t on) {
+  Instance* in = I(h);
+  if (!in) return HICR_ERR_INVALID;
+  in->prof = on != 0;
+  return HICR_OK;
+}
+
+hicr_status hicr_profile_reset(hicr_instance_t h) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  in->prof_used = 0;
+  return HICR_OK;
+}
+
+hicr_status hicr_profile_read(hicr_instance_t h, float* copy_ms, uint32_t* launches) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  float tot = 0.f;
+  for (size_t k = 0; k + 1 < in->prof_used; k += 2) {
+    float ms = 0.f;
+    HICR_CUDA(in, cudaEventElapsedTime(&ms, in->prof_ev[k], in->prof_ev[k + 1]));
+    tot += ms;
+  }
+  if (copy_ms) *copy_ms = tot;
+  if (launches) *launches = (uint32_t)(in->prof_used / 2);
+  return HICR_OK;
+}
+
+hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint64_t count, uint32_t reps,
+                                hicr_batch_config_t* best, float* best_ms) {
+  Instance* in = I(h);
+  if (!in || !d_ops || count == 0 || reps == 0 || in->capturing) return HICR_ERR_INVALID;
+  hicr_status s = hicr_flush(h);
+  if (s != HICR_OK) return s;
+  if ((s = ensure_scratch(in, count)) != HICR_OK) return s;
+  const hicr_batch_config_t base = in->cfg;
+  std::vector<hicr_batch_config_t> cands;
+  const uint32_t chunks[] = {32u << 10, 64u << 10, 128u << 10, 256u << 10};
+  const uint32_t shapes[][2] = {{1, 1024}, {2, 512}, {4, 256}, {2, 1024}, {4, 512}};
+  const uint32_t costs[] = {1024, 4096};
+  for (uint32_t ch : chunks)
+    for (auto& sh : shapes)
+      for (uint32_t oc : costs) {
+        hicr_batch_config_t c = base;
+        c.chunk_bytes = ch;
+        c.blocks_per_sm = sh[0];
+        c.threads = sh[1];
+        c.op_cost_bytes = oc;
+        c.engine = 0;
+        cands.push_back(c);
+      }
+  cudaEvent_t e0, e1;
+  HICR_CUDA(in, cudaEventCreate(&e0));
+  HICR_CUDA(in, cudaEventCreate(&e1));
+  cudaStream_t st = in->comm();
+  float best_t = 1e30f;
+  hicr_batch_config_t best_c = base;
+  for (auto& c : cands) {
+    // skip shapes the device cannot hold
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_copy, c.threads, 0);
+    if (per_sm < (int)c.blocks_per_sm) continue;
+    in->cfg = c;
+    std::vector<float> ts;
+    for (uint32_t r = 0; r <= reps; ++r) {
+      cudaEventRecord(e0, st);
+      s = launch_batch(in, d_ops, count, st);
+      if (s != HICR_OK) break;
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        s = cuda_fail(in, e, "autotune");
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r) ts.push_back(ms);
+    }
+    if (s != HICR_OK) break;
+    std::sort(ts.begin(), ts.end());
+    const float med = ts[ts.size() / 2];
+    if (med < best_t) {
+      best_t = med;
+      best_c = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  in->cfg = best_c;
+  if (s != HICR_OK) return s;
+  hicr_status bst = HICR_OK;
+  uint64_t bad = 0;
+  hicr_batch_error(h, &bst, &bad);
+  if (bst != HICR_OK) return bst;
+  if (best) *best = best_c;
+  if (best_ms) *best_ms = best_t;
+  return record_done(in);
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Device fill and digest utilities (no counterpart in the HiCR paper): the
+// seeded slot contents of the synthetic workloads and a word digest that lets
+// large results be compared without copying them to the host.
+#include "hicr_internal.h"
+#include "splitmix.cuh"
+
+namespace hicr {
+
+// Byte i of the slot (i in [off, off+n)) = byte (i mod 8), little endian, of
+// first_output(key_base + i/8). Whole 8-byte words are stored at once when
+// the slot base is 8-byte aligned.
+__global__ void k_fill(uint8_t* base, unsigned long long off, unsigned long long n, unsigned long long key_base) {
+  const unsigned long long end = off + n;
+  const unsigned long long w0 = off >> 3, w1 = (end + 7) >> 3;
+  const bool aligned = ((uintptr_t)base & 7u) == 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long w = w0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+    const uint64_t v = sm64_first_output(key_base + w);
+    const unsigned long long b = w << 3;
+    if (aligned && b >= off && b + 8 <= end) {
+      *reinterpret_cast<uint64_t*>(base + b) = v;
+    } else {
+      for (int k = 0; k < 8; ++k) {
+        const unsigned long long i = b + k;
+        if (i >= off && i < end) base[i] = (uint8_t)(v >> (8 * k));
+      }
+    }
+  }
+}
+
+// out += sum_j w_j * (2j + 1) over the little-endian words of p[0, n), the
+// last word zero-padded (*out must start at zero).
+__global__ void k_digest(const uint8_t* p, unsigned long long n, unsigned long long* out) {
+  const unsigned long long nw = (n + 7) >> 3;
+  const bool aligned = ((uintptr_t)p & 7u) == 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long acc = 0;
+  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < nw; j += stride) {
+    uint64_t w = 0;
+    const unsigned long long b = j << 3;
+    if (aligned && b + 8 <= n) {
+      w = *reinterpret_cast<const uint64_t*>(p + b);
+    } else {
+      for (int k = 0; k < 8; ++k)
+        if (b + k < n) w |= (uint64_t)p[b + k] << (8 * k);
+    }
+    acc += w * (2ull * j + 1ull);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+const void* builtin_fill_kernel() { return (const void*)k_fill; }
+const void* builtin_digest_kernel() { return (const void*)k_digest; }
+
+}  // namespace hicr
+
+using namespace hicr;
+
+extern "C" {
+
+hicr_status hicr_util_fill(hicr_instance_t h, hicr_slot_t slot, uint64_t off, uint64_t n, uint64_t key_base) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || slot >= in->slots.size() || !in->slots[slot].live || in->capturing) return HICR_ERR_INVALID;
+  const HostSlot& s = in->slots[slot];
+  if (off > s.size || n > s.size - off) return HICR_ERR_BOUNDS;
+  if (n == 0) return HICR_OK;
+  const unsigned grid = (unsigned)in->sm_count * 8;
+  k_fill<<<grid, 256, 0, in->comm()>>>((uint8_t*)s.base, off, n, key_base);
+  HICR_CUDA(in, cudaGetLastError());
+  return record_done(in);
+}
+
+hicr_status hicr_util_digest(hicr_instance_t h, hicr_slot_t slot, uint64_t off, uint64_t n, uint64_t* out) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || !out || slot >= in->slots.size() || !in->slots[slot].live || in->capturing) return HICR_ERR_INVALID;
+  const HostSlot& s = in->slots[slot];
+  if (off > s.size || n > s.size - off) return HICR_ERR_BOUNDS;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  unsigned long long* d = in->dt.sticky + 1;  // spare word next to the sticky error
+  cudaStream_t cs = in->comm();
+  HICR_CUDA(in, cudaMemsetAsync(d, 0, 8, cs));
+  if (n) {
+    const unsigned grid = (unsigned)in->sm_count * 8;
+    k_digest<<<grid, 256, 0, cs>>>((const uint8_t*)s.base + off, n, d);
+    HICR_CUDA(in, cudaGetLastError());
+  }
+  unsigned long long v = 0;
+  HICR_CUDA(in, cudaMemcpyAsync(&v, d, 8, cudaMemcpyDeviceToHost, cs));
+  HICR_CUDA(in, cudaStreamSynchronize(cs));
+  *out = v;
+  return record_done(in);
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+"""ctypes binding of libhicr_gb300.so: the C-ABI calls under the same names.
+
+Argument marshalling only. Every function returns the hicr_status code first,
+followed by its out-parameters, e.g. ``st, inst = hicr_init(0)``. ``check``
+turns a non-zero status into ``HicrError``. Buffers may be passed as integers
+(addresses), numpy arrays or objects exposing ``data_ptr()`` (torch tensors).
+
+The library must have been built (``paper_2509_01425_gb300.build.build()``);
+importing this module without it raises ImportError -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhicr_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_2509_01425_gb300.build.build()")
+lib = C.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------------------
+# Constants (values of include/hicr.h)
+# ---------------------------------------------------------------------------
+HICR_OK = 0
+HICR_ERR_INVALID = -1
+HICR_ERR_UNSUPPORTED = -2
+HICR_ERR_BOUNDS = -3
+HICR_ERR_OVERLAP = -4
+HICR_ERR_HAZARD = -5
+HICR_ERR_NOMEM = -6
+HICR_ERR_FULL = -7
+HICR_ERR_EMPTY = -8
+HICR_ERR_TOO_LARGE = -9
+HICR_ERR_TIMEOUT = -10
+HICR_ERR_BUSY = -11
+HICR_ERR_DEVICE = -12
+
+HICR_MAX_SLOTS = 65536
+HICR_MAX_TAGS = 1024
+HICR_MAX_SPACES = 4
+HICR_MAX_RESOURCES = 4
+HICR_SPACE_HBM = 0
+HICR_SPACE_HOST = 1
+HICR_RESOURCE_GPU = 0
+
+u8, u32, u64, i32 = C.c_uint8, C.c_uint32, C.c_uint64, C.c_int32
+vp = C.c_void_p
+
+
+class hicr_op_t(C.Structure):
+    _fields_ = [("dst", u32), ("src", u32), ("dst_off", u64), ("src_off", u64), ("n", u64)]
+
+
+class hicr_memory_space_t(C.Structure):
+    _fields_ = [("id", u32), ("kind", u32), ("device", i32), ("reserved", u32),
+                ("phys_size", u64), ("free_size", u64)]
+
+
+class hicr_compute_resource_t(C.Structure):
+    _fields_ = [("id", u32), ("kind", u32), ("device", i32), ("sm_count", u32),
+                ("max_threads_per_sm", u32), ("cc_major", u32), ("cc_minor", u32), ("reserved", u32),
+                ("l2_bytes", u64), ("smem_per_block_optin", u64)]
+
+
+class hicr_topology_t(C.Structure):
+    _fields_ = [("device", i32), ("n_spaces", u32), ("n_resources", u32), ("reserved", u32),
+                ("name", C.c_char * 128), ("spaces", hicr_memory_space_t * HICR_MAX_SPACES),
+                ("resources", hicr_compute_resource_t * HICR_MAX_RESOURCES)]
+
+
+class hicr_batch_config_t(C.Structure):
+    _fields_ = [("chunk_bytes", u32), ("op_cost_bytes", u32), ("blocks_per_sm", u32), ("threads", u32),
+                ("engine", u32), ("tma_min_bytes", u32), ("reserved", u32 * 2)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class hicr_exec_unit_t(C.Structure):
+    _fields_ = [("func", vp), ("grid", u32 * 3), ("block", u32 * 3), ("smem_bytes", u32), ("n_args", u32)]
+
+
+class HicrError(RuntimeError):
+    def __init__(self, status, what=""):
+        super().__init__(f"{what}: {hicr_status_str(status)} ({status})")
+        self.status = status
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, C.Array) or isinstance(x, C.Structure):
+        return C.addressof(x)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _decl(name, args, res=i32):
+    f = getattr(lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+H = vp  # hicr_instance_t
+
+_status_str = _decl("hicr_status_str", [i32], C.c_char_p)
+_init = _decl("hicr_init", [C.c_int, C.POINTER(vp)])
+_finalize = _decl("hicr_finalize", [H])
+_is_root = _decl("hicr_is_root", [H, C.POINTER(i32)])
+_topology = _decl("hicr_topology_query", [H, C.POINTER(hicr_topology_t)])
+_mem_alloc = _decl("hicr_mem_alloc", [H, u32, u64, u32, C.POINTER(u32)])
+_mem_free = _decl("hicr_mem_free", [H, u32])
+_slot_register = _decl("hicr_slot_register", [H, u32, vp, u64, u32, C.POINTER(u32)])
+_slot_deregister = _decl("hicr_slot_deregister", [H, u32])
+_slot_info = _decl("hicr_slot_info", [H, u32, C.POINTER(vp), C.POINTER(u64), C.POINTER(u32), C.POINTER(u32)])
+_memcpy = _decl("hicr_memcpy", [H, u32, u64, u32, u64, u64])
+_flush = _decl("hicr_flush", [H])
+_memcpy_batch = _decl("hicr_memcpy_batch", [H, vp, u64, C.POINTER(u64)])
+_memcpy_batch_device = _decl("hicr_memcpy_batch_device", [H, vp, u64])
+_batch_error = _decl("hicr_batch_error", [H, C.POINTER(i32), C.POINTER(u64)])
+_batch_reserve = _decl("hicr_batch_reserve", [H, u64])
+_set_checked = _decl("hicr_set_checked", [H, i32])
+_fence = _decl("hicr_fence", [H, u32, u64])
+_fence_slot = _decl("hicr_fence_slot", [H, u32, u64, u64, u64])
+_slot_counters = _decl("hicr_slot_counters", [H, u32, C.POINTER(u64), C.POINTER(u64)])
+_slot_counters_range = _decl("hicr_slot_counters_range", [H, u32, u32, vp, vp])
+_tag_counter = _decl("hicr_tag_counter", [H, u32, C.POINTER(u64)])
+_memcpy_batch_plain = _decl("hicr_memcpy_batch_plain", [H, vp, u64, C.POINTER(u64)])
+_batch_get_config = _decl("hicr_batch_get_config", [H, C.POINTER(hicr_batch_config_t)])
+_batch_set_config = _decl("hicr_batch_set_config", [H, C.POINTER(hicr_batch_config_t)])
+_batch_autotune = _decl("hicr_batch_autotune", [H, vp, u64, u32, C.POINTER(hicr_batch_config_t),
+                                                C.POINTER(C.c_float)])
+_graph_begin = _decl("hicr_graph_begin", [H])
+_graph_end = _decl("hicr_graph_end", [H, C.POINTER(u64)])
+_graph_launch = _decl("hicr_graph_launch", [H, u64])
+_graph_destroy = _decl("hicr_graph_destroy", [H, u64])
+_profile_enable = _decl("hicr_profile_enable", [H, i32])
+_profile_reset = _decl("hicr_profile_reset", [H])
+_profile_read = _decl("hicr_profile_read", [H, C.POINTER(C.c_float), C.POINTER(u32)])
+_pu_create = _decl("hicr_pu_create", [H, vp, C.POINTER(u32)])
+_pu_destroy = _decl("hicr_pu_destroy", [H, u32])
+_pu_stream = _decl("hicr_pu_stream", [H, u32, C.POINTER(vp)])
+_comm_set_pu = _decl("hicr_comm_set_pu", [H, u32])
+_exec_unit_builtin = _decl("hicr_exec_unit_builtin", [C.c_char_p, C.POINTER(hicr_exec_unit_t)])
+_exec_launch = _decl("hicr_exec_launch", [H, u32, C.POINTER(hicr_exec_unit_t), C.POINTER(vp), C.POINTER(u64)])
+_exec_query = _decl("hicr_exec_query", [H, u64, C.POINTER(i32)])
+_exec_await = _decl("hicr_exec_await", [H, u64, u64])
+_last_error_string = _decl("hicr_last_error_string", [H, C.c_char_p, u64])
+_util_fill = _decl("hicr_util_fill", [H, u32, u64, u64, u64])
+_util_digest = _decl("hicr_util_digest", [H, u32, u64, u64, C.POINTER(u64)])
+
+
+def hicr_status_str(s: int) -> str:
+    return _status_str(s).decode()
+
+
+def check(st, what="hicr"):
+    """Raise HicrError unless st (or st[0] of a tuple) is HICR_OK; return the outs."""
+    if isinstance(st, tuple):
+        if st[0] != HICR_OK:
+            raise HicrError(st[0], what)
+        return st[1] if len(st) == 2 else st[1:]
+    if st != HICR_OK:
+        raise HicrError(st, what)
+    return None
+
+
+def hicr_init(device: int = 0):
+    h = vp()
+    st = _init(device, C.byref(h))
+    return st, h
+
+
+def hicr_finalize(inst):
+    return _finalize(inst)
+
+
+def hicr_is_root(inst):
+    v = i32()
+    st = _is_root(inst, C.byref(v))
+    return st, v.value
+
+
+def hicr_topology_query(inst):
+    t = hicr_topology_t()
+    st = _topology(inst, C.byref(t))
+    return st, t
+
+
+def hicr_mem_alloc(inst, space, size, tag=0):
+    s = u32()
+    st = _mem_alloc(inst, space, size, tag, C.byref(s))
+    return st, s.value
+
+
+def hicr_mem_free(inst, slot):
+    return _mem_free(inst, slot)
+
+
+def hicr_slot_register(inst, space, ptr, size, tag=0):
+    s = u32()
+    st = _slot_register(inst, space, _ptr(ptr), size, tag, C.byref(s))
+    return st, s.value
+
+
+def hicr_slot_deregister(inst, slot):
+    return _slot_deregister(inst, slot)
+
+
+def hicr_slot_info(inst, slot):
+    p, n, sp, tg = vp(), u64(), u32(), u32()
+    st = _slot_info(inst, slot, C.byref(p), C.byref(n), C.byref(sp), C.byref(tg))
+    return st, (p.value or 0), n.value, sp.value, tg.value
+
+
+def hicr_memcpy(inst, dst, dst_off, src, src_off, n):
+    return _memcpy(inst, dst, dst_off, src, src_off, n)
+
+
+def hicr_flush(inst):
+    return _flush(inst)
+
+
+def _ops_ptr(ops):
+    if isinstance(ops, np.ndarray):
+        if ops.dtype.itemsize != 32 or not ops.flags.c_contiguous:
+            raise TypeError("op table must be a C-contiguous array of 32-byte records")
+        return ops.ctypes.data, len(ops)
+    raise TypeError("op table must be a numpy structured array")
+
+
+def hicr_memcpy_batch(inst, ops):
+    p, n = _ops_ptr(ops)
+    bad = u64(0)
+    st = _memcpy_batch(inst, p, n, C.byref(bad))
+    return st, bad.value
+
+
+def hicr_memcpy_batch_device(inst, d_ops, count):
+    return _memcpy_batch_device(inst, _ptr(d_ops), count)
+
+
+def hicr_batch_error(inst):
+    s, b = i32(), u64()
+    st = _batch_error(inst, C.byref(s), C.byref(b))
+    return st, s.value, b.value
+
+
+def hicr_batch_reserve(inst, max_ops):
+    return _batch_reserve(inst, max_ops)
+
+
+def hicr_set_checked(inst, on):
+    return _set_checked(inst, 1 if on else 0)
+
+
+def hicr_fence(inst, tag=0, timeout_ns=30_000_000_000):
+    return _fence(inst, tag, timeout_ns)
+
+
+def hicr_fence_slot(inst, slot, expect_sent, expect_recv, timeout_ns=30_000_000_000):
+    return _fence_slot(inst, slot, expect_sent, expect_recv, timeout_ns)
+
+
+def hicr_slot_counters(inst, slot):
+    s, r = u64(), u64()
+    st = _slot_counters(inst, slot, C.byref(s), C.byref(r))
+    return st, s.value, r.value
+
+
+def hicr_slot_counters_range(inst, first, count):
+    sent = np.zeros(count, dtype=np.uint64)
+    recv = np.zeros(count, dtype=np.uint64)
+    st = _slot_counters_range(inst, first, count, sent.ctypes.data, recv.ctypes.data)
+    return st, sent, recv
+
+
+def hicr_tag_counter(inst, tag):
+    v = u64()
+    st = _tag_counter(inst, tag, C.byref(v))
+    return st, v.value
+
+
+def hicr_memcpy_batch_plain(inst, ops):
+    p, n = _ops_ptr(ops)
+    bad = u64(0)
+    st = _memcpy_batch_plain(inst, p, n, C.byref(bad))
+    return st, bad.value
+
+
+def hicr_batch_get_config(inst):
+    c = hicr_batch_config_t()
+    st = _batch_get_config(inst, C.byref(c))
+    return st, c
+
+
+def hicr_batch_set_config(inst, cfg):
+    if isinstance(cfg, dict):
+        c = hicr_batch_config_t()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        cfg = c
+    return _batch_set_config(inst, C.byref(cfg))
+
+
+def hicr_batch_autotune(inst, d_ops, count, reps=3):
+    c = hicr_batch_config_t()
+    ms = C.c_float()
+    st = _batch_autotune(inst, _ptr(d_ops), count, reps, C.byref(c), C.byref(ms))
+    return st, c, ms.value
+
+
+def hicr_graph_begin(inst):
+    return _graph_begin(inst)
+
+
+def hicr_graph_end(inst):
+    g = u64()
+    st = _graph_end(inst, C.byref(g))
+    return st, g.value
+
+
+def hicr_graph_launch(inst, g):
+    return _graph_launch(inst, g)
+
+
+def hicr_graph_destroy(inst, g):
+    return _graph_destroy(inst, g)
+
+
+def hicr_profile_enable(inst, on):
+    return _profile_enable(inst, 1 if on else 0)
+
+
+def hicr_profile_reset(inst):
+    return _profile_reset(inst)
+
+
+def hicr_profile_read(inst):
+    ms, n = C.c_float(), u32()
+    st = _profile_read(inst, C.byref(ms), C.byref(n))
+    return st, ms.value, n.value
+
+
+def hicr_pu_create(inst, stream=None):
+    p = u32()
+    st = _pu_create(inst, _ptr(stream) if stream is not None else None, C.byref(p))
+    return st, p.value
+
+
+def hicr_pu_destroy(inst, pu):
+    return _pu_destroy(inst, pu)
+
+
+def hicr_pu_stream(inst, pu):
+    s = vp()
+    st = _pu_stream(inst, pu, C.byref(s))
+    return st, (s.value or 0)
+
+
+def hicr_comm_set_pu(inst, pu):
+    return _comm_set_pu(inst, pu)
+
+
+def hicr_exec_unit_builtin(name):
+    u = hicr_exec_unit_t()
+    st = _exec_unit_builtin(name.encode(), C.byref(u))
+    return st, u
+
+
+def hicr_exec_launch(inst, pu, unit, arg_values):
+    """arg_values: list of ctypes scalars (c_void_p, c_uint64, ...) in kernel
+    parameter order; their addresses are passed as cudaLaunchKernel expects."""
+    arr = (vp * max(1, len(arg_values)))(*[C.cast(C.pointer(a), vp) for a in arg_values])
+    e = u64()
+    st = _exec_launch(inst, pu, C.byref(unit), arr, C.byref(e))
+    return st, e.value
+
+
+def hicr_exec_query(inst, e):
+    d = i32()
+    st = _exec_query(inst, e, C.byref(d))
+    return st, d.value
+
+
+def hicr_exec_await(inst, e, timeout_ns=30_000_000_000):
+    return _exec_await(inst, e, timeout_ns)
+
+
+def hicr_last_error_string(inst):
+    buf = C.create_string_buffer(1024)
+    st = _last_error_string(inst, buf, 1024)
+    return st, buf.value.decode(errors="replace")
+
+
+def hicr_util_fill(inst, slot, off, n, key_base):
+    return _util_fill(inst, slot, off, n, key_base)
+
+
+def hicr_util_digest(inst, slot, off, n):
+    v = u64()
+    st = _util_digest(inst, slot, off, n, C.byref(v))
+    return st, v.value

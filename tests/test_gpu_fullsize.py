@@ -1,0 +1,57 @@
+"""Full-size batched memcpy (256 slots, 16 GiB, 100,000 ops, all fence epochs)
+in the launch configuration bench.py times (autotuned config, one CUDA graph
+per step): sampled bytes one by one against the oracle, counters exactly."""
+import numpy as np
+import pytest
+import torch
+
+import bench
+from oracle import memcpy as om
+from workloads import configs, splitmix
+from tests.gpu_util import device_bytes, h, inst  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _positions(w, slot, rng, n_random=4096):
+    size = int(w.slot_sizes[slot])
+    m = w.ops["dst"] == slot
+    d = w.ops["dst_off"][m].astype(np.int64)
+    n = w.ops["n"][m].astype(np.int64)
+    edges = np.concatenate([d - 1, d, d + n - 1, d + n, d + n // 2])
+    pos = np.concatenate([edges, rng.integers(0, size, n_random)])
+    return np.unique(pos[(pos >= 0) & (pos < size)])
+
+
+@pytest.mark.parametrize("maker", [configs.batched, configs.batched_large])
+def test_full_size_sampled_parity(h, inst, maker):
+    seed = 0
+    w = maker(seed)
+    ids = bench.setup_slots(h, inst, w, seed)
+    dops = bench.device_ops(bench.remap(w.ops, ids))
+    torch.cuda.synchronize()
+    bench.autotune(h, inst, dops, w.epochs)
+    g = bench.capture_epochs(h, inst, dops, w.epochs)
+    steps = 2
+    for _ in range(steps):
+        assert h.hicr_graph_launch(inst, g) == 0
+        assert h.hicr_fence(inst, 0, bench.FENCE_TIMEOUT) == 0
+    rng = np.random.default_rng(123)
+    init = lambda s, p: splitmix.fill_byte_at(seed, s, p)  # noqa: E731
+    checked = 0
+    for s in range(len(ids)):
+        st, ptr, size, _, _ = h.hicr_slot_info(inst, ids[s])
+        view = device_bytes(ptr, size)
+        pos = _positions(w, s, rng) if s in set(w.dst_slots.tolist()) else rng.integers(0, size, 2048)
+        got = view[torch.from_numpy(np.asarray(pos, dtype=np.int64)).cuda()].cpu().numpy()
+        exp = om.expected_bytes_at(w.ops, w.epochs, s, pos, init)
+        bad = np.nonzero(got != exp)[0]
+        assert len(bad) == 0, f"slot {s}: {len(bad)} of {len(pos)} sampled bytes differ, first at {pos[bad[0]]}"
+        checked += len(pos)
+    assert checked > 500_000
+    sent, recv = om.counters_from_ops(w.ops, len(ids))
+    st, gs, gr = h.hicr_slot_counters_range(inst, ids[0], len(ids))
+    assert st == 0
+    assert (gs == steps * sent).all() and (gr == steps * recv).all()
+    assert h.hicr_tag_counter(inst, 0) == (0, steps * len(w.ops))
+    assert h.hicr_graph_destroy(inst, g) == 0
