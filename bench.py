@@ -48,7 +48,23 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-side", action="store_true", help="headline only (no plain/large/e2e/channels/CPU)")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU work for the oracle baseline")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
     return p.parse_args(argv)
+
+
+def copy_traffic(alg_bytes_per_launch):
+    """DRAM bytes per k_copy launch scaled from the committed ncu capture, or
+    None when the kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_copy_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    src = open(os.path.join(ROOT, d["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+        return None
+    return d["traffic_over_algorithmic"] * alg_bytes_per_launch
 
 
 def peaks():
@@ -116,6 +132,16 @@ def remap(ops, ids):
     o["dst"] = m[ops["dst"]]
     o["src"] = m[ops["src"]]
     return o
+
+
+def scaled_batched(seed, scale=1.0, large=False):
+    """The batched-memcpy workload, or a fraction of it (slots, bytes and ops
+    scaled together; the size distributions are unchanged)."""
+    if scale == 1.0:
+        return configs.batched_large(seed) if large else configs.batched(seed)
+    kw = dict(n_slots=max(8, int(round(256 * scale))), total_bytes=int(16 * GiB * scale) // 4096 * 4096,
+              n_ops=max(100, int(100_000 * scale)))
+    return configs.batched_large(seed, **kw) if large else configs.batched(seed, **kw)
 
 
 def setup_slots(h, inst, w, seed):
@@ -267,7 +293,7 @@ def run_ours(args):
     stream = torch.cuda.ExternalStream(stream_ptr)
     peak, peak_src = peaks()
 
-    w = configs.batched(args.seed)
+    w = scaled_batched(args.seed, args.scale)
     ids = setup_slots(h, inst, w, args.seed)
     lops = remap(w.ops, ids)
     dops = device_ops(lops)
@@ -294,15 +320,19 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "batched memcpy: 256 HBM slots totalling 16 GiB (log-uniform 1-256 MiB), "
-                               "100,000 ops log-uniform 16 B-4 MiB, 10% unaligned, "
+        "config": {"workload": f"batched memcpy: {len(ids)} HBM slots totalling "
+                               f"{int(w.slot_sizes.sum()) / GiB:g} GiB (log-uniform 1-256 MiB), "
+                               f"{len(w.ops):,} ops log-uniform 16 B-4 MiB, 10% unaligned, "
                                f"{n_epochs} fence epochs, one CUDA graph per step + fence(0)",
+                   "scale": args.scale,
                    "ops_per_step": int(len(w.ops)), "bytes_moved_per_step": int(w.total_bytes),
                    "algorithmic_bytes_per_step": int(bytes_step), "epochs": n_epochs,
                    "l2": "no flush: 16 GiB of slots >> 126 MB L2", "batch_config": tuned,
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": copy_traffic(bytes_step / n_epochs),
+                     "algorithmic_bytes_per_launch": bytes_step / n_epochs,
                      "kernel": "k_copy", "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "launches_timed": launches},
         "gpu_launches": args.steps * 3 * n_epochs,
@@ -312,7 +342,7 @@ def run_ours(args):
     if not args.no_side:
         side = {}
         # large-segment case (1-4 MiB aligned): the >= 80% of peak gate
-        wl = configs.batched_large(args.seed)
+        wl = scaled_batched(args.seed, args.scale, large=True)
         assert (wl.slot_sizes == w.slot_sizes).all()
         dl = device_ops(remap(wl.ops, ids))
         h.check(h.hicr_profile_enable(inst, 1), "profile")
