@@ -203,6 +203,33 @@ hicr_status hicr_memcpy_batch(hicr_instance_t inst, const hicr_op_t* ops, uint64
  * hicr_batch_reserve while capturing), DEVICE. */
 hicr_status hicr_memcpy_batch_device(hicr_instance_t inst, const hicr_op_t* d_ops, uint64_t count);
 
+/* Largest op count hicr_memcpy_batch_noalloc accepts. */
+#define HICR_NOALLOC_MAX_OPS 32768u
+
+/* hicr_memcpy_batch_device for callers that must not allocate GPU memory at
+ * the moment they issue copies: a host framework that owns all device memory
+ * through its own pool and forbids allocations outside it, a latency-critical
+ * loop that cannot absorb the implicit device-wide synchronisation of
+ * cudaMalloc/cudaFree, or a process whose HBM is already handed to another
+ * allocator. The HiCR paper has no counterpart to this call; it only changes
+ * where this library keeps its per-batch scratch.
+ *  - This call allocates nothing: no cudaMalloc, cudaFree or allocating
+ *    library routine. Its scratch is one file-scope device array of 640.5 KiB
+ *    that every GPU which loads the library holds until the process exits.
+ *  - count <= HICR_NOALLOC_MAX_OPS, otherwise HICR_ERR_TOO_LARGE and nothing
+ *    is launched.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress, with the instance's device current); make that
+ *    first call before any stream capture begins.
+ *  - Every call, from every instance on the device, shares the one array,
+ *    which keeps the last call's contents: calls whose work overlaps on the
+ *    GPU race. Issue them on one stream, or order them with events.
+ *  - Same validation, copies, counters and error reporting at the next fence
+ *    as hicr_memcpy_batch_device; also BUSY while single ops queued by
+ *    hicr_memcpy wait for a flush (flushing may allocate): call hicr_flush
+ *    first. */
+hicr_status hicr_memcpy_batch_noalloc(hicr_instance_t inst, const hicr_op_t* d_ops, uint64_t count);
+
 /* Status and first bad op index of the last failed device-validated batch;
  * reading clears it. *status is HICR_OK when none failed. */
 hicr_status hicr_batch_error(hicr_instance_t inst, hicr_status* status, uint64_t* first_bad);

@@ -1,0 +1,110 @@
+// hicr_memcpy_batch_noalloc: the device-validated batched memcpy for callers
+// that may not allocate GPU memory when they issue copies.
+//
+// Some callers cannot call cudaMalloc at the point where they issue a batch:
+// a host framework that owns all device memory through its own pool and
+// forbids allocations outside it, a latency-critical loop that cannot afford
+// the implicit device-wide synchronisation cudaMalloc/cudaFree may cause, or a
+// process that has already handed nearly all HBM to another allocator. The
+// regular entry point (hicr_memcpy_batch_device) grows its per-batch scratch
+// with cudaMalloc; this one keeps that scratch in the file-scope array below,
+// which every GPU that loads the library holds until the process exits.
+//
+// The copy work itself is the same: the plan, scan and copy kernels of
+// memcpy.cu run unchanged, pointed at this array instead of the instance's
+// scratch.
+#include <mutex>
+
+#include "hicr_internal.h"
+
+namespace hicr {
+
+// Kernels defined in memcpy.cu.
+__global__ void k_plan(BatchArgs a);
+__global__ void k_scan(BatchArgs a);
+__global__ void k_copy(BatchArgs a);
+
+// Layout of the array, in 8-byte words: the batch control block (padded to
+// 256 bytes), per-op costs, the prefix sums (one extra entry), then the
+// per-op piece counters (4 bytes each).
+static constexpr uint64_t NA_MAX = HICR_NOALLOC_MAX_OPS;
+static constexpr uint64_t NA_CTRL_WORDS = 32;
+static constexpr uint64_t NA_COST_WORDS = NA_MAX;
+static constexpr uint64_t NA_CSTART_WORDS = ((NA_MAX + 1 + 31) / 32) * 32;
+static constexpr uint64_t NA_DONE_WORDS = NA_MAX / 2;
+static constexpr uint64_t NA_WORDS = NA_CTRL_WORDS + NA_COST_WORDS + NA_CSTART_WORDS + NA_DONE_WORDS;
+static_assert(sizeof(BatchCtrl) <= NA_CTRL_WORDS * 8, "control block does not fit");
+static_assert(NA_MAX % 2 == 0, "piece counters are packed two per word");
+
+static __device__ __align__(256) unsigned long long hicr_noalloc_scratch[NA_WORDS];
+
+// Device address of the array, resolved once per device. In host code the
+// array's name is only a stand-in for the device symbol, never an address a
+// kernel could use.
+static constexpr int NA_MAX_DEVICES = 64;
+static unsigned long long* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
+static std::mutex g_na_mutex;
+
+static hicr_status noalloc_scratch(Instance* in, unsigned long long** out) {
+  if (in->device < 0 || in->device >= NA_MAX_DEVICES) return HICR_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[in->device]) {
+    int prev = 0;
+    HICR_CUDA(in, cudaGetDevice(&prev));
+    HICR_CUDA(in, cudaSetDevice(in->device));
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, hicr_noalloc_scratch);
+    cudaError_t e2 = cudaSetDevice(prev);
+    if (e != cudaSuccess) return cuda_fail(in, e, "cudaGetSymbolAddress(hicr_noalloc_scratch)");
+    if (e2 != cudaSuccess) return cuda_fail(in, e2, "cudaSetDevice");
+    if (!p) return HICR_ERR_DEVICE;
+    g_na_ptr[in->device] = (unsigned long long*)p;
+  }
+  *out = g_na_ptr[in->device];
+  return HICR_OK;
+}
+
+}  // namespace hicr
+
+using namespace hicr;
+
+extern "C" hicr_status hicr_memcpy_batch_noalloc(hicr_instance_t h, const hicr_op_t* d_ops, uint64_t count) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || (count && !d_ops) || ((uintptr_t)d_ops & 7u)) return HICR_ERR_INVALID;
+  if (count > NA_MAX) return HICR_ERR_TOO_LARGE;
+  if (count == 0) return HICR_OK;
+  // Flushing queued single ops could allocate staging memory: refuse instead.
+  if (!in->queue.empty()) return HICR_ERR_BUSY;
+  unsigned long long* base = nullptr;
+  hicr_status s = noalloc_scratch(in, &base);
+  if (s != HICR_OK) return s;
+
+  BatchArgs a;
+  a.ops = d_ops;
+  a.count = count;
+  a.dt = in->dt;
+  a.ctrl = reinterpret_cast<BatchCtrl*>(base);
+  a.cost = base + NA_CTRL_WORDS;
+  a.cstart = a.cost + NA_COST_WORDS;
+  a.done = reinterpret_cast<unsigned int*>(a.cstart + NA_CSTART_WORDS);
+  a.chunk = in->cfg.chunk_bytes;
+  a.op_cost = in->cfg.op_cost_bytes;
+  a.support = in->support;
+  a.engine = in->cfg.engine;
+  a.tma_min = in->cfg.tma_min_bytes;
+  a.tma_stage = 0;
+
+  cudaStream_t st = in->comm();
+  // The array keeps whatever the previous call left. The plan kernel zeroes
+  // the piece counters and the scan kernel rewrites the prefix sums, the
+  // chunk count and the claim counter; only the "first bad op" word must be
+  // reset to its empty value (all ones) before the plan kernel min-reduces
+  // into it.
+  HICR_CUDA(in, cudaMemsetAsync(&a.ctrl->bad, 0xFF, sizeof(a.ctrl->bad), st));
+  const unsigned pb = (unsigned)((count + 255) / 256);
+  k_plan<<<pb, 256, 0, st>>>(a);
+  k_scan<<<1, 1024, 0, st>>>(a);
+  k_copy<<<(unsigned)in->sm_count * in->cfg.blocks_per_sm, in->cfg.threads, 0, st>>>(a);
+  HICR_CUDA(in, cudaGetLastError());
+  return record_done(in);
+}

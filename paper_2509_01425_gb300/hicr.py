@@ -39,6 +39,7 @@ HICR_ERR_TIMEOUT = -10
 HICR_ERR_BUSY = -11
 HICR_ERR_DEVICE = -12
 
+HICR_NOALLOC_MAX_OPS = 32768
 HICR_MAX_SLOTS = 65536
 HICR_MAX_TAGS = 1024
 HICR_MAX_SPACES = 4
@@ -127,6 +128,7 @@ _memcpy = _decl("hicr_memcpy", [H, u32, u64, u32, u64, u64])
 _flush = _decl("hicr_flush", [H])
 _memcpy_batch = _decl("hicr_memcpy_batch", [H, vp, u64, C.POINTER(u64)])
 _memcpy_batch_device = _decl("hicr_memcpy_batch_device", [H, vp, u64])
+_memcpy_batch_noalloc = _decl("hicr_memcpy_batch_noalloc", [H, vp, u64])
 _batch_error = _decl("hicr_batch_error", [H, C.POINTER(i32), C.POINTER(u64)])
 _batch_reserve = _decl("hicr_batch_reserve", [H, u64])
 _set_checked = _decl("hicr_set_checked", [H, i32])
@@ -248,6 +250,10 @@ def hicr_memcpy_batch(inst, ops):
 
 def hicr_memcpy_batch_device(inst, d_ops, count):
     return _memcpy_batch_device(inst, _ptr(d_ops), count)
+
+
+def hicr_memcpy_batch_noalloc(inst, d_ops, count):
+    return _memcpy_batch_noalloc(inst, _ptr(d_ops), count)
 
 
 def hicr_batch_error(inst):

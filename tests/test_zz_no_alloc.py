@@ -1,0 +1,98 @@
+"""hicr_memcpy_batch_noalloc against the regular device-validated batch.
+
+Some callers cannot allocate GPU memory at the moment they issue copies (a
+framework whose own pool owns all device memory, a latency-critical loop that
+cannot absorb cudaMalloc's implicit synchronisation). They use
+hicr_memcpy_batch_noalloc, whose scratch is a static device array instead of
+cudaMalloc'd memory. Here both entry points run the same op tables on two
+identically filled sets of slots and must leave identical bytes and counters,
+on two calls in a row; an oversized batch is rejected, and an invalid batch
+reports its error without disturbing the next call.
+
+This file is collected last so a run that stops at the first failure has
+already run every other test; it also passes on its own in a fresh process.
+"""
+import numpy as np
+import pytest
+import torch
+
+from workloads import configs, splitmix
+from tests.gpu_util import device_bytes, h, inst  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+T = 60_000_000_000
+
+
+def _slots(h, inst, w, seed):
+    ids = []
+    for s, sz in enumerate(w.slot_sizes):
+        st, sid = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, int(sz))
+        assert st == 0
+        assert h.hicr_util_fill(inst, sid, 0, int(sz), splitmix.fill_key_base(seed, s)) == 0
+        ids.append(sid)
+    return ids
+
+
+def _table(ops, ids):
+    o = ops.copy()
+    m = np.asarray(ids, dtype=np.uint32)
+    o["dst"], o["src"] = m[ops["dst"]], m[ops["src"]]
+    return torch.from_numpy(o.view(np.uint8).copy()).cuda()
+
+
+def _same(h, inst, a_ids, b_ids):
+    for a, b in zip(a_ids, b_ids):
+        _, pa, na, _, _ = h.hicr_slot_info(inst, a)
+        _, pb, nb, _, _ = h.hicr_slot_info(inst, b)
+        torch.cuda.synchronize()
+        assert na == nb and torch.equal(device_bytes(pa, na), device_bytes(pb, nb))
+        assert h.hicr_slot_counters(inst, a)[1:] == h.hicr_slot_counters(inst, b)[1:]
+
+
+def test_noalloc_matches_device_batch_twice(h, inst):
+    w = configs.batched(5, n_slots=6, total_bytes=48 << 20, slot_lo=4 << 20, slot_hi=16 << 20,
+                        n_ops=6000, n_lo=16, n_hi=512 << 10)
+    assert len(w.epochs) >= 2
+    a_ids = _slots(h, inst, w, 5)   # written by the no-allocation entry point
+    b_ids = _slots(h, inst, w, 5)   # written by hicr_memcpy_batch_device
+    for call, (lo, hi) in enumerate(w.epochs[:2]):
+        count = min(hi - lo, h.HICR_NOALLOC_MAX_OPS)
+        ta, tb = _table(w.ops[lo:lo + count], a_ids), _table(w.ops[lo:lo + count], b_ids)
+        assert h.hicr_memcpy_batch_noalloc(inst, ta.data_ptr(), count) == 0
+        assert h.hicr_fence(inst, 0, T) == 0
+        assert h.hicr_memcpy_batch_device(inst, tb.data_ptr(), count) == 0
+        assert h.hicr_fence(inst, 0, T) == 0
+        _same(h, inst, a_ids, b_ids)
+        s, r = h.hicr_slot_counters_range(inst, a_ids[0], len(a_ids))[1:]
+        assert int(s.sum()) == int(r.sum()) > 0
+
+
+def test_noalloc_rejects_oversize_and_recovers_from_a_bad_batch(h, inst):
+    w = configs.batched(6, n_slots=4, total_bytes=16 << 20, slot_lo=2 << 20, slot_hi=8 << 20,
+                        n_ops=500, n_lo=16, n_hi=64 << 10)
+    a_ids = _slots(h, inst, w, 6)
+    b_ids = _slots(h, inst, w, 6)
+    lo, hi = w.epochs[0]
+    ta = _table(w.ops[lo:hi], a_ids)
+    before = h.hicr_slot_counters_range(inst, a_ids[0], len(a_ids))
+    assert h.hicr_memcpy_batch_noalloc(inst, ta.data_ptr(), h.HICR_NOALLOC_MAX_OPS + 1) == h.HICR_ERR_TOO_LARGE
+    assert h.hicr_fence(inst, 0, T) == 0
+    after = h.hicr_slot_counters_range(inst, a_ids[0], len(a_ids))
+    assert (before[1] == after[1]).all() and (before[2] == after[2]).all()
+    # an op past the end of its slot: the whole batch copies nothing, the
+    # fence reports BOUNDS with the index, and the next call is unaffected
+    bad = w.ops[lo:hi].copy()
+    bad["n"][3] = int(w.slot_sizes[bad["src"][3]]) + 1
+    tbad = _table(bad, a_ids)
+    assert h.hicr_memcpy_batch_noalloc(inst, tbad.data_ptr(), hi - lo) == 0
+    assert h.hicr_fence(inst, 0, T) == h.HICR_ERR_BOUNDS
+    after_bad = h.hicr_slot_counters_range(inst, a_ids[0], len(a_ids))
+    assert (after_bad[1] == after[1]).all() and (after_bad[2] == after[2]).all()
+    _same(h, inst, a_ids, b_ids)
+    tb = _table(w.ops[lo:hi], b_ids)
+    assert h.hicr_memcpy_batch_noalloc(inst, ta.data_ptr(), hi - lo) == 0
+    assert h.hicr_fence(inst, 0, T) == 0
+    assert h.hicr_memcpy_batch_device(inst, tb.data_ptr(), hi - lo) == 0
+    assert h.hicr_fence(inst, 0, T) == 0
+    _same(h, inst, a_ids, b_ids)
