@@ -1,0 +1,163 @@
+/*
+ * hicr_channels.h -- SPSC and MPSC channels of libhicr_gb300.so.
+ *
+ * HiCR paper Sec. 4.3 (Built-in Frontends, Channels): a channel is a
+ * pre-allocated circular buffer at the consumer; a producer pushes while it is
+ * not full and otherwise waits until the consumer reports consumption.
+ * Single-producer/single-consumer (SPSC) channels carry fixed-size tokens;
+ * multiple-producer/single-consumer (MPSC) channels in "locking" mode share one
+ * buffer that an exclusive access keeps from overflowing.
+ *
+ * Here the buffer (ring), its head/tail counters and the MPSC metadata live in
+ * HBM and are updated with release/acquire atomics, so producers and
+ * consumers can be device threads. The host calls below run one small kernel
+ * each and return when it has finished (synchronous, non-blocking semantics:
+ * FULL / EMPTY instead of waiting).
+ *
+ * Conventions as in hicr.h.
+ */
+#ifndef HICR_CHANNELS_H
+#define HICR_CHANNELS_H
+
+#include <stdint.h>
+
+#include "hicr.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef uint32_t hicr_channel_t;
+
+/* Description of one buffered message (peek). */
+typedef struct {
+  uint64_t offset;   /* byte offset of the payload in the channel ring */
+  uint64_t size;     /* payload bytes */
+  uint32_t producer; /* producer index (0 for SPSC) */
+  uint32_t reserved;
+  uint64_t seq;      /* per-producer sequence number (SPSC: token index) */
+} hicr_msg_info_t;
+
+/* SPSC channel of `capacity` tokens of `token_size` bytes (both >= 1,
+ * capacity * token_size <= 2^40). head and tail are 64-bit monotonic token
+ * counts; token t sits at ring offset (t mod capacity) * token_size.
+ * Errors: INVALID, NOMEM, DEVICE. */
+hicr_status hicr_spsc_create(hicr_instance_t inst, uint32_t token_size, uint32_t capacity,
+                             hicr_channel_t* out);
+
+/* MPSC channel (locking-mode semantics) with `n_producers` producers, a
+ * payload ring of `ring_bytes` (a power of two, 64 B .. 2^39) and at most
+ * `max_msgs` (a power of two, 1 .. 2^23) messages in flight.
+ * Placement rule: each message reserves its size rounded up to 16 bytes; a
+ * message that would cross the ring end skips to the ring start and the
+ * skipped bytes count as reserved; reservations happen in ticket order and the
+ * consumer frees in that order. A push succeeds only if reserved-but-unfreed
+ * bytes stay <= ring_bytes and in-flight messages <= max_msgs.
+ * Errors: INVALID (not powers of two, zero producers), NOMEM, DEVICE. */
+hicr_status hicr_mpsc_create(hicr_instance_t inst, uint32_t n_producers, uint64_t ring_bytes,
+                             uint32_t max_msgs, hicr_channel_t* out);
+
+/* Free a channel's device memory. Errors: INVALID. */
+hicr_status hicr_channel_destroy(hicr_instance_t inst, hicr_channel_t ch);
+
+/* The channel ring as a (library-owned) HBM memory slot, so a consumer can
+ * copy payloads out with hicr_memcpy using the offsets peek reports.
+ * Errors: INVALID. */
+hicr_status hicr_channel_ring(hicr_instance_t inst, hicr_channel_t ch, hicr_slot_t* ring_slot);
+
+/* Push from slot `src` at byte `off`:
+ *  SPSC: `n` tokens (n * token_size bytes), all or nothing; FULL when fewer
+ *        than n tokens are free. `producer` must be 0.
+ *  MPSC: one message of `n` bytes from producer `producer`; FULL when the
+ *        placement rule finds no room, TOO_LARGE when the rounded size
+ *        exceeds the ring.
+ * Errors: INVALID (bad channel/producer/slot), BOUNDS (off + bytes > slot
+ * size), UNSUPPORTED (source not in HBM), FULL, TOO_LARGE, DEVICE. */
+hicr_status hicr_channel_push(hicr_instance_t inst, hicr_channel_t ch, uint32_t producer, hicr_slot_t src,
+                              uint64_t off, uint64_t n);
+
+/* Describe the k-th oldest unpopped message (k = 0 is the next to pop)
+ * without changing state. EMPTY when k >= depth (for MPSC: or when that
+ * message has been reserved but not yet published by a device producer). */
+hicr_status hicr_channel_peek(hicr_instance_t inst, hicr_channel_t ch, uint64_t k, hicr_msg_info_t* out);
+
+/* Consume the `count` oldest messages (SPSC: tokens), freeing their ring
+ * space. All or nothing: EMPTY when fewer are buffered. */
+hicr_status hicr_channel_pop(hicr_instance_t inst, hicr_channel_t ch, uint64_t count);
+
+/* Messages (tokens) buffered and ring bytes held (MPSC: reserved, including
+ * skipped bytes, minus freed). */
+hicr_status hicr_channel_depth(hicr_instance_t inst, hicr_channel_t ch, uint64_t* msgs, uint64_t* bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Device-driven streaming (producers and consumers are device threads).     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t pushed;        /* tokens the producer published */
+  uint64_t popped;        /* tokens the consumer consumed */
+  uint64_t mismatches;    /* consumed 8-byte words that differ from the payload rule */
+  uint64_t digest;        /* sum_j w_j * (2j + 1) mod 2^64 over the consumed word stream */
+  uint64_t max_occupancy; /* largest head - tail a push had to respect (<= capacity) */
+  int32_t status;         /* HICR_OK or HICR_ERR_TIMEOUT */
+  uint32_t reserved;
+} hicr_spsc_result_t;
+
+/* Stream `tokens` tokens through each of the `n` SPSC channels `chans`
+ * (token_size a multiple of 16, all starting empty) with one producer CTA and
+ * one consumer CTA per channel, launched together as one cooperative grid so
+ * both sides are resident at once. Word w of token s on the i-th channel of
+ * the call is the SplitMix64 first output for state i * 2^40 + s *
+ * (token_size / 8) + w. The producer publishes `batch` tokens per head update
+ * (1 .. capacity); the consumer checks every word, accumulates the digest and
+ * releases the tail per batch. Every wait gives up after `timeout_ns`
+ * (result status TIMEOUT). Synchronous; `results` is a host array of n.
+ * Errors: INVALID (bad channel, token size, batch, empty list), DEVICE,
+ * TIMEOUT (any channel timed out; the results say which). */
+hicr_status hicr_spsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                             uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results);
+
+/* One consumed MPSC message, as the consumer logs it in ticket order. */
+typedef struct {
+  uint32_t producer;
+  uint32_t seq;
+  uint32_t size;
+  uint32_t reserved;
+  uint64_t offset;  /* ring offset */
+  uint64_t digest;  /* word digest of the payload (last word zero-padded) */
+} hicr_mpsc_log_t;
+
+typedef struct {
+  uint64_t consumed;           /* messages consumed */
+  uint64_t bytes;              /* payload bytes consumed */
+  uint64_t max_inflight_bytes; /* largest reserved-minus-freed bytes at a reservation (<= ring) */
+  uint64_t max_inflight_msgs;  /* largest in-flight message count at a reservation */
+  int32_t status;              /* HICR_OK or HICR_ERR_TIMEOUT */
+  uint32_t reserved;
+} hicr_mpsc_result_t;
+
+/* Stream messages from `n_producers` producers into `n_consumers` MPSC
+ * channels `chans` (all empty, each created with at least
+ * ceil(n_producers / n_consumers) producers); producer p feeds channel
+ * p mod n_consumers and sends `msgs_per_producer` messages in order.
+ * Message (p, s) has d_sizes[p * msgs_per_producer + s] bytes (device array,
+ * u64) taken from slot `staging` at byte d_src_off[p * msgs_per_producer + s]
+ * (device array, u64). Each producer is one warp and reserves up to `group`
+ * consecutive messages (1 .. 8) per exclusive access; each consumer is one
+ * CTA that drains in ticket order, digests each payload and writes its log to
+ * d_log + c * log_stride (device, at least as many entries as it receives).
+ * One cooperative grid; every wait gives up after `timeout_ns`.
+ * Synchronous; `results` is a host array of n_consumers.
+ * Errors: INVALID, BOUNDS (a message outside the staging slot), TOO_LARGE (a
+ * message larger than its ring), DEVICE, TIMEOUT. */
+hicr_status hicr_mpsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
+                             uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                             const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                             uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
+                             hicr_mpsc_result_t* results);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HICR_CHANNELS_H */

@@ -26,6 +26,16 @@ extern "C" {
 hicr_status hicr_util_fill(hicr_instance_t inst, hicr_slot_t slot, uint64_t off, uint64_t n,
                            uint64_t key_base);
 
+/* Seeded fill of `count` segments of `slot`. d_seg is a device array of
+ * count triples {off, n, key_base} (u64): byte j of segment [off, off+n) is
+ * byte (j mod 8), little endian, of the SplitMix64 first output for state
+ * key_base + floor(j/8) -- each segment restarts its own word count.
+ * Asynchronous on the communication stream. A segment that does not lie
+ * inside the slot is skipped.
+ * Errors: INVALID, UNSUPPORTED (host slot), DEVICE. */
+hicr_status hicr_util_fill_segments(hicr_instance_t inst, hicr_slot_t slot, const uint64_t* d_seg,
+                                    uint64_t count);
+
 /* Word digest of bytes [off, off+n) of `slot`: with w_j the little-endian
  * 8-byte words of that range (last word zero-padded), D = sum_j w_j * (2j+1)
  * mod 2^64. Synchronous (waits for the communication stream first).

@@ -1,13 +1,1029 @@
 // SPSC and MPSC channels (HiCR paper Sec. 4.3, Channels frontend).
+//
+// A channel is a circular buffer (ring) in HBM at the consumer plus 64-bit
+// coordination counters, each on its own 128-byte line:
+//   SPSC  head = tokens published, tail = tokens consumed;
+//         token t lives at ring offset (t mod capacity) * token_size.
+//   MPSC  reserve = (ticket mod 2^24) << 40 | (reserved bytes mod 2^40),
+//         freed   = bytes freed (mod 2^40), msg_tail = messages freed,
+//         plus a metadata ring of max_msgs entries {start, size, producer,
+//         seq, ready}. The "locking" mode's exclusive access is one
+//         compare-and-swap of `reserve`, taken only when the placement rule
+//         (16-byte rounding, skip to the ring start instead of crossing its
+//         end, reserved-minus-freed <= ring bytes, in-flight <= max_msgs)
+//         finds room; a producer then copies its payload with the warp copy
+//         of the memcpy path and publishes the entry with a release store of
+//         `ready`. The consumer drains tickets in order and frees with
+//         release stores.
+// Ring bytes and max_msgs are powers of two, so positions modulo 2^40 and
+// tickets modulo 2^24 map consistently onto the rings.
+//
+// Host calls run a one-CTA kernel and read its result from a mapped host
+// mailbox. The streaming runs launch producers and consumers as one
+// cooperative grid (all CTAs resident at once); every wait is bounded by the
+// %globaltimer deadline and raises a shared abort flag on expiry.
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/hicr_channels.h"
+#include "copy.cuh"
 #include "hicr_internal.h"
+#include "splitmix.cuh"
 
 namespace hicr {
 
-struct Channel {};
+static constexpr unsigned long long MASK40 = (1ull << 40) - 1;
+static constexpr unsigned long long MASK24 = (1ull << 24) - 1;
+static constexpr unsigned FULLM = 0xffffffffu;
 
-void destroy_channels(Instance* in) {
-  for (Channel* c : in->channels) delete c;
-  in->channels.clear();
+struct alignas(128) Line {
+  unsigned long long v;
+  unsigned long long pad[15];
+};
+struct SpscState {
+  Line head;
+  Line tail;
+};
+struct MpscState {
+  Line reserve;
+  Line freed;
+  Line msg_tail;
+  Line max_bytes;
+  Line max_msgs;
+};
+struct MpscMeta {
+  unsigned long long start;
+  unsigned int size;
+  unsigned int producer;
+  unsigned int seq;
+  unsigned int flags;
+  unsigned long long ready;
+};
+static_assert(sizeof(MpscMeta) == 32, "metadata entry is 32 bytes");
+
+struct Mailbox {
+  int status;
+  unsigned int pad;
+  unsigned long long v[6];
+};
+
+struct Channel {
+  int kind = 0;  // 0 SPSC, 1 MPSC
+  bool live = false;
+  uint32_t token_size = 0, capacity = 0;
+  uint32_t n_producers = 0, max_msgs = 0;
+  uint64_t ring_bytes = 0;
+  uint8_t* ring = nullptr;
+  void* state = nullptr;
+  MpscMeta* meta = nullptr;
+  hicr_slot_t ring_slot = 0;
+  std::vector<uint32_t> seq;  // host-API producers' next sequence numbers
+};
+
+// ---------------------------------------------------------------------------
+// Device primitives.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ld_acq(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool aborted(const unsigned int* abort) {
+  return *(volatile const unsigned int*)abort != 0u;
+}
+__host__ __device__ __forceinline__ unsigned long long round16(unsigned long long n) { return (n + 15) & ~15ull; }
+
+// ---------------------------------------------------------------------------
+// Host-call kernels (one CTA, result in the mailbox).
+// ---------------------------------------------------------------------------
+struct SpscView {
+  uint8_t* ring;
+  SpscState* st;
+  unsigned int ts;
+  unsigned int cap;
+};
+struct MpscView {
+  uint8_t* ring;
+  MpscState* st;
+  MpscMeta* meta;
+  unsigned long long R;
+  unsigned int M;
+};
+
+// Copy n bytes with every warp of the CTA taking an equal share.
+__device__ __forceinline__ void cta_copy(uint8_t* d, const uint8_t* s, unsigned long long n) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long a = n * w / nw, b = n * (w + 1) / nw;
+  if (b > a) warp_copy(d + a, s + a, b - a, lane);
 }
 
+__global__ void k_spsc_push_host(SpscView v, const uint8_t* src, unsigned long long k, Mailbox* mb) {
+  __shared__ unsigned long long s_head;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    const unsigned long long h = ld_rlx(&v.st->head.v), t = ld_acq(&v.st->tail.v);
+    s_ok = (h - t + k <= v.cap);
+    s_head = h;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    return;
+  }
+  // at most two contiguous runs: up to the ring end, then from its start
+  const unsigned long long first = s_head % v.cap;
+  const unsigned long long run1 = min(k, (unsigned long long)v.cap - first);
+  cta_copy(v.ring + first * v.ts, src, run1 * v.ts);
+  if (k > run1) cta_copy(v.ring, src + run1 * v.ts, (k - run1) * v.ts);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st_rel(&v.st->head.v, s_head + k);
+    mb->v[0] = s_head;
+    mb->status = HICR_OK;
+  }
+}
+
+// op 0 = peek(k), 1 = pop(k), 2 = depth
+__global__ void k_spsc_ctl(SpscView v, int op, unsigned long long k, Mailbox* mb) {
+  const unsigned long long h = ld_acq(&v.st->head.v), t = ld_acq(&v.st->tail.v);
+  const unsigned long long depth = h - t;
+  if (op == 2) {
+    mb->v[0] = depth;
+    mb->v[1] = depth * v.ts;
+    mb->status = HICR_OK;
+  } else if (op == 0) {
+    if (k >= depth) {
+      mb->status = HICR_ERR_EMPTY;
+      return;
+    }
+    mb->v[0] = ((t + k) % v.cap) * v.ts;
+    mb->v[1] = v.ts;
+    mb->v[2] = 0;
+    mb->v[3] = t + k;
+    mb->status = HICR_OK;
+  } else {
+    if (k > depth) {
+      mb->status = HICR_ERR_EMPTY;
+      return;
+    }
+    st_rel(&v.st->tail.v, t + k);
+    mb->status = HICR_OK;
+  }
+}
+
+// One MPSC reservation attempt for k messages whose rounded sizes are r[0..k)
+// starting from reserve word W: fills start[] and returns the end position.
+__device__ __forceinline__ unsigned long long mpsc_place(unsigned long long W, const unsigned long long* r, int k,
+                                                          unsigned long long R, unsigned long long* start) {
+  unsigned long long b = W & MASK40;
+  for (int i = 0; i < k; ++i) {
+    const unsigned long long pos = b & (R - 1);
+    if (pos + r[i] > R) b = (b + (R - pos)) & MASK40;
+    start[i] = b;
+    b = (b + r[i]) & MASK40;
+  }
+  return b;
+}
+
+__global__ void k_mpsc_push_host(MpscView v, unsigned int producer, unsigned int seq, const uint8_t* src,
+                                 unsigned long long n, Mailbox* mb) {
+  __shared__ unsigned long long s_start, s_ticket;
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    const unsigned long long r = round16(n);
+    int ok = 0;
+    for (int attempt = 0; attempt < 1000; ++attempt) {
+      const unsigned long long W = ld_rlx(&v.st->reserve.v);
+      unsigned long long start;
+      const unsigned long long end = mpsc_place(W, &r, 1, v.R, &start);
+      const unsigned long long freed = ld_acq(&v.st->freed.v);
+      const unsigned long long mt = ld_acq(&v.st->msg_tail.v);
+      const unsigned long long t0 = W >> 40;
+      const unsigned long long inflight = (end - freed) & MASK40;
+      const unsigned long long msgs = ((t0 + 1) - mt) & MASK24;
+      if (inflight > v.R || msgs > v.M) break;  // FULL under the placement rule
+      const unsigned long long nw = (((t0 + 1) & MASK24) << 40) | end;
+      if (atomicCAS(&v.st->reserve.v, W, nw) == W) {
+        ok = 1;
+        s_start = start;
+        s_ticket = t0;
+        atomicMax(&v.st->max_bytes.v, inflight);
+        atomicMax(&v.st->max_msgs.v, msgs);
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    return;
+  }
+  cta_copy(v.ring + (s_start & (v.R - 1)), src, n);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    MpscMeta* e = v.meta + (s_ticket & (v.M - 1));
+    e->start = s_start;
+    e->size = (unsigned int)n;
+    e->producer = producer;
+    e->seq = seq;
+    e->flags = 0;
+    st_rel(&e->ready, (s_ticket & MASK24) + 1);
+    mb->v[0] = s_start & (v.R - 1);
+    mb->v[1] = s_ticket;
+    mb->status = HICR_OK;
+  }
+}
+
+// op 0 = peek(k), 1 = pop(k), 2 = depth
+__global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb) {
+  const unsigned long long W = ld_acq(&v.st->reserve.v);
+  const unsigned long long mt = ld_acq(&v.st->msg_tail.v);
+  const unsigned long long freed = ld_acq(&v.st->freed.v);
+  const unsigned long long depth = ((W >> 40) - mt) & MASK24;
+  if (op == 2) {
+    mb->v[0] = depth;
+    mb->v[1] = ((W & MASK40) - freed) & MASK40;
+    mb->status = HICR_OK;
+    return;
+  }
+  if (op == 0) {
+    if (k >= depth) {
+      mb->status = HICR_ERR_EMPTY;
+      return;
+    }
+    const unsigned long long t = mt + k;
+    MpscMeta* e = v.meta + (t & (v.M - 1));
+    if (ld_acq(&e->ready) != (t & MASK24) + 1) {
+      mb->status = HICR_ERR_EMPTY;
+      return;
+    }
+    mb->v[0] = __ldcg(&e->start) & (v.R - 1);
+    mb->v[1] = __ldcg(&e->size);
+    mb->v[2] = __ldcg(&e->producer);
+    mb->v[3] = __ldcg(&e->seq);
+    mb->status = HICR_OK;
+    return;
+  }
+  if (k > depth) {
+    mb->status = HICR_ERR_EMPTY;
+    return;
+  }
+  if (k == 0) {
+    mb->status = HICR_OK;
+    return;
+  }
+  for (unsigned long long i = 0; i < k; ++i) {
+    const unsigned long long t = mt + i;
+    if (ld_acq(&v.meta[t & (v.M - 1)].ready) != (t & MASK24) + 1) {
+      mb->status = HICR_ERR_EMPTY;
+      return;
+    }
+  }
+  const MpscMeta* last = v.meta + ((mt + k - 1) & (v.M - 1));
+  const unsigned long long end = (__ldcg(&last->start) + round16(__ldcg(&last->size))) & MASK40;
+  st_rel(&v.st->freed.v, end);
+  st_rel(&v.st->msg_tail.v, mt + k);
+  mb->status = HICR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SPSC streaming: CTA 2i produces into channel i, CTA 2i+1 consumes it.
+// ---------------------------------------------------------------------------
+struct SpscStreamArgs {
+  const SpscView* chans;
+  unsigned int n;
+  unsigned int batch;
+  unsigned long long tokens;
+  unsigned long long timeout_ns;
+  hicr_spsc_result_t* res;
+  unsigned int* abort;
+};
+
+__global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
+  __shared__ int s_stop;
+  __shared__ unsigned long long s_red[2][16];
+  const unsigned ci = blockIdx.x >> 1;
+  const bool producer = (blockIdx.x & 1u) == 0;
+  const SpscView v = a.chans[ci];
+  const unsigned vpt = v.ts / 16;  // 16-byte vectors per token
+  const unsigned long long wpt = v.ts / 8;
+  const unsigned long long key0 = (unsigned long long)ci << 40;
+  const unsigned long long deadline = gtime() + a.timeout_ns;
+  const unsigned tid = threadIdx.x;
+  // The channel starts empty (head == tail); token s of this run has counter
+  // value base + s and ring slot (base + s) mod capacity.
+  __shared__ unsigned long long s_base;
+  if (tid == 0) s_base = ld_acq(producer ? &v.st->head.v : &v.st->tail.v);
+  __syncthreads();
+  const unsigned long long base = s_base;
+  unsigned long long cached = base, max_occ = 0, done = 0, mism = 0, dig = 0;
+  int stop = 0;
+  for (unsigned long long s0 = 0; s0 < a.tokens; s0 += a.batch) {
+    const unsigned long long k = min((unsigned long long)a.batch, a.tokens - s0);
+    if (tid == 0) {
+      stop = 0;
+      if (producer) {
+        // room for k more tokens: s0 + k - tail <= capacity
+        while (base + s0 + k - cached > v.cap) {
+          cached = ld_acq(&v.st->tail.v);
+          if (base + s0 + k - cached <= v.cap) break;
+          if (aborted(a.abort) || gtime() > deadline) { stop = 1; break; }
+          __nanosleep(32);
+        }
+        if (!stop) max_occ = max(max_occ, base + s0 + k - cached);
+      } else {
+        // k more tokens published: head >= base + s0 + k
+        while (cached < base + s0 + k) {
+          cached = ld_acq(&v.st->head.v);
+          if (cached >= base + s0 + k) break;
+          if (aborted(a.abort) || gtime() > deadline) { stop = 1; break; }
+          __nanosleep(32);
+        }
+      }
+      if (stop) atomicExch(a.abort, 1u);
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const unsigned long long nv = k * vpt;
+    for (unsigned long long q = tid; q < nv; q += blockDim.x) {
+      const unsigned long long tok = s0 + q / vpt;
+      const unsigned long long word = tok * wpt + (q % vpt) * 2;  // index of the first 8-byte word
+      uint4* p = reinterpret_cast<uint4*>(v.ring + ((base + tok) % v.cap) * v.ts) + (q % vpt);
+      if (producer) {
+        const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
+        uint4 x;
+        x.x = (unsigned)w0;
+        x.y = (unsigned)(w0 >> 32);
+        x.z = (unsigned)w1;
+        x.w = (unsigned)(w1 >> 32);
+        *p = x;
+      } else {
+        const uint4 x = __ldcg(p);
+        const unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+        const unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+        mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+        dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+      }
+    }
+    if (producer) __threadfence();
+    __syncthreads();
+    if (tid == 0) st_rel(producer ? &v.st->head.v : &v.st->tail.v, base + s0 + k);
+    done = s0 + k;
+  }
+  // block reduction of the consumer's counts
+  for (int o = 16; o > 0; o >>= 1) {
+    mism += __shfl_xor_sync(FULLM, mism, o);
+    dig += __shfl_xor_sync(FULLM, dig, o);
+  }
+  if ((tid & 31) == 0) {
+    s_red[0][tid >> 5] = mism;
+    s_red[1][tid >> 5] = dig;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    hicr_spsc_result_t* r = a.res + ci;
+    if (producer) {
+      r->pushed = done;
+      r->max_occupancy = max_occ;
+    } else {
+      unsigned long long m = 0, d = 0;
+      for (unsigned w = 0; w < blockDim.x / 32; ++w) {
+        m += s_red[0][w];
+        d += s_red[1][w];
+      }
+      r->popped = done;
+      r->mismatches = m;
+      r->digest = d;
+    }
+    if (s_stop) r->status = HICR_ERR_TIMEOUT;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// MPSC streaming: CTAs [0, n_cons) consume, the rest hold one producer per
+// warp; producer p feeds consumer p mod n_cons.
+// ---------------------------------------------------------------------------
+struct MpscStreamArgs {
+  const MpscView* chans;
+  unsigned int n_cons;
+  unsigned int n_prod;
+  unsigned int mpp;
+  unsigned int group;
+  const unsigned long long* sizes;
+  const unsigned long long* src_off;
+  const uint8_t* staging;
+  unsigned long long timeout_ns;
+  hicr_mpsc_log_t* log;
+  unsigned long long log_stride;
+  hicr_mpsc_result_t* res;
+  unsigned int* abort;
+};
+
+static constexpr int MPSC_MAX_GROUP = 8;
+static constexpr int MPSC_WIN_PER_WARP = 4;
+
+__device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline) {
+  const unsigned c = p % a.n_cons;
+  const MpscView v = a.chans[c];
+  const unsigned long long half = v.R / 2;
+  for (unsigned s = 0; s < a.mpp;) {
+    // the group: up to `group` messages whose rounded sizes sum to <= R/2
+    unsigned long long r[MPSC_MAX_GROUP], st[MPSC_MAX_GROUP];
+    int k = 0;
+    unsigned long long sum = 0;
+    for (; k < (int)a.group && s + k < a.mpp; ++k) {
+      const unsigned long long rk = round16(a.sizes[(unsigned long long)p * a.mpp + s + k]);
+      if (k > 0 && sum + rk > half) break;
+      r[k] = rk;
+      sum += rk;
+    }
+    unsigned long long W = 0, end = 0, freed = 0, mt = 0;
+    int stop = 0;
+    if (lane == 0) {
+      for (;;) {
+        W = ld_rlx(&v.st->reserve.v);
+        end = mpsc_place(W, r, k, v.R, st);
+        freed = ld_acq(&v.st->freed.v);
+        mt = ld_acq(&v.st->msg_tail.v);
+        const unsigned long long t0 = W >> 40;
+        const bool room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        if (room) {
+          const unsigned long long nw = (((t0 + k) & MASK24) << 40) | end;
+          if (atomicCAS(&v.st->reserve.v, W, nw) == W) break;
+        }
+        if (aborted(a.abort) || gtime() > deadline) {
+          stop = 1;
+          atomicExch(a.abort, 1u);
+          break;
+        }
+        if (!room) __nanosleep(64);
+      }
+    }
+    stop = __shfl_sync(FULLM, stop, 0);
+    if (stop) {
+      if (lane == 0) a.res[c].status = HICR_ERR_TIMEOUT;
+      return;
+    }
+    W = __shfl_sync(FULLM, W, 0);
+    const unsigned long long t0 = W >> 40;
+    for (int i = 0; i < k; ++i) {
+      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+      const unsigned long long idx = (unsigned long long)p * a.mpp + s + i;
+      warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
+    }
+    __threadfence();
+    __syncwarp();
+    for (int i = 0; i < k; ++i) {
+      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+      if (lane == (unsigned)i) {
+        const unsigned long long t = t0 + i;
+        MpscMeta* e = v.meta + (t & (v.M - 1));
+        e->start = si;
+        e->size = (unsigned int)a.sizes[(unsigned long long)p * a.mpp + s + i];
+        e->producer = p;
+        e->seq = s + i;
+        e->flags = 0;
+        st_rel(&e->ready, (t & MASK24) + 1);
+      }
+    }
+    if (lane == 0) {
+      atomicMax(&v.st->max_bytes.v, (end - freed) & MASK40);
+      atomicMax(&v.st->max_msgs.v, ((t0 + k) - mt) & MASK24);
+    }
+    s += k;
+  }
+}
+
+__device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline) {
+  __shared__ int s_stop;
+  __shared__ unsigned long long s_avail, s_end, s_bytes[32];
+  const MpscView v = a.chans[c];
+  const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  // messages this consumer receives: producers c, c + n_cons, ...
+  const unsigned long long nprod = (a.n_prod > c) ? (a.n_prod - c + a.n_cons - 1) / a.n_cons : 0;
+  const unsigned long long expect = nprod * a.mpp;
+  const unsigned long long win_max = (unsigned long long)nwarp * MPSC_WIN_PER_WARP;
+  unsigned long long t = 0, consumed = 0, bytes = 0;
+  if (tid == 0) t = ld_acq(&v.st->msg_tail.v);
+  t = __shfl_sync(FULLM, t, 0);
+  __shared__ unsigned long long s_t0;
+  if (tid == 0) s_t0 = t;
+  __syncthreads();
+  t = s_t0;
+  hicr_mpsc_log_t* log = a.log + a.log_stride * c;
+  while (consumed < expect) {
+    if (tid == 0) {
+      int stop = 0;
+      unsigned long long avail = 0;
+      for (;;) {
+        const unsigned long long W = ld_acq(&v.st->reserve.v);
+        avail = ((W >> 40) - t) & MASK24;
+        if (avail) break;
+        if (aborted(a.abort) || gtime() > deadline) {
+          stop = 1;
+          atomicExch(a.abort, 1u);
+          break;
+        }
+        __nanosleep(64);
+      }
+      s_avail = min(min(avail, win_max), expect - consumed);
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const unsigned long long navail = s_avail;
+    for (unsigned long long j = warp; j < navail; j += nwarp) {
+      const unsigned long long tk = t + j;
+      MpscMeta* e = v.meta + (tk & (v.M - 1));
+      int stop = 0;
+      if (lane == 0) {
+        while (ld_acq(&e->ready) != (tk & MASK24) + 1) {
+          if (aborted(a.abort) || gtime() > deadline) {
+            stop = 1;
+            atomicExch(a.abort, 1u);
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      stop = __shfl_sync(FULLM, stop, 0);
+      if (stop) {
+        if (lane == 0) s_stop = 1;
+        break;
+      }
+      const unsigned long long start = __ldcg(&e->start);
+      const unsigned long long n = __ldcg(&e->size);
+      const unsigned int prod = __ldcg(&e->producer), seq = __ldcg(&e->seq);
+      const uint4* base = reinterpret_cast<const uint4*>(v.ring + (start & (v.R - 1)));
+      const unsigned long long nvec = (n + 15) / 16;
+      unsigned long long d = 0;
+      for (unsigned long long q = lane; q < nvec; q += 32) {
+        const uint4 x = __ldcg(base + q);
+        unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+        unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+        const unsigned long long b0 = 16 * q;  // byte index of w0
+        if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
+        if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
+        d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
+      if (lane == 0) {
+        hicr_mpsc_log_t L;
+        L.producer = prod;
+        L.seq = seq;
+        L.size = (uint32_t)n;
+        L.reserved = 0;
+        L.offset = start & (v.R - 1);
+        L.digest = d;
+        log[consumed + j] = L;
+        bytes += n;
+        if (j == navail - 1) s_end = (start + round16(n)) & MASK40;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    if (tid == 0) {
+      st_rel(&v.st->freed.v, s_end);
+      st_rel(&v.st->msg_tail.v, t + navail);
+    }
+    t += navail;
+    consumed += navail;
+  }
+  if (lane == 0) s_bytes[warp] = bytes;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long b = 0;
+    for (unsigned w = 0; w < nwarp; ++w) b += s_bytes[w];
+    hicr_mpsc_result_t* r = a.res + c;
+    r->consumed = consumed;
+    r->bytes = b;
+    if (s_stop) r->status = HICR_ERR_TIMEOUT;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_mpsc_stream(MpscStreamArgs a) {
+  const unsigned long long deadline = gtime() + a.timeout_ns;
+  if (blockIdx.x < a.n_cons) {
+    mpsc_consumer(a, blockIdx.x, deadline);
+    return;
+  }
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned p = (blockIdx.x - a.n_cons) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p < a.n_prod) mpsc_producer(a, p, lane, deadline);
+}
+
+// Checks run before a stream: every message lies inside the staging slot and
+// is at most half its ring (so a reservation always fits an emptied ring).
+__global__ void k_mpsc_check(MpscStreamArgs a, unsigned long long staging_size, int* bad) {
+  const unsigned long long total = (unsigned long long)a.n_prod * a.mpp;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long n = a.sizes[i], off = a.src_off[i];
+    const unsigned c = (unsigned)((i / a.mpp) % a.n_cons);
+    if (off > staging_size || n > staging_size - off) atomicCAS(bad, 0, HICR_ERR_BOUNDS);
+    else if (round16(n) > a.chans[c].R / 2 || n > 0xffffffffull) atomicCAS(bad, 0, HICR_ERR_TOO_LARGE);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static Channel* get(Instance* in, hicr_channel_t ch) {
+  if (ch >= in->channels.size() || !in->channels[ch] || !in->channels[ch]->live) return nullptr;
+  return in->channels[ch];
+}
+
+static hicr_status mailbox(Instance* in, Mailbox** host, Mailbox** dev) {
+  if (!in->mbox_host) {
+    void* p = nullptr;
+    HICR_CUDA(in, cudaHostAlloc(&p, 4096, cudaHostAllocMapped));
+    void* d = nullptr;
+    HICR_CUDA(in, cudaHostGetDevicePointer(&d, p, 0));
+    in->mbox_host = p;
+    in->mbox_dev = d;
+  }
+  *host = (Mailbox*)in->mbox_host;
+  *dev = (Mailbox*)in->mbox_dev;
+  (*host)->status = 1;  // "not written"
+  return HICR_OK;
+}
+
+static hicr_status finish(Instance* in, Mailbox* mh) {
+  HICR_CUDA(in, cudaGetLastError());
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  if (mh->status == 1) return HICR_ERR_DEVICE;
+  return mh->status;
+}
+
+static hicr_status dev_buffer(Instance* in, size_t bytes, void** out) {
+  if (in->chan_buf_cap < bytes) {
+    HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+    if (in->chan_buf) cudaFree(in->chan_buf);
+    in->chan_buf = nullptr;
+    in->chan_buf_cap = 0;
+    size_t cap = bytes < 65536 ? 65536 : bytes;
+    HICR_CUDA(in, cudaMalloc(&in->chan_buf, cap));
+    in->chan_buf_cap = cap;
+  }
+  *out = in->chan_buf;
+  return HICR_OK;
+}
+
+static SpscView spsc_view(Channel* c) {
+  SpscView v;
+  v.ring = c->ring;
+  v.st = (SpscState*)c->state;
+  v.ts = c->token_size;
+  v.cap = c->capacity;
+  return v;
+}
+static MpscView mpsc_view(Channel* c) {
+  MpscView v;
+  v.ring = c->ring;
+  v.st = (MpscState*)c->state;
+  v.meta = c->meta;
+  v.R = c->ring_bytes;
+  v.M = c->max_msgs;
+  return v;
+}
+
+static hicr_status add_channel(hicr_instance_t h, Channel* c, size_t ring_bytes, size_t state_bytes,
+                               size_t meta_bytes, hicr_channel_t* out) {
+  Instance* in = &h->impl;
+  char* p = nullptr;
+  const size_t ring_al = (ring_bytes + 255) & ~(size_t)255;
+  const size_t st_al = (state_bytes + 255) & ~(size_t)255;
+  cudaError_t e = cudaMalloc(&p, ring_al + st_al + meta_bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    delete c;
+    return HICR_ERR_NOMEM;
+  }
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(in, e, "cudaMalloc(channel)");
+  }
+  c->ring = (uint8_t*)p;
+  c->state = p + ring_al;
+  c->meta = meta_bytes ? (MpscMeta*)(p + ring_al + st_al) : nullptr;
+  e = cudaMemsetAsync(p + ring_al, 0, st_al + meta_bytes, in->comm());
+  if (e == cudaSuccess) e = cudaStreamSynchronize(in->comm());
+  if (e != cudaSuccess) {
+    cudaFree(p);
+    delete c;
+    return cuda_fail(in, e, "channel init");
+  }
+  hicr_slot_t rs;
+  hicr_status st = hicr_slot_register(h, HICR_SPACE_HBM, p, ring_bytes, 0, &rs);
+  if (st != HICR_OK) {
+    cudaFree(p);
+    delete c;
+    return st;
+  }
+  c->ring_slot = rs;
+  c->live = true;
+  for (size_t i = 0; i < in->channels.size(); ++i) {
+    if (!in->channels[i]) {
+      in->channels[i] = c;
+      *out = (hicr_channel_t)i;
+      return HICR_OK;
+    }
+  }
+  in->channels.push_back(c);
+  *out = (hicr_channel_t)(in->channels.size() - 1);
+  return HICR_OK;
+}
+
+void destroy_channels(Instance* in) {
+  for (Channel* c : in->channels) {
+    if (c) {
+      if (c->ring) cudaFree(c->ring);
+      delete c;
+    }
+  }
+  in->channels.clear();
+  if (in->mbox_host) cudaFreeHost(in->mbox_host);
+  in->mbox_host = in->mbox_dev = nullptr;
+  if (in->chan_buf) cudaFree(in->chan_buf);
+  in->chan_buf = nullptr;
+  in->chan_buf_cap = 0;
+}
+
+static bool pow2(unsigned long long x) { return x && !(x & (x - 1)); }
+
 }  // namespace hicr
+
+using namespace hicr;
+
+static Instance* I(hicr_instance_t h) { return h ? &h->impl : nullptr; }
+
+extern "C" {
+
+hicr_status hicr_spsc_create(hicr_instance_t h, uint32_t token_size, uint32_t capacity, hicr_channel_t* out) {
+  Instance* in = I(h);
+  if (!in || !out || token_size == 0 || capacity == 0 || in->capturing) return HICR_ERR_INVALID;
+  if ((unsigned long long)token_size * capacity > (1ull << 40)) return HICR_ERR_INVALID;
+  Channel* c = new Channel();
+  c->kind = 0;
+  c->token_size = token_size;
+  c->capacity = capacity;
+  c->seq.assign(1, 0);
+  return add_channel(h, c, (size_t)token_size * capacity, sizeof(SpscState), 0, out);
+}
+
+hicr_status hicr_mpsc_create(hicr_instance_t h, uint32_t n_producers, uint64_t ring_bytes, uint32_t max_msgs,
+                             hicr_channel_t* out) {
+  Instance* in = I(h);
+  if (!in || !out || n_producers == 0 || in->capturing) return HICR_ERR_INVALID;
+  if (!pow2(ring_bytes) || ring_bytes < 64 || ring_bytes > (1ull << 39)) return HICR_ERR_INVALID;
+  if (!pow2(max_msgs) || max_msgs > (1u << 23)) return HICR_ERR_INVALID;
+  Channel* c = new Channel();
+  c->kind = 1;
+  c->n_producers = n_producers;
+  c->ring_bytes = ring_bytes;
+  c->max_msgs = max_msgs;
+  c->seq.assign(n_producers, 0);
+  return add_channel(h, c, ring_bytes, sizeof(MpscState), sizeof(MpscMeta) * (size_t)max_msgs, out);
+}
+
+hicr_status hicr_channel_destroy(hicr_instance_t h, hicr_channel_t ch) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  hicr_slot_deregister(h, c->ring_slot);
+  cudaFree(c->ring);
+  delete c;
+  in->channels[ch] = nullptr;
+  return HICR_OK;
+}
+
+hicr_status hicr_channel_ring(hicr_instance_t h, hicr_channel_t ch, hicr_slot_t* ring_slot) {
+  Instance* in = I(h);
+  if (!in || !ring_slot) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  *ring_slot = c->ring_slot;
+  return HICR_OK;
+}
+
+hicr_status hicr_channel_push(hicr_instance_t h, hicr_channel_t ch, uint32_t producer, hicr_slot_t src,
+                              uint64_t off, uint64_t n) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  void* sp = nullptr;
+  uint64_t ssize = 0;
+  uint32_t sspace = 0;
+  if (hicr_slot_info(h, src, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+  if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  Mailbox *mh, *md;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  if ((st = mailbox(in, &mh, &md)) != HICR_OK) return st;
+  if (c->kind == 0) {
+    if (producer != 0) return HICR_ERR_INVALID;
+    if (n > (1ull << 40) / c->token_size) return HICR_ERR_FULL;
+    const uint64_t bytes = n * c->token_size;
+    if (off > ssize || bytes > ssize - off) return HICR_ERR_BOUNDS;
+    if (n > c->capacity) return HICR_ERR_FULL;
+    k_spsc_push_host<<<1, 256, 0, in->comm()>>>(spsc_view(c), (const uint8_t*)sp + off, n, md);
+    st = finish(in, mh);
+  } else {
+    if (producer >= c->n_producers) return HICR_ERR_INVALID;
+    if (off > ssize || n > ssize - off) return HICR_ERR_BOUNDS;
+    if (round16(n) > c->ring_bytes || n > 0xffffffffull) return HICR_ERR_TOO_LARGE;
+    k_mpsc_push_host<<<1, 256, 0, in->comm()>>>(mpsc_view(c), producer, c->seq[producer], (const uint8_t*)sp + off,
+                                               n, md);
+    st = finish(in, mh);
+    if (st == HICR_OK) c->seq[producer]++;
+  }
+  if (st == HICR_OK) st = record_done(in);
+  return st;
+}
+
+static hicr_status ctl(Instance* in, Channel* c, int op, uint64_t k, Mailbox** out) {
+  Mailbox *mh, *md;
+  hicr_status st = mailbox(in, &mh, &md);
+  if (st != HICR_OK) return st;
+  if (c->kind == 0) k_spsc_ctl<<<1, 1, 0, in->comm()>>>(spsc_view(c), op, k, md);
+  else k_mpsc_ctl<<<1, 1, 0, in->comm()>>>(mpsc_view(c), op, k, md);
+  st = finish(in, mh);
+  *out = mh;
+  return st;
+}
+
+hicr_status hicr_channel_peek(hicr_instance_t h, hicr_channel_t ch, uint64_t k, hicr_msg_info_t* out) {
+  Instance* in = I(h);
+  if (!in || !out || in->capturing) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  Mailbox* mb = nullptr;
+  hicr_status st = ctl(in, c, 0, k, &mb);
+  if (st != HICR_OK) return st;
+  out->offset = mb->v[0];
+  out->size = mb->v[1];
+  out->producer = (uint32_t)mb->v[2];
+  out->reserved = 0;
+  out->seq = mb->v[3];
+  return HICR_OK;
+}
+
+hicr_status hicr_channel_pop(hicr_instance_t h, hicr_channel_t ch, uint64_t count) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  Mailbox* mb = nullptr;
+  return ctl(in, c, 1, count, &mb);
+}
+
+hicr_status hicr_channel_depth(hicr_instance_t h, hicr_channel_t ch, uint64_t* msgs, uint64_t* bytes) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c) return HICR_ERR_INVALID;
+  Mailbox* mb = nullptr;
+  hicr_status st = ctl(in, c, 2, 0, &mb);
+  if (st != HICR_OK) return st;
+  if (msgs) *msgs = mb->v[0];
+  if (bytes) *bytes = mb->v[1];
+  return HICR_OK;
+}
+
+hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                             uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results) {
+  Instance* in = I(h);
+  if (!in || !chans || !results || n == 0 || batch == 0 || in->capturing) return HICR_ERR_INVALID;
+  std::vector<SpscView> views(n);
+  for (uint32_t i = 0; i < n; ++i) {
+    Channel* c = get(in, chans[i]);
+    if (!c || c->kind != 0 || c->token_size % 16 || batch > c->capacity) return HICR_ERR_INVALID;
+    views[i] = spsc_view(c);
+  }
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  const size_t vb = ((sizeof(SpscView) * n + 255) / 256) * 256;
+  const size_t rb = sizeof(hicr_spsc_result_t) * n;
+  void* buf = nullptr;
+  if ((st = dev_buffer(in, vb + rb + 256, &buf)) != HICR_OK) return st;
+  char* p = (char*)buf;
+  cudaStream_t s = in->comm();
+  HICR_CUDA(in, cudaMemcpyAsync(p, views.data(), sizeof(SpscView) * n, cudaMemcpyHostToDevice, s));
+  HICR_CUDA(in, cudaMemsetAsync(p + vb, 0, rb + 256, s));
+  SpscStreamArgs a;
+  a.chans = (const SpscView*)p;
+  a.n = n;
+  a.batch = batch;
+  a.tokens = tokens;
+  a.timeout_ns = timeout_ns;
+  a.res = (hicr_spsc_result_t*)(p + vb);
+  a.abort = (unsigned int*)(p + vb + rb);
+  void* args[] = {&a};
+  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_spsc_stream, dim3(2 * n), dim3(512), args, 0, s));
+  HICR_CUDA(in, cudaMemcpyAsync(results, a.res, rb, cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaStreamSynchronize(s));
+  if ((st = record_done(in)) != HICR_OK) return st;
+  for (uint32_t i = 0; i < n; ++i)
+    if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
+  return HICR_OK;
+}
+
+hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                             uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                             const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                             uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
+                             hicr_mpsc_result_t* results) {
+  Instance* in = I(h);
+  if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
+      group == 0 || group > (uint32_t)MPSC_MAX_GROUP || in->capturing)
+    return HICR_ERR_INVALID;
+  void* sp = nullptr;
+  uint64_t ssize = 0;
+  uint32_t sspace = 0;
+  if (hicr_slot_info(h, staging, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+  if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  std::vector<MpscView> views(n_consumers);
+  const uint64_t per = (n_producers + n_consumers - 1) / n_consumers;
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    Channel* c = get(in, chans[i]);
+    if (!c || c->kind != 1 || c->n_producers < per) return HICR_ERR_INVALID;
+    views[i] = mpsc_view(c);
+  }
+  if (log_stride < per * msgs_per_producer) return HICR_ERR_INVALID;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  const size_t vb = ((sizeof(MpscView) * n_consumers + 255) / 256) * 256;
+  const size_t rb = ((sizeof(hicr_mpsc_result_t) * n_consumers + 255) / 256) * 256;
+  void* buf = nullptr;
+  if ((st = dev_buffer(in, vb + rb + 256, &buf)) != HICR_OK) return st;
+  char* p = (char*)buf;
+  cudaStream_t s = in->comm();
+  HICR_CUDA(in, cudaMemcpyAsync(p, views.data(), sizeof(MpscView) * n_consumers, cudaMemcpyHostToDevice, s));
+  HICR_CUDA(in, cudaMemsetAsync(p + vb, 0, rb + 256, s));
+  MpscStreamArgs a;
+  a.chans = (const MpscView*)p;
+  a.n_cons = n_consumers;
+  a.n_prod = n_producers;
+  a.mpp = msgs_per_producer;
+  a.group = group;
+  a.sizes = (const unsigned long long*)d_sizes;
+  a.src_off = (const unsigned long long*)d_src_off;
+  a.staging = (const uint8_t*)sp;
+  a.timeout_ns = timeout_ns;
+  a.log = d_log;
+  a.log_stride = log_stride;
+  a.res = (hicr_mpsc_result_t*)(p + vb);
+  a.abort = (unsigned int*)(p + vb + rb);
+  int* bad = (int*)(p + vb + rb + 128);
+  k_mpsc_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
+  int hbad = 0;
+  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaStreamSynchronize(s));
+  if (hbad) return hbad;
+  // reset the channels' high-water marks so the results describe this run
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    MpscState* ms = (MpscState*)get(in, chans[i])->state;
+    HICR_CUDA(in, cudaMemsetAsync(&ms->max_bytes, 0, sizeof(Line) * 2, s));
+  }
+  const unsigned warps = 256 / 32;
+  const unsigned grid = n_consumers + (n_producers + warps - 1) / warps;
+  void* args[] = {&a};
+  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3(grid), dim3(256), args, 0, s));
+  HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaStreamSynchronize(s));
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    MpscState* ms = (MpscState*)get(in, chans[i])->state;
+    unsigned long long mx[2];
+    HICR_CUDA(in, cudaMemcpy(&mx[0], &ms->max_bytes.v, 8, cudaMemcpyDeviceToHost));
+    HICR_CUDA(in, cudaMemcpy(&mx[1], &ms->max_msgs.v, 8, cudaMemcpyDeviceToHost));
+    results[i].max_inflight_bytes = mx[0];
+    results[i].max_inflight_msgs = mx[1];
+  }
+  if ((st = record_done(in)) != HICR_OK) return st;
+  for (uint32_t i = 0; i < n_consumers; ++i)
+    if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
+  return HICR_OK;
+}
+
+}  // extern "C"

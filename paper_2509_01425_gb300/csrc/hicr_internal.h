@@ -133,6 +133,10 @@ struct Instance {
   size_t prof_used = 0;
 
   std::vector<Channel*> channels;
+  void* mbox_host = nullptr;  // mapped page-locked mailbox for channel host calls
+  void* mbox_dev = nullptr;
+  void* chan_buf = nullptr;   // device buffer for streaming-run arguments/results
+  size_t chan_buf_cap = 0;
   std::string last_err;
 
   cudaStream_t comm() const { return pus[comm_pu].stream; }

@@ -50,6 +50,29 @@ __global__ void k_digest(const uint8_t* p, unsigned long long n, unsigned long l
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
+// One warp per segment {off, n, key_base}: byte j of the segment is byte
+// (j mod 8) of first_output(key_base + j/8).
+__global__ void k_fill_segments(uint8_t* base, unsigned long long size, const unsigned long long* seg,
+                                unsigned long long count) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long i = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
+    const unsigned long long off = seg[3 * i], n = seg[3 * i + 1], key = seg[3 * i + 2];
+    if (off > size || n > size - off) continue;  // outside the slot: skipped
+    uint8_t* d = base + off;
+    const bool aligned = ((uintptr_t)d & 7u) == 0;
+    const unsigned long long nw = (n + 7) >> 3;
+    for (unsigned long long w = lane; w < nw; w += 32) {
+      const uint64_t v = sm64_first_output(key + w);
+      if (aligned && 8 * w + 8 <= n) {
+        *reinterpret_cast<uint64_t*>(d + 8 * w) = v;
+      } else {
+        for (unsigned k = 0; k < 8 && 8 * w + k < n; ++k) d[8 * w + k] = (uint8_t)(v >> (8 * k));
+      }
+    }
+  }
+}
+
 const void* builtin_fill_kernel() { return (const void*)k_fill; }
 const void* builtin_digest_kernel() { return (const void*)k_digest; }
 
@@ -67,6 +90,19 @@ hicr_status hicr_util_fill(hicr_instance_t h, hicr_slot_t slot, uint64_t off, ui
   if (n == 0) return HICR_OK;
   const unsigned grid = (unsigned)in->sm_count * 8;
   k_fill<<<grid, 256, 0, in->comm()>>>((uint8_t*)s.base, off, n, key_base);
+  HICR_CUDA(in, cudaGetLastError());
+  return record_done(in);
+}
+
+hicr_status hicr_util_fill_segments(hicr_instance_t h, hicr_slot_t slot, const uint64_t* d_seg, uint64_t count) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || (count && !d_seg) || slot >= in->slots.size() || !in->slots[slot].live || in->capturing)
+    return HICR_ERR_INVALID;
+  const HostSlot& s = in->slots[slot];
+  if (s.space != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  if (count == 0) return HICR_OK;
+  const unsigned grid = (unsigned)in->sm_count * 8;
+  k_fill_segments<<<grid, 256, 0, in->comm()>>>((uint8_t*)s.base, s.size, (const unsigned long long*)d_seg, count);
   HICR_CUDA(in, cudaGetLastError());
   return record_done(in);
 }

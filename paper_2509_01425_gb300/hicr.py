@@ -159,6 +159,7 @@ _exec_query = _decl("hicr_exec_query", [H, u64, C.POINTER(i32)])
 _exec_await = _decl("hicr_exec_await", [H, u64, u64])
 _last_error_string = _decl("hicr_last_error_string", [H, C.c_char_p, u64])
 _util_fill = _decl("hicr_util_fill", [H, u32, u64, u64, u64])
+_util_fill_segments = _decl("hicr_util_fill_segments", [H, u32, vp, u64])
 _util_digest = _decl("hicr_util_digest", [H, u32, u64, u64, C.POINTER(u64)])
 
 
@@ -413,7 +414,107 @@ def hicr_util_fill(inst, slot, off, n, key_base):
     return _util_fill(inst, slot, off, n, key_base)
 
 
+def hicr_util_fill_segments(inst, slot, d_seg, count):
+    return _util_fill_segments(inst, slot, _ptr(d_seg), count)
+
+
 def hicr_util_digest(inst, slot, off, n):
     v = u64()
     st = _util_digest(inst, slot, off, n, C.byref(v))
     return st, v.value
+
+
+# ---------------------------------------------------------------------------
+# Channels (include/hicr_channels.h)
+# ---------------------------------------------------------------------------
+class hicr_msg_info_t(C.Structure):
+    _fields_ = [("offset", u64), ("size", u64), ("producer", u32), ("reserved", u32), ("seq", u64)]
+
+
+class hicr_spsc_result_t(C.Structure):
+    _fields_ = [("pushed", u64), ("popped", u64), ("mismatches", u64), ("digest", u64),
+                ("max_occupancy", u64), ("status", i32), ("reserved", u32)]
+
+
+class hicr_mpsc_log_t(C.Structure):
+    _fields_ = [("producer", u32), ("seq", u32), ("size", u32), ("reserved", u32), ("offset", u64),
+                ("digest", u64)]
+
+
+MPSC_LOG_DTYPE = np.dtype([("producer", "<u4"), ("seq", "<u4"), ("size", "<u4"), ("reserved", "<u4"),
+                           ("offset", "<u8"), ("digest", "<u8")])
+
+
+class hicr_mpsc_result_t(C.Structure):
+    _fields_ = [("consumed", u64), ("bytes", u64), ("max_inflight_bytes", u64), ("max_inflight_msgs", u64),
+                ("status", i32), ("reserved", u32)]
+
+
+_spsc_create = _decl("hicr_spsc_create", [H, u32, u32, C.POINTER(u32)])
+_mpsc_create = _decl("hicr_mpsc_create", [H, u32, u64, u32, C.POINTER(u32)])
+_channel_destroy = _decl("hicr_channel_destroy", [H, u32])
+_channel_ring = _decl("hicr_channel_ring", [H, u32, C.POINTER(u32)])
+_channel_push = _decl("hicr_channel_push", [H, u32, u32, u32, u64, u64])
+_channel_peek = _decl("hicr_channel_peek", [H, u32, u64, C.POINTER(hicr_msg_info_t)])
+_channel_pop = _decl("hicr_channel_pop", [H, u32, u64])
+_channel_depth = _decl("hicr_channel_depth", [H, u32, C.POINTER(u64), C.POINTER(u64)])
+_spsc_stream = _decl("hicr_spsc_stream", [H, vp, u32, u64, u32, u64, vp])
+_mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u64, vp, u64, vp])
+
+
+def hicr_spsc_create(inst, token_size, capacity):
+    c = u32()
+    st = _spsc_create(inst, token_size, capacity, C.byref(c))
+    return st, c.value
+
+
+def hicr_mpsc_create(inst, n_producers, ring_bytes, max_msgs):
+    c = u32()
+    st = _mpsc_create(inst, n_producers, ring_bytes, max_msgs, C.byref(c))
+    return st, c.value
+
+
+def hicr_channel_destroy(inst, ch):
+    return _channel_destroy(inst, ch)
+
+
+def hicr_channel_ring(inst, ch):
+    s = u32()
+    st = _channel_ring(inst, ch, C.byref(s))
+    return st, s.value
+
+
+def hicr_channel_push(inst, ch, producer, src, off, n):
+    return _channel_push(inst, ch, producer, src, off, n)
+
+
+def hicr_channel_peek(inst, ch, k):
+    m = hicr_msg_info_t()
+    st = _channel_peek(inst, ch, k, C.byref(m))
+    return st, (m.offset, m.size, m.producer, m.seq)
+
+
+def hicr_channel_pop(inst, ch, count):
+    return _channel_pop(inst, ch, count)
+
+
+def hicr_channel_depth(inst, ch):
+    a, b = u64(), u64()
+    st = _channel_depth(inst, ch, C.byref(a), C.byref(b))
+    return st, a.value, b.value
+
+
+def hicr_spsc_stream(inst, chans, tokens, batch, timeout_ns=60_000_000_000):
+    arr = (u32 * len(chans))(*chans)
+    res = (hicr_spsc_result_t * len(chans))()
+    st = _spsc_stream(inst, C.addressof(arr), len(chans), tokens, batch, timeout_ns, C.addressof(res))
+    return st, list(res)
+
+
+def hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                     d_log, log_stride, timeout_ns=120_000_000_000):
+    arr = (u32 * len(chans))(*chans)
+    res = (hicr_mpsc_result_t * len(chans))()
+    st = _mpsc_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
+                      _ptr(d_src_off), staging, group, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
+    return st, list(res)

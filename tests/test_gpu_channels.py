@@ -1,0 +1,202 @@
+"""GPU parity of the SPSC / MPSC channels against the channel oracle.
+
+Host calls (push / peek / pop / depth) are deterministic and must match the
+oracle exactly: statuses, ring offsets, sizes, producers, sequence numbers
+and payload bytes. Device streaming runs interleave producers freely: the
+SPSC stream must deliver the exact token stream (digest of every word), the
+MPSC stream must pass the interleaving-agnostic checker (multiset, per-
+producer order, sizes, ring offsets replayed from the placement rule) and
+carry the exact payloads (digests), without ever exceeding capacity.
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+from oracle import channels as oc
+from oracle import digest as od
+from oracle import memcpy as om
+from workloads import configs, splitmix
+from tests.gpu_util import device_bytes, h, inst  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+ST = {"OK": om.OK, "FULL": om.ERR_FULL, "EMPTY": om.ERR_EMPTY, "TOO_LARGE": om.ERR_TOO_LARGE}
+
+
+def ring_bytes(h, inst, ch, off, n):
+    st, rs = h.hicr_channel_ring(inst, ch)
+    st, ptr, size, _, _ = h.hicr_slot_info(inst, rs)
+    torch.cuda.synchronize()
+    return device_bytes(ptr + off, n).cpu().numpy()
+
+
+def src_slot(h, inst, data: np.ndarray):
+    t = torch.from_numpy(np.ascontiguousarray(data)).cuda()
+    st, s = h.hicr_slot_register(inst, h.HICR_SPACE_HBM, t.data_ptr(), t.numel())
+    assert st == 0
+    return s, t
+
+
+@pytest.mark.parametrize("seed,ts,cap", [(0, 8, 5), (1, 24, 7), (2, 64, 16)])
+def test_spsc_host_calls_match_oracle(h, inst, seed, ts, cap):
+    rng = np.random.default_rng(seed)
+    st, ch = h.hicr_spsc_create(inst, ts, cap)
+    assert st == 0
+    orc = oc.SpscOracle(ts, cap)
+    pool = rng.integers(0, 256, ts * 4 * cap, dtype=np.uint8)
+    s, keep = src_slot(h, inst, pool)
+    for step in range(300):
+        r = rng.random()
+        if r < 0.45:
+            k = int(rng.integers(0, cap + 2))
+            off = int(rng.integers(0, len(pool) - k * ts + 1))
+            exp = orc.push(pool[off:off + k * ts])
+            assert h.hicr_channel_push(inst, ch, 0, s, off, k) == exp, step
+        elif r < 0.7:
+            k = int(rng.integers(0, cap + 2))
+            assert h.hicr_channel_pop(inst, ch, k) == orc.pop(k), step
+        elif r < 0.9:
+            k = int(rng.integers(0, cap + 1))
+            est, info = orc.peek(k)
+            gst, ginfo = h.hicr_channel_peek(inst, ch, k)
+            assert gst == est, step
+            if est == om.OK:
+                assert ginfo == info
+                assert (ring_bytes(h, inst, ch, ginfo[0], ts) == orc.token(k)).all()
+        else:
+            assert h.hicr_channel_depth(inst, ch)[1:] == orc.depth()
+    assert h.hicr_channel_push(inst, ch, 1, s, 0, 1) == h.HICR_ERR_INVALID  # SPSC has producer 0 only
+    assert h.hicr_channel_push(inst, ch, 0, s, len(pool), 1) == h.HICR_ERR_BOUNDS
+    assert h.hicr_channel_destroy(inst, ch) == 0
+    assert h.hicr_channel_depth(inst, ch)[0] == h.HICR_ERR_INVALID
+
+
+def test_mpsc_golden_wraparound_through_the_abi(h, inst):
+    from tests.test_oracle_channels import load_mpsc_golden
+    prog = load_mpsc_golden()
+    R, M, P = map(int, prog[0][1:])
+    st, ch = h.hicr_mpsc_create(inst, P, R, M)
+    assert st == 0
+    pool = np.concatenate([splitmix.mpsc_payload_bytes(p, q, 128) for p in range(P) for q in range(8)])
+    s, keep = src_slot(h, inst, pool)
+    seq = [0] * P
+    for f in prog[1:]:
+        if f[0] == "push":
+            p, n = int(f[1]), int(f[2])
+            off = (p * 8 + seq[p]) * 128
+            got = h.hicr_channel_push(inst, ch, p, s, off, n)
+            assert got == ST[f[3]], f
+            if got == om.OK:
+                seq[p] += 1
+        elif f[0] == "pop":
+            assert h.hicr_channel_pop(inst, ch, int(f[1])) == ST[f[2]], f
+        elif f[0] == "peek":
+            gst, info = h.hicr_channel_peek(inst, ch, int(f[1]))
+            assert gst == ST[f[2]], f
+            if gst == om.OK:
+                assert list(info) == [int(x) for x in f[3:7]], f
+                o, n, p, q = info
+                assert (ring_bytes(h, inst, ch, o, n) == pool[(p * 8 + q) * 128:(p * 8 + q) * 128 + n]).all()
+        elif f[0] == "depth":
+            assert h.hicr_channel_depth(inst, ch)[1:] == (int(f[1]), int(f[2])), f
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_mpsc_host_calls_match_oracle(h, inst, seed):
+    rng = np.random.default_rng(seed)
+    P, R, M = 4, 1 << 12, 8
+    st, ch = h.hicr_mpsc_create(inst, P, R, M)
+    assert st == 0
+    orc = oc.MpscOracle(P, R, M)
+    pool = rng.integers(0, 256, 1 << 16, dtype=np.uint8)
+    s, keep = src_slot(h, inst, pool)
+    for step in range(400):
+        r = rng.random()
+        if r < 0.5:
+            p = int(rng.integers(0, P))
+            n = int(rng.choice([0, 1, 7, 16, 17, 100, 500, 1500, 2100, 4096, 5000]))
+            off = int(rng.integers(0, len(pool) - n + 1))
+            exp = orc.push(p, pool[off:off + n])
+            assert h.hicr_channel_push(inst, ch, p, s, off, n) == exp, (step, p, n)
+        elif r < 0.75:
+            k = int(rng.integers(0, 4))
+            assert h.hicr_channel_pop(inst, ch, k) == orc.pop(k), step
+        elif r < 0.92:
+            k = int(rng.integers(0, M + 1))
+            est, info = orc.peek(k)
+            gst, ginfo = h.hicr_channel_peek(inst, ch, k)
+            assert gst == est, step
+            if est == om.OK:
+                assert ginfo == info, step
+                assert (ring_bytes(h, inst, ch, ginfo[0], ginfo[1]) == orc.payload(k)).all()
+        else:
+            assert h.hicr_channel_depth(inst, ch)[1:] == orc.depth(), step
+    assert h.hicr_channel_push(inst, ch, P, s, 0, 8) == h.HICR_ERR_INVALID
+    assert h.hicr_mpsc_create(inst, 2, 3000, 8)[0] == h.HICR_ERR_INVALID   # ring not a power of two
+
+
+def _spsc_expected_digest(channel, tokens, wpt=8):
+    d = 0
+    step = 1 << 20
+    for t0 in range(0, tokens, step):
+        n = min(step, tokens - t0)
+        d = (d + od.word_digest(splitmix.spsc_token_words(channel, t0, n, wpt), t0 * wpt)) % (1 << 64)
+    return d
+
+
+@pytest.mark.parametrize("n_ch,cap,ts,tokens,batch", [
+    (64, 4096, 64, 100_000, 256),
+    (8, 16, 64, 1003, 16),
+    (4, 64, 32, 5000, 1),
+    (2, 4096, 128, 70_000, 4096),
+])
+def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
+    chans = [h.hicr_spsc_create(inst, ts, cap)[1] for _ in range(n_ch)]
+    st, res = h.hicr_spsc_stream(inst, chans, tokens, batch)
+    assert st == 0
+    for i, r in enumerate(res):
+        assert (r.pushed, r.popped, r.mismatches, r.status) == (tokens, tokens, 0, 0)
+        assert 0 < r.max_occupancy <= cap
+        assert r.digest == _spsc_expected_digest(i, tokens, ts // 8), i
+        assert h.hicr_channel_depth(inst, chans[i])[1] == 0
+    # a second run continues from the channels' counters
+    st, res2 = h.hicr_spsc_stream(inst, chans[:1], 100, min(batch, 100))
+    assert st == 0 and res2[0].digest == _spsc_expected_digest(0, 100, ts // 8)
+
+
+def _check_mpsc(w, logs, res, ring, sample=1.0, seed=0):
+    rng = np.random.default_rng(seed)
+    C = w.n_consumers
+    for c in range(C):
+        n = int(res[c].consumed)
+        L = logs[c][:n]
+        assert res[c].status == 0
+        assert int(res[c].max_inflight_bytes) <= ring
+        assert int(res[c].max_inflight_msgs) <= w.max_msgs
+        probs = oc.check_mpsc_log(w.sizes, C, c, list(zip(L["producer"], L["seq"], L["size"], L["offset"])), ring)
+        assert probs == [], (c, probs[:5])
+        assert int(res[c].bytes) == int(L["size"].astype(np.int64).sum())
+        idx = np.nonzero(rng.random(n) < sample)[0]
+        for j in idx:
+            p, q, sz = int(L["producer"][j]), int(L["seq"][j]), int(L["size"][j])
+            assert int(L["digest"][j]) == od.byte_digest(splitmix.mpsc_payload_bytes(p, q, sz)), (c, j)
+
+
+@pytest.mark.parametrize("P,C,M,ring,max_msgs,hi,group", [
+    (64, 4, 64, 1 << 20, 256, 16 << 10, 4),
+    (48, 3, 40, 1 << 16, 64, 4 << 10, 1),
+    (33, 5, 17, 1 << 14, 32, 2 << 10, 8),
+])
+def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, group):
+    w = configs.mpsc(7, n_producers=P, n_consumers=C, msgs_per_producer=M, ring_bytes=ring, max_msgs=max_msgs,
+                     hi=hi)
+    run = bench.MpscRun(h, inst, w, group=group)
+    st, res = run.run()
+    assert st == 0
+    _check_mpsc(w, run.logs(), res, ring)
+    # the rings wrapped (skip-to-start exercised) and are empty again
+    assert sum(int(r.bytes) for r in res) > ring
+    for ch in run.chans:
+        assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
+    run.free()
