@@ -132,6 +132,10 @@ typedef struct {
   uint64_t bytes;              /* payload bytes consumed */
   uint64_t max_inflight_bytes; /* largest reserved-minus-freed bytes at a reservation (<= ring) */
   uint64_t max_inflight_msgs;  /* largest in-flight message count at a reservation */
+  uint64_t windows;            /* consumer rounds (consumed / windows = mean window) */
+  uint64_t room_waits;         /* producer polls that found no room */
+  uint64_t cas_failures;       /* producer reservations lost to another producer */
+  uint64_t consumer_ns[3];     /* consumer time in: waiting for/acquiring tickets, digesting, logging+freeing */
   int32_t status;              /* HICR_OK or HICR_ERR_TIMEOUT */
   uint32_t reserved;
 } hicr_mpsc_result_t;

@@ -438,12 +438,16 @@ struct MpscStreamArgs {
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
-static constexpr int MPSC_WIN_PER_WARP = 4;
 
 __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline) {
   const unsigned c = p % a.n_cons;
   const MpscView v = a.chans[c];
   const unsigned long long half = v.R / 2;
+  unsigned long long freed = 0, mt = 0, cas_fail = 0, room_wait = 0;
+  if (lane == 0) {
+    freed = ld_acq(&v.st->freed.v);
+    mt = ld_acq(&v.st->msg_tail.v);
+  }
   for (unsigned s = 0; s < a.mpp;) {
     // the group: up to `group` messages whose rounded sizes sum to <= R/2
     unsigned long long r[MPSC_MAX_GROUP], st[MPSC_MAX_GROUP];
@@ -455,26 +459,40 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
       r[k] = rk;
       sum += rk;
     }
-    unsigned long long W = 0, end = 0, freed = 0, mt = 0;
+    unsigned long long W = 0, end = 0;
     int stop = 0;
     if (lane == 0) {
+      // freed / msg_tail only grow, so a stale copy can only under-report
+      // room; they are re-read only when the cached copies say "full", with
+      // an exponentially growing pause so that waiting producers do not
+      // crowd the lines the consumer releases.
+      unsigned sleep_ns = 32;
       for (;;) {
         W = ld_rlx(&v.st->reserve.v);
         end = mpsc_place(W, r, k, v.R, st);
-        freed = ld_acq(&v.st->freed.v);
-        mt = ld_acq(&v.st->msg_tail.v);
         const unsigned long long t0 = W >> 40;
-        const bool room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        bool room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        if (!room) {
+          freed = ld_acq(&v.st->freed.v);
+          mt = ld_acq(&v.st->msg_tail.v);
+          room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        }
         if (room) {
           const unsigned long long nw = (((t0 + k) & MASK24) << 40) | end;
           if (atomicCAS(&v.st->reserve.v, W, nw) == W) break;
+          ++cas_fail;
+        } else {
+          ++room_wait;
         }
         if (aborted(a.abort) || gtime() > deadline) {
           stop = 1;
           atomicExch(a.abort, 1u);
           break;
         }
-        if (!room) __nanosleep(64);
+        if (!room) {
+          __nanosleep(sleep_ns);
+          sleep_ns = min(sleep_ns * 2, 4096u);
+        }
       }
     }
     stop = __shfl_sync(FULLM, stop, 0);
@@ -510,26 +528,46 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
     }
     s += k;
   }
+  if (lane == 0) {
+    if (cas_fail) atomicAdd((unsigned long long*)&a.res[c].cas_failures, cas_fail);
+    if (room_wait) atomicAdd((unsigned long long*)&a.res[c].room_waits, room_wait);
+  }
 }
+
+// Consumer: one CTA per channel. Each round takes a window of up to
+// MPSC_WIN tickets that producers have already reserved (so every one of them
+// will be published without waiting for ring space) and
+//   A. warps acquire the tickets' `ready` words and stage their metadata in
+//      shared memory;
+//   B. the whole CTA digests the window's payloads in 8 KiB pieces of single
+//      messages, one piece per warp at a time;
+//   C. warps write the log entries, then one thread frees every byte up to the
+//      window's last message and advances msg_tail (release stores).
+static constexpr int MPSC_WIN = 64;
+static constexpr int MPSC_PIECE = 512;  // 16-byte vectors per digest piece (8 KiB)
 
 __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline) {
   __shared__ int s_stop;
-  __shared__ unsigned long long s_avail, s_end, s_bytes[32];
+  __shared__ unsigned long long s_avail, s_t0, s_bytes;
+  __shared__ unsigned long long s_start[MPSC_WIN], s_ppre[MPSC_WIN + 1], s_dig[MPSC_WIN];
+  __shared__ unsigned int s_size[MPSC_WIN], s_prod[MPSC_WIN], s_seq[MPSC_WIN];
   const MpscView v = a.chans[c];
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarp = blockDim.x >> 5;
   // messages this consumer receives: producers c, c + n_cons, ...
   const unsigned long long nprod = (a.n_prod > c) ? (a.n_prod - c + a.n_cons - 1) / a.n_cons : 0;
   const unsigned long long expect = nprod * a.mpp;
-  const unsigned long long win_max = (unsigned long long)nwarp * MPSC_WIN_PER_WARP;
-  unsigned long long t = 0, consumed = 0, bytes = 0;
-  if (tid == 0) t = ld_acq(&v.st->msg_tail.v);
-  t = __shfl_sync(FULLM, t, 0);
-  __shared__ unsigned long long s_t0;
-  if (tid == 0) s_t0 = t;
+  const unsigned long long win_max = min((unsigned long long)MPSC_WIN, (unsigned long long)(v.M / 2 ? v.M / 2 : 1));
+  if (tid == 0) {
+    s_t0 = ld_acq(&v.st->msg_tail.v);
+    s_bytes = 0;
+    s_stop = 0;
+  }
   __syncthreads();
-  t = s_t0;
+  unsigned long long t = s_t0, consumed = 0, windows = 0;
   hicr_mpsc_log_t* log = a.log + a.log_stride * c;
+  unsigned long long ns_a = 0, ns_b = 0, ns_c = 0, tm = 0;
   while (consumed < expect) {
+    if (tid == 0) tm = gtime();
     if (tid == 0) {
       int stop = 0;
       unsigned long long avail = 0;
@@ -549,12 +587,13 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
     }
     __syncthreads();
     if (s_stop) break;
-    const unsigned long long navail = s_avail;
-    for (unsigned long long j = warp; j < navail; j += nwarp) {
+    const unsigned navail = (unsigned)s_avail;
+    // A. acquire and stage metadata
+    for (unsigned j = warp; j < navail; j += nwarp) {
       const unsigned long long tk = t + j;
       MpscMeta* e = v.meta + (tk & (v.M - 1));
-      int stop = 0;
       if (lane == 0) {
+        int stop = 0;
         while (ld_acq(&e->ready) != (tk & MASK24) + 1) {
           if (aborted(a.abort) || gtime() > deadline) {
             stop = 1;
@@ -563,63 +602,127 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
           }
           __nanosleep(32);
         }
-      }
-      stop = __shfl_sync(FULLM, stop, 0);
-      if (stop) {
-        if (lane == 0) s_stop = 1;
-        break;
-      }
-      const unsigned long long start = __ldcg(&e->start);
-      const unsigned long long n = __ldcg(&e->size);
-      const unsigned int prod = __ldcg(&e->producer), seq = __ldcg(&e->seq);
-      const uint4* base = reinterpret_cast<const uint4*>(v.ring + (start & (v.R - 1)));
-      const unsigned long long nvec = (n + 15) / 16;
-      unsigned long long d = 0;
-      for (unsigned long long q = lane; q < nvec; q += 32) {
-        const uint4 x = __ldcg(base + q);
-        unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-        unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
-        const unsigned long long b0 = 16 * q;  // byte index of w0
-        if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
-        if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
-        d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
-      }
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
-      if (lane == 0) {
-        hicr_mpsc_log_t L;
-        L.producer = prod;
-        L.seq = seq;
-        L.size = (uint32_t)n;
-        L.reserved = 0;
-        L.offset = start & (v.R - 1);
-        L.digest = d;
-        log[consumed + j] = L;
-        bytes += n;
-        if (j == navail - 1) s_end = (start + round16(n)) & MASK40;
+        if (stop) {
+          s_stop = 1;
+        } else {
+          s_start[j] = __ldcg(&e->start);
+          s_size[j] = __ldcg(&e->size);
+          s_prod[j] = __ldcg(&e->producer);
+          s_seq[j] = __ldcg(&e->seq);
+          s_dig[j] = 0;
+        }
       }
     }
     __syncthreads();
     if (s_stop) break;
     if (tid == 0) {
-      st_rel(&v.st->freed.v, s_end);
+      const unsigned long long x = gtime();
+      ns_a += x - tm;
+      tm = x;
+    }
+    if (warp == 0) {
+      // exclusive prefix of piece counts (navail <= 64: two values per lane)
+      const unsigned long long p0 = lane < navail ? (((unsigned long long)s_size[lane] + 15) / 16 + MPSC_PIECE - 1) / MPSC_PIECE : 0;
+      const unsigned long long p1 =
+          lane + 32 < navail ? (((unsigned long long)s_size[lane + 32] + 15) / 16 + MPSC_PIECE - 1) / MPSC_PIECE : 0;
+      unsigned long long x0 = p0, x1 = p1;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y0 = __shfl_up_sync(FULLM, x0, o), y1 = __shfl_up_sync(FULLM, x1, o);
+        if (lane >= (unsigned)o) {
+          x0 += y0;
+          x1 += y1;
+        }
+      }
+      const unsigned long long tot0 = __shfl_sync(FULLM, x0, 31);
+      s_ppre[lane] = x0 - p0;
+      s_ppre[lane + 32] = tot0 + x1 - p1;
+      if (lane == 31) s_ppre[64] = tot0 + x1;
+    }
+    __syncthreads();
+    // B. digest: each message is cut into pieces of MPSC_PIECE 16-byte vectors
+    // (one vector per lane, MPSC_PIECE / 32 loads in flight per lane); warps
+    // take pieces round-robin and add each piece's warp-reduced digest to the
+    // message's shared accumulator.
+    const unsigned long long npieces = s_ppre[navail];
+    for (unsigned long long pc = warp; pc < npieces; pc += nwarp) {
+      unsigned lo = 0, hi = navail;  // largest j < navail with s_ppre[j] <= pc
+      while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (s_ppre[mid] <= pc) lo = mid;
+        else hi = mid;
+      }
+      const unsigned j = lo;
+      const unsigned long long n = s_size[j];
+      const unsigned long long nv = (n + 15) / 16;
+      const unsigned long long q0 = (pc - s_ppre[j]) * MPSC_PIECE;
+      const uint4* base = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
+      uint4 x[MPSC_PIECE / 32];
+#pragma unroll
+      for (int u = 0; u < MPSC_PIECE / 32; ++u) {
+        const unsigned long long q = q0 + lane + 32 * u;
+        if (q < nv) x[u] = __ldcg(base + q);
+      }
+      unsigned long long d = 0;
+#pragma unroll
+      for (int u = 0; u < MPSC_PIECE / 32; ++u) {
+        const unsigned long long q = q0 + lane + 32 * u;
+        if (q < nv) {
+          unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
+          unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
+          const unsigned long long b0 = 16 * q;
+          if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
+          if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
+          d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
+      if (lane == 0) atomicAdd(&s_dig[j], d);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const unsigned long long x = gtime();
+      ns_b += x - tm;
+      tm = x;
+    }
+    // C. log, then free up to the window's last message
+    for (unsigned j = tid; j < navail; j += blockDim.x) {
+      hicr_mpsc_log_t L;
+      L.producer = s_prod[j];
+      L.seq = s_seq[j];
+      L.size = s_size[j];
+      L.reserved = 0;
+      L.offset = s_start[j] & (v.R - 1);
+      L.digest = s_dig[j];
+      log[consumed + j] = L;
+    }
+    if (tid == 0) {
+      unsigned long long b = 0;
+      for (unsigned j = 0; j < navail; ++j) b += s_size[j];
+      s_bytes += b;
+      st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
       st_rel(&v.st->msg_tail.v, t + navail);
     }
     t += navail;
     consumed += navail;
+    ++windows;
+    __syncthreads();
+    if (tid == 0) ns_c += gtime() - tm;
   }
-  if (lane == 0) s_bytes[warp] = bytes;
-  __syncthreads();
   if (tid == 0) {
-    unsigned long long b = 0;
-    for (unsigned w = 0; w < nwarp; ++w) b += s_bytes[w];
     hicr_mpsc_result_t* r = a.res + c;
     r->consumed = consumed;
-    r->bytes = b;
+    r->bytes = s_bytes;
+    r->windows = windows;
+    r->consumer_ns[0] = ns_a;
+    r->consumer_ns[1] = ns_b;
+    r->consumer_ns[2] = ns_c;
     if (s_stop) r->status = HICR_ERR_TIMEOUT;
   }
 }
 
-__global__ void __launch_bounds__(256) k_mpsc_stream(MpscStreamArgs a) {
+static constexpr unsigned MPSC_THREADS = 512;
+
+__global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) {
   const unsigned long long deadline = gtime() + a.timeout_ns;
   if (blockIdx.x < a.n_cons) {
     mpsc_consumer(a, blockIdx.x, deadline);
@@ -1006,10 +1109,10 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
     MpscState* ms = (MpscState*)get(in, chans[i])->state;
     HICR_CUDA(in, cudaMemsetAsync(&ms->max_bytes, 0, sizeof(Line) * 2, s));
   }
-  const unsigned warps = 256 / 32;
+  const unsigned warps = MPSC_THREADS / 32;
   const unsigned grid = n_consumers + (n_producers + warps - 1) / warps;
   void* args[] = {&a};
-  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3(grid), dim3(256), args, 0, s));
+  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3(grid), dim3(MPSC_THREADS), args, 0, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   for (uint32_t i = 0; i < n_consumers; ++i) {

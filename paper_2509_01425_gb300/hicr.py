@@ -447,6 +447,7 @@ MPSC_LOG_DTYPE = np.dtype([("producer", "<u4"), ("seq", "<u4"), ("size", "<u4"),
 
 class hicr_mpsc_result_t(C.Structure):
     _fields_ = [("consumed", u64), ("bytes", u64), ("max_inflight_bytes", u64), ("max_inflight_msgs", u64),
+                ("windows", u64), ("room_waits", u64), ("cas_failures", u64), ("consumer_ns", u64 * 3),
                 ("status", i32), ("reserved", u32)]
 
 

@@ -58,3 +58,33 @@ def test_full_size_sampled_parity(h, inst, maker):
     assert (gs - s0 == steps * sent).all() and (gr - r0 == steps * recv).all()
     assert h.hicr_tag_counter(inst, 0) == (0, t0 + steps * len(w.ops))
     assert h.hicr_graph_destroy(inst, g) == 0
+
+
+def test_spsc_full_size(h, inst):
+    """64 channels x capacity 4,096 x 64 B, 10^7 tokens per channel: every word
+    checked on the device against the payload rule, exact counts, capacity
+    respected, and the whole-stream digest of two channels against the oracle."""
+    from tests.test_gpu_channels import _spsc_expected_digest
+    w = configs.SpscWorkload()
+    chans = [h.hicr_spsc_create(inst, w.token_bytes, w.capacity)[1] for _ in range(w.n_channels)]
+    st, res = h.hicr_spsc_stream(inst, chans, w.tokens_per_channel, 256)
+    assert st == 0
+    for r in res:
+        assert (r.pushed, r.popped, r.mismatches, r.status) == (w.tokens_per_channel,) * 2 + (0, 0)
+        assert r.max_occupancy <= w.capacity
+    for i in (0, w.n_channels - 1):
+        assert res[i].digest == _spsc_expected_digest(i, w.tokens_per_channel)
+
+
+def test_mpsc_full_size(h, inst):
+    """1,024 producers -> 16 consumers, 1,024 messages each (log-uniform
+    8 B - 256 KiB), 1 GiB rings: every consumer's log passes the checker; a
+    sample of payload digests matches the oracle."""
+    from tests.test_gpu_channels import _check_mpsc
+    w = configs.mpsc(0)
+    run = bench.MpscRun(h, inst, w, group=4)
+    st, res = run.run()
+    assert st == 0
+    assert sum(int(r.consumed) for r in res) == w.sizes.size
+    _check_mpsc(w, run.logs(), res, w.ring_bytes, sample=0.003)
+    run.free()
