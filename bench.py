@@ -301,6 +301,109 @@ def bench_mpsc(h, inst, reps=3, group=4):
 
 
 # ---------------------------------------------------------------------------
+# Serving.
+# ---------------------------------------------------------------------------
+class ServeSetup:
+    """Source slots of a batched workload (its source half only), request
+    templates, the burst staging slot and a serving engine."""
+
+    def __init__(self, h, inst, src_w, tmpl, seed=0, budget=64 * GiB, n_channels=16, ring_bytes=1 * GiB,
+                 max_msgs=65536, chunk_bytes=128 << 10, op_cost_bytes=4096, verify=False):
+        import torch
+        self.h, self.inst, self.tmpl = h, inst, tmpl
+        self.slot_of = {}
+        for s in np.asarray(src_w.src_slots):
+            sz = int(src_w.slot_sizes[s])
+            sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, sz, 0), "alloc source")
+            h.check(h.hicr_util_fill(inst, sid, 0, sz, splitmix.fill_key_base(seed, int(s))), "fill source")
+            self.slot_of[int(s)] = sid
+        cfg = dict(budget_bytes=budget, n_channels=n_channels, max_msgs=max_msgs, ring_bytes=ring_bytes,
+                   chunk_bytes=chunk_bytes, op_cost_bytes=op_cost_bytes, verify=1 if verify else 0)
+        self.srv = h.check(h.hicr_serve_create(inst, cfg), "serve_create")
+        # memcpy templates
+        m = np.vectorize(self.slot_of.get, otypes=[np.uint32])
+        for t in range(len(tmpl.region_bytes)):
+            a, b = int(tmpl.op_start[t]), int(tmpl.op_start[t + 1])
+            ops = tmpl.ops[a:b].copy()
+            ops["src"] = m(ops["src"])
+            h.check(h.hicr_serve_add_memcpy_template(inst, self.srv, ops, int(tmpl.region_bytes[t])), "memcpy tmpl")
+        # burst staging: message m of template t = MPSC payload (producer t, seq m)
+        sizes = tmpl.msg_sizes.astype(np.uint64)
+        padded = ((sizes + np.uint64(15)) // np.uint64(16)) * np.uint64(16)
+        offs = np.zeros(len(sizes), dtype=np.uint64)
+        offs[1:] = np.cumsum(padded)[:-1]
+        self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, max(int(padded.sum()), 16)), "staging")
+        nt = len(tmpl.msg_start) - 1
+        tt = np.repeat(np.arange(nt, dtype=np.uint64), np.diff(tmpl.msg_start))
+        mm = np.concatenate([np.arange(c, dtype=np.uint64) for c in np.diff(tmpl.msg_start)])
+        keys = (np.uint64(1) << np.uint64(63)) | (tt << np.uint64(40)) | (mm << np.uint64(16))
+        seg = np.stack([offs, sizes, keys], 1).astype(np.uint64)
+        d_seg = torch.from_numpy(seg.view(np.int64).copy()).cuda()
+        h.check(h.hicr_util_fill_segments(inst, self.staging, d_seg.data_ptr(), len(sizes)), "fill staging")
+        for t in range(nt):
+            a, b = int(tmpl.msg_start[t]), int(tmpl.msg_start[t + 1])
+            h.check(h.hicr_serve_add_burst_template(inst, self.srv, sizes[a:b], offs[a:b], self.staging), "burst tmpl")
+        torch.cuda.synchronize()
+        del d_seg
+
+    def requests(self, trace):
+        r = np.zeros(len(trace.arrival_ns), dtype=self.h.SERVE_REQ_DTYPE)
+        r["arrival_ns"] = trace.arrival_ns
+        r["kind"] = trace.kind
+        r["tmpl"] = trace.template
+        return r
+
+    def free(self):
+        h, inst = self.h, self.inst
+        h.check(h.hicr_serve_destroy(inst, self.srv), "serve_destroy")
+        h.check(h.hicr_mem_free(inst, self.staging), "free staging")
+        for sid in self.slot_of.values():
+            h.check(h.hicr_mem_free(inst, sid), "free source")
+
+
+def latency_summary(res, mask=None):
+    lat = res["latency_ns"] if mask is None else res["latency_ns"][mask]
+    if len(lat) == 0:
+        return {}
+    return {"p50_us": float(np.percentile(lat, 50)) / 1e3, "p99_us": float(np.percentile(lat, 99)) / 1e3,
+            "mean_us": float(lat.mean()) / 1e3, "max_us": float(lat.max()) / 1e3}
+
+
+def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
+    """Config 5: Poisson 20,000 req/s, 70% memcpy batches of log-uniform 1-4,096
+    ops (16 B-4 MiB) over config 2's source slots, 30% MPSC bursts of
+    log-uniform 1-512 messages (8 B-256 KiB), 64 GiB budget (16 x 1 GiB rings +
+    48 GiB destination arena)."""
+    src_w = configs.batched(seed)
+    tmpl = configs.serve_templates(seed, src_w)
+    ss = ServeSetup(h, inst, src_w, tmpl, seed=seed)
+    tr = configs.serve_trace(seed, rate=20000.0, duration_s=seconds)
+    reqs = ss.requests(tr)
+    st, res, stats = h.hicr_serve_run(inst, ss.srv, reqs, 0, int((seconds + 120) * 1e9))
+    h.check(st, "serve_run")
+    out = {"workload": f"Poisson 20,000 req/s for {seconds:g} s ({len(reqs):,} requests): 70% memcpy batches of "
+                       "log-uniform 1-4,096 ops (16 B-4 MiB), 30% MPSC bursts of log-uniform 1-512 msgs "
+                       "(8 B-256 KiB); 64 GiB budget = 16 x 1 GiB rings + 48 GiB arena",
+           "requests": int(stats.completed), "wall_s": stats.wall_ns / 1e9,
+           "GB_per_s_moved": stats.bytes_moved / (stats.wall_ns / 1e9) / 1e9,
+           "req_per_s": stats.completed / (stats.wall_ns / 1e9),
+           "max_inflight": int(stats.max_inflight), "arena_high_water_GB": stats.max_region_bytes / 1e9,
+           "latency_all": latency_summary(res), "latency_memcpy": latency_summary(res, reqs["kind"] == 0),
+           "latency_burst": latency_summary(res, reqs["kind"] == 1)}
+    # the plain form on the first plain_seconds of the same trace
+    hz = int(plain_seconds * 1e9)
+    st, pres, pst = h.hicr_serve_run_plain(inst, ss.srv, reqs, hz, int((plain_seconds + 600) * 1e9))
+    h.check(st, "serve_run_plain")
+    m = reqs["arrival_ns"] <= hz
+    out["plain_form"] = {"horizon_s": plain_seconds, "requests": int(pst.completed),
+                         "wall_s": pst.wall_ns / 1e9, "GB_per_s_moved": pst.bytes_moved / (pst.wall_ns / 1e9) / 1e9,
+                         "latency_all": latency_summary(pres[: int(m.sum())]),
+                         "engine_latency_same_requests": latency_summary(res[: int(m.sum())])}
+    ss.free()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle baseline: the oracle as it stands on a bounded sample.
 # ---------------------------------------------------------------------------
 CPU_SAMPLE = dict(n_slots=32, total_bytes=2 * GiB, slot_lo=1 << 20, slot_hi=256 << 20, n_ops=12_500)

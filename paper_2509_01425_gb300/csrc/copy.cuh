@@ -91,4 +91,26 @@ __device__ __forceinline__ void warp_copy(uint8_t* __restrict__ d, const uint8_t
   if (lane < tail) d[nw * 16 + lane] = s[nw * 16 + lane];
 }
 
+// Largest i < count with cstart[i] <= key (cstart[0] = 0 <= key), found by
+// the whole warp: each round the lanes probe 32 evenly spaced positions.
+__device__ __forceinline__ unsigned long long find_op(const unsigned long long* __restrict__ cstart,
+                                                      unsigned long long count, unsigned long long key,
+                                                      unsigned lane) {
+  unsigned long long L = 0, R = count;
+  while (R - L > 32) {
+    const unsigned long long step = (R - L + 31) / 32;
+    const unsigned long long pos = L + lane * step;
+    const bool le = pos < R && cstart[pos] <= key;
+    const unsigned m = __ballot_sync(0xffffffffu, le);
+    const unsigned k = 31u - __clz(m);
+    const unsigned long long nL = L + k * step;
+    R = min(R, nL + step);
+    L = nL;
+  }
+  const unsigned long long pos = L + lane;
+  const bool le = pos < R && cstart[pos] <= key;
+  const unsigned m = __ballot_sync(0xffffffffu, le);
+  return L + (31u - __clz(m));
+}
+
 }  // namespace hicr

@@ -111,28 +111,6 @@ __global__ void __launch_bounds__(1024) k_scan(BatchArgs a) {
   }
 }
 
-// Largest i < count with cstart[i] <= key (cstart[0] = 0 <= key), found by
-// the whole warp: each round the lanes probe 32 evenly spaced positions.
-__device__ __forceinline__ unsigned long long find_op(const unsigned long long* __restrict__ cstart,
-                                                      unsigned long long count, unsigned long long key,
-                                                      unsigned lane) {
-  unsigned long long L = 0, R = count;
-  while (R - L > 32) {
-    const unsigned long long step = (R - L + 31) / 32;
-    const unsigned long long pos = L + lane * step;
-    const bool le = pos < R && cstart[pos] <= key;
-    const unsigned m = __ballot_sync(FULL, le);
-    const unsigned k = 31u - __clz(m);
-    const unsigned long long nL = L + k * step;
-    R = min(R, nL + step);
-    L = nL;
-  }
-  const unsigned long long pos = L + lane;
-  const bool le = pos < R && cstart[pos] <= key;
-  const unsigned m = __ballot_sync(FULL, le);
-  return L + (31u - __clz(m));
-}
-
 __device__ __forceinline__ void op_complete(const BatchArgs& a, const hicr_op_t& op) {
   __threadfence();
   atomicAdd(&a.dt.sent[op.src], 1ull);

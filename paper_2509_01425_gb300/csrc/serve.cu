@@ -1,0 +1,1122 @@
+// Continuous-batching request engine (see include/hicr_serve.h).
+//
+// Host side (hicr_serve_run, calling thread): arrivals -> FIFO admission under
+// the arena budget (first-fit allocator) -> descriptor + doorbell in mapped
+// host memory -> poll per-request completion words the device writes into
+// mapped host memory -> free the region, record latency.
+//
+// Device side: one cooperative persistent kernel, all CTAs resident:
+//   CTA 0, warp 0   dispatcher: acquires the doorbell, copies each new request
+//                   into the per-request device table, gives it a contiguous range
+//                   of work units (memcpy: one unit per cost chunk of its
+//                   template; burst: one unit) and publishes units_pub;
+//   CTAs 1..C       one MPSC consumer per channel (windowed drain as in the
+//                   channel stream kernel); completes burst requests;
+//   other CTAs      worker warps: claim the next unit, wait until it is
+//                   published, find its request and either copy one cost
+//                   chunk of the template's ops (same warp copy and chunking
+//                   as the batch path) or push the burst's messages in order.
+// Every wait is bounded by the run deadline (%globaltimer).
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "../../include/hicr_serve.h"
+#include "channel_common.cuh"
+#include "copy.cuh"
+#include "hicr_internal.h"
+
+namespace hicr {
+
+static constexpr unsigned SRV_THREADS = 512;
+static constexpr unsigned SRV_MAX_CH = 64;
+static constexpr int SRV_WIN = 64;
+static constexpr int SRV_PIECE = 512;
+
+struct SrvReq {
+  unsigned long long U;       // first unit
+  unsigned long long id;      // request index
+  unsigned long long dst;     // destination region base (memcpy)
+  unsigned long long done;    // completed chunks / consumed messages
+  unsigned long long digest;  // burst digest accumulator
+  unsigned int N, need, kind, tmpl;
+};
+
+struct SrvHostDesc {
+  unsigned int kind, tmpl;
+  unsigned long long dst;
+};
+
+struct SrvCtl {
+  Line claim, units_pub, req_pub, stop, final_units, abort;
+  unsigned long long final_msgs[SRV_MAX_CH];
+};
+
+struct SrvArgs {
+  SrvCtl* ctl;
+  SrvReq* req;                          // per-request state, indexed by request id
+  const SrvHostDesc* hdesc;             // mapped host memory
+  const unsigned long long* hdoor;      // mapped: requests published
+  const unsigned long long* hstop;      // mapped: no more requests
+  unsigned long long* hcompl;           // mapped: completion time per request (0 = pending)
+  unsigned long long* hdigest;          // mapped: burst digest per request
+  const hicr_op_t* tops;
+  const unsigned long long* tcstart;
+  const unsigned long long* t_opbase;
+  const unsigned long long* t_nops;
+  const unsigned long long* t_cbase;
+  const unsigned long long* t_chunks;
+  const unsigned long long* t_total;
+  const unsigned long long* msizes;
+  const unsigned long long* moffs;
+  const unsigned long long* t_mbase;
+  const unsigned long long* t_nmsg;
+  const uint8_t* staging;
+  DevTables dt;
+  const MpscView* chans;
+  unsigned int n_ch;
+  unsigned int chunk;
+  unsigned int op_cost;
+  unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acq_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ bool srv_abort(const SrvArgs& a, unsigned long long deadline) {
+  if (*(volatile unsigned long long*)&a.ctl->abort.v) return true;
+  if (gtime() > deadline) {
+    atomicExch(&a.ctl->abort.v, 1ull);
+    return true;
+  }
+  return false;
+}
+
+// The request that finishes writes its completion into host memory.
+__device__ __forceinline__ void srv_complete(const SrvArgs& a, SrvReq* e) {
+  __threadfence();
+  const unsigned long long id = e->id;
+  a.hdigest[id] = atomicAdd(&e->digest, 0ull);
+  __threadfence_system();
+  st_rel_sys(&a.hcompl[id], gtime() | 1ull);
+}
+
+__device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
+  unsigned long long r = 0, U = 0;
+  unsigned long long msgs[SRV_MAX_CH];
+  for (unsigned c = 0; c < a.n_ch; ++c) msgs[c] = 0;
+  unsigned sleep_ns = 64;
+  for (;;) {
+    const unsigned long long door = ld_acq_sys(a.hdoor);
+    bool progressed = false;
+    while (r < door) {
+      SrvReq* e = a.req + r;
+      const unsigned long long w0 = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r));
+      const unsigned long long dst = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r) + 1);
+      const unsigned kind = (unsigned)w0, t = (unsigned)(w0 >> 32);
+      const unsigned long long N = kind == 0 ? a.t_chunks[t] : 1ull;
+      const unsigned long long need = kind == 0 ? a.t_chunks[t] : a.t_nmsg[t];
+      e->U = U;
+      e->id = r;
+      e->dst = dst;
+      e->done = 0;
+      e->digest = 0;
+      e->N = (unsigned)N;
+      e->need = (unsigned)need;
+      e->kind = kind;
+      e->tmpl = t;
+      if (kind == 1) msgs[r % a.n_ch] += need;
+      if (need == 0) srv_complete(a, e);
+      __threadfence();
+      st_rel(&a.ctl->req_pub.v, r + 1);
+      st_rel(&a.ctl->units_pub.v, U + N);
+      U += N;
+      ++r;
+      progressed = true;
+    }
+    if (progressed) {
+      sleep_ns = 64;
+      continue;
+    }
+    if (ld_acq_sys(a.hstop) && ld_acq_sys(a.hdoor) == r) {
+      for (unsigned c = 0; c < a.n_ch; ++c) a.ctl->final_msgs[c] = msgs[c];
+      a.ctl->final_units.v = U;
+      __threadfence();
+      st_rel(&a.ctl->stop.v, 1ull);
+      return;
+    }
+    if (srv_abort(a, deadline)) return;
+    __nanosleep(sleep_ns);
+    sleep_ns = min(sleep_ns * 2, 1024u);
+  }
+}
+
+// Largest r in [lo, hi) with req[r].U <= u (req[lo].U <= u holds).
+__device__ __forceinline__ unsigned long long srv_find(const SrvArgs& a, unsigned long long lo, unsigned long long hi,
+                                                       unsigned long long u, unsigned lane) {
+  while (hi - lo > 32) {
+    const unsigned long long step = (hi - lo + 31) / 32;
+    const unsigned long long pos = lo + lane * step;
+    const bool le = pos < hi && ld_rlx(&a.req[pos].U) <= u;
+    const unsigned m = __ballot_sync(FULLM, le);
+    const unsigned k = 31u - __clz(m);
+    const unsigned long long nlo = lo + k * step;
+    hi = min(hi, nlo + step);
+    lo = nlo;
+  }
+  const unsigned long long pos = lo + lane;
+  const bool le = pos < hi && ld_rlx(&a.req[pos].U) <= u;
+  const unsigned m = __ballot_sync(FULLM, le);
+  return lo + (31u - __clz(m));
+}
+
+__device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, unsigned long long k, unsigned lane) {
+  const unsigned t = e->tmpl;
+  const hicr_op_t* ops = a.tops + a.t_opbase[t];
+  const unsigned long long nops = a.t_nops[t];
+  const unsigned long long* cstart = a.tcstart + a.t_cbase[t];
+  const unsigned long long chunk = a.chunk, total = a.t_total[t];
+  const unsigned long long lo = k * chunk, hi = min(lo + chunk, total);
+  const unsigned long long dst = e->dst;
+  for (unsigned long long i = find_op(cstart, nops, lo, lane); i < nops; ++i) {
+    const unsigned long long cs = cstart[i];
+    if (cs >= hi) break;
+    const hicr_op_t op = ops[i];
+    const unsigned long long bs = cs + a.op_cost, be = bs + op.n;
+    const unsigned long long b0 = lo > bs ? lo - bs : 0ull;
+    const unsigned long long cap = hi < be ? hi : be;
+    const unsigned long long b1 = cap > bs ? cap - bs : 0ull;
+    if (b1 > b0) {
+      uint8_t* d = reinterpret_cast<uint8_t*>(dst) + op.dst_off + b0;
+      const uint8_t* s = reinterpret_cast<const uint8_t*>(a.dt.slot_base[op.src]) + op.src_off + b0;
+      warp_copy(d, s, b1 - b0, lane);
+    }
+  }
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) {
+    const unsigned long long prev = atomicAdd(&e->done, 1ull);
+    if (prev + 1 == e->need) srv_complete(a, e);
+  }
+}
+
+// Push every message of a burst, in order, as producer = request index.
+__device__ bool srv_push_burst(const SrvArgs& a, SrvReq* e, unsigned lane, unsigned long long deadline) {
+  const unsigned long long id = e->id;
+  const unsigned t = e->tmpl;
+  const MpscView v = a.chans[id % a.n_ch];
+  const unsigned long long mbase = a.t_mbase[t], nmsg = a.t_nmsg[t];
+  const unsigned long long half = v.R / 2;
+  unsigned long long freed = 0, mt = 0;
+  if (lane == 0) {
+    freed = ld_acq(&v.st->freed.v);
+    mt = ld_acq(&v.st->msg_tail.v);
+  }
+  for (unsigned long long s = 0; s < nmsg;) {
+    unsigned long long r[8], st[8];
+    int k = 0;
+    unsigned long long sum = 0;
+    for (; k < 8 && s + k < nmsg; ++k) {
+      const unsigned long long rk = round16(a.msizes[mbase + s + k]);
+      if (k > 0 && sum + rk > half) break;
+      r[k] = rk;
+      sum += rk;
+    }
+    unsigned long long W = 0;
+    int stop = 0;
+    if (lane == 0) {
+      unsigned sleep_ns = 32;
+      for (;;) {
+        W = ld_rlx(&v.st->reserve.v);
+        const unsigned long long end = mpsc_place(W, r, k, v.R, st);
+        const unsigned long long t0 = W >> 40;
+        bool room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        if (!room) {
+          freed = ld_acq(&v.st->freed.v);
+          mt = ld_acq(&v.st->msg_tail.v);
+          room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
+        }
+        if (room && atomicCAS(&v.st->reserve.v, W, (((t0 + k) & MASK24) << 40) | end) == W) break;
+        if (srv_abort(a, deadline)) {
+          stop = 1;
+          break;
+        }
+        if (!room) {
+          __nanosleep(sleep_ns);
+          sleep_ns = min(sleep_ns * 2, 4096u);
+        }
+      }
+    }
+    if (__shfl_sync(FULLM, stop, 0)) return false;
+    W = __shfl_sync(FULLM, W, 0);
+    const unsigned long long t0 = W >> 40;
+    for (int i = 0; i < k; ++i) {
+      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+      warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.moffs[mbase + s + i], a.msizes[mbase + s + i], lane);
+    }
+    __threadfence();
+    __syncwarp();
+    for (int i = 0; i < k; ++i) {
+      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+      if (lane == (unsigned)i) {
+        const unsigned long long tk = t0 + i;
+        MpscMeta* m = v.meta + (tk & (v.M - 1));
+        m->start = si;
+        m->size = (unsigned int)a.msizes[mbase + s + i];
+        m->producer = (unsigned int)id;
+        m->seq = (unsigned int)(s + i);
+        m->flags = 0;
+        st_rel(&m->ready, (tk & MASK24) + 1);
+      }
+    }
+    s += k;
+  }
+  return true;
+}
+
+__device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned long long hint = 0;  // request of the previous unit
+  for (;;) {
+    unsigned long long u = 0;
+    int exit_now = 0;
+    if (lane == 0) {
+      u = atomicAdd(&a.ctl->claim.v, 1ull);
+      unsigned sleep_ns = 32;
+      for (;;) {
+        if (ld_acq(&a.ctl->units_pub.v) > u) break;
+        if (ld_acq(&a.ctl->stop.v) && u >= *(volatile unsigned long long*)&a.ctl->final_units.v) {
+          exit_now = 1;
+          break;
+        }
+        if (srv_abort(a, deadline)) {
+          exit_now = 1;
+          break;
+        }
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 512u);
+      }
+    }
+    if (__shfl_sync(FULLM, exit_now, 0)) return;
+    u = __shfl_sync(FULLM, u, 0);
+    const unsigned long long hi = ld_acq(&a.ctl->req_pub.v);
+    unsigned long long r;
+    // fast path: the same or the next request as the previous unit (every
+    // published entry is final, so reading it needs no further care)
+    if (hint < hi && a.req[hint].U <= u && u < a.req[hint].U + a.req[hint].N) {
+      r = hint;
+    } else if (hint + 1 < hi && a.req[hint + 1].U <= u && u < a.req[hint + 1].U + a.req[hint + 1].N) {
+      r = hint + 1;
+    } else {
+      r = srv_find(a, 0, hi, u, lane);
+    }
+    hint = r;
+    SrvReq* e = a.req + r;
+    if (e->kind == 0) {
+      srv_copy_chunk(a, e, u - e->U, lane);
+    } else if (!srv_push_burst(a, e, lane, deadline)) {
+      return;
+    }
+  }
+}
+
+__device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long deadline) {
+  __shared__ int s_stop;
+  __shared__ unsigned long long s_avail;
+  __shared__ unsigned long long s_start[SRV_WIN], s_ppre[SRV_WIN + 1], s_dig[SRV_WIN];
+  __shared__ unsigned int s_size[SRV_WIN], s_prod[SRV_WIN], s_seq[SRV_WIN];
+  const MpscView v = a.chans[c];
+  const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  const unsigned long long win_max = min((unsigned long long)SRV_WIN, (unsigned long long)(v.M / 2 ? v.M / 2 : 1));
+  __shared__ unsigned long long s_t0;
+  if (tid == 0) s_t0 = ld_acq(&v.st->msg_tail.v);
+  __syncthreads();
+  unsigned long long t = s_t0, consumed = 0;
+  for (;;) {
+    if (tid == 0) {
+      int stop = 0;
+      unsigned long long avail = 0;
+      unsigned sleep_ns = 64;
+      for (;;) {
+        const unsigned long long W = ld_acq(&v.st->reserve.v);
+        avail = ((W >> 40) - t) & MASK24;
+        if (avail) break;
+        if (ld_acq(&a.ctl->stop.v) && consumed >= *(volatile unsigned long long*)&a.ctl->final_msgs[c]) {
+          stop = 2;  // done
+          break;
+        }
+        if (srv_abort(a, deadline)) {
+          stop = 1;
+          break;
+        }
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 1024u);
+      }
+      s_avail = min(avail, win_max);
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const unsigned navail = (unsigned)s_avail;
+    for (unsigned j = warp; j < navail; j += nwarp) {
+      const unsigned long long tk = t + j;
+      MpscMeta* m = v.meta + (tk & (v.M - 1));
+      if (lane == 0) {
+        int stop = 0;
+        while (ld_acq(&m->ready) != (tk & MASK24) + 1) {
+          if (srv_abort(a, deadline)) {
+            stop = 1;
+            break;
+          }
+          __nanosleep(32);
+        }
+        if (stop) {
+          s_stop = 1;
+        } else {
+          s_start[j] = __ldcg(&m->start);
+          s_size[j] = __ldcg(&m->size);
+          s_prod[j] = __ldcg(&m->producer);
+          s_seq[j] = __ldcg(&m->seq);
+          s_dig[j] = 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) return;
+    if (warp == 0) {
+      const unsigned long long p0 =
+          lane < navail ? (((unsigned long long)s_size[lane] + 15) / 16 + SRV_PIECE - 1) / SRV_PIECE : 0;
+      const unsigned long long p1 =
+          lane + 32 < navail ? (((unsigned long long)s_size[lane + 32] + 15) / 16 + SRV_PIECE - 1) / SRV_PIECE : 0;
+      unsigned long long x0 = p0, x1 = p1;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y0 = __shfl_up_sync(FULLM, x0, o), y1 = __shfl_up_sync(FULLM, x1, o);
+        if (lane >= (unsigned)o) {
+          x0 += y0;
+          x1 += y1;
+        }
+      }
+      const unsigned long long tot0 = __shfl_sync(FULLM, x0, 31);
+      s_ppre[lane] = x0 - p0;
+      s_ppre[lane + 32] = tot0 + x1 - p1;
+      if (lane == 31) s_ppre[64] = tot0 + x1;
+    }
+    __syncthreads();
+    const unsigned long long npieces = s_ppre[navail];
+    for (unsigned long long pc = warp; pc < npieces; pc += nwarp) {
+      unsigned lo = 0, hi = navail;
+      while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (s_ppre[mid] <= pc) lo = mid;
+        else hi = mid;
+      }
+      const unsigned j = lo;
+      const unsigned long long n = s_size[j], nv = (n + 15) / 16;
+      const unsigned long long q0 = (pc - s_ppre[j]) * SRV_PIECE;
+      const uint4* base = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
+      uint4 x[SRV_PIECE / 32];
+#pragma unroll
+      for (int uu = 0; uu < SRV_PIECE / 32; ++uu) {
+        const unsigned long long q = q0 + lane + 32 * uu;
+        if (q < nv) x[uu] = __ldcg(base + q);
+      }
+      unsigned long long d = 0;
+#pragma unroll
+      for (int uu = 0; uu < SRV_PIECE / 32; ++uu) {
+        const unsigned long long q = q0 + lane + 32 * uu;
+        if (q < nv) {
+          unsigned long long w0 = (unsigned long long)x[uu].x | ((unsigned long long)x[uu].y << 32);
+          unsigned long long w1 = (unsigned long long)x[uu].z | ((unsigned long long)x[uu].w << 32);
+          const unsigned long long b0 = 16 * q;
+          if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
+          if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
+          d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
+      if (lane == 0) atomicAdd(&s_dig[j], d);
+    }
+    __syncthreads();
+    // per-request accounting: message digest weighted by its index in the burst
+    for (unsigned j = tid; j < navail; j += blockDim.x) {
+      SrvReq* e = a.req + s_prod[j];
+      atomicAdd(&e->digest, s_dig[j] * (2ull * s_seq[j] + 1ull));
+      __threadfence();
+      const unsigned long long prev = atomicAdd(&e->done, 1ull);
+      if (prev + 1 == e->need) srv_complete(a, e);
+    }
+    if (tid == 0) {
+      st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
+      st_rel(&v.st->msg_tail.v, t + navail);
+    }
+    t += navail;
+    consumed += navail;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(SRV_THREADS) k_serve(SrvArgs a) {
+  __shared__ unsigned long long s_deadline;
+  if (threadIdx.x == 0) s_deadline = gtime() + a.timeout_ns;
+  __syncthreads();
+  const unsigned long long deadline = s_deadline;
+  if (blockIdx.x == 0) {
+    if (threadIdx.x == 0) srv_dispatcher(a, deadline);
+    return;
+  }
+  if (blockIdx.x <= a.n_ch) {
+    srv_consumer(a, blockIdx.x - 1, deadline);
+    return;
+  }
+  srv_worker(a, deadline);
+}
+
+// Verify mode: digest of every op's destination bytes, weighted by the op's
+// index in its template, summed per request. One warp per (request, op).
+struct VerifyItem {
+  unsigned long long addr, n, req, k;
+};
+__global__ void k_serve_verify(const VerifyItem* items, unsigned long long count, unsigned long long* out) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long i = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < count; i += warps) {
+    const VerifyItem it = items[i];
+    const uint8_t* p = reinterpret_cast<const uint8_t*>(it.addr);
+    const unsigned long long nw = (it.n + 7) / 8;
+    unsigned long long d = 0;
+    for (unsigned long long j = lane; j < nw; j += 32) {
+      unsigned long long w = 0;
+      for (int b = 0; b < 8; ++b)
+        if (8 * j + b < it.n) w |= (unsigned long long)p[8 * j + b] << (8 * b);
+      d += w * (2ull * j + 1ull);
+    }
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
+    if (lane == 0) atomicAdd(out + it.req, d * (2ull * it.k + 1ull));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct Arena {
+  // first-fit over free ranges (offset -> size), 256-byte granules
+  std::map<uint64_t, uint64_t> free_;
+  uint64_t size = 0, used = 0, high = 0;
+  void reset(uint64_t n) {
+    free_.clear();
+    free_[0] = n;
+    size = n;
+    used = high = 0;
+  }
+  bool alloc(uint64_t n, uint64_t* off) {
+    n = std::max<uint64_t>(256, (n + 255) & ~255ull);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const uint64_t rest = it->second - n, start = it->first + n;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used += n;
+        high = std::max(high, used);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t n) {
+    n = std::max<uint64_t>(256, (n + 255) & ~255ull);
+    used -= n;
+    auto next = free_.lower_bound(off);
+    uint64_t a = off, b = off + n;
+    if (next != free_.begin()) {
+      auto prev = std::prev(next);
+      if (prev->first + prev->second == a) {
+        a = prev->first;
+        free_.erase(prev);
+      }
+    }
+    next = free_.lower_bound(b);
+    if (next != free_.end() && next->first == b) {
+      b += next->second;
+      free_.erase(next);
+    }
+    free_[a] = b - a;
+  }
+};
+
+struct Server {
+  hicr_serve_config_t cfg{};
+  bool live = false;
+  hicr_slot_t arena_slot = 0;
+  uint8_t* arena = nullptr;
+  uint8_t* rings = nullptr;           // n_ch rings, states and metadata (one allocation)
+  std::vector<MpscView> views;
+  // templates (host copies; uploaded lazily)
+  std::vector<hicr_op_t> tops;
+  std::vector<unsigned long long> tcstart, t_opbase, t_nops, t_cbase, t_chunks, t_total, t_region;
+  std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg;
+  hicr_slot_t staging = 0;
+  bool have_staging = false;
+  bool uploaded = false;
+  void* dev_tmpl = nullptr;  // one allocation for all template arrays
+  SrvArgs base{};
+  SrvCtl* ctl = nullptr;
+  MpscView* d_views = nullptr;
+  std::vector<unsigned long long> t_bytes, m_bytes;  // payload bytes per template
+};
+
+static Server* srv_get(Instance* in, hicr_serve_t s);
+
+}  // namespace hicr
+
+// the instance keeps its servers in a side table keyed by instance pointer
+#include <unordered_map>
+namespace hicr {
+static std::unordered_map<Instance*, std::vector<Server*>> g_servers;
+static Server* srv_get(Instance* in, hicr_serve_t s) {
+  auto it = g_servers.find(in);
+  if (it == g_servers.end() || s == 0 || s > it->second.size()) return nullptr;
+  Server* v = it->second[s - 1];
+  return (v && v->live) ? v : nullptr;
+}
+
+template <class T>
+static char* put(char* p, const std::vector<T>& v, const T** dst) {
+  const size_t n = v.size() * sizeof(T);
+  *dst = (const T*)p;
+  return p + ((n + 255) & ~(size_t)255);
+}
+
+static hicr_status srv_upload(Instance* in, Server* sv) {
+  if (sv->uploaded) return HICR_OK;
+  if (sv->t_nops.empty()) sv->t_nops.push_back(0), sv->t_opbase.push_back(0), sv->t_cbase.push_back(0),
+      sv->t_chunks.push_back(0), sv->t_total.push_back(0), sv->t_region.push_back(0), sv->tcstart.push_back(0);
+  if (sv->t_nmsg.empty()) sv->t_nmsg.push_back(0), sv->t_mbase.push_back(0);
+  if (sv->tops.empty()) sv->tops.push_back(hicr_op_t{0, 0, 0, 0, 0});
+  if (sv->msizes.empty()) sv->msizes.push_back(0), sv->moffs.push_back(0);
+  std::vector<const void*> dummy;
+  auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
+  const size_t bytes = al(sv->tops.size() * sizeof(hicr_op_t)) +
+                       8 * (al(sv->tcstart.size() * 8) + al(sv->t_opbase.size() * 8) + al(sv->t_nops.size() * 8) +
+                            al(sv->t_cbase.size() * 8) + al(sv->t_chunks.size() * 8) + al(sv->t_total.size() * 8) +
+                            al(sv->msizes.size() * 8) + al(sv->moffs.size() * 8) + al(sv->t_mbase.size() * 8) +
+                            al(sv->t_nmsg.size() * 8)) / 8;
+  char* d = nullptr;
+  HICR_CUDA(in, cudaMalloc(&d, bytes + 4096));
+  sv->dev_tmpl = d;
+  char* p = d;
+  SrvArgs& a = sv->base;
+  auto up = [&](const void* src, size_t n) -> hicr_status {
+    HICR_CUDA(in, cudaMemcpy(p, src, n, cudaMemcpyHostToDevice));
+    p += al(n);
+    return HICR_OK;
+  };
+  a.tops = (const hicr_op_t*)p;
+  if (up(sv->tops.data(), sv->tops.size() * sizeof(hicr_op_t))) return HICR_ERR_DEVICE;
+#define UP(field, vec)                                   \
+  a.field = (const unsigned long long*)p;                \
+  if (up(vec.data(), vec.size() * 8)) return HICR_ERR_DEVICE;
+  UP(tcstart, sv->tcstart);
+  UP(t_opbase, sv->t_opbase);
+  UP(t_nops, sv->t_nops);
+  UP(t_cbase, sv->t_cbase);
+  UP(t_chunks, sv->t_chunks);
+  UP(t_total, sv->t_total);
+  UP(msizes, sv->msizes);
+  UP(moffs, sv->moffs);
+  UP(t_mbase, sv->t_mbase);
+  UP(t_nmsg, sv->t_nmsg);
+#undef UP
+  sv->uploaded = true;
+  return HICR_OK;
+}
+
+}  // namespace hicr
+
+using namespace hicr;
+
+static Instance* I(hicr_instance_t h) { return h ? &h->impl : nullptr; }
+
+static bool pow2u(unsigned long long x) { return x && !(x & (x - 1)); }
+
+extern "C" {
+
+hicr_status hicr_serve_create(hicr_instance_t h, const hicr_serve_config_t* cfg, hicr_serve_t* out) {
+  Instance* in = I(h);
+  if (!in || !cfg || !out || in->capturing) return HICR_ERR_INVALID;
+  if (cfg->n_channels == 0 || cfg->n_channels > SRV_MAX_CH || !pow2u(cfg->ring_bytes) || cfg->ring_bytes < 64 ||
+      cfg->ring_bytes > (1ull << 39) || !pow2u(cfg->max_msgs) || cfg->max_msgs > (1u << 23) ||
+      cfg->chunk_bytes < 1024 || cfg->chunk_bytes % 1024 || cfg->op_cost_bytes == 0)
+    return HICR_ERR_INVALID;
+  const uint64_t ring_total = (uint64_t)cfg->n_channels * cfg->ring_bytes;
+  if (cfg->budget_bytes <= ring_total) return HICR_ERR_INVALID;
+  Server* sv = new Server();
+  sv->cfg = *cfg;
+  const uint64_t arena_bytes = cfg->budget_bytes - ring_total;
+  hicr_status st = hicr_mem_alloc(h, HICR_SPACE_HBM, arena_bytes, 0, &sv->arena_slot);
+  if (st != HICR_OK) {
+    delete sv;
+    return st;
+  }
+  void* ap = nullptr;
+  hicr_slot_info(h, sv->arena_slot, &ap, nullptr, nullptr, nullptr);
+  sv->arena = (uint8_t*)ap;
+  // rings + channel states + metadata + control block + request ring
+  const size_t n = cfg->n_channels;
+  const size_t st_b = (sizeof(MpscState) + 255) & ~(size_t)255;
+  const size_t meta_b = ((sizeof(MpscMeta) * (size_t)cfg->max_msgs) + 255) & ~(size_t)255;
+  const size_t ctl_b = (sizeof(SrvCtl) + 255) & ~(size_t)255;
+  const size_t views_b = (sizeof(MpscView) * n + 255) & ~(size_t)255;
+  const size_t total = ring_total + n * (st_b + meta_b) + ctl_b + views_b;
+  char* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, total);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    hicr_mem_free(h, sv->arena_slot);
+    delete sv;
+    return e == cudaErrorMemoryAllocation ? HICR_ERR_NOMEM : HICR_ERR_DEVICE;
+  }
+  sv->rings = (uint8_t*)p;
+  char* q = p + ring_total;
+  for (size_t c = 0; c < n; ++c) {
+    MpscView v;
+    v.ring = (uint8_t*)p + c * cfg->ring_bytes;
+    v.st = (MpscState*)q;
+    q += st_b;
+    v.meta = (MpscMeta*)q;
+    q += meta_b;
+    v.R = cfg->ring_bytes;
+    v.M = cfg->max_msgs;
+    sv->views.push_back(v);
+  }
+  const size_t zero_from = ring_total;
+  sv->ctl = (SrvCtl*)q;
+  q += ctl_b;
+  sv->d_views = (MpscView*)q;
+  HICR_CUDA(in, cudaMemset(p + zero_from, 0, total - zero_from));
+  HICR_CUDA(in, cudaMemcpy(sv->d_views, sv->views.data(), sizeof(MpscView) * n, cudaMemcpyHostToDevice));
+  sv->live = true;
+  auto& vec = g_servers[in];
+  vec.push_back(sv);
+  *out = (hicr_serve_t)vec.size();
+  return HICR_OK;
+}
+
+hicr_status hicr_serve_destroy(hicr_instance_t h, hicr_serve_t s) {
+  Instance* in = I(h);
+  if (!in) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaDeviceSynchronize());
+  hicr_mem_free(h, sv->arena_slot);
+  cudaFree(sv->rings);
+  if (sv->dev_tmpl) cudaFree(sv->dev_tmpl);
+  sv->live = false;
+  g_servers[in][s - 1] = nullptr;
+  delete sv;
+  return HICR_OK;
+}
+
+hicr_status hicr_serve_add_memcpy_template(hicr_instance_t h, hicr_serve_t s, const hicr_op_t* ops, uint64_t count,
+                                           uint64_t region_bytes, uint32_t* tmpl) {
+  Instance* in = I(h);
+  if (!in || !tmpl || (count && !ops)) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv || sv->uploaded) return HICR_ERR_INVALID;
+  const uint64_t region = (region_bytes + 255) & ~255ull;
+  if (region > sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes) return HICR_ERR_NOMEM;
+  for (uint64_t i = 0; i < count; ++i) {
+    const hicr_op_t& o = ops[i];
+    void* sp = nullptr;
+    uint64_t ssize = 0;
+    uint32_t sspace = 0;
+    if (hicr_slot_info(h, o.src, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+    if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+    if (o.src_off > ssize || o.n > ssize - o.src_off) return HICR_ERR_BOUNDS;
+    if (o.dst_off > region_bytes || o.n > region_bytes - o.dst_off) return HICR_ERR_BOUNDS;
+  }
+  const uint32_t t = (uint32_t)sv->t_nops.size();
+  sv->t_opbase.push_back(sv->tops.size());
+  sv->t_nops.push_back(count);
+  sv->t_cbase.push_back(sv->tcstart.size());
+  unsigned long long c = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    sv->tops.push_back(ops[i]);
+    sv->tcstart.push_back(c);
+    c += ops[i].n + sv->cfg.op_cost_bytes;
+  }
+  sv->tcstart.push_back(c);
+  sv->t_total.push_back(c);
+  sv->t_chunks.push_back((c + sv->cfg.chunk_bytes - 1) / sv->cfg.chunk_bytes);
+  sv->t_region.push_back(region_bytes);
+  unsigned long long tb = 0;
+  for (uint64_t i = 0; i < count; ++i) tb += ops[i].n;
+  sv->t_bytes.push_back(tb);
+  *tmpl = t;
+  return HICR_OK;
+}
+
+hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, const uint64_t* sizes,
+                                          const uint64_t* staging_off, uint64_t count, hicr_slot_t staging,
+                                          uint32_t* tmpl) {
+  Instance* in = I(h);
+  if (!in || !tmpl || (count && (!sizes || !staging_off))) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv || sv->uploaded) return HICR_ERR_INVALID;
+  void* sp = nullptr;
+  uint64_t ssize = 0;
+  uint32_t sspace = 0;
+  if (hicr_slot_info(h, staging, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+  if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  if (sv->have_staging && staging != sv->staging) return HICR_ERR_INVALID;  // one staging slot per engine
+  for (uint64_t i = 0; i < count; ++i) {
+    if (staging_off[i] > ssize || sizes[i] > ssize - staging_off[i]) return HICR_ERR_BOUNDS;
+    if (round16(sizes[i]) > sv->cfg.ring_bytes / 2) return HICR_ERR_TOO_LARGE;
+  }
+  sv->staging = staging;
+  sv->have_staging = true;
+  sv->base.staging = (const uint8_t*)sp;
+  const uint32_t t = (uint32_t)sv->t_nmsg.size();
+  sv->t_mbase.push_back(sv->msizes.size());
+  sv->t_nmsg.push_back(count);
+  unsigned long long mb = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    sv->msizes.push_back(sizes[i]);
+    sv->moffs.push_back(staging_off[i]);
+    mb += sizes[i];
+  }
+  sv->m_bytes.push_back(mb);
+  *tmpl = t;
+  return HICR_OK;
+}
+
+hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                           uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
+                           hicr_serve_stats_t* stats) {
+  Instance* in = I(h);
+  if (!in || (n && !reqs) || mode > 1 || in->capturing) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv) return HICR_ERR_INVALID;
+  for (uint64_t i = 0; i < n; ++i) {
+    const hicr_serve_request_t& r = reqs[i];
+    if (r.kind > 1) return HICR_ERR_INVALID;
+    if (r.kind == 0 && r.tmpl >= sv->t_nops.size()) return HICR_ERR_INVALID;
+    if (r.kind == 1 && r.tmpl >= sv->t_nmsg.size()) return HICR_ERR_INVALID;
+    if (i && r.arrival_ns < reqs[i - 1].arrival_ns) return HICR_ERR_INVALID;
+    if (r.kind == 1 && !sv->have_staging) return HICR_ERR_INVALID;
+  }
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  if ((st = srv_upload(in, sv)) != HICR_OK) return st;
+
+  // mapped host memory: descriptors, doorbell, stop, completion, digests
+  const size_t hbytes = sizeof(SrvHostDesc) * (n + 1) + 256 + 16 * (n + 1);
+  char* hp = nullptr;
+  HICR_CUDA(in, cudaHostAlloc((void**)&hp, hbytes, cudaHostAllocMapped));
+  memset(hp, 0, hbytes);
+  char* dp = nullptr;
+  cudaError_t ce = cudaHostGetDevicePointer((void**)&dp, hp, 0);
+  if (ce != cudaSuccess) {
+    cudaFreeHost(hp);
+    return cuda_fail(in, ce, "cudaHostGetDevicePointer");
+  }
+  SrvHostDesc* hdesc = (SrvHostDesc*)hp;
+  const size_t o_door = sizeof(SrvHostDesc) * (n + 1);
+  std::atomic<unsigned long long>* door = (std::atomic<unsigned long long>*)(hp + o_door);
+  std::atomic<unsigned long long>* hstop = (std::atomic<unsigned long long>*)(hp + o_door + 128);
+  std::atomic<unsigned long long>* compl_ = (std::atomic<unsigned long long>*)(hp + o_door + 256);
+  unsigned long long* digest = (unsigned long long*)(hp + o_door + 256 + 8 * (n + 1));
+
+  // fresh control block and per-request state for this run; channels keep
+  // their counters
+  SrvReq* dreq = nullptr;
+  ce = cudaMalloc(&dreq, sizeof(SrvReq) * (n + 1));
+  if (ce != cudaSuccess) {
+    cudaFreeHost(hp);
+    return cuda_fail(in, ce, "cudaMalloc(requests)");
+  }
+  HICR_CUDA(in, cudaMemset(dreq, 0, sizeof(SrvReq) * (n + 1)));
+  HICR_CUDA(in, cudaMemset(sv->ctl, 0, sizeof(SrvCtl)));
+  SrvArgs a = sv->base;
+  a.ctl = sv->ctl;
+  a.req = dreq;
+  a.hdesc = (const SrvHostDesc*)dp;
+  a.hdoor = (const unsigned long long*)(dp + o_door);
+  a.hstop = (const unsigned long long*)(dp + o_door + 128);
+  a.hcompl = (unsigned long long*)(dp + o_door + 256);
+  a.hdigest = (unsigned long long*)(dp + o_door + 256 + 8 * (n + 1));
+  a.dt = in->dt;
+  a.chans = sv->d_views;
+  a.n_ch = sv->cfg.n_channels;
+  a.chunk = sv->cfg.chunk_bytes;
+  a.op_cost = sv->cfg.op_cost_bytes;
+  a.timeout_ns = timeout_ns;
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_serve, SRV_THREADS, 0));
+  const unsigned grid = (unsigned)(in->sm_count * std::max(1, per_sm));
+  if (grid < a.n_ch + 2) {
+    cudaFreeHost(hp);
+    cudaFree(dreq);
+    return HICR_ERR_INVALID;
+  }
+  void* args[] = {&a};
+  cudaStream_t cs = in->comm();
+  ce = cudaLaunchCooperativeKernel((const void*)k_serve, dim3(grid), dim3(SRV_THREADS), args, 0, cs);
+  if (ce != cudaSuccess) {
+    cudaFreeHost(hp);
+    cudaFree(dreq);
+    return cuda_fail(in, ce, "cudaLaunchCooperativeKernel(k_serve)");
+  }
+
+  Arena arena;
+  arena.reset(sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
+  std::vector<uint64_t> region_off(n, 0), region_len(n, 0), admit_t(n, 0);
+  std::vector<uint64_t> inflight;
+  uint64_t next_arrival = 0, next_admit = 0, completed = 0, max_inflight = 0, bytes = 0;
+  std::vector<uint64_t> waiting;  // arrived, not admitted (FIFO)
+  size_t wait_head = 0;
+  const uint64_t t0 = now_ns();
+  uint64_t last_done = t0;
+  hicr_status result = HICR_OK;
+  for (;;) {
+    const uint64_t now = now_ns() - t0;
+    if (now > timeout_ns) {
+      result = HICR_ERR_TIMEOUT;
+      break;
+    }
+    // arrivals
+    if (mode == 0) {
+      while (next_arrival < n && reqs[next_arrival].arrival_ns <= now) waiting.push_back(next_arrival++);
+    } else if (inflight.empty() && next_arrival < n && wait_head == waiting.size()) {
+      waiting.push_back(next_arrival++);  // alone: the next request once the previous completed
+    }
+    // FIFO admission under the arena budget
+    bool published = false;
+    while (wait_head < waiting.size()) {
+      const uint64_t r = waiting[wait_head];
+      const hicr_serve_request_t& q = reqs[r];
+      uint64_t off = 0;
+      if (q.kind == 0) {
+        const uint64_t need = sv->t_region[q.tmpl];
+        if (!arena.alloc(need, &off)) break;
+        region_len[r] = need;
+        region_off[r] = off;
+      }
+      hdesc[r].kind = q.kind;
+      hdesc[r].tmpl = q.tmpl;
+      hdesc[r].dst = (unsigned long long)(sv->arena + off);
+      admit_t[r] = now_ns() - t0;
+      inflight.push_back(r);
+      max_inflight = std::max<uint64_t>(max_inflight, inflight.size());
+      ++wait_head;
+      ++next_admit;
+      published = true;
+    }
+    if (published) door->store(next_admit, std::memory_order_release);
+    // completions
+    for (size_t i = 0; i < inflight.size();) {
+      const uint64_t r = inflight[i];
+      if (compl_[r].load(std::memory_order_acquire) != 0) {
+        const uint64_t tnow = now_ns();
+        if (results) {
+          results[r].latency_ns = (tnow - t0) - std::min<uint64_t>(tnow - t0, mode == 0 ? reqs[r].arrival_ns : admit_t[r]);
+          results[r].admit_ns = mode == 0 ? admit_t[r] - std::min(admit_t[r], reqs[r].arrival_ns) : 0;
+          results[r].digest = digest[r];
+          results[r].dst_offset = region_off[r];
+        }
+        if (reqs[r].kind == 0) {
+          bytes += sv->t_bytes[reqs[r].tmpl];
+          if (!sv->cfg.verify) arena.release(region_off[r], region_len[r]);
+        } else {
+          bytes += sv->m_bytes[reqs[r].tmpl];
+        }
+        ++completed;
+        last_done = tnow;
+        inflight[i] = inflight.back();
+        inflight.pop_back();
+      } else {
+        ++i;
+      }
+    }
+    if (completed == n) break;
+    if (next_admit < n && wait_head == waiting.size() && mode == 0 && next_arrival < n) {
+      const uint64_t gap = reqs[next_arrival].arrival_ns > now ? reqs[next_arrival].arrival_ns - now : 0;
+      if (gap > 50000 && inflight.empty()) std::this_thread::sleep_for(std::chrono::nanoseconds(gap - 20000));
+    }
+  }
+  hstop->store(1, std::memory_order_release);
+  ce = cudaStreamSynchronize(cs);
+  cudaFree(dreq);
+  if (ce != cudaSuccess) {
+    cudaFreeHost(hp);
+    return cuda_fail(in, ce, "k_serve");
+  }
+  if (stats) {
+    stats->completed = completed;
+    stats->bytes_moved = bytes;
+    stats->wall_ns = last_done - t0 - (n && mode == 0 ? std::min<uint64_t>(last_done - t0, reqs[0].arrival_ns) : 0);
+    stats->max_inflight = max_inflight;
+    stats->max_region_bytes = arena.high;
+    stats->status = result;
+  }
+  cudaFreeHost(hp);
+  HICR_CUDA(in, cudaGetLastError());
+  return result;
+}
+
+hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                                 uint64_t horizon_ns, uint64_t timeout_ns, hicr_serve_result_t* results,
+                                 hicr_serve_stats_t* stats) {
+  Instance* in = I(h);
+  if (!in || (n && !reqs) || in->capturing) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv) return HICR_ERR_INVALID;
+  uint64_t m = 0;
+  while (m < n && reqs[m].arrival_ns <= horizon_ns) ++m;
+  for (uint64_t i = 0; i < m; ++i) {
+    if (reqs[i].kind == 0 && reqs[i].tmpl >= sv->t_nops.size()) return HICR_ERR_INVALID;
+    if (reqs[i].kind == 1 && (reqs[i].tmpl >= sv->t_nmsg.size() || !sv->have_staging)) return HICR_ERR_INVALID;
+  }
+  cudaStream_t cs = in->comm();
+  HICR_CUDA(in, cudaStreamSynchronize(cs));
+  const size_t EV = 8192;
+  std::vector<cudaEvent_t> ev(EV);
+  for (auto& e : ev) HICR_CUDA(in, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  Arena arena;
+  arena.reset(sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
+  std::vector<uint64_t> region_off(m, 0), region_len(m, 0);
+  std::vector<uint64_t> ring_pos(sv->cfg.n_channels, 0);
+  uint64_t next = 0, head = 0, completed = 0, bytes = 0, max_inflight = 0;  // in-flight = [head, next)
+  const uint64_t t0 = now_ns();
+  uint64_t last_done = t0;
+  hicr_status result = HICR_OK;
+  const uint8_t* staging = sv->base.staging;
+  while (completed < m) {
+    const uint64_t now = now_ns() - t0;
+    if (now > timeout_ns) {
+      result = HICR_ERR_TIMEOUT;
+      break;
+    }
+    while (next < m && reqs[next].arrival_ns <= now && next - head < EV) {
+      const hicr_serve_request_t& q = reqs[next];
+      const unsigned t = q.tmpl;
+      if (q.kind == 0) {
+        uint64_t off = 0;
+        if (!arena.alloc(sv->t_region[t], &off)) break;
+        region_off[next] = off;
+        region_len[next] = sv->t_region[t];
+        for (uint64_t k = 0; k < sv->t_nops[t]; ++k) {
+          const hicr_op_t& o = sv->tops[sv->t_opbase[t] + k];
+          if (o.n == 0) continue;
+          HICR_CUDA(in, cudaMemcpyAsync(sv->arena + off + o.dst_off, (const void*)(in->slots[o.src].base + o.src_off),
+                                        o.n, cudaMemcpyDeviceToDevice, cs));
+        }
+      } else {
+        const unsigned c = (unsigned)(next % sv->cfg.n_channels);
+        for (uint64_t k = 0; k < sv->t_nmsg[t]; ++k) {
+          const uint64_t sz = sv->msizes[sv->t_mbase[t] + k], r16 = round16(sz);
+          if (ring_pos[c] + r16 > sv->cfg.ring_bytes) ring_pos[c] = 0;
+          HICR_CUDA(in, cudaMemcpyAsync(sv->views[c].ring + ring_pos[c], staging + sv->moffs[sv->t_mbase[t] + k], sz,
+                                        cudaMemcpyDeviceToDevice, cs));
+          ring_pos[c] += r16;
+        }
+      }
+      HICR_CUDA(in, cudaEventRecord(ev[next % EV], cs));
+      ++next;
+      max_inflight = std::max(max_inflight, next - head);
+    }
+    while (head < next) {
+      cudaError_t e = cudaEventQuery(ev[head % EV]);
+      if (e == cudaErrorNotReady) break;
+      HICR_CUDA(in, e);
+      const uint64_t tnow = now_ns();
+      const hicr_serve_request_t& q = reqs[head];
+      if (results) {
+        results[head].latency_ns = (tnow - t0) - std::min<uint64_t>(tnow - t0, q.arrival_ns);
+        results[head].admit_ns = 0;
+        results[head].digest = 0;
+        results[head].dst_offset = region_off[head];
+      }
+      if (q.kind == 0) {
+        bytes += sv->t_bytes[q.tmpl];
+        arena.release(region_off[head], region_len[head]);
+      } else {
+        bytes += sv->m_bytes[q.tmpl];
+      }
+      ++completed;
+      ++head;
+      last_done = tnow;
+    }
+  }
+  cudaStreamSynchronize(cs);
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (stats) {
+    stats->completed = completed;
+    stats->bytes_moved = bytes;
+    stats->wall_ns = last_done - t0 - (m ? std::min<uint64_t>(last_done - t0, reqs[0].arrival_ns) : 0);
+    stats->max_inflight = max_inflight;
+    stats->max_region_bytes = arena.high;
+    stats->status = result;
+  }
+  return result;
+}
+
+hicr_status hicr_serve_digests(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                               hicr_serve_result_t* results) {
+  Instance* in = I(h);
+  if (!in || (n && (!reqs || !results))) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv || !sv->cfg.verify) return HICR_ERR_INVALID;
+  std::vector<VerifyItem> items;
+  for (uint64_t r = 0; r < n; ++r) {
+    if (reqs[r].kind != 0) continue;
+    const unsigned t = reqs[r].tmpl;
+    if (t >= sv->t_nops.size()) return HICR_ERR_INVALID;
+    for (uint64_t k = 0; k < sv->t_nops[t]; ++k) {
+      const hicr_op_t& o = sv->tops[sv->t_opbase[t] + k];
+      items.push_back({(unsigned long long)(sv->arena + results[r].dst_offset + o.dst_off), o.n, r, k});
+    }
+  }
+  VerifyItem* d_items = nullptr;
+  unsigned long long* d_out = nullptr;
+  HICR_CUDA(in, cudaMalloc(&d_items, sizeof(VerifyItem) * std::max<size_t>(1, items.size())));
+  cudaError_t e = cudaMalloc(&d_out, 8 * std::max<uint64_t>(1, n));
+  if (e != cudaSuccess) {
+    cudaFree(d_items);
+    return cuda_fail(in, e, "cudaMalloc");
+  }
+  cudaStream_t cs = in->comm();
+  std::vector<unsigned long long> out(n, 0);
+  e = cudaMemcpyAsync(d_items, items.data(), sizeof(VerifyItem) * items.size(), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, 8 * std::max<uint64_t>(1, n), cs);
+  if (e == cudaSuccess && !items.empty()) {
+    k_serve_verify<<<in->sm_count * 8, 256, 0, cs>>>(d_items, items.size(), d_out);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out.data(), d_out, 8 * n, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaFree(d_items);
+  cudaFree(d_out);
+  if (e != cudaSuccess) return cuda_fail(in, e, "serve digests");
+  for (uint64_t r = 0; r < n; ++r)
+    if (reqs[r].kind == 0) results[r].digest = out[r];
+  return HICR_OK;
+}
+
+}  // extern "C"

@@ -519,3 +519,81 @@ def hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src
     st = _mpsc_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
                       _ptr(d_src_off), staging, group, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
     return st, list(res)
+
+
+# ---------------------------------------------------------------------------
+# Serving (include/hicr_serve.h)
+# ---------------------------------------------------------------------------
+class hicr_serve_config_t(C.Structure):
+    _fields_ = [("budget_bytes", u64), ("n_channels", u32), ("max_msgs", u32), ("ring_bytes", u64),
+                ("chunk_bytes", u32), ("op_cost_bytes", u32), ("verify", u32), ("reserved", u32)]
+
+
+class hicr_serve_stats_t(C.Structure):
+    _fields_ = [("completed", u64), ("bytes_moved", u64), ("wall_ns", u64), ("max_inflight", u64),
+                ("max_region_bytes", u64), ("status", i32), ("reserved", u32)]
+
+
+SERVE_REQ_DTYPE = np.dtype([("arrival_ns", "<u8"), ("kind", "<u4"), ("tmpl", "<u4")])
+SERVE_RES_DTYPE = np.dtype([("latency_ns", "<u8"), ("admit_ns", "<u8"), ("digest", "<u8"), ("dst_offset", "<u8")])
+
+_serve_create = _decl("hicr_serve_create", [H, C.POINTER(hicr_serve_config_t), C.POINTER(u64)])
+_serve_destroy = _decl("hicr_serve_destroy", [H, u64])
+_serve_add_memcpy = _decl("hicr_serve_add_memcpy_template", [H, u64, vp, u64, u64, C.POINTER(u32)])
+_serve_add_burst = _decl("hicr_serve_add_burst_template", [H, u64, vp, vp, u64, u32, C.POINTER(u32)])
+_serve_run = _decl("hicr_serve_run", [H, u64, vp, u64, u32, u64, vp, C.POINTER(hicr_serve_stats_t)])
+_serve_run_plain = _decl("hicr_serve_run_plain", [H, u64, vp, u64, u64, u64, vp, C.POINTER(hicr_serve_stats_t)])
+_serve_digests = _decl("hicr_serve_digests", [H, u64, vp, u64, vp])
+
+
+def hicr_serve_create(inst, cfg):
+    if isinstance(cfg, dict):
+        c = hicr_serve_config_t()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        cfg = c
+    s = u64()
+    st = _serve_create(inst, C.byref(cfg), C.byref(s))
+    return st, s.value
+
+
+def hicr_serve_destroy(inst, srv):
+    return _serve_destroy(inst, srv)
+
+
+def hicr_serve_add_memcpy_template(inst, srv, ops, region_bytes):
+    p, n = _ops_ptr(ops)
+    t = u32()
+    st = _serve_add_memcpy(inst, srv, p, n, region_bytes, C.byref(t))
+    return st, t.value
+
+
+def hicr_serve_add_burst_template(inst, srv, sizes, staging_off, staging):
+    sizes = np.ascontiguousarray(sizes, dtype=np.uint64)
+    offs = np.ascontiguousarray(staging_off, dtype=np.uint64)
+    t = u32()
+    st = _serve_add_burst(inst, srv, sizes.ctypes.data, offs.ctypes.data, len(sizes), staging, C.byref(t))
+    return st, t.value
+
+
+def hicr_serve_run(inst, srv, reqs, mode=0, timeout_ns=300_000_000_000):
+    reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
+    res = np.zeros(len(reqs), dtype=SERVE_RES_DTYPE)
+    stats = hicr_serve_stats_t()
+    st = _serve_run(inst, srv, reqs.ctypes.data, len(reqs), mode, timeout_ns, res.ctypes.data, C.byref(stats))
+    return st, res, stats
+
+
+def hicr_serve_run_plain(inst, srv, reqs, horizon_ns, timeout_ns=300_000_000_000):
+    reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
+    res = np.zeros(len(reqs), dtype=SERVE_RES_DTYPE)
+    stats = hicr_serve_stats_t()
+    st = _serve_run_plain(inst, srv, reqs.ctypes.data, len(reqs), horizon_ns, timeout_ns, res.ctypes.data,
+                          C.byref(stats))
+    return st, res, stats
+
+
+def hicr_serve_digests(inst, srv, reqs, results):
+    reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
+    st = _serve_digests(inst, srv, reqs.ctypes.data, len(reqs), results.ctypes.data)
+    return st

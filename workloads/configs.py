@@ -275,20 +275,16 @@ def mpsc(seed: int = 0, n_producers: int = 1024, n_consumers: int = 16,
 class ServeTrace:
     arrival_ns: np.ndarray   # int64, sorted
     kind: np.ndarray         # 0 = memcpy batch, 1 = MPSC burst
-    count: np.ndarray        # ops (kind 0) or messages (kind 1)
-    template: np.ndarray     # request template index
+    template: np.ndarray     # template index within its kind
     rate: float
     duration_s: float
 
 
 def serve_trace(seed: int = 0, rate: float = 20000.0, duration_s: float = 60.0,
-                memcpy_frac: float = 0.7, max_ops: int = 4096, max_msgs: int = 512,
-                n_templates: int = 1024) -> ServeTrace:
-    """Poisson arrivals (exponential gaps of mean 1/rate); 70% memcpy requests
-    of log-uniform [1, max_ops] ops, 30% MPSC bursts of log-uniform
-    [1, max_msgs] messages. Each request names one of ``n_templates`` templates
-    of its kind (uniform), whose op/message table is built by
-    ``serve_templates``."""
+                memcpy_frac: float = 0.7, n_templates: int = 1024) -> ServeTrace:
+    """Poisson arrivals (exponential gaps of mean 1/rate, from stream 501);
+    each request is a memcpy batch with probability memcpy_frac, else an MPSC
+    burst (stream 502), and names a template of its kind uniformly (503)."""
     expected = int(rate * duration_s * 1.1) + 64
     gaps = -np.log1p(-Stream(seed, 501).uniform(expected)) / rate
     t = np.cumsum(gaps)
@@ -296,28 +292,29 @@ def serve_trace(seed: int = 0, rate: float = 20000.0, duration_s: float = 60.0,
     t = t[:m]
     kind = (Stream(seed, 502).uniform(m) >= memcpy_frac).astype(np.int32)
     template = Stream(seed, 503).integers(0, n_templates - 1, m)
-    return ServeTrace((t * 1e9).astype(np.int64), kind, np.zeros(m, dtype=np.int64),
-                      template.astype(np.int64), rate, duration_s)
+    return ServeTrace((t * 1e9).astype(np.int64), kind, template.astype(np.int64), rate, duration_s)
 
 
 @dataclass
 class ServeTemplates:
-    """Request templates: memcpy templates hold ops with destination offsets
-    relative to the request's own destination region (packed, 16-byte aligned
-    starts); MPSC templates hold message sizes and a producer id."""
+    """memcpy templates: ops whose dst_off is relative to the request's own
+    region (packed, 16-byte aligned starts), src = source slot index of the
+    source workload; MPSC burst templates: message sizes. Message m of burst
+    template t carries the MPSC payload of (producer t, seq m)."""
     op_start: np.ndarray      # int64 [n_templates + 1] into ops
-    ops: np.ndarray           # OP_DTYPE; dst = 0 (the request region), src = source slot
+    ops: np.ndarray           # OP_DTYPE; dst = 0
     region_bytes: np.ndarray  # int64 per memcpy template
     msg_start: np.ndarray     # int64 [n_templates + 1] into msg_sizes
     msg_sizes: np.ndarray     # int64
-    msg_producer: np.ndarray  # int64 per MPSC template
 
 
-def serve_templates(seed: int, src: MemcpyWorkload, n_templates: int = 1024,
-                    max_ops: int = 4096, max_msgs: int = 512, n_lo: int = 16,
-                    n_hi: int = 4 * MiB, msg_lo: int = 8, msg_hi: int = 256 * KiB,
-                    n_producers: int = 1024) -> ServeTemplates:
-    """Templates drawn from streams 510-516; sources are ``src``'s source slots."""
+def serve_templates(seed: int, src: MemcpyWorkload, n_templates: int = 1024, max_ops: int = 4096,
+                    max_msgs: int = 512, n_lo: int = 16, n_hi: int = 4 * MiB, msg_lo: int = 8,
+                    msg_hi: int = 256 * KiB) -> ServeTemplates:
+    """Op counts log-uniform [1, max_ops] (stream 510), sizes log-uniform
+    [n_lo, n_hi] (511), source slot uniform among the source slots that hold
+    the op (512), 16-byte aligned source offset uniform (513); message counts
+    log-uniform [1, max_msgs] (514), sizes log-uniform [msg_lo, msg_hi] (515)."""
     counts = Stream(seed, 510).log_uniform(1, max_ops, n_templates)
     total = int(counts.sum())
     n = Stream(seed, 511).log_uniform(n_lo, n_hi, total)
@@ -325,26 +322,22 @@ def serve_templates(seed: int, src: MemcpyWorkload, n_templates: int = 1024,
     u_soff = Stream(seed, 513).uniform(total)
     isz = src.slot_sizes.astype(np.int64)
     srcs = np.asarray(src.src_slots)
-    ok_sizes = isz[srcs]
-    pick = np.empty(total, dtype=np.int64)
-    soff = np.empty(total, dtype=np.int64)
-    for i in range(total):
-        cand = srcs[ok_sizes >= n[i] + 16]
-        s = int(cand[min(int(u_src[i] * len(cand)), len(cand) - 1)])
-        pick[i] = s
-        span = (int(isz[s]) - int(n[i])) // 16
-        soff[i] = 16 * min(int(u_soff[i] * (span + 1)), span)
+    order = np.argsort(isz[srcs], kind="stable")
+    sorted_sizes = isz[srcs][order]
+    first = np.searchsorted(sorted_sizes, n + 16, side="left")
+    if (first >= len(srcs)).any():
+        raise ValueError("an op is larger than every source slot")
+    pick_idx = first + np.minimum((u_src * (len(srcs) - first)).astype(np.int64), len(srcs) - first - 1)
+    pick = srcs[order[pick_idx]]
+    span = (isz[pick] - n) // 16
+    soff = 16 * np.minimum((u_soff * (span + 1)).astype(np.int64), span)
     op_start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
-    doff = np.empty(total, dtype=np.int64)
-    region = np.empty(n_templates, dtype=np.int64)
-    for t in range(n_templates):
-        a, b = op_start[t], op_start[t + 1]
-        sz16 = ((n[a:b] + 15) // 16) * 16
-        doff[a:b] = np.concatenate([[0], np.cumsum(sz16)[:-1]])
-        region[t] = int(sz16.sum())
+    sz16 = ((n + 15) // 16) * 16
+    csum = np.concatenate([[0], np.cumsum(sz16)])
+    doff = csum[:-1] - np.repeat(csum[op_start[:-1]], counts)
+    region = csum[op_start[1:]] - csum[op_start[:-1]]
     ops = make_ops(0, pick, doff, soff, n)
     mcounts = Stream(seed, 514).log_uniform(1, max_msgs, n_templates)
     msg_start = np.concatenate([[0], np.cumsum(mcounts)]).astype(np.int64)
     msizes = Stream(seed, 515).log_uniform(msg_lo, msg_hi, int(mcounts.sum()))
-    mprod = Stream(seed, 516).integers(0, n_producers - 1, n_templates)
-    return ServeTemplates(op_start, ops, region, msg_start, msizes, mprod)
+    return ServeTemplates(op_start, ops, region.astype(np.int64), msg_start, msizes)
