@@ -13,7 +13,7 @@
  *  - requests are admitted in arrival order as the destination arena (the
  *    device-memory budget minus the channel rings) has room for their region;
  *  - admitted requests are published through a doorbell in mapped host memory;
- *    a dispatcher warp moves them into a device-side request ring and cuts
+ *    a dispatcher warp moves them into a device-side request table and cuts
  *    them into work units; worker warps claim units from every admitted
  *    request at once (continuous batching: work of requests admitted at
  *    different times overlaps on the device);
@@ -69,6 +69,11 @@ typedef struct {
   uint64_t wall_ns;          /* first arrival to last completion */
   uint64_t max_inflight;     /* most requests admitted and not complete at once */
   uint64_t max_region_bytes; /* high-water mark of the arena */
+  uint64_t admitted;         /* requests published to the device */
+  uint64_t dev_units;        /* work units the dispatcher published */
+  uint64_t dev_claimed;      /* work units claimed by workers */
+  uint64_t dev_requests;     /* requests the dispatcher took over */
+  uint64_t dev_flags;        /* bit 0 stop seen, bit 1 abort (deadline), bit 2 self-check */
   int32_t status;            /* HICR_OK or HICR_ERR_TIMEOUT */
   uint32_t reserved;
 } hicr_serve_stats_t;
@@ -100,7 +105,8 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t inst, hicr_serve_t srv
  * request i completed). results: host array of n (may be NULL); stats may be
  * NULL. Synchronous. Errors: INVALID (unknown template, unsorted), NOMEM (a
  * request's region exceeds the arena), DEVICE, TIMEOUT (not finished within
- * timeout_ns; the engine stops). */
+ * timeout_ns; the engine stops, and if its kernel has not ended 10 s later
+ * the call returns anyway and leaves the run's buffers allocated). */
 hicr_status hicr_serve_run(hicr_instance_t inst, hicr_serve_t srv, const hicr_serve_request_t* reqs, uint64_t n,
                            uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
                            hicr_serve_stats_t* stats);

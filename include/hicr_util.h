@@ -43,6 +43,15 @@ hicr_status hicr_util_fill_segments(hicr_instance_t inst, hicr_slot_t slot, cons
 hicr_status hicr_util_digest(hicr_instance_t inst, hicr_slot_t slot, uint64_t off, uint64_t n,
                              uint64_t* out);
 
+/* Self-test of the bounded device waits that every spin in this library
+ * uses: launches one thread that waits on a device flag nothing sets, giving up
+ * after timeout_ns of %globaltimer time, and reports what happened:
+ * *status = HICR_ERR_TIMEOUT when the wait gave up (expected), HICR_OK if the
+ * flag was seen; *waited_ns = device time spent waiting. Synchronous.
+ * Errors: INVALID, DEVICE. */
+hicr_status hicr_util_wait_test(hicr_instance_t inst, uint64_t timeout_ns, hicr_status* status,
+                                uint64_t* waited_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,7 +52,7 @@ struct SrvHostDesc {
 };
 
 struct SrvCtl {
-  Line claim, units_pub, req_pub, stop, final_units, abort;
+  Line claim, units_pub, req_pub, stop, final_units, abort, bad;
   unsigned long long final_msgs[SRV_MAX_CH];
 };
 
@@ -82,6 +82,9 @@ struct SrvArgs {
   unsigned int chunk;
   unsigned int op_cost;
   unsigned long long timeout_ns;
+  unsigned long long n_req;   // requests in this run
+  unsigned int n_mt, n_bt;    // memcpy / burst templates
+  unsigned long long arena_lo, arena_hi;
 };
 
 __device__ __forceinline__ unsigned long long ld_acq_sys(const unsigned long long* p) {
@@ -107,10 +110,29 @@ __device__ __forceinline__ bool srv_abort(const SrvArgs& a, unsigned long long d
   return false;
 }
 
+// Request entries are written by the dispatcher while the kernel runs, so
+// every read of one goes to L2 (ld.global.cg): an SM's L1 may still hold the
+// line from before the entry was written.
+struct ReqView {
+  unsigned long long U, id, dst;
+  unsigned int N, need, kind, tmpl;
+};
+__device__ __forceinline__ ReqView load_req(const SrvReq* e) {
+  ReqView r;
+  r.U = __ldcg(&e->U);
+  r.id = __ldcg(&e->id);
+  r.dst = __ldcg(&e->dst);
+  r.N = __ldcg(&e->N);
+  r.need = __ldcg(&e->need);
+  r.kind = __ldcg(&e->kind);
+  r.tmpl = __ldcg(&e->tmpl);
+  return r;
+}
+
 // The request that finishes writes its completion into host memory.
 __device__ __forceinline__ void srv_complete(const SrvArgs& a, SrvReq* e) {
   __threadfence();
-  const unsigned long long id = e->id;
+  const unsigned long long id = __ldcg(&e->id);
   a.hdigest[id] = atomicAdd(&e->digest, 0ull);
   __threadfence_system();
   st_rel_sys(&a.hcompl[id], gtime() | 1ull);
@@ -185,14 +207,14 @@ __device__ __forceinline__ unsigned long long srv_find(const SrvArgs& a, unsigne
   return lo + (31u - __clz(m));
 }
 
-__device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, unsigned long long k, unsigned lane) {
-  const unsigned t = e->tmpl;
+__device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, const ReqView& rv, unsigned long long k, unsigned lane) {
+  const unsigned t = rv.tmpl;
   const hicr_op_t* ops = a.tops + a.t_opbase[t];
   const unsigned long long nops = a.t_nops[t];
   const unsigned long long* cstart = a.tcstart + a.t_cbase[t];
   const unsigned long long chunk = a.chunk, total = a.t_total[t];
   const unsigned long long lo = k * chunk, hi = min(lo + chunk, total);
-  const unsigned long long dst = e->dst;
+  const unsigned long long dst = rv.dst;
   for (unsigned long long i = find_op(cstart, nops, lo, lane); i < nops; ++i) {
     const unsigned long long cs = cstart[i];
     if (cs >= hi) break;
@@ -211,14 +233,14 @@ __device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, unsigned long long k
   __syncwarp();
   if (lane == 0) {
     const unsigned long long prev = atomicAdd(&e->done, 1ull);
-    if (prev + 1 == e->need) srv_complete(a, e);
+    if (prev + 1 == rv.need) srv_complete(a, e);
   }
 }
 
 // Push every message of a burst, in order, as producer = request index.
-__device__ bool srv_push_burst(const SrvArgs& a, SrvReq* e, unsigned lane, unsigned long long deadline) {
-  const unsigned long long id = e->id;
-  const unsigned t = e->tmpl;
+__device__ bool srv_push_burst(const SrvArgs& a, const ReqView& rv, unsigned lane, unsigned long long deadline) {
+  const unsigned long long id = rv.id;
+  const unsigned t = rv.tmpl;
   const MpscView v = a.chans[id % a.n_ch];
   const unsigned long long mbase = a.t_mbase[t], nmsg = a.t_nmsg[t];
   const unsigned long long half = v.R / 2;
@@ -316,20 +338,34 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
     u = __shfl_sync(FULLM, u, 0);
     const unsigned long long hi = ld_acq(&a.ctl->req_pub.v);
     unsigned long long r;
-    // fast path: the same or the next request as the previous unit (every
-    // published entry is final, so reading it needs no further care)
-    if (hint < hi && a.req[hint].U <= u && u < a.req[hint].U + a.req[hint].N) {
+    // fast path: the same or the next request as the previous unit (only
+    // published entries, read at L2)
+    ReqView rv;
+    if (hint < hi && (rv = load_req(a.req + hint), rv.U <= u && u < rv.U + rv.N)) {
       r = hint;
-    } else if (hint + 1 < hi && a.req[hint + 1].U <= u && u < a.req[hint + 1].U + a.req[hint + 1].N) {
+    } else if (hint + 1 < hi && (rv = load_req(a.req + hint + 1), rv.U <= u && u < rv.U + rv.N)) {
       r = hint + 1;
     } else {
       r = srv_find(a, 0, hi, u, lane);
+      rv = load_req(a.req + r);
     }
     hint = r;
     SrvReq* e = a.req + r;
-    if (e->kind == 0) {
-      srv_copy_chunk(a, e, u - e->U, lane);
-    } else if (!srv_push_burst(a, e, lane, deadline)) {
+    // self-check: a request outside this run or with an unknown template is
+    // reported (ctl->bad) and stops the engine instead of being executed
+    const bool ok = r < a.n_req && rv.id == r &&
+                    ((rv.kind == 0 && rv.tmpl < a.n_mt && rv.dst >= a.arena_lo && rv.dst < a.arena_hi) ||
+                     (rv.kind == 1 && rv.tmpl < a.n_bt));
+    if (!ok) {
+      if (lane == 0) {
+        atomicCAS(&a.ctl->bad.v, 0ull, 1ull + r);
+        atomicExch(&a.ctl->abort.v, 1ull);
+      }
+      return;
+    }
+    if (rv.kind == 0) {
+      srv_copy_chunk(a, e, rv, u - rv.U, lane);
+    } else if (!srv_push_burst(a, rv, lane, deadline)) {
       return;
     }
   }
@@ -454,11 +490,16 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
     __syncthreads();
     // per-request accounting: message digest weighted by its index in the burst
     for (unsigned j = tid; j < navail; j += blockDim.x) {
+      if (s_prod[j] >= a.n_req) {  // self-check, as in the workers
+        atomicCAS(&a.ctl->bad.v, 0ull, 1ull + s_prod[j]);
+        atomicExch(&a.ctl->abort.v, 1ull);
+        continue;
+      }
       SrvReq* e = a.req + s_prod[j];
       atomicAdd(&e->digest, s_dig[j] * (2ull * s_seq[j] + 1ull));
       __threadfence();
       const unsigned long long prev = atomicAdd(&e->done, 1ull);
-      if (prev + 1 == e->need) srv_complete(a, e);
+      if (prev + 1 == __ldcg(&e->need)) srv_complete(a, e);
     }
     if (tid == 0) {
       st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
@@ -867,6 +908,11 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   a.chunk = sv->cfg.chunk_bytes;
   a.op_cost = sv->cfg.op_cost_bytes;
   a.timeout_ns = timeout_ns;
+  a.n_req = n;
+  a.n_mt = (unsigned)sv->t_nops.size();
+  a.n_bt = (unsigned)sv->t_nmsg.size();
+  a.arena_lo = (unsigned long long)sv->arena;
+  a.arena_hi = (unsigned long long)sv->arena + (sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
   int per_sm = 0;
   HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_serve, SRV_THREADS, 0));
   const unsigned grid = (unsigned)(in->sm_count * std::max(1, per_sm));
@@ -961,11 +1007,57 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     }
   }
   hstop->store(1, std::memory_order_release);
-  ce = cudaStreamSynchronize(cs);
+  // Wait for the engine with a bound: its own deadline ends every device
+  // wait, so it should stop by then; if it has not 10 s later, report and
+  // return without freeing what it may still touch.
+  const uint64_t wait_until = now_ns() + (timeout_ns > now_ns() - t0 ? timeout_ns - (now_ns() - t0) : 0) +
+                              10ull * 1000000000ull;
+  for (;;) {
+    ce = cudaStreamQuery(cs);
+    if (ce != cudaErrorNotReady) break;
+    if (now_ns() > wait_until) break;
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  // device-side progress counters (readable while the kernel runs)
+  unsigned long long dv[6] = {0, 0, 0, 0, 0, 0};
+  {
+    cudaStream_t ps = nullptr;
+    if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) == cudaSuccess) {
+      cudaMemcpyAsync(&dv[0], &sv->ctl->units_pub.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[1], &sv->ctl->claim.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[2], &sv->ctl->req_pub.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[3], &sv->ctl->stop.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[4], &sv->ctl->abort.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[5], &sv->ctl->bad.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaStreamSynchronize(ps);
+      cudaStreamDestroy(ps);
+    }
+    (void)cudaGetLastError();
+  }
+  if (stats) {
+    stats->admitted = next_admit;
+    stats->dev_units = dv[0];
+    stats->dev_claimed = dv[1];
+    stats->dev_requests = dv[2];
+    stats->dev_flags = (dv[3] ? 1ull : 0ull) | (dv[4] ? 2ull : 0ull) | (dv[5] ? 4ull : 0ull);
+  }
+  if (ce == cudaErrorNotReady) {
+    in->last_err = "serving engine kernel did not stop after its deadline";
+    if (stats) {
+      stats->completed = completed;
+      stats->status = HICR_ERR_TIMEOUT;
+    }
+    return HICR_ERR_TIMEOUT;
+  }
   cudaFree(dreq);
   if (ce != cudaSuccess) {
     cudaFreeHost(hp);
     return cuda_fail(in, ce, "k_serve");
+  }
+  const unsigned long long bad = dv[5];
+  if (bad) {
+    in->last_err = "serving engine self-check failed at request " + std::to_string(bad - 1);
+    result = HICR_ERR_DEVICE;
   }
   if (stats) {
     stats->completed = completed;
@@ -1064,7 +1156,12 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
       last_done = tnow;
     }
   }
-  cudaStreamSynchronize(cs);
+  {
+    const uint64_t until = now_ns() + 60ull * 1000000000ull;
+    while (cudaStreamQuery(cs) == cudaErrorNotReady && now_ns() < until)
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    (void)cudaGetLastError();
+  }
   for (auto& e : ev) cudaEventDestroy(e);
   if (stats) {
     stats->completed = completed;

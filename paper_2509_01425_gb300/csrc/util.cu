@@ -1,6 +1,7 @@
 // Device fill and digest utilities (no counterpart in the HiCR paper): the
 // seeded slot contents of the synthetic workloads and a word digest that lets
 // large results be compared without copying them to the host.
+#include "channel_common.cuh"
 #include "hicr_internal.h"
 #include "splitmix.cuh"
 
@@ -73,6 +74,23 @@ __global__ void k_fill_segments(uint8_t* base, unsigned long long size, const un
   }
 }
 
+// Waits on flag[0] (which nothing sets) until the deadline; out[0] = status,
+// out[1] = device time waited.
+__global__ void k_wait_test(unsigned long long* flag, unsigned long long timeout_ns, unsigned long long* out) {
+  const unsigned long long t0 = gtime(), deadline = t0 + timeout_ns;
+  int st = HICR_ERR_TIMEOUT;
+  for (;;) {
+    if (ld_acq(flag) != 0) {
+      st = HICR_OK;
+      break;
+    }
+    if (gtime() > deadline) break;
+    __nanosleep(1000);
+  }
+  out[0] = (unsigned long long)(long long)st;
+  out[1] = gtime() - t0;
+}
+
 const void* builtin_fill_kernel() { return (const void*)k_fill; }
 const void* builtin_digest_kernel() { return (const void*)k_digest; }
 
@@ -105,6 +123,27 @@ hicr_status hicr_util_fill_segments(hicr_instance_t h, hicr_slot_t slot, const u
   k_fill_segments<<<grid, 256, 0, in->comm()>>>((uint8_t*)s.base, s.size, (const unsigned long long*)d_seg, count);
   HICR_CUDA(in, cudaGetLastError());
   return record_done(in);
+}
+
+hicr_status hicr_util_wait_test(hicr_instance_t h, uint64_t timeout_ns, hicr_status* status, uint64_t* waited_ns) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || !status || !waited_ns || in->capturing || timeout_ns > 60ull * 1000000000ull) return HICR_ERR_INVALID;
+  unsigned long long* d = nullptr;
+  HICR_CUDA(in, cudaMalloc(&d, 3 * 8));
+  cudaStream_t cs = in->comm();
+  unsigned long long out[2] = {0, 0};
+  cudaError_t e = cudaMemsetAsync(d, 0, 3 * 8, cs);
+  if (e == cudaSuccess) {
+    k_wait_test<<<1, 1, 0, cs>>>(d, timeout_ns, d + 1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 1, 16, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(in, e, "wait test");
+  *status = (hicr_status)(long long)out[0];
+  *waited_ns = out[1];
+  return HICR_OK;
 }
 
 hicr_status hicr_util_digest(hicr_instance_t h, hicr_slot_t slot, uint64_t off, uint64_t n, uint64_t* out) {

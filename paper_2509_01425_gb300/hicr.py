@@ -160,6 +160,7 @@ _exec_await = _decl("hicr_exec_await", [H, u64, u64])
 _last_error_string = _decl("hicr_last_error_string", [H, C.c_char_p, u64])
 _util_fill = _decl("hicr_util_fill", [H, u32, u64, u64, u64])
 _util_fill_segments = _decl("hicr_util_fill_segments", [H, u32, vp, u64])
+_util_wait_test = _decl("hicr_util_wait_test", [H, u64, C.POINTER(i32), C.POINTER(u64)])
 _util_digest = _decl("hicr_util_digest", [H, u32, u64, u64, C.POINTER(u64)])
 
 
@@ -418,6 +419,12 @@ def hicr_util_fill_segments(inst, slot, d_seg, count):
     return _util_fill_segments(inst, slot, _ptr(d_seg), count)
 
 
+def hicr_util_wait_test(inst, timeout_ns):
+    st_, w = i32(), u64()
+    st = _util_wait_test(inst, timeout_ns, C.byref(st_), C.byref(w))
+    return st, st_.value, w.value
+
+
 def hicr_util_digest(inst, slot, off, n):
     v = u64()
     st = _util_digest(inst, slot, off, n, C.byref(v))
@@ -531,7 +538,11 @@ class hicr_serve_config_t(C.Structure):
 
 class hicr_serve_stats_t(C.Structure):
     _fields_ = [("completed", u64), ("bytes_moved", u64), ("wall_ns", u64), ("max_inflight", u64),
-                ("max_region_bytes", u64), ("status", i32), ("reserved", u32)]
+                ("max_region_bytes", u64), ("admitted", u64), ("dev_units", u64), ("dev_claimed", u64),
+                ("dev_requests", u64), ("dev_flags", u64), ("status", i32), ("reserved", u32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 SERVE_REQ_DTYPE = np.dtype([("arrival_ns", "<u8"), ("kind", "<u4"), ("tmpl", "<u4")])

@@ -335,3 +335,11 @@ def test_torch_stream_as_processing_unit(h, inst):
     assert (slot_bytes(h, inst, ids[1]) == splitmix.fill_bytes(6, 0, 0, 1 << 20)).all()
     assert h.hicr_comm_set_pu(inst, 0) == 0
     assert h.hicr_pu_destroy(inst, pu) == 0
+
+
+def test_bounded_device_wait_gives_up(h, inst):
+    """Every spin in the library ends at a %globaltimer deadline: a wait on a
+    flag that nothing sets must return TIMEOUT after about the set time."""
+    st, status, waited = h.hicr_util_wait_test(inst, 200_000_000)
+    assert st == 0 and status == h.HICR_ERR_TIMEOUT
+    assert 200_000_000 <= waited < 2_000_000_000
