@@ -85,7 +85,21 @@ struct SrvArgs {
   unsigned long long n_req;   // requests in this run
   unsigned int n_mt, n_bt;    // memcpy / burst templates
   unsigned long long arena_lo, arena_hi;
+  unsigned int* wstate;       // per warp: where it is (diagnostics)
 };
+
+// Warp states recorded in SrvArgs::wstate (diagnostics of a stuck run).
+enum : unsigned {
+  WS_CLAIM = 1, WS_COPY = 2, WS_RESERVE = 3, WS_PUSH = 4, WS_WORKER_DONE = 5,
+  WS_C_AVAIL = 10, WS_C_READY = 11, WS_C_DIGEST = 12, WS_C_ACCOUNT = 13, WS_C_DONE = 14,
+  WS_DISPATCH = 20, WS_DISPATCH_DONE = 21
+};
+__device__ __forceinline__ void ws_set(const SrvArgs& a, unsigned st) {
+  if ((threadIdx.x & 31u) == 0) {
+    const unsigned w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    *(volatile unsigned*)&a.wstate[w] = st;
+  }
+}
 
 __device__ __forceinline__ unsigned long long ld_acq_sys(const unsigned long long* p) {
   unsigned long long v;
@@ -139,6 +153,7 @@ __device__ __forceinline__ void srv_complete(const SrvArgs& a, SrvReq* e) {
 }
 
 __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
+  ws_set(a, WS_DISPATCH);
   unsigned long long r = 0, U = 0;
   unsigned long long msgs[SRV_MAX_CH];
   for (unsigned c = 0; c < a.n_ch; ++c) msgs[c] = 0;
@@ -180,9 +195,13 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
       a.ctl->final_units.v = U;
       __threadfence();
       st_rel(&a.ctl->stop.v, 1ull);
+      ws_set(a, WS_DISPATCH_DONE);
       return;
     }
-    if (srv_abort(a, deadline)) return;
+    if (srv_abort(a, deadline)) {
+      ws_set(a, WS_DISPATCH_DONE);
+      return;
+    }
     __nanosleep(sleep_ns);
     sleep_ns = min(sleep_ns * 2, 1024u);
   }
@@ -261,6 +280,7 @@ __device__ bool srv_push_burst(const SrvArgs& a, const ReqView& rv, unsigned lan
     }
     unsigned long long W = 0;
     int stop = 0;
+    ws_set(a, WS_RESERVE);
     if (lane == 0) {
       unsigned sleep_ns = 32;
       for (;;) {
@@ -285,6 +305,7 @@ __device__ bool srv_push_burst(const SrvArgs& a, const ReqView& rv, unsigned lan
       }
     }
     if (__shfl_sync(FULLM, stop, 0)) return false;
+    ws_set(a, WS_PUSH);
     W = __shfl_sync(FULLM, W, 0);
     const unsigned long long t0 = W >> 40;
     for (int i = 0; i < k; ++i) {
@@ -317,6 +338,7 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
   for (;;) {
     unsigned long long u = 0;
     int exit_now = 0;
+    ws_set(a, WS_CLAIM);
     if (lane == 0) {
       u = atomicAdd(&a.ctl->claim.v, 1ull);
       unsigned sleep_ns = 32;
@@ -334,8 +356,12 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
         sleep_ns = min(sleep_ns * 2, 512u);
       }
     }
-    if (__shfl_sync(FULLM, exit_now, 0)) return;
+    if (__shfl_sync(FULLM, exit_now, 0)) {
+      ws_set(a, WS_WORKER_DONE);
+      return;
+    }
     u = __shfl_sync(FULLM, u, 0);
+    ws_set(a, WS_COPY);
     const unsigned long long hi = ld_acq(&a.ctl->req_pub.v);
     unsigned long long r;
     // fast path: the same or the next request as the previous unit (only
@@ -361,11 +387,13 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
         atomicCAS(&a.ctl->bad.v, 0ull, 1ull + r);
         atomicExch(&a.ctl->abort.v, 1ull);
       }
+      ws_set(a, WS_WORKER_DONE);
       return;
     }
     if (rv.kind == 0) {
       srv_copy_chunk(a, e, rv, u - rv.U, lane);
     } else if (!srv_push_burst(a, rv, lane, deadline)) {
+      ws_set(a, WS_WORKER_DONE);
       return;
     }
   }
@@ -384,6 +412,7 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
   __syncthreads();
   unsigned long long t = s_t0, consumed = 0;
   for (;;) {
+    ws_set(a, WS_C_AVAIL);
     if (tid == 0) {
       int stop = 0;
       unsigned long long avail = 0;
@@ -407,8 +436,12 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       s_stop = stop;
     }
     __syncthreads();
-    if (s_stop) return;
+    if (s_stop) {
+      ws_set(a, WS_C_DONE);
+      return;
+    }
     const unsigned navail = (unsigned)s_avail;
+    ws_set(a, WS_C_READY);
     for (unsigned j = warp; j < navail; j += nwarp) {
       const unsigned long long tk = t + j;
       MpscMeta* m = v.meta + (tk & (v.M - 1));
@@ -433,7 +466,11 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       }
     }
     __syncthreads();
-    if (s_stop) return;
+    if (s_stop) {
+      ws_set(a, WS_C_DONE);
+      return;
+    }
+    ws_set(a, WS_C_DIGEST);
     if (warp == 0) {
       const unsigned long long p0 =
           lane < navail ? (((unsigned long long)s_size[lane] + 15) / 16 + SRV_PIECE - 1) / SRV_PIECE : 0;
@@ -488,6 +525,7 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       if (lane == 0) atomicAdd(&s_dig[j], d);
     }
     __syncthreads();
+    ws_set(a, WS_C_ACCOUNT);
     // per-request accounting: message digest weighted by its index in the burst
     for (unsigned j = tid; j < navail; j += blockDim.x) {
       if (s_prod[j] >= a.n_req) {  // self-check, as in the workers
@@ -916,9 +954,15 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   int per_sm = 0;
   HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_serve, SRV_THREADS, 0));
   const unsigned grid = (unsigned)(in->sm_count * std::max(1, per_sm));
+  const size_t n_warps = (size_t)grid * (SRV_THREADS / 32);
+  unsigned int* wstate = nullptr;
+  HICR_CUDA(in, cudaMalloc(&wstate, 4 * n_warps));
+  HICR_CUDA(in, cudaMemset(wstate, 0, 4 * n_warps));
+  a.wstate = wstate;
   if (grid < a.n_ch + 2) {
     cudaFreeHost(hp);
     cudaFree(dreq);
+    cudaFree(wstate);
     return HICR_ERR_INVALID;
   }
   void* args[] = {&a};
@@ -927,6 +971,7 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   if (ce != cudaSuccess) {
     cudaFreeHost(hp);
     cudaFree(dreq);
+    cudaFree(wstate);
     return cuda_fail(in, ce, "cudaLaunchCooperativeKernel(k_serve)");
   }
 
@@ -1018,11 +1063,20 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     if (now_ns() > wait_until) break;
     std::this_thread::sleep_for(std::chrono::microseconds(200));
   }
-  // device-side progress counters (readable while the kernel runs)
+  // device-side progress counters and warp states (readable while the
+  // kernel runs, on a side stream)
   unsigned long long dv[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<unsigned int> ws(n_warps, 0);
+  const bool overdue = ce == cudaErrorNotReady;
   {
     cudaStream_t ps = nullptr;
     if (cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) == cudaSuccess) {
+      cudaMemcpyAsync(ws.data(), wstate, 4 * n_warps, cudaMemcpyDeviceToHost, ps);
+      if (overdue) {
+        // ask every bounded wait to give up now
+        static const unsigned long long one = 1;
+        cudaMemcpyAsync(&sv->ctl->abort.v, &one, 8, cudaMemcpyHostToDevice, ps);
+      }
       cudaMemcpyAsync(&dv[0], &sv->ctl->units_pub.v, 8, cudaMemcpyDeviceToHost, ps);
       cudaMemcpyAsync(&dv[1], &sv->ctl->claim.v, 8, cudaMemcpyDeviceToHost, ps);
       cudaMemcpyAsync(&dv[2], &sv->ctl->req_pub.v, 8, cudaMemcpyDeviceToHost, ps);
@@ -1041,14 +1095,28 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     stats->dev_requests = dv[2];
     stats->dev_flags = (dv[3] ? 1ull : 0ull) | (dv[4] ? 2ull : 0ull) | (dv[5] ? 4ull : 0ull);
   }
-  if (ce == cudaErrorNotReady) {
-    in->last_err = "serving engine kernel did not stop after its deadline";
-    if (stats) {
-      stats->completed = completed;
-      stats->status = HICR_ERR_TIMEOUT;
-    }
-    return HICR_ERR_TIMEOUT;
+  if (overdue || result != HICR_OK) {
+    std::map<unsigned, unsigned> hist;
+    for (unsigned w : ws) hist[w]++;
+    std::string msg = overdue ? "engine kernel overdue; warp states:" : "engine timed out; warp states:";
+    for (auto& kv : hist) msg += " " + std::to_string(kv.first) + "x" + std::to_string(kv.second);
+    msg += "; units_pub " + std::to_string(dv[0]) + " claimed " + std::to_string(dv[1]) + " req_pub " +
+           std::to_string(dv[2]) + " admitted " + std::to_string(next_admit) + " completed " + std::to_string(completed);
+    in->last_err = msg;
   }
+  if (overdue) {
+    const uint64_t until = now_ns() + 10ull * 1000000000ull;
+    while ((ce = cudaStreamQuery(cs)) == cudaErrorNotReady && now_ns() < until)
+      std::this_thread::sleep_for(std::chrono::microseconds(200));
+    if (ce == cudaErrorNotReady) {
+      if (stats) {
+        stats->completed = completed;
+        stats->status = HICR_ERR_TIMEOUT;
+      }
+      return HICR_ERR_TIMEOUT;
+    }
+  }
+  cudaFree(wstate);
   cudaFree(dreq);
   if (ce != cudaSuccess) {
     cudaFreeHost(hp);
