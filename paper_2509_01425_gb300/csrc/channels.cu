@@ -459,7 +459,12 @@ static constexpr int MPSC_WIN = 64;
 static constexpr int MPSC_PIECE = 512;  // 16-byte vectors per digest piece (8 KiB)
 
 __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline) {
-  __shared__ int s_stop;
+  // s_stop is written only by thread 0 before the first barrier of a round;
+  // phase-A waits that give up write s_abort_a, read after the second
+  // barrier and cleared by thread 0 at the start of the next round (after the
+  // round's last barrier), so no thread can see a flag meant for a later
+  // check and leave while others wait at a barrier.
+  __shared__ int s_stop, s_abort_a;
   __shared__ unsigned long long s_avail, s_t0, s_bytes;
   __shared__ unsigned long long s_start[MPSC_WIN], s_ppre[MPSC_WIN + 1], s_dig[MPSC_WIN];
   __shared__ unsigned int s_size[MPSC_WIN], s_prod[MPSC_WIN], s_seq[MPSC_WIN];
@@ -473,6 +478,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
     s_t0 = ld_acq(&v.st->msg_tail.v);
     s_bytes = 0;
     s_stop = 0;
+    s_abort_a = 0;
   }
   __syncthreads();
   unsigned long long t = s_t0, consumed = 0, windows = 0;
@@ -496,6 +502,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       }
       s_avail = min(min(avail, win_max), expect - consumed);
       s_stop = stop;
+      s_abort_a = 0;
     }
     __syncthreads();
     if (s_stop) break;
@@ -515,7 +522,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
           __nanosleep(32);
         }
         if (stop) {
-          s_stop = 1;
+          s_abort_a = 1;
         } else {
           s_start[j] = __ldcg(&e->start);
           s_size[j] = __ldcg(&e->size);
@@ -526,7 +533,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       }
     }
     __syncthreads();
-    if (s_stop) break;
+    if (s_abort_a) break;
     if (tid == 0) {
       const unsigned long long x = gtime();
       ns_a += x - tm;
@@ -628,7 +635,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
     r->consumer_ns[0] = ns_a;
     r->consumer_ns[1] = ns_b;
     r->consumer_ns[2] = ns_c;
-    if (s_stop) r->status = HICR_ERR_TIMEOUT;
+    if (s_stop || s_abort_a) r->status = HICR_ERR_TIMEOUT;
   }
 }
 

@@ -400,7 +400,12 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
 }
 
 __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long deadline) {
-  __shared__ int s_stop;
+  // s_stop is written only by thread 0 before the first barrier of a round;
+  // phase-A waits that give up write s_abort_a, read after the second
+  // barrier and cleared by thread 0 at the start of the next round (after the
+  // round's last barrier), so no thread can see a flag meant for a later
+  // check and leave while others wait at a barrier.
+  __shared__ int s_stop, s_abort_a;
   __shared__ unsigned long long s_avail;
   __shared__ unsigned long long s_start[SRV_WIN], s_ppre[SRV_WIN + 1], s_dig[SRV_WIN];
   __shared__ unsigned int s_size[SRV_WIN], s_prod[SRV_WIN], s_seq[SRV_WIN];
@@ -434,6 +439,7 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       }
       s_avail = min(avail, win_max);
       s_stop = stop;
+      s_abort_a = 0;
     }
     __syncthreads();
     if (s_stop) {
@@ -455,7 +461,7 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
           __nanosleep(32);
         }
         if (stop) {
-          s_stop = 1;
+          s_abort_a = 1;
         } else {
           s_start[j] = __ldcg(&m->start);
           s_size[j] = __ldcg(&m->size);
@@ -466,7 +472,7 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       }
     }
     __syncthreads();
-    if (s_stop) {
+    if (s_abort_a) {
       ws_set(a, WS_C_DONE);
       return;
     }

@@ -72,6 +72,8 @@ def test_budget_limits_admission_and_everything_completes(h, inst):
     tr = configs.serve_trace(SEED + 1, rate=500_000.0, duration_s=0.001, n_templates=16)
     reqs = ss.requests(tr)
     st, res, stats = h.hicr_serve_run(inst, ss.srv, reqs, 0, 20_000_000_000)
+    if st != 0 or stats.completed != len(reqs):
+        print("serve run failed:", st, stats.as_dict(), h.hicr_last_error_string(inst), flush=True)
     assert st == 0 and stats.completed == len(reqs), (st, stats.as_dict(), h.hicr_last_error_string(inst))
     assert stats.max_region_bytes <= 2 << 20
     assert (res["admit_ns"] > 0).any(), "no request had to wait for memory"
