@@ -1,5 +1,6 @@
 // Instance, topology, memory slots, processing units, execution states,
 // fence and counters of the HiCR C ABI (HiCR paper Sec. 3.1.1-3.1.5).
+#include <stdio.h>
 #include <string.h>
 #include <unistd.h>
 
@@ -206,6 +207,30 @@ hicr_status hicr_finalize(hicr_instance_t h) {
     cudaGraph_t g = nullptr;
     cudaStreamEndCapture(in->comm(), &g);
     if (g) cudaGraphDestroy(g);
+  }
+  // Outstanding work on the instance's streams gets a bounded wait: if it
+  // does not finish, nothing is freed (it may still be in use) and the call
+  // reports BUSY instead of blocking forever.
+  {
+    const uint64_t until = now_ns() + 30ull * 1000000000ull;
+    bool busy = false;
+    for (auto& p : in->pus) {
+      if (!p.live) continue;
+      while (cudaStreamQuery(p.stream) == cudaErrorNotReady) {
+        if (now_ns() > until) {
+          busy = true;
+          break;
+        }
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));
+      }
+      if (busy) break;
+    }
+    (void)cudaGetLastError();
+    if (busy) {
+      fprintf(stderr, "hicr_finalize: work still running after 30 s; instance left allocated\n");
+      fflush(stderr);
+      return HICR_ERR_BUSY;
+    }
   }
   cudaDeviceSynchronize();
   destroy_channels(in);

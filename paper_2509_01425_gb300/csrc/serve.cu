@@ -17,6 +17,7 @@
 //                   chunk of the template's ops (same warp copy and chunking
 //                   as the batch path) or push the burst's messages in order.
 // Every wait is bounded by the run deadline (%globaltimer).
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -1107,8 +1108,12 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     std::string msg = overdue ? "engine kernel overdue; warp states:" : "engine timed out; warp states:";
     for (auto& kv : hist) msg += " " + std::to_string(kv.first) + "x" + std::to_string(kv.second);
     msg += "; units_pub " + std::to_string(dv[0]) + " claimed " + std::to_string(dv[1]) + " req_pub " +
-           std::to_string(dv[2]) + " admitted " + std::to_string(next_admit) + " completed " + std::to_string(completed);
+           std::to_string(dv[2]) + " admitted " + std::to_string(next_admit) + " completed " + std::to_string(completed) +
+           " of " + std::to_string(n) + " flags stop/abort/bad " + std::to_string(dv[3]) + "/" + std::to_string(dv[4]) +
+           "/" + std::to_string(dv[5]);
     in->last_err = msg;
+    fprintf(stderr, "hicr_serve_run: %s\n", msg.c_str());
+    fflush(stderr);
   }
   if (overdue) {
     const uint64_t until = now_ns() + 10ull * 1000000000ull;

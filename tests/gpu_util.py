@@ -44,4 +44,5 @@ def inst(h):
     st, i = h.hicr_init(0)
     assert st == 0, h.hicr_status_str(st)
     yield i
-    assert h.hicr_finalize(i) == 0
+    st = h.hicr_finalize(i)
+    assert st == 0, h.hicr_status_str(st)
