@@ -53,7 +53,7 @@ struct SrvHostDesc {
 };
 
 struct SrvCtl {
-  Line claim, units_pub, req_pub, stop, final_units, abort, bad;
+  Line claim, units_pub, req_pub, stop, final_units, abort, bad, exited;
   unsigned long long final_msgs[SRV_MAX_CH];
 };
 
@@ -563,13 +563,12 @@ __global__ void __launch_bounds__(SRV_THREADS) k_serve(SrvArgs a) {
   const unsigned long long deadline = s_deadline;
   if (blockIdx.x == 0) {
     if (threadIdx.x == 0) srv_dispatcher(a, deadline);
-    return;
-  }
-  if (blockIdx.x <= a.n_ch) {
+  } else if (blockIdx.x <= a.n_ch) {
     srv_consumer(a, blockIdx.x - 1, deadline);
-    return;
+  } else {
+    srv_worker(a, deadline);
   }
-  srv_worker(a, deadline);
+  atomicAdd(&a.ctl->exited.v, 1ull);  // diagnostics: threads that reached the end
 }
 
 // Verify mode: digest of every op's destination bytes, weighted by the op's
@@ -1072,7 +1071,8 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   }
   // device-side progress counters and warp states (readable while the
   // kernel runs, on a side stream)
-  unsigned long long dv[6] = {0, 0, 0, 0, 0, 0};
+  unsigned long long dv[7] = {0, 0, 0, 0, 0, 0, 0};
+  std::vector<SrvReq> stuck_req;
   std::vector<unsigned int> ws(n_warps, 0);
   const bool overdue = ce == cudaErrorNotReady;
   {
@@ -1090,6 +1090,12 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
       cudaMemcpyAsync(&dv[3], &sv->ctl->stop.v, 8, cudaMemcpyDeviceToHost, ps);
       cudaMemcpyAsync(&dv[4], &sv->ctl->abort.v, 8, cudaMemcpyDeviceToHost, ps);
       cudaMemcpyAsync(&dv[5], &sv->ctl->bad.v, 8, cudaMemcpyDeviceToHost, ps);
+      cudaMemcpyAsync(&dv[6], &sv->ctl->exited.v, 8, cudaMemcpyDeviceToHost, ps);
+      if (result != HICR_OK || overdue) {
+        stuck_req.resize(std::min<size_t>(inflight.size(), 8));
+        for (size_t i = 0; i < stuck_req.size(); ++i)
+          cudaMemcpyAsync(&stuck_req[i], dreq + inflight[i], sizeof(SrvReq), cudaMemcpyDeviceToHost, ps);
+      }
       cudaStreamSynchronize(ps);
       cudaStreamDestroy(ps);
     }
@@ -1110,7 +1116,12 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     msg += "; units_pub " + std::to_string(dv[0]) + " claimed " + std::to_string(dv[1]) + " req_pub " +
            std::to_string(dv[2]) + " admitted " + std::to_string(next_admit) + " completed " + std::to_string(completed) +
            " of " + std::to_string(n) + " flags stop/abort/bad " + std::to_string(dv[3]) + "/" + std::to_string(dv[4]) +
-           "/" + std::to_string(dv[5]);
+           "/" + std::to_string(dv[5]) + " threads exited " + std::to_string(dv[6]) + " of " +
+           std::to_string(n_warps * 32) + "; pending:";
+    for (size_t i = 0; i < stuck_req.size(); ++i)
+      msg += " [r" + std::to_string(inflight[i]) + " kind " + std::to_string(stuck_req[i].kind) + " done " +
+             std::to_string(stuck_req[i].done) + "/" + std::to_string(stuck_req[i].need) + " units " +
+             std::to_string(stuck_req[i].U) + "+" + std::to_string(stuck_req[i].N) + "]";
     in->last_err = msg;
     fprintf(stderr, "hicr_serve_run: %s\n", msg.c_str());
     fflush(stderr);

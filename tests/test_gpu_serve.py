@@ -18,7 +18,7 @@ from tests.gpu_util import h, inst  # noqa: F401
 pytestmark = pytest.mark.gpu
 
 SEED = 3
-T = 60_000_000_000
+T = 30_000_000_000
 
 
 def small_setup(h, inst, verify=True, budget=512 << 20):
