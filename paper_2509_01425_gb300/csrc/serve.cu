@@ -363,19 +363,34 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
     }
     u = __shfl_sync(FULLM, u, 0);
     ws_set(a, WS_COPY);
-    const unsigned long long hi = ld_acq(&a.ctl->req_pub.v);
-    unsigned long long r;
-    // fast path: the same or the next request as the previous unit (only
-    // published entries, read at L2)
-    ReqView rv;
-    if (hint < hi && (rv = load_req(a.req + hint), rv.U <= u && u < rv.U + rv.N)) {
-      r = hint;
-    } else if (hint + 1 < hi && (rv = load_req(a.req + hint + 1), rv.U <= u && u < rv.U + rv.N)) {
-      r = hint + 1;
-    } else {
-      r = srv_find(a, 0, hi, u, lane);
-      rv = load_req(a.req + r);
+    // Lane 0 alone reads the live request count and takes the decisions, then
+    // broadcasts them: lanes reading req_pub separately could see different
+    // values and split between the fast path and the warp-collective search.
+    unsigned long long hi = 0, r = 0;
+    int fast = 0;
+    if (lane == 0) {
+      hi = ld_acq(&a.ctl->req_pub.v);
+      // fast path: the same or the next request as the previous unit
+      if (hint < hi) {
+        const ReqView h0 = load_req(a.req + hint);
+        if (h0.U <= u && u < h0.U + h0.N) {
+          r = hint;
+          fast = 1;
+        }
+      }
+      if (!fast && hint + 1 < hi) {
+        const ReqView h1 = load_req(a.req + hint + 1);
+        if (h1.U <= u && u < h1.U + h1.N) {
+          r = hint + 1;
+          fast = 1;
+        }
+      }
     }
+    hi = __shfl_sync(FULLM, hi, 0);
+    fast = __shfl_sync(FULLM, fast, 0);
+    r = __shfl_sync(FULLM, r, 0);
+    if (!fast) r = srv_find(a, 0, hi, u, lane);  // every lane, same hi
+    const ReqView rv = load_req(a.req + r);      // published entry: the same for every lane
     hint = r;
     SrvReq* e = a.req + r;
     // self-check: a request outside this run or with an unknown template is
