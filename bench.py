@@ -48,6 +48,9 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--no-side", action="store_true", help="headline only (no plain/large/e2e/channels/CPU)")
     p.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU work for the oracle baseline")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="length of the serving trace (0 = skip)")
+    p.add_argument("--plain-serve-seconds", type=float, default=0.25,
+                   help="prefix of the serving trace replayed through the per-op plain form")
     p.add_argument("--scale", type=float, default=1.0,
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
     return p.parse_args(argv)
@@ -592,11 +595,20 @@ def run_ours(args):
                                                 "hicr_slot_counters_range per step"}
         side["spsc"] = bench_spsc(h, inst)
         side["mpsc"] = bench_mpsc(h, inst)
+        if args.serve_seconds > 0:
+            h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")
+            g = None
+            for sid in ids:  # the serving run allocates its own copy of the source slots
+                h.check(h.hicr_mem_free(inst, sid), "free")
+            ids = []
+            side["serving"] = bench_serve(h, inst, seconds=args.serve_seconds,
+                                          plain_seconds=args.plain_serve_seconds, seed=args.seed)
         line["side"] = side
         if world == 1 and rank == 0:
             line["cpu_baseline"] = cpu_baseline(args.seed, args.cpu_seconds)
 
-    h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")
+    if g is not None:
+        h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")
     h.check(h.hicr_finalize(inst), "finalize")
     if rank == 0:
         print(json.dumps(line), flush=True)
