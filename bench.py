@@ -541,7 +541,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": bytes_step / n_epochs,
                      "kernel": "k_copy", "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "launches_timed": launches},
-        "gpu_launches": args.steps * 3 * n_epochs,
+        "gpu_launches": args.steps * 2 * n_epochs,
         "clocks": clk,
     }
 

@@ -55,6 +55,8 @@ struct Scratch {
   unsigned long long* cstart = nullptr;  // [cap + 1]
   unsigned int* done = nullptr;          // [cap]
   BatchCtrl* ctrl = nullptr;
+  unsigned long long* tiles = nullptr;   // look-back words of the fused plan+scan, then a tile counter
+  uint64_t n_tiles = 0;                  // capacity of `tiles` (excluding the counter)
 };
 
 struct BatchArgs {

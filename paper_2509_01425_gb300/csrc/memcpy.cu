@@ -111,6 +111,126 @@ __global__ void __launch_bounds__(1024) k_scan(BatchArgs a) {
   }
 }
 
+// Fused plan + scan for the main path: one CTA per tile of PS_TILE ops
+// (tiles numbered in the order CTAs start, by an atomic counter). Each CTA
+// validates and costs its ops, scans them in the block and chains the tile
+// prefixes by decoupled look-back: a tile publishes its aggregate, sums
+// predecessors' aggregates until it reaches a published inclusive prefix,
+// then publishes its own inclusive prefix. Predecessors started earlier, so
+// the look-back always progresses; it is still bounded by a deadline. The
+// look-back words and the tile counter are zeroed before each batch (memset).
+// The last tile finishes the batch as k_scan does.
+static constexpr unsigned PS_THREADS = 256, PS_ITEMS = 8, PS_TILE = PS_THREADS * PS_ITEMS;
+static constexpr unsigned long long PS_AGG = 1ull << 62, PS_INC = 2ull << 62, PS_VAL = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long ps_ld_acq(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void ps_st_rel(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ps_time() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__global__ void __launch_bounds__(PS_THREADS) k_plan_scan(BatchArgs a, unsigned long long* tiles,
+                                                           unsigned long long n_tiles) {
+  __shared__ unsigned long long s_tile, s_prefix, s_warp[PS_THREADS / 32];
+  const unsigned t = threadIdx.x, lane = t & 31, w = t >> 5;
+  unsigned int* tile_ctr = reinterpret_cast<unsigned int*>(tiles + n_tiles);
+  if (t == 0) s_tile = atomicAdd(tile_ctr, 1u);
+  __syncthreads();
+  const unsigned long long tile = s_tile;
+  const unsigned long long n = a.count;
+  const unsigned long long i0 = tile * PS_TILE + (unsigned long long)t * PS_ITEMS;
+  unsigned long long c[PS_ITEMS];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < (int)PS_ITEMS; ++j) {
+    const unsigned long long i = i0 + j;
+    c[j] = 0;
+    if (i < n) {
+      const hicr_op_t op = a.ops[i];
+      const int st = dev_validate(a.dt, a.support, op);
+      if (st != HICR_OK) atomicMin(&a.ctrl->bad, (i << 8) | (unsigned long long)(-st));
+      c[j] = op.n + a.op_cost;
+      a.done[i] = 0;
+    }
+    sum += c[j];
+  }
+  // block exclusive scan of the per-thread sums
+  unsigned long long x = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(FULL, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __threadfence();  // this thread's validation results before the tile is published
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long acc = 0;
+    for (unsigned k = 0; k < PS_THREADS / 32; ++k) {
+      const unsigned long long v = s_warp[k];
+      s_warp[k] = acc;
+      acc += v;
+    }
+    const unsigned long long agg = acc;
+    unsigned long long prefix = 0;
+    if (tile == 0) {
+      ps_st_rel(&tiles[0], PS_INC | agg);
+    } else {
+      ps_st_rel(&tiles[tile], PS_AGG | agg);
+      const unsigned long long deadline = ps_time() + 10000000000ull;
+      for (unsigned long long p = tile; p-- > 0;) {
+        unsigned long long v;
+        for (;;) {
+          v = ps_ld_acq(&tiles[p]);
+          if (v >> 62) break;
+          if (ps_time() > deadline) break;
+          __nanosleep(32);
+        }
+        if (!(v >> 62)) {  // predecessor never published: fail the batch, do not hang
+          atomicMin(&a.ctrl->bad, (0ull << 8) | (unsigned long long)(-HICR_ERR_TIMEOUT));
+          break;
+        }
+        prefix += v & PS_VAL;
+        if ((v >> 62) == 2) break;
+      }
+      ps_st_rel(&tiles[tile], PS_INC | (prefix + agg));
+    }
+    s_prefix = prefix;
+    s_tile = agg;  // reuse: the tile aggregate
+  }
+  __syncthreads();
+  unsigned long long run = s_prefix + s_warp[w] + (x - sum);
+#pragma unroll
+  for (int j = 0; j < (int)PS_ITEMS; ++j) {
+    const unsigned long long i = i0 + j;
+    if (i < n) a.cstart[i] = run;
+    run += c[j];
+  }
+  const unsigned long long last = (n + PS_TILE - 1) / PS_TILE - 1;
+  if (tile == last && t == 0) {
+    const unsigned long long total = s_prefix + s_tile;
+    a.cstart[n] = total;
+    const unsigned long long bad = atomicAdd(&a.ctrl->bad, 0ull);
+    a.ctrl->total = total;
+    a.ctrl->claim = 0;
+    if (bad != NO_BAD) {
+      a.ctrl->nchunks = 0;
+      atomicCAS(a.dt.sticky, 0ull, bad);
+    } else {
+      a.ctrl->nchunks = (total + a.chunk - 1) / a.chunk;
+    }
+    a.ctrl->bad = NO_BAD;
+  }
+}
+
 __device__ __forceinline__ void op_complete(const BatchArgs& a, const hicr_op_t& op) {
   __threadfence();
   atomicAdd(&a.dt.sent[op.src], 1ull);
@@ -192,7 +312,10 @@ hicr_status ensure_scratch(Instance* in, uint64_t count) {
   HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
   if (in->scratch.cost) cudaFree(in->scratch.cost);
   in->scratch = Scratch();
-  const size_t bytes = cap * 8 + (cap + 1) * 8 + cap * 4 + 64 + sizeof(BatchCtrl);
+  const uint64_t n_tiles = (cap + PS_TILE - 1) / PS_TILE + 1;
+  const size_t ctrl_off = ((cap * 8 + (cap + 1) * 8 + cap * 4 + 63) / 64) * 64;
+  const size_t tiles_off = ((ctrl_off + sizeof(BatchCtrl) + 255) / 256) * 256;
+  const size_t bytes = tiles_off + (n_tiles + 1) * 8;
   char* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
   if (e == cudaErrorMemoryAllocation) {
@@ -204,7 +327,9 @@ hicr_status ensure_scratch(Instance* in, uint64_t count) {
   in->scratch.cost = (unsigned long long*)p;
   in->scratch.cstart = (unsigned long long*)(p + cap * 8);
   in->scratch.done = (unsigned int*)(p + cap * 8 + (cap + 1) * 8);
-  in->scratch.ctrl = (BatchCtrl*)(p + ((cap * 8 + (cap + 1) * 8 + cap * 4 + 63) / 64) * 64);
+  in->scratch.ctrl = (BatchCtrl*)(p + ctrl_off);
+  in->scratch.tiles = (unsigned long long*)(p + tiles_off);
+  in->scratch.n_tiles = n_tiles;
   BatchCtrl init;
   init.claim = 0;
   init.nchunks = 0;
@@ -253,9 +378,9 @@ hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, c
   hicr_status s = ensure_scratch(in, count);
   if (s != HICR_OK) return s;
   BatchArgs a = make_args(in, d_ops, count);
-  const unsigned pb = (unsigned)((count + 255) / 256);
-  k_plan<<<pb, 256, 0, st>>>(a);
-  k_scan<<<1, 1024, 0, st>>>(a);
+  const unsigned long long nt = (count + PS_TILE - 1) / PS_TILE;
+  HICR_CUDA(in, cudaMemsetAsync(in->scratch.tiles, 0, (in->scratch.n_tiles + 1) * 8, st));
+  k_plan_scan<<<(unsigned)nt, PS_THREADS, 0, st>>>(a, in->scratch.tiles, in->scratch.n_tiles);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (in->prof) {
     if ((s = prof_event(in, &e0)) != HICR_OK) return s;
