@@ -238,6 +238,13 @@ hicr_status hicr_batch_error(hicr_instance_t inst, hicr_status* status, uint64_t
  * before capturing graphs; grows automatically otherwise). */
 hicr_status hicr_batch_reserve(hicr_instance_t inst, uint64_t max_ops);
 
+/* Memory-space pairs the communication manager accepts (Sec. 3.1.4: a
+ * memcpy is initiated when the manager supports the pair of spaces and
+ * rejected otherwise). Default: HBM <- HBM only. With host copies on, every
+ * pair of HBM and HOST (page-locked Grace memory, reached by the copy
+ * kernels over NVLink-C2C) is accepted. Errors: INVALID. */
+hicr_status hicr_set_host_copies(hicr_instance_t inst, int32_t on);
+
 /* Checked mode: hicr_memcpy_batch and the hicr_memcpy queue also reject
  * cross-op hazards within one epoch (O(k log k) host check). Default off. */
 hicr_status hicr_set_checked(hicr_instance_t inst, int32_t on);

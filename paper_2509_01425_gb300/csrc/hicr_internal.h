@@ -169,6 +169,9 @@ hicr_status check_config(const Instance* in, const hicr_batch_config_t* c);
 // channels.cu
 void destroy_channels(Instance* in);
 
+// dataobject.cu
+void forget_data_objects(const Instance* in);
+
 inline uint64_t now_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
              std::chrono::steady_clock::now().time_since_epoch())

@@ -234,6 +234,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
   }
   cudaDeviceSynchronize();
   destroy_channels(in);
+  forget_data_objects(in);
   for (auto& g : in->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
@@ -510,6 +511,18 @@ hicr_status hicr_batch_error(hicr_instance_t h, hicr_status* status, uint64_t* f
   }
   if (status) *status = v ? -(hicr_status)(v & 0xFF) : HICR_OK;
   if (first_bad) *first_bad = v ? (v >> 8) : 0;
+  return HICR_OK;
+}
+
+hicr_status hicr_set_host_copies(hicr_instance_t h, int32_t on) {
+  Instance* in = I(h);
+  if (!in || in->capturing) return HICR_ERR_INVALID;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  const uint32_t hbm = 1u << (HICR_SPACE_HBM * 8 + HICR_SPACE_HBM);
+  const uint32_t host = (1u << (HICR_SPACE_HBM * 8 + HICR_SPACE_HOST)) | (1u << (HICR_SPACE_HOST * 8 + HICR_SPACE_HBM)) |
+                        (1u << (HICR_SPACE_HOST * 8 + HICR_SPACE_HOST));
+  in->support = on ? (hbm | host) : hbm;
   return HICR_OK;
 }
 

@@ -132,6 +132,7 @@ _memcpy_batch_noalloc = _decl("hicr_memcpy_batch_noalloc", [H, vp, u64])
 _batch_error = _decl("hicr_batch_error", [H, C.POINTER(i32), C.POINTER(u64)])
 _batch_reserve = _decl("hicr_batch_reserve", [H, u64])
 _set_checked = _decl("hicr_set_checked", [H, i32])
+_set_host_copies = _decl("hicr_set_host_copies", [H, i32])
 _fence = _decl("hicr_fence", [H, u32, u64])
 _fence_slot = _decl("hicr_fence_slot", [H, u32, u64, u64, u64])
 _slot_counters = _decl("hicr_slot_counters", [H, u32, C.POINTER(u64), C.POINTER(u64)])
@@ -270,6 +271,17 @@ def hicr_batch_reserve(inst, max_ops):
 
 def hicr_set_checked(inst, on):
     return _set_checked(inst, 1 if on else 0)
+
+
+def hicr_set_host_copies(inst, on):
+    return _set_host_copies(inst, 1 if on else 0)
+
+
+def host_bytes(ptr, nbytes):
+    """numpy uint8 view of host memory [ptr, ptr+nbytes) (no copy)."""
+    if nbytes == 0:
+        return np.zeros(0, dtype=np.uint8)
+    return np.ctypeslib.as_array((C.c_uint8 * nbytes).from_address(ptr))
 
 
 def hicr_fence(inst, tag=0, timeout_ns=30_000_000_000):
@@ -608,3 +620,36 @@ def hicr_serve_digests(inst, srv, reqs, results):
     reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
     st = _serve_digests(inst, srv, reqs.ctypes.data, len(reqs), results.ctypes.data)
     return st
+
+
+# ---------------------------------------------------------------------------
+# Data Object frontend (include/hicr_dataobject.h)
+# ---------------------------------------------------------------------------
+class hicr_dobj_handle_t(C.Structure):
+    _fields_ = [("id", u64), ("size", u64), ("space", u32), ("instance", u32)]
+
+
+_dobj_publish = _decl("hicr_dobj_publish", [H, u32, u64, u64, C.POINTER(u64)])
+_dobj_get_handle = _decl("hicr_dobj_get_handle", [H, u64, C.POINTER(hicr_dobj_handle_t)])
+_dobj_get = _decl("hicr_dobj_get", [H, C.POINTER(hicr_dobj_handle_t), u32, u64])
+_dobj_release = _decl("hicr_dobj_release", [H, u64])
+
+
+def hicr_dobj_publish(inst, slot, off, n):
+    i = u64()
+    st = _dobj_publish(inst, slot, off, n, C.byref(i))
+    return st, i.value
+
+
+def hicr_dobj_get_handle(inst, obj_id):
+    hd = hicr_dobj_handle_t()
+    st = _dobj_get_handle(inst, obj_id, C.byref(hd))
+    return st, hd
+
+
+def hicr_dobj_get(inst, handle, dst, dst_off):
+    return _dobj_get(inst, C.byref(handle), dst, dst_off)
+
+
+def hicr_dobj_release(inst, obj_id):
+    return _dobj_release(inst, obj_id)
