@@ -281,6 +281,29 @@ def bench_spsc(h, inst, reps=3):
             "bound": "L2 + handoff latency (rings total 16 MiB, L2-resident)"}
 
 
+def bench_pingpong(h, inst):
+    """Test Case 1 on one GPU: goodput G(s) and one-way time over two opposing
+    single-message SPSC channels, 1 B - 2 GiB, 10 timed round trips each."""
+    top = 2 << 30
+    sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, top), "alloc")
+    h.check(h.hicr_util_fill(inst, sid, 0, top, splitmix.fill_key_base(0, 999)), "fill")
+    rows = []
+    for e in range(0, 32, 3):
+        nbytes = min(1 << e, top)
+        ctas = 1 if nbytes <= (64 << 10) else (16 if nbytes <= (16 << 20) else 64)
+        st, r = h.hicr_pingpong(inst, sid, 0, nbytes, 10, 2, ctas)
+        h.check(st, "pingpong")
+        rows.append({"bytes": nbytes, "ctas_per_side": ctas, "one_way_us": r.half_rtt_ns / 1e3,
+                     "goodput_GB_per_s": r.goodput_gbs})
+    st, r = h.hicr_pingpong(inst, sid, 0, top, 10, 2, 64)
+    h.check(st, "pingpong")
+    rows.append({"bytes": top, "ctas_per_side": 64, "one_way_us": r.half_rtt_ns / 1e3,
+                 "goodput_GB_per_s": r.goodput_gbs})
+    h.check(h.hicr_mem_free(inst, sid), "free")
+    return {"workload": "ping-pong over two opposing capacity-1 SPSC channels (paper Test Case 1), "
+                        "10 timed round trips after 2 warm-up, one agent = 1-64 CTAs", "curve": rows}
+
+
 def bench_mpsc(h, inst, reps=3, group=4):
     """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB, 1 GiB rings."""
     w = configs.mpsc(0)
@@ -594,6 +617,7 @@ def run_ours(args):
                        "steps": esteps, "call": "hicr_memcpy_batch (host ops) + hicr_fence per epoch, "
                                                 "hicr_slot_counters_range per step"}
         side["spsc"] = bench_spsc(h, inst)
+        side["pingpong"] = bench_pingpong(h, inst)
         side["mpsc"] = bench_mpsc(h, inst)
         if args.serve_seconds > 0:
             h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")

@@ -160,6 +160,34 @@ hicr_status hicr_mpsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, 
                              uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
                              hicr_mpsc_result_t* results);
 
+/* ------------------------------------------------------------------------ */
+/* Ping-pong over two opposing single-message SPSC channels (HiCR paper      */
+/* Sec. 5.1, Test Case 1, restated for one GPU).                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint64_t bytes;          /* message size */
+  uint32_t reps;           /* timed round trips */
+  uint32_t ctas_per_side;  /* CTAs of each agent */
+  double half_rtt_ns;      /* device time of one direction (round trip / 2) */
+  double goodput_gbs;      /* bytes / half_rtt, GB/s (the paper's G(s)) */
+  uint64_t digest_a;       /* word digest of agent A's buffer after the run */
+  uint64_t digest_b;       /* word digest of agent B's buffer after the run */
+  int32_t status;          /* HICR_OK or HICR_ERR_TIMEOUT */
+  uint32_t reserved;
+} hicr_pingpong_result_t;
+
+/* Agent A sends bytes [src_off, src_off+bytes) of slot `src` into agent B's
+ * single-message buffer; B echoes the message into A's buffer; repeat. Each
+ * buffer holds exactly one message at the consumer, so a sender never has
+ * more than one message outstanding. Each agent is `ctas_per_side` CTAs (1 ..
+ * 64) of one cooperative grid that copy equal shares; a side's arrival count
+ * is the channel head the other side acquires. `warmup` untimed round trips
+ * come first. After the run both buffers must hold the message (the digests
+ * let the caller check). Every wait gives up after timeout_ns.
+ * Errors: INVALID, BOUNDS, NOMEM, DEVICE, TIMEOUT. */
+hicr_status hicr_pingpong(hicr_instance_t inst, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
+                          uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -482,6 +482,21 @@ _spsc_stream = _decl("hicr_spsc_stream", [H, vp, u32, u64, u32, u64, vp])
 _mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u64, vp, u64, vp])
 
 
+class hicr_pingpong_result_t(C.Structure):
+    _fields_ = [("bytes", u64), ("reps", u32), ("ctas_per_side", u32), ("half_rtt_ns", C.c_double),
+                ("goodput_gbs", C.c_double), ("digest_a", u64), ("digest_b", u64), ("status", i32),
+                ("reserved", u32)]
+
+
+_pingpong = _decl("hicr_pingpong", [H, u32, u64, u64, u32, u32, u32, u64, C.POINTER(hicr_pingpong_result_t)])
+
+
+def hicr_pingpong(inst, src, src_off, nbytes, reps=10, warmup=2, ctas_per_side=1, timeout_ns=30_000_000_000):
+    r = hicr_pingpong_result_t()
+    st = _pingpong(inst, src, src_off, nbytes, reps, warmup, ctas_per_side, timeout_ns, C.byref(r))
+    return st, r
+
+
 def hicr_spsc_create(inst, token_size, capacity):
     c = u32()
     st = _spsc_create(inst, token_size, capacity, C.byref(c))

@@ -200,3 +200,18 @@ def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, 
     for ch in run.chans:
         assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
     run.free()
+
+
+@pytest.mark.parametrize("nbytes,ctas", [(1, 1), (17, 1), (4096, 2), ((1 << 20) + 3, 8), (64 << 20, 32)])
+def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
+    """Test Case 1 restated on one GPU: after the round trips both
+    single-message buffers hold exactly the message (oracle digest)."""
+    size = nbytes + 100
+    st, s = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
+    assert h.hicr_util_fill(inst, s, 0, size, splitmix.fill_key_base(5, 1)) == 0
+    st, r = h.hicr_pingpong(inst, s, 7, nbytes, reps=10, warmup=2, ctas_per_side=ctas)
+    assert st == 0 and r.status == 0
+    exp = od.byte_digest(splitmix.fill_bytes(5, 1, 7, nbytes))
+    assert r.digest_a == exp and r.digest_b == exp
+    assert r.half_rtt_ns > 0 and r.goodput_gbs > 0
+    assert h.hicr_pingpong(inst, s, 200, size, 1, 0, 1)[0] == h.HICR_ERR_BOUNDS
