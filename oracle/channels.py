@@ -200,3 +200,79 @@ def check_mpsc_log(workload_sizes, n_consumers: int, consumer: int, log, ring_by
     if bad:
         problems.append(f"{len(bad)} ring offsets differ from the reservation rule (first ticket {bad[0]})")
     return problems
+
+
+class MpscNonLockingOracle:
+    """Non-locking MPSC (Sec. 4.3): one ring per producer, no shared exclusive
+    access. Each producer ring follows the placement rule of MpscOracle
+    (16-byte rounding, skip to the start, capacity per ring). Reading for the
+    host calls: the consumer drains producers in index order, each producer's
+    messages oldest first, so peek(k) is the k-th message of that order."""
+
+    def __init__(self, n_producers: int, ring_bytes: int, max_msgs: int):
+        self.rings = [MpscOracle(1, ring_bytes, max_msgs) for _ in range(n_producers)]
+
+    def push(self, producer: int, payload: np.ndarray) -> int:
+        if producer < 0 or producer >= len(self.rings):
+            return ERR_INVALID
+        return self.rings[producer].push(0, payload)
+
+    def _locate(self, k: int):
+        for p, r in enumerate(self.rings):
+            d = r.depth()[0]
+            if k < d:
+                return p, k
+            k -= d
+        return None
+
+    def peek(self, k: int):
+        loc = self._locate(k)
+        if loc is None:
+            return ERR_EMPTY, None
+        p, j = loc
+        st, (off, n, _, s) = self.rings[p].peek(j)
+        return OK, (off, n, p, s)
+
+    def payload(self, k: int) -> np.ndarray:
+        p, j = self._locate(k)
+        return self.rings[p].payload(j)
+
+    def pop(self, count: int) -> int:
+        if count > self.depth()[0]:
+            return ERR_EMPTY
+        for r in self.rings:
+            take = min(count, r.depth()[0])
+            r.pop(take)
+            count -= take
+        return OK
+
+    def depth(self):
+        m = sum(r.depth()[0] for r in self.rings)
+        b = sum(r.depth()[1] for r in self.rings)
+        return m, b
+
+
+def check_mpsc_nl_log(workload_sizes, n_consumers: int, consumer: int, log, ring_bytes: int):
+    """Interleaving-agnostic check of one non-locking consumer's log
+    (producer, seq, size, ring offset) in consumption order: every message of
+    the consumer's producers exactly once, each producer in push order, sizes
+    equal, and each producer's offsets equal the placement rule replayed over
+    that producer's own ring."""
+    problems = []
+    P, M = workload_sizes.shape
+    per = {}
+    for t, (p, s, n, off) in enumerate(log):
+        per.setdefault(int(p), []).append((int(s), int(n), int(off), t))
+    mine = list(range(consumer, P, n_consumers))
+    if sorted(per) != mine:
+        problems.append(f"producers seen {sorted(per)[:5]}... expected {mine[:5]}...")
+    for p in mine:
+        lst = per.get(p, [])
+        if [x[0] for x in lst] != list(range(M)):
+            problems.append(f"producer {p}: sequence numbers {[x[0] for x in lst][:8]}... not 0..{M - 1} in order")
+            continue
+        if [x[1] for x in lst] != [int(v) for v in workload_sizes[p]]:
+            problems.append(f"producer {p}: sizes differ")
+        if [x[2] for x in lst] != replay_offsets([x[1] for x in lst], ring_bytes):
+            problems.append(f"producer {p}: ring offsets differ from the placement rule")
+    return problems

@@ -226,3 +226,46 @@ def test_mpsc_planted_mistakes_are_caught(mutant):
     except (AssertionError, ValueError, IndexError):
         mism = ["raised"]
     assert mism
+
+
+def test_nonlocking_reduces_to_per_producer_fifos():
+    rng = np.random.default_rng(21)
+    P, R, M = 3, 1024, 8
+    ch = oc.MpscNonLockingOracle(P, R, M)
+    refs = [deque() for _ in range(P)]
+    for step in range(3000):
+        if rng.random() < 0.55:
+            p = int(rng.integers(0, P))
+            n = int(rng.integers(0, 300))
+            payload = rng.integers(0, 256, n, dtype=np.uint8)
+            st = ch.push(p, payload)
+            if st == om.OK:
+                refs[p].append(bytes(payload))
+            else:
+                assert st in (om.ERR_FULL, om.ERR_TOO_LARGE)
+        else:
+            flat = [m for r in refs for m in r]
+            k = int(rng.integers(0, 4))
+            if k < len(flat):
+                assert bytes(ch.payload(k)) == flat[k]
+            c = int(rng.integers(0, 3))
+            st = ch.pop(c)
+            if c <= len(flat):
+                assert st == om.OK
+                for _ in range(c):  # remove in index order
+                    for r in refs:
+                        if r:
+                            r.popleft()
+                            break
+            else:
+                assert st == om.ERR_EMPTY
+        assert ch.depth()[0] == sum(len(r) for r in refs)
+
+
+def test_check_mpsc_nl_log():
+    sizes = np.array([[10, 20], [30, 40], [50, 60], [70, 80]])
+    log = [(0, 0, 10, 0), (2, 0, 50, 0), (0, 1, 20, 16), (2, 1, 60, 64)]
+    assert oc.check_mpsc_nl_log(sizes, 2, 0, log, 128) == []
+    bad = [log[2], log[1], log[0], log[3]]
+    assert oc.check_mpsc_nl_log(sizes, 2, 0, bad, 128)
+    assert oc.check_mpsc_nl_log(sizes, 2, 0, log[:3], 128)
