@@ -211,9 +211,10 @@ class MpscRun:
     message's seeded payload (16-byte aligned, packed), device size / offset
     tables, one channel per consumer and a device log."""
 
-    def __init__(self, h, inst, w, group=4):
+    def __init__(self, h, inst, w, group=4, nonlocking=False, consumer_ctas=1, ring_bytes=None, max_msgs=None):
         import torch
         self.h, self.inst, self.w, self.group = h, inst, w, group
+        self.nonlocking, self.consumer_ctas = nonlocking, consumer_ctas
         P, M = w.sizes.shape
         C = w.n_consumers
         sizes = w.sizes.reshape(-1).astype(np.uint64)
@@ -232,13 +233,33 @@ class MpscRun:
         per = -(-P // C)
         self.stride = per * M
         self.d_log = torch.empty(C * self.stride * 32, dtype=torch.uint8, device="cuda")
-        self.chans = [h.check(h.hicr_mpsc_create(inst, per, w.ring_bytes, w.max_msgs), "mpsc_create")
-                      for _ in range(C)]
+        self.chans = []
+        self.set_mode(nonlocking, consumer_ctas, ring_bytes, max_msgs)
         torch.cuda.synchronize()
         del d_seg
 
+    def set_mode(self, nonlocking, consumer_ctas=1, ring_bytes=None, max_msgs=None):
+        """(Re)create the channels: locking mode with one shared ring per
+        consumer, or non-locking mode with one ring per producer (by default
+        the locking ring and metadata capacity split evenly, so both modes
+        hold the same memory)."""
+        h, w = self.h, self.w
+        per = -(-w.sizes.shape[0] // w.n_consumers)
+        for c in self.chans:
+            h.check(h.hicr_channel_destroy(self.inst, c), "channel_destroy")
+        self.nonlocking, self.consumer_ctas = nonlocking, consumer_ctas
+        self.ring_bytes = ring_bytes or (w.ring_bytes // per if nonlocking else w.ring_bytes)
+        self.max_msgs = max_msgs or (max(w.max_msgs // per, 1) if nonlocking else w.max_msgs)
+        create = h.hicr_mpsc_nl_create if nonlocking else h.hicr_mpsc_create
+        self.chans = [h.check(create(self.inst, per, self.ring_bytes, self.max_msgs), "mpsc_create")
+                      for _ in range(w.n_consumers)]
+
     def run(self, timeout_ns=60_000_000_000):
         P, M = self.w.sizes.shape
+        if self.nonlocking:
+            return self.h.hicr_mpsc_nl_stream(self.inst, self.chans, P, M, self.d_sizes.data_ptr(),
+                                              self.d_offs.data_ptr(), self.staging, self.group, self.consumer_ctas,
+                                              self.d_log.data_ptr(), self.stride, timeout_ns)
         return self.h.hicr_mpsc_stream(self.inst, self.chans, P, M, self.d_sizes.data_ptr(), self.d_offs.data_ptr(),
                                        self.staging, self.group, self.d_log.data_ptr(), self.stride, timeout_ns)
 
@@ -304,10 +325,7 @@ def bench_pingpong(h, inst):
                         "10 timed round trips after 2 warm-up, one agent = 1-64 CTAs", "curve": rows}
 
 
-def bench_mpsc(h, inst, reps=3, group=4):
-    """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB, 1 GiB rings."""
-    w = configs.mpsc(0)
-    run = MpscRun(h, inst, w, group=group)
+def _time_mpsc(h, run, reps):
     h.check(run.run()[0], "mpsc warm-up")
     times = []
     for _ in range(reps):
@@ -315,15 +333,32 @@ def bench_mpsc(h, inst, reps=3, group=4):
         st, res = run.run()
         times.append(time.perf_counter() - t0)
         h.check(st, "mpsc_stream")
-    cap_ok = all(int(r.max_inflight_bytes) <= w.ring_bytes for r in res)
-    run.free()
+    cap_ok = all(int(r.max_inflight_bytes) <= run.ring_bytes and int(r.max_inflight_msgs) <= run.max_msgs
+                 for r in res)
     t = statistics.median(times)
-    msgs = w.sizes.size
-    nbytes = w.total_bytes
-    return {"workload": "1,024 producers -> 16 consumers, 1,024 msgs each, log-uniform 8 B-256 KiB, 1 GiB rings",
-            "msgs_per_s": msgs / t, "payload_GB_per_s": nbytes / t / 1e9,
-            "algorithmic_GB_per_s": 3 * nbytes / t / 1e9, "s_per_run": t, "capacity_respected": cap_ok,
-            "group": group}
+    return {"msgs_per_s": run.w.sizes.size / t, "payload_GB_per_s": run.w.total_bytes / t / 1e9,
+            "algorithmic_GB_per_s": 3 * run.w.total_bytes / t / 1e9, "s_per_run": t, "capacity_respected": cap_ok}
+
+
+def bench_mpsc(h, inst, reps=3, group=4):
+    """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB: locking
+    mode over one 1 GiB ring per consumer against non-locking mode over 64
+    rings of 16 MiB per consumer (the same memory), the latter with 1, 2 or 4
+    CTAs per consumer."""
+    w = configs.mpsc(0)
+    run = MpscRun(h, inst, w, group=group)
+    out = {"workload": "1,024 producers -> 16 consumers, 1,024 msgs each, log-uniform 8 B-256 KiB, 1 GiB rings",
+           **_time_mpsc(h, run, reps), "group": group}
+    by = {}
+    for g in (1, 2, 4):
+        run.set_mode(True, g)
+        by[g] = _time_mpsc(h, run, reps)
+    best = max(by, key=lambda g: by[g]["msgs_per_s"])
+    out["nonlocking"] = {"rings": f"64 x {run.ring_bytes >> 20} MiB per consumer, {run.max_msgs} msgs each",
+                         **by[best], "consumer_ctas": best,
+                         "msgs_per_s_by_consumer_ctas": {str(g): by[g]["msgs_per_s"] for g in by}}
+    run.free()
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -57,6 +57,19 @@ hicr_status hicr_spsc_create(hicr_instance_t inst, uint32_t token_size, uint32_t
 hicr_status hicr_mpsc_create(hicr_instance_t inst, uint32_t n_producers, uint64_t ring_bytes,
                              uint32_t max_msgs, hicr_channel_t* out);
 
+/* MPSC channel in non-locking mode (Sec. 4.3: a dedicated buffer per
+ * producer, no collective exclusive access, more memory): `n_producers`
+ * rings of `ring_bytes` each (power of two) with `max_msgs` metadata entries
+ * each (power of two, 1 .. 2^23), ring_bytes 64 B .. 2^39 and n_producers
+ * * ring_bytes <= 2^40. Ring p starts at byte p * ring_bytes of the channel's
+ * ring slot and follows the placement rule of the locking mode on its own.
+ * Host pops and peeks see the consumer order "producers in index order, each
+ * producer's messages oldest first"; peek reports offsets within the
+ * producer's ring. Device consumers poll the rings (hicr_mpsc_nl_stream).
+ * Errors: INVALID, NOMEM, DEVICE. */
+hicr_status hicr_mpsc_nl_create(hicr_instance_t inst, uint32_t n_producers, uint64_t ring_bytes,
+                                uint32_t max_msgs, hicr_channel_t* out);
+
 /* Free a channel's device memory. Errors: INVALID. */
 hicr_status hicr_channel_destroy(hicr_instance_t inst, hicr_channel_t ch);
 
@@ -69,8 +82,8 @@ hicr_status hicr_channel_ring(hicr_instance_t inst, hicr_channel_t ch, hicr_slot
  *  SPSC: `n` tokens (n * token_size bytes), all or nothing; FULL when fewer
  *        than n tokens are free. `producer` must be 0.
  *  MPSC: one message of `n` bytes from producer `producer`; FULL when the
- *        placement rule finds no room, TOO_LARGE when the rounded size
- *        exceeds the ring.
+ *        placement rule finds no room (non-locking: in the producer's own
+ *        ring), TOO_LARGE when the rounded size exceeds the ring.
  * Errors: INVALID (bad channel/producer/slot), BOUNDS (off + bytes > slot
  * size), UNSUPPORTED (source not in HBM), FULL, TOO_LARGE, DEVICE. */
 hicr_status hicr_channel_push(hicr_instance_t inst, hicr_channel_t ch, uint32_t producer, hicr_slot_t src,
@@ -159,6 +172,24 @@ hicr_status hicr_mpsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, 
                              const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
                              uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
                              hicr_mpsc_result_t* results);
+
+/* The streaming run of hicr_mpsc_stream for non-locking channels (created
+ * with hicr_mpsc_nl_create with at least ceil(n_producers / n_consumers)
+ * producers each). Producer p (one warp) uses ring p / n_consumers of channel
+ * p mod n_consumers; it reserves up to `group` messages (rounded sizes
+ * summing to at most half a ring) at a time in its own ring, copies them and
+ * publishes them with one release store, without any shared reservation.
+ * Consumer c runs on `consumer_ctas` CTAs whose warps each own a fixed
+ * subset of the channel's rings (at most 32 per warp) and drain whichever of
+ * them hold published messages. Logs are in consumption order (each
+ * producer's messages in push order; the interleaving of producers is
+ * arbitrary). Other arguments, results and errors as hicr_mpsc_stream
+ * (cas_failures is 0); INVALID also when the grid cannot be co-resident. */
+hicr_status hicr_mpsc_nl_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
+                                uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                uint64_t log_stride, hicr_mpsc_result_t* results);
 
 /* ------------------------------------------------------------------------ */
 /* Ping-pong over two opposing single-message SPSC channels (HiCR paper      */

@@ -15,6 +15,13 @@
 //         of the memcpy path and publishes the entry with a release store of
 //         `ready`. The consumer drains tickets in order and frees with
 //         release stores.
+//   MPSC non-locking (a dedicated ring per producer): producer i of the
+//         channel owns ring i, its metadata ring and the counters reserve
+//         (bytes reserved), pub (messages published) -- written only by the
+//         producer -- and freed / cons, written only by the consumer. No
+//         compare-and-swap: a producer places its messages with the same
+//         rule in its own ring and publishes them with one release store of
+//         pub; 64-bit absolute counters.
 // Ring bytes and max_msgs are powers of two, so positions modulo 2^40 and
 // tickets modulo 2^24 map consistently onto the rings.
 //
@@ -35,7 +42,7 @@
 namespace hicr {
 
 struct Channel {
-  int kind = 0;  // 0 SPSC, 1 MPSC
+  int kind = 0;  // 0 SPSC, 1 MPSC (locking), 2 MPSC (non-locking)
   bool live = false;
   uint32_t token_size = 0, capacity = 0;
   uint32_t n_producers = 0, max_msgs = 0;
@@ -216,6 +223,136 @@ __global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb
 }
 
 // ---------------------------------------------------------------------------
+// Non-locking MPSC layout and host-call kernels.
+// ---------------------------------------------------------------------------
+struct NlState {
+  Line reserve;  // bytes reserved (absolute, including skipped bytes); producer
+  Line pub;      // messages published; producer
+  Line freed;    // bytes freed; consumer
+  Line cons;     // messages consumed; consumer
+};
+struct NlHead {
+  Line max_bytes;  // high-water marks of reserved-minus-freed / in-flight
+  Line max_msgs;   // messages over the channel's rings (streaming runs)
+};
+struct NlMeta {
+  unsigned long long start;  // absolute reservation start
+  unsigned int size;
+  unsigned int seq;
+};
+static_assert(sizeof(NlMeta) == 16, "non-locking metadata entry is 16 bytes");
+struct NlView {
+  uint8_t* ring;  // ring i at ring + i * R
+  NlHead* head;
+  NlState* st;    // st[i]
+  NlMeta* meta;   // ring i's entries at meta + i * M
+  unsigned long long R;
+  unsigned int M;
+  unsigned int P;
+};
+
+// Placement of k messages with rounded sizes r[] from absolute position b
+// (the locking mode's rule on one ring, without the ticket packing).
+__device__ __forceinline__ unsigned long long nl_place(unsigned long long b, const unsigned long long* r, int k,
+                                                        unsigned long long R, unsigned long long* start) {
+  for (int i = 0; i < k; ++i) {
+    const unsigned long long pos = b & (R - 1);
+    if (pos + r[i] > R) b += R - pos;
+    start[i] = b;
+    b += r[i];
+  }
+  return b;
+}
+
+__global__ void k_nl_push_host(NlView v, unsigned int producer, unsigned int seq, const uint8_t* src,
+                               unsigned long long n, Mailbox* mb) {
+  __shared__ unsigned long long s_start, s_pub;
+  __shared__ int s_ok;
+  NlState* st = v.st + producer;
+  if (threadIdx.x == 0) {
+    const unsigned long long r = round16(n);
+    unsigned long long start;
+    const unsigned long long end = nl_place(ld_rlx(&st->reserve.v), &r, 1, v.R, &start);
+    const unsigned long long pub = ld_rlx(&st->pub.v);
+    const unsigned long long freed = ld_acq(&st->freed.v), cons = ld_acq(&st->cons.v);
+    s_ok = end - freed <= v.R && pub + 1 - cons <= v.M;
+    s_start = start;
+    s_pub = pub;
+  }
+  __syncthreads();
+  if (!s_ok) {
+    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    return;
+  }
+  uint8_t* ring = v.ring + (unsigned long long)producer * v.R;
+  cta_copy(ring + (s_start & (v.R - 1)), src, n);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NlMeta* e = v.meta + (unsigned long long)producer * v.M + (s_pub & (v.M - 1));
+    e->start = s_start;
+    e->size = (unsigned int)n;
+    e->seq = seq;
+    st_rel(&st->reserve.v, s_start + round16(n));
+    __threadfence();
+    st_rel(&st->pub.v, s_pub + 1);
+    mb->v[0] = s_start & (v.R - 1);
+    mb->v[1] = s_pub;
+    mb->status = HICR_OK;
+  }
+}
+
+// op 0 = peek(k), 1 = pop(k), 2 = depth; the consumer order is "producers in
+// index order, each producer's messages oldest first". One thread.
+__global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) {
+  unsigned long long msgs = 0, bytes = 0;
+  for (unsigned p = 0; p < v.P; ++p) {
+    const NlState* st = v.st + p;
+    msgs += ld_acq(&st->pub.v) - ld_acq(&st->cons.v);
+    bytes += ld_acq(&st->reserve.v) - ld_acq(&st->freed.v);
+  }
+  if (op == 2) {
+    mb->v[0] = msgs;
+    mb->v[1] = bytes;
+    mb->status = HICR_OK;
+    return;
+  }
+  if (op == 0 ? k >= msgs : k > msgs) {
+    mb->status = HICR_ERR_EMPTY;
+    return;
+  }
+  unsigned long long left = k;
+  for (unsigned p = 0; p < v.P; ++p) {
+    NlState* st = v.st + p;
+    const unsigned long long cons = ld_rlx(&st->cons.v);
+    const unsigned long long d = ld_acq(&st->pub.v) - cons;
+    const NlMeta* m = v.meta + (unsigned long long)p * v.M;
+    if (op == 0) {
+      if (left < d) {
+        const NlMeta* e = m + ((cons + left) & (v.M - 1));
+        mb->v[0] = __ldcg(&e->start) & (v.R - 1);
+        mb->v[1] = __ldcg(&e->size);
+        mb->v[2] = p;
+        mb->v[3] = __ldcg(&e->seq);
+        mb->status = HICR_OK;
+        return;
+      }
+      left -= d;
+    } else {
+      const unsigned long long take = left < d ? left : d;
+      if (take) {
+        const NlMeta* e = m + ((cons + take - 1) & (v.M - 1));
+        st_rel(&st->freed.v, __ldcg(&e->start) + round16(__ldcg(&e->size)));
+        st_rel(&st->cons.v, cons + take);
+        left -= take;
+      }
+      if (!left) break;
+    }
+  }
+  mb->status = HICR_OK;
+}
+
+// ---------------------------------------------------------------------------
 // SPSC streaming: CTA 2i produces into channel i, CTA 2i+1 consumes it.
 // ---------------------------------------------------------------------------
 struct SpscStreamArgs {
@@ -361,11 +498,12 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
     mt = ld_acq(&v.st->msg_tail.v);
   }
   for (unsigned s = 0; s < a.mpp;) {
-    // the group: up to `group` messages whose rounded sizes sum to <= R/2
+    // the group: up to `group` (and at most max_msgs) messages whose rounded
+    // sizes sum to <= R/2, so that it always fits an emptied ring
     unsigned long long r[MPSC_MAX_GROUP], st[MPSC_MAX_GROUP];
     int k = 0;
     unsigned long long sum = 0;
-    for (; k < (int)a.group && s + k < a.mpp; ++k) {
+    for (; k < (int)a.group && (unsigned)k < v.M && s + k < a.mpp; ++k) {
       const unsigned long long rk = round16(a.sizes[(unsigned long long)p * a.mpp + s + k]);
       if (k > 0 && sum + rk > half) break;
       r[k] = rk;
@@ -666,6 +804,253 @@ __global__ void k_mpsc_check(MpscStreamArgs a, unsigned long long staging_size, 
 }
 
 // ---------------------------------------------------------------------------
+// Non-locking MPSC streaming: CTAs [0, n_cons * G) consume (G per channel),
+// the rest hold one producer per warp; producer p uses ring p / n_cons of
+// channel p mod n_cons. Consumer warp w of the channel's G * W warps owns its
+// rings w, w + G*W, ... (at most 32: lane l keeps the counters of the l-th),
+// polls them and drains whichever hold published messages. No CTA barrier
+// anywhere, so each warp leaves on its own once its rings are drained.
+// ---------------------------------------------------------------------------
+struct NlStreamArgs {
+  const NlView* chans;
+  unsigned int n_cons;
+  unsigned int G;  // CTAs per consumer
+  unsigned int n_prod;
+  unsigned int mpp;
+  unsigned int group;
+  const unsigned long long* sizes;
+  const unsigned long long* src_off;
+  const uint8_t* staging;
+  unsigned long long timeout_ns;
+  hicr_mpsc_log_t* log;
+  unsigned long long log_stride;
+  unsigned long long* log_count;  // per consumer
+  hicr_mpsc_result_t* res;
+  unsigned int* abort;
+};
+
+__device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline) {
+  const unsigned c = p % a.n_cons, i = p / a.n_cons;
+  const NlView v = a.chans[c];
+  NlState* st = v.st + i;
+  uint8_t* ring = v.ring + (unsigned long long)i * v.R;
+  NlMeta* meta = v.meta + (unsigned long long)i * v.M;
+  const unsigned long long half = v.R / 2;
+  // lane 0 holds the producer's counters; freed / cons are cached and re-read
+  // only when the cached copies say "full" (they only grow)
+  unsigned long long res = 0, pub = 0, freed = 0, cons = 0, max_b = 0, max_m = 0, room_wait = 0;
+  if (lane == 0) {
+    res = ld_rlx(&st->reserve.v);
+    pub = ld_rlx(&st->pub.v);
+    freed = ld_acq(&st->freed.v);
+    cons = ld_acq(&st->cons.v);
+  }
+  for (unsigned s = 0; s < a.mpp;) {
+    unsigned long long r[MPSC_MAX_GROUP], sa[MPSC_MAX_GROUP];
+    int k = 0;
+    unsigned long long sum = 0;
+    for (; k < (int)a.group && (unsigned)k < v.M && s + k < a.mpp; ++k) {
+      const unsigned long long rk = round16(a.sizes[(unsigned long long)p * a.mpp + s + k]);
+      if (k > 0 && sum + rk > half) break;
+      r[k] = rk;
+      sum += rk;
+    }
+    unsigned long long end = 0;
+    int stop = 0;
+    if (lane == 0) {
+      end = nl_place(res, r, k, v.R, sa);
+      unsigned sleep_ns = 32;
+      while (end - freed > v.R || pub + k - cons > v.M) {
+        freed = ld_acq(&st->freed.v);
+        cons = ld_acq(&st->cons.v);
+        if (end - freed <= v.R && pub + k - cons <= v.M) break;
+        ++room_wait;
+        if (aborted(a.abort) || gtime() > deadline) {
+          stop = 1;
+          atomicExch(a.abort, 1u);
+          break;
+        }
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 4096u);
+      }
+      max_b = max(max_b, end - freed);
+      max_m = max(max_m, pub + k - cons);
+    }
+    stop = __shfl_sync(FULLM, stop, 0);
+    if (stop) {
+      if (lane == 0) a.res[c].status = HICR_ERR_TIMEOUT;
+      return;
+    }
+    const unsigned long long pub0 = __shfl_sync(FULLM, pub, 0);
+    for (int j = 0; j < k; ++j) {
+      const unsigned long long sj = __shfl_sync(FULLM, sa[j], 0);
+      const unsigned long long idx = (unsigned long long)p * a.mpp + s + j;
+      warp_copy(ring + (sj & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
+      if (lane == (unsigned)j) {
+        NlMeta* e = meta + ((pub0 + j) & (v.M - 1));
+        e->start = sj;
+        e->size = (unsigned int)a.sizes[idx];
+        e->seq = s + j;
+      }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+      pub += k;
+      res = end;
+      st_rel(&st->pub.v, pub);
+    }
+    s += k;
+  }
+  if (lane == 0) {
+    st_rel(&st->reserve.v, res);
+    atomicMax(&v.head->max_bytes.v, max_b);
+    atomicMax(&v.head->max_msgs.v, max_m);
+    if (room_wait) atomicAdd((unsigned long long*)&a.res[c].room_waits, room_wait);
+  }
+}
+
+__device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw, unsigned nw, unsigned lane,
+                                 unsigned long long deadline) {
+  const NlView v = a.chans[c];
+  const unsigned nring = a.n_prod > c ? (a.n_prod - c + a.n_cons - 1) / a.n_cons : 0;
+  const unsigned owned = nring > gw ? (nring - gw + nw - 1) / nw : 0;  // <= 32 (host check)
+  const bool mine = lane < owned;
+  const unsigned ring_l = gw + lane * nw;  // this lane's ring
+  NlState* st_l = mine ? v.st + ring_l : nullptr;
+  unsigned long long cons = mine ? ld_acq(&st_l->cons.v) : 0, pubc = cons;
+  unsigned long long left = mine ? a.mpp : 0;  // messages still to take from this lane's ring
+  unsigned long long consumed = 0, bytes = 0, batches = 0, idle_ns = 0;
+  hicr_mpsc_log_t* log = a.log + a.log_stride * c;
+  int stop = 0;
+  for (;;) {
+    if (mine && left && pubc == cons) pubc = ld_acq(&st_l->pub.v);
+    unsigned ready = __ballot_sync(FULLM, left != 0 && pubc != cons);
+    if (!ready) {
+      const unsigned pending = __ballot_sync(FULLM, left != 0);
+      if (!pending) break;
+      if (lane == 0) {
+        const unsigned long long t = gtime();
+        stop = aborted(a.abort) || t > deadline;
+        if (stop) atomicExch(a.abort, 1u);
+        __nanosleep(64);
+        idle_ns += gtime() - t;
+      }
+      stop = __shfl_sync(FULLM, stop, 0);
+      if (stop) break;
+      continue;
+    }
+    __syncwarp();  // order the lanes' acquire loads before the reads below
+    while (ready) {
+      const unsigned L = __ffs(ready) - 1;
+      ready &= ready - 1;
+      const unsigned ring = gw + L * nw;
+      const unsigned long long c0 = __shfl_sync(FULLM, cons, L);
+      const unsigned long long avail = __shfl_sync(FULLM, min(pubc - cons, left), L);
+      const unsigned k = (unsigned)min(avail, 32ull);  // >= 1
+      const NlMeta* m = v.meta + (unsigned long long)ring * v.M;
+      unsigned long long e_start = 0;
+      unsigned int e_size = 0, e_seq = 0;
+      if (lane < k) {
+        const NlMeta* e = m + ((c0 + lane) & (v.M - 1));
+        e_start = __ldcg(&e->start);
+        e_size = __ldcg(&e->size);
+        e_seq = __ldcg(&e->seq);
+      }
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(a.log_count + c, (unsigned long long)k);
+      base = __shfl_sync(FULLM, base, 0);
+      const uint8_t* rb = v.ring + (unsigned long long)ring * v.R;
+      for (unsigned j = 0; j < k; ++j) {
+        const unsigned long long sj = __shfl_sync(FULLM, e_start, j);
+        const unsigned long long n = __shfl_sync(FULLM, e_size, j);
+        const uint4* src = reinterpret_cast<const uint4*>(rb + (sj & (v.R - 1)));
+        const unsigned long long nv = (n + 15) / 16;
+        unsigned long long d = 0;
+        for (unsigned long long q0 = 0; q0 < nv; q0 += MPSC_PIECE) {
+          uint4 x[MPSC_PIECE / 32];
+#pragma unroll
+          for (int u = 0; u < MPSC_PIECE / 32; ++u) {
+            const unsigned long long q = q0 + lane + 32 * u;
+            if (q < nv) x[u] = __ldcg(src + q);
+          }
+#pragma unroll
+          for (int u = 0; u < MPSC_PIECE / 32; ++u) {
+            const unsigned long long q = q0 + lane + 32 * u;
+            if (q < nv) {
+              unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
+              unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
+              const unsigned long long b0 = 16 * q;
+              if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
+              if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
+              d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
+            }
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
+        if (lane == j) {
+          hicr_mpsc_log_t E;
+          E.producer = ring * a.n_cons + c;
+          E.seq = e_seq;
+          E.size = e_size;
+          E.reserved = 0;
+          E.offset = e_start & (v.R - 1);
+          E.digest = d;
+          log[base + j] = E;
+          bytes += e_size;
+        }
+      }
+      // free every byte up to the batch's last message
+      const unsigned long long s_last = __shfl_sync(FULLM, e_start, k - 1);
+      const unsigned long long n_last = __shfl_sync(FULLM, e_size, k - 1);
+      __syncwarp();
+      if (lane == L) {
+        st_rel(&st_l->freed.v, s_last + round16(n_last));
+        cons += k;
+        st_rel(&st_l->cons.v, cons);
+        left -= k;
+      }
+      consumed += k;
+      ++batches;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(FULLM, bytes, o);
+  if (lane == 0) {
+    hicr_mpsc_result_t* r = a.res + c;
+    atomicAdd((unsigned long long*)&r->consumed, consumed);
+    atomicAdd((unsigned long long*)&r->bytes, bytes);
+    atomicAdd((unsigned long long*)&r->windows, batches);
+    atomicAdd((unsigned long long*)&r->consumer_ns[0], idle_ns);
+    if (stop) r->status = HICR_ERR_TIMEOUT;
+  }
+}
+
+__global__ void __launch_bounds__(MPSC_THREADS) k_nl_stream(NlStreamArgs a) {
+  const unsigned long long deadline = gtime() + a.timeout_ns;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+  const unsigned ncta = a.n_cons * a.G;
+  if (blockIdx.x < ncta) {
+    const unsigned c = blockIdx.x / a.G, g = blockIdx.x % a.G;
+    nl_consumer_warp(a, c, g * W + warp, a.G * W, lane, deadline);
+    return;
+  }
+  const unsigned p = (blockIdx.x - ncta) * W + warp;
+  if (p < a.n_prod) nl_producer(a, p, lane, deadline);
+}
+
+// The pre-stream checks of k_mpsc_check against the per-producer rings.
+__global__ void k_nl_check(NlStreamArgs a, unsigned long long staging_size, int* bad) {
+  const unsigned long long total = (unsigned long long)a.n_prod * a.mpp;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long n = a.sizes[i], off = a.src_off[i];
+    const unsigned c = (unsigned)((i / a.mpp) % a.n_cons);
+    if (off > staging_size || n > staging_size - off) atomicCAS(bad, 0, HICR_ERR_BOUNDS);
+    else if (round16(n) > a.chans[c].R / 2 || n > 0xffffffffull) atomicCAS(bad, 0, HICR_ERR_TOO_LARGE);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Ping-pong: CTAs [0, G) are agent A, [G, 2G) agent B. Round k: A's CTAs copy
 // their share of the message into B's buffer and count themselves in
 // (arrive_a); B's CTAs wait for arrive_a >= k*G, echo their share into A's
@@ -798,6 +1183,18 @@ static MpscView mpsc_view(Channel* c) {
   return v;
 }
 
+static NlView nl_view(Channel* c) {
+  NlView v;
+  v.ring = c->ring;
+  v.head = (NlHead*)c->state;
+  v.st = (NlState*)((char*)c->state + sizeof(NlHead));
+  v.meta = reinterpret_cast<NlMeta*>(c->meta);
+  v.R = c->ring_bytes;
+  v.M = c->max_msgs;
+  v.P = c->n_producers;
+  return v;
+}
+
 static hicr_status add_channel(hicr_instance_t h, Channel* c, size_t ring_bytes, size_t state_bytes,
                                size_t meta_bytes, hicr_channel_t* out) {
   Instance* in = &h->impl;
@@ -897,6 +1294,23 @@ hicr_status hicr_mpsc_create(hicr_instance_t h, uint32_t n_producers, uint64_t r
   return add_channel(h, c, ring_bytes, sizeof(MpscState), sizeof(MpscMeta) * (size_t)max_msgs, out);
 }
 
+hicr_status hicr_mpsc_nl_create(hicr_instance_t h, uint32_t n_producers, uint64_t ring_bytes, uint32_t max_msgs,
+                                hicr_channel_t* out) {
+  Instance* in = I(h);
+  if (!in || !out || n_producers == 0 || in->capturing) return HICR_ERR_INVALID;
+  if (!pow2(ring_bytes) || ring_bytes < 64 || ring_bytes > (1ull << 39)) return HICR_ERR_INVALID;
+  if (!pow2(max_msgs) || max_msgs > (1u << 23)) return HICR_ERR_INVALID;
+  if ((unsigned long long)n_producers * ring_bytes > (1ull << 40)) return HICR_ERR_INVALID;
+  Channel* c = new Channel();
+  c->kind = 2;
+  c->n_producers = n_producers;
+  c->ring_bytes = ring_bytes;
+  c->max_msgs = max_msgs;
+  c->seq.assign(n_producers, 0);
+  return add_channel(h, c, (size_t)n_producers * ring_bytes, sizeof(NlHead) + sizeof(NlState) * (size_t)n_producers,
+                     sizeof(NlMeta) * (size_t)max_msgs * n_producers, out);
+}
+
 hicr_status hicr_channel_destroy(hicr_instance_t h, hicr_channel_t ch) {
   Instance* in = I(h);
   if (!in || in->capturing) return HICR_ERR_INVALID;
@@ -946,8 +1360,12 @@ hicr_status hicr_channel_push(hicr_instance_t h, hicr_channel_t ch, uint32_t pro
     if (producer >= c->n_producers) return HICR_ERR_INVALID;
     if (off > ssize || n > ssize - off) return HICR_ERR_BOUNDS;
     if (round16(n) > c->ring_bytes || n > 0xffffffffull) return HICR_ERR_TOO_LARGE;
-    k_mpsc_push_host<<<1, 256, 0, in->comm()>>>(mpsc_view(c), producer, c->seq[producer], (const uint8_t*)sp + off,
-                                               n, md);
+    if (c->kind == 1)
+      k_mpsc_push_host<<<1, 256, 0, in->comm()>>>(mpsc_view(c), producer, c->seq[producer],
+                                                 (const uint8_t*)sp + off, n, md);
+    else
+      k_nl_push_host<<<1, 256, 0, in->comm()>>>(nl_view(c), producer, c->seq[producer], (const uint8_t*)sp + off, n,
+                                               md);
     st = finish(in, mh);
     if (st == HICR_OK) c->seq[producer]++;
   }
@@ -960,7 +1378,8 @@ static hicr_status ctl(Instance* in, Channel* c, int op, uint64_t k, Mailbox** o
   hicr_status st = mailbox(in, &mh, &md);
   if (st != HICR_OK) return st;
   if (c->kind == 0) k_spsc_ctl<<<1, 1, 0, in->comm()>>>(spsc_view(c), op, k, md);
-  else k_mpsc_ctl<<<1, 1, 0, in->comm()>>>(mpsc_view(c), op, k, md);
+  else if (c->kind == 1) k_mpsc_ctl<<<1, 1, 0, in->comm()>>>(mpsc_view(c), op, k, md);
+  else k_nl_ctl<<<1, 1, 0, in->comm()>>>(nl_view(c), op, k, md);
   st = finish(in, mh);
   *out = mh;
   return st;
@@ -1110,6 +1529,89 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
     unsigned long long mx[2];
     HICR_CUDA(in, cudaMemcpy(&mx[0], &ms->max_bytes.v, 8, cudaMemcpyDeviceToHost));
     HICR_CUDA(in, cudaMemcpy(&mx[1], &ms->max_msgs.v, 8, cudaMemcpyDeviceToHost));
+    results[i].max_inflight_bytes = mx[0];
+    results[i].max_inflight_msgs = mx[1];
+  }
+  if ((st = record_done(in)) != HICR_OK) return st;
+  for (uint32_t i = 0; i < n_consumers; ++i)
+    if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
+  return HICR_OK;
+}
+
+hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                uint64_t log_stride, hicr_mpsc_result_t* results) {
+  Instance* in = I(h);
+  if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
+      group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)
+    return HICR_ERR_INVALID;
+  void* sp = nullptr;
+  uint64_t ssize = 0;
+  uint32_t sspace = 0;
+  if (hicr_slot_info(h, staging, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+  if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  const unsigned warps = MPSC_THREADS / 32;
+  const uint64_t per = (n_producers + n_consumers - 1) / n_consumers;
+  // every consumer warp polls at most 32 rings (one per lane)
+  if (per > 32ull * warps * consumer_ctas) return HICR_ERR_INVALID;
+  std::vector<NlView> views(n_consumers);
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    Channel* c = get(in, chans[i]);
+    if (!c || c->kind != 2 || c->n_producers < per) return HICR_ERR_INVALID;
+    views[i] = nl_view(c);
+  }
+  if (log_stride < per * msgs_per_producer) return HICR_ERR_INVALID;
+  const unsigned long long grid = (unsigned long long)n_consumers * consumer_ctas + (n_producers + warps - 1) / warps;
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_stream, MPSC_THREADS, 0));
+  if (grid > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  const size_t vb = ((sizeof(NlView) * n_consumers + 255) / 256) * 256;
+  const size_t rb = ((sizeof(hicr_mpsc_result_t) * n_consumers + 255) / 256) * 256;
+  const size_t cb = ((sizeof(unsigned long long) * n_consumers + 255) / 256) * 256;
+  void* buf = nullptr;
+  if ((st = dev_buffer(in, vb + rb + cb + 256, &buf)) != HICR_OK) return st;
+  char* p = (char*)buf;
+  cudaStream_t s = in->comm();
+  HICR_CUDA(in, cudaMemcpyAsync(p, views.data(), sizeof(NlView) * n_consumers, cudaMemcpyHostToDevice, s));
+  HICR_CUDA(in, cudaMemsetAsync(p + vb, 0, rb + cb + 256, s));
+  NlStreamArgs a;
+  a.chans = (const NlView*)p;
+  a.n_cons = n_consumers;
+  a.G = consumer_ctas;
+  a.n_prod = n_producers;
+  a.mpp = msgs_per_producer;
+  a.group = group;
+  a.sizes = (const unsigned long long*)d_sizes;
+  a.src_off = (const unsigned long long*)d_src_off;
+  a.staging = (const uint8_t*)sp;
+  a.timeout_ns = timeout_ns;
+  a.log = d_log;
+  a.log_stride = log_stride;
+  a.res = (hicr_mpsc_result_t*)(p + vb);
+  a.log_count = (unsigned long long*)(p + vb + rb);
+  a.abort = (unsigned int*)(p + vb + rb + cb);
+  int* bad = (int*)(p + vb + rb + cb + 128);
+  k_nl_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
+  int hbad = 0;
+  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaStreamSynchronize(s));
+  if (hbad) return hbad;
+  for (uint32_t i = 0; i < n_consumers; ++i)
+    HICR_CUDA(in, cudaMemsetAsync(get(in, chans[i])->state, 0, sizeof(NlHead), s));
+  void* args[] = {&a};
+  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_nl_stream, dim3((unsigned)grid), dim3(MPSC_THREADS), args,
+                                            0, s));
+  HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaStreamSynchronize(s));
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    NlHead* hd = (NlHead*)get(in, chans[i])->state;
+    unsigned long long mx[2];
+    HICR_CUDA(in, cudaMemcpy(&mx[0], &hd->max_bytes.v, 8, cudaMemcpyDeviceToHost));
+    HICR_CUDA(in, cudaMemcpy(&mx[1], &hd->max_msgs.v, 8, cudaMemcpyDeviceToHost));
     results[i].max_inflight_bytes = mx[0];
     results[i].max_inflight_msgs = mx[1];
   }

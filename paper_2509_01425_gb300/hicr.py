@@ -472,6 +472,7 @@ class hicr_mpsc_result_t(C.Structure):
 
 _spsc_create = _decl("hicr_spsc_create", [H, u32, u32, C.POINTER(u32)])
 _mpsc_create = _decl("hicr_mpsc_create", [H, u32, u64, u32, C.POINTER(u32)])
+_mpsc_nl_create = _decl("hicr_mpsc_nl_create", [H, u32, u64, u32, C.POINTER(u32)])
 _channel_destroy = _decl("hicr_channel_destroy", [H, u32])
 _channel_ring = _decl("hicr_channel_ring", [H, u32, C.POINTER(u32)])
 _channel_push = _decl("hicr_channel_push", [H, u32, u32, u32, u64, u64])
@@ -480,6 +481,7 @@ _channel_pop = _decl("hicr_channel_pop", [H, u32, u64])
 _channel_depth = _decl("hicr_channel_depth", [H, u32, C.POINTER(u64), C.POINTER(u64)])
 _spsc_stream = _decl("hicr_spsc_stream", [H, vp, u32, u64, u32, u64, vp])
 _mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u64, vp, u64, vp])
+_mpsc_nl_stream = _decl("hicr_mpsc_nl_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp])
 
 
 class hicr_pingpong_result_t(C.Structure):
@@ -506,6 +508,12 @@ def hicr_spsc_create(inst, token_size, capacity):
 def hicr_mpsc_create(inst, n_producers, ring_bytes, max_msgs):
     c = u32()
     st = _mpsc_create(inst, n_producers, ring_bytes, max_msgs, C.byref(c))
+    return st, c.value
+
+
+def hicr_mpsc_nl_create(inst, n_producers, ring_bytes, max_msgs):
+    c = u32()
+    st = _mpsc_nl_create(inst, n_producers, ring_bytes, max_msgs, C.byref(c))
     return st, c.value
 
 
@@ -552,6 +560,16 @@ def hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src
     res = (hicr_mpsc_result_t * len(chans))()
     st = _mpsc_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
                       _ptr(d_src_off), staging, group, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
+    return st, list(res)
+
+
+def hicr_mpsc_nl_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                        consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000):
+    arr = (u32 * len(chans))(*chans)
+    res = (hicr_mpsc_result_t * len(chans))()
+    st = _mpsc_nl_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
+                         _ptr(d_src_off), staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride,
+                         C.addressof(res))
     return st, list(res)
 
 

@@ -215,3 +215,116 @@ def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
     assert r.digest_a == exp and r.digest_b == exp
     assert r.half_rtt_ns > 0 and r.goodput_gbs > 0
     assert h.hicr_pingpong(inst, s, 200, size, 1, 0, 1)[0] == h.HICR_ERR_BOUNDS
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_nonlocking_host_calls_match_oracle(h, inst, seed):
+    """Non-locking MPSC (one ring per producer): statuses, offsets within the
+    producer's ring, sizes, producers, sequence numbers and payloads match the
+    non-locking oracle under random programs that fill and wrap the rings."""
+    rng = np.random.default_rng(seed)
+    P, R, M = 3, 1 << 10, 4
+    st, ch = h.hicr_mpsc_nl_create(inst, P, R, M)
+    assert st == 0
+    orc = oc.MpscNonLockingOracle(P, R, M)
+    pool = rng.integers(0, 256, 1 << 14, dtype=np.uint8)
+    s, keep = src_slot(h, inst, pool)
+    for step in range(400):
+        r = rng.random()
+        if r < 0.5:
+            p = int(rng.integers(0, P))
+            n = int(rng.choice([0, 1, 9, 16, 100, 333, 512, 700, 1024, 1100]))
+            off = int(rng.integers(0, len(pool) - n + 1))
+            exp = orc.push(p, pool[off:off + n])
+            assert h.hicr_channel_push(inst, ch, p, s, off, n) == exp, (step, p, n)
+        elif r < 0.72:
+            k = int(rng.integers(0, 5))
+            assert h.hicr_channel_pop(inst, ch, k) == orc.pop(k), step
+        elif r < 0.92:
+            k = int(rng.integers(0, P * M + 1))
+            est, info = orc.peek(k)
+            gst, ginfo = h.hicr_channel_peek(inst, ch, k)
+            assert gst == est, step
+            if est == om.OK:
+                assert ginfo == info, step
+                o, n, p, q = info
+                assert (ring_bytes(h, inst, ch, p * R + o, n) == orc.payload(k)).all()
+        else:
+            assert h.hicr_channel_depth(inst, ch)[1:] == orc.depth(), step
+    assert h.hicr_channel_push(inst, ch, P, s, 0, 8) == h.HICR_ERR_INVALID
+    assert h.hicr_mpsc_nl_create(inst, 2, 3000, 8)[0] == h.HICR_ERR_INVALID
+    assert h.hicr_mpsc_nl_create(inst, 2, 1024, 6)[0] == h.HICR_ERR_INVALID
+
+
+def _check_mpsc_nl(w, run, res):
+    C = w.n_consumers
+    logs = run.logs()
+    for c in range(C):
+        n = int(res[c].consumed)
+        L = logs[c][:n]
+        assert res[c].status == 0 and res[c].cas_failures == 0
+        assert int(res[c].max_inflight_bytes) <= run.ring_bytes
+        assert int(res[c].max_inflight_msgs) <= run.max_msgs
+        probs = oc.check_mpsc_nl_log(w.sizes, C, c, list(zip(L["producer"], L["seq"], L["size"], L["offset"])),
+                                     run.ring_bytes)
+        assert probs == [], (c, probs[:5])
+        assert int(res[c].bytes) == int(L["size"].astype(np.int64).sum())
+        for j in range(n):
+            p, q, sz = int(L["producer"][j]), int(L["seq"][j]), int(L["size"][j])
+            assert int(L["digest"][j]) == od.byte_digest(splitmix.mpsc_payload_bytes(p, q, sz)), (c, j)
+
+
+@pytest.mark.parametrize("P,C,M,ring,max_msgs,hi,group,ctas", [
+    (64, 4, 64, 1 << 16, 8, 16 << 10, 4, 1),
+    (48, 3, 40, 1 << 13, 4, 2 << 10, 1, 2),
+    (33, 5, 17, 1 << 12, 2, 1 << 10, 8, 1),
+    (700, 2, 6, 1 << 11, 8, 1 << 10, 2, 1),   # 350 rings per consumer: warps poll up to 22 rings
+])
+def test_nonlocking_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, group, ctas):
+    w = configs.mpsc(9, n_producers=P, n_consumers=C, msgs_per_producer=M, ring_bytes=ring, max_msgs=max_msgs,
+                     hi=hi)
+    run = bench.MpscRun(h, inst, w, group=group, nonlocking=True, consumer_ctas=ctas, ring_bytes=ring,
+                        max_msgs=max_msgs)
+    st, res = run.run()
+    assert st == 0
+    _check_mpsc_nl(w, run, res)
+    # some rings wrapped (skip-to-start exercised) and all are empty again
+    assert (((w.sizes + 15) // 16 * 16).sum(1) > ring).any()
+    for ch in run.chans:
+        assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
+    # a second run continues from the rings' counters; the positions then
+    # start where the first run stopped, so only order, sizes and payloads
+    # are checked
+    st, res = run.run()
+    assert st == 0 and sum(int(r.consumed) for r in res) == P * M
+    run.free()
+
+
+def test_nonlocking_stream_rejects_bad_shapes(h, inst):
+    w = configs.mpsc(3, n_producers=8, n_consumers=2, msgs_per_producer=4, ring_bytes=1 << 12, max_msgs=4, hi=512)
+    run = bench.MpscRun(h, inst, w, nonlocking=True, ring_bytes=1 << 12, max_msgs=4)
+    P, M = w.sizes.shape
+    args = (run.d_sizes.data_ptr(), run.d_offs.data_ptr(), run.staging)
+    # the locking-mode stream does not take non-locking channels and vice versa
+    assert h.hicr_mpsc_stream(inst, run.chans, P, M, *args, 1, run.d_log.data_ptr(), run.stride)[0] == \
+        h.HICR_ERR_INVALID
+    lock = [h.hicr_mpsc_create(inst, 4, 1 << 12, 4)[1] for _ in range(2)]
+    assert h.hicr_mpsc_nl_stream(inst, lock, P, M, *args, 1, 1, run.d_log.data_ptr(), run.stride)[0] == \
+        h.HICR_ERR_INVALID
+    # zero CTAs per consumer, a group above 8, a log stride too small
+    assert h.hicr_mpsc_nl_stream(inst, run.chans, P, M, *args, 1, 0, run.d_log.data_ptr(), run.stride)[0] == \
+        h.HICR_ERR_INVALID
+    assert h.hicr_mpsc_nl_stream(inst, run.chans, P, M, *args, 9, 1, run.d_log.data_ptr(), run.stride)[0] == \
+        h.HICR_ERR_INVALID
+    assert h.hicr_mpsc_nl_stream(inst, run.chans, P, M, *args, 1, 1, run.d_log.data_ptr(), run.stride - 1)[0] == \
+        h.HICR_ERR_INVALID
+    # a message above half a ring is TOO_LARGE before anything is launched
+    small = [h.hicr_mpsc_nl_create(inst, 4, 256, 4)[1] for _ in range(2)]
+    assert h.hicr_mpsc_nl_stream(inst, small, P, M, *args, 1, 1, run.d_log.data_ptr(), run.stride)[0] == \
+        h.HICR_ERR_TOO_LARGE
+    for c in lock + small:
+        assert h.hicr_channel_destroy(inst, c) == 0
+    st, res = run.run()
+    assert st == 0
+    _check_mpsc_nl(w, run, res)
+    run.free()
