@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -299,7 +300,8 @@ def bench_spsc(h, inst, reps=3):
     return {"workload": "64 channels x capacity 4,096 x 64 B tokens, 10^7 tokens/channel, "
                         "1 producer + 1 consumer CTA per channel (cooperative grid)", "batch_tokens": batch,
             "msgs_per_s": tokens / t, "GB_per_s": tokens * 128 / t / 1e9, "s_per_run": t,
-            "bound": "L2 + handoff latency (rings total 16 MiB, L2-resident)"}
+            "frac_of_hbm_peak": tokens * 128 / t / 1e9 / peaks()[0],
+            "bound": "L2 + handoff latency (rings total 16 MiB, L2-resident: the HBM fraction is context only)"}
 
 
 def bench_pingpong(h, inst):
@@ -343,15 +345,17 @@ def _time_mpsc(h, run, reps):
 def bench_mpsc(h, inst, reps=3, group=4):
     """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB: locking
     mode over one 1 GiB ring per consumer against non-locking mode over 64
-    rings of 16 MiB per consumer (the same memory), the latter with 1, 2 or 4
-    CTAs per consumer."""
+    rings of 16 MiB per consumer (the same memory), the latter with 1, 2, 4
+    or 5 CTAs per consumer (5 fills the 152 SMs with the 64 producer CTAs)."""
     w = configs.mpsc(0)
     run = MpscRun(h, inst, w, group=group)
     out = {"workload": "1,024 producers -> 16 consumers, 1,024 msgs each, log-uniform 8 B-256 KiB, 1 GiB rings",
            **_time_mpsc(h, run, reps), "group": group}
     by = {}
-    for g in (1, 2, 4):
+    for g in (1, 2, 4, 5):
         run.set_mode(True, g)
+        if run.run()[0] == h.HICR_ERR_INVALID:  # grid not co-resident on this GPU
+            continue
         by[g] = _time_mpsc(h, run, reps)
     best = max(by, key=lambda g: by[g]["msgs_per_s"])
     out["nonlocking"] = {"rings": f"64 x {run.ring_bytes >> 20} MiB per consumer, {run.max_msgs} msgs each",
@@ -460,8 +464,43 @@ def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
                          "wall_s": pst.wall_ns / 1e9, "GB_per_s_moved": pst.bytes_moved / (pst.wall_ns / 1e9) / 1e9,
                          "latency_all": latency_summary(pres[: int(m.sum())]),
                          "engine_latency_same_requests": latency_summary(res[: int(m.sum())])}
+    out["rate_sweep"] = serve_rate_sweep(h, inst, ss, seed)
     ss.free()
     return out
+
+
+SERVE_P99_BOUND_MS = 50.0
+
+
+def serve_rate_sweep(h, inst, ss, seed=0, engine_rates=(15000, 20000, 25000, 30000, 40000), engine_s=3.0,
+                     plain_rates=(100, 200, 400, 800), plain_s=2.0):
+    """Each form's highest sustainable arrival rate: the highest swept Poisson
+    rate (same request mix) whose p99 latency stays within
+    SERVE_P99_BOUND_MS over a short trace."""
+    def sweep(rates, seconds, plain):
+        rows = []
+        for r in rates:
+            reqs = ss.requests(configs.serve_trace(seed + 1, rate=float(r), duration_s=seconds))
+            if plain:
+                st, res, stats = h.hicr_serve_run_plain(inst, ss.srv, reqs, int(seconds * 1e9),
+                                                        int((seconds + 600) * 1e9))
+            else:
+                st, res, stats = h.hicr_serve_run(inst, ss.srv, reqs, 0, int((seconds + 120) * 1e9))
+            h.check(st, "serve sweep")
+            n = int((reqs["arrival_ns"] <= int(seconds * 1e9)).sum())
+            lat = latency_summary(res[:n])
+            rows.append({"rate": r, "requests": n, "p50_us": lat.get("p50_us"), "p99_us": lat.get("p99_us"),
+                         "GB_per_s_moved": stats.bytes_moved / (stats.wall_ns / 1e9) / 1e9,
+                         "sustainable": bool(n and lat["p99_us"] <= SERVE_P99_BOUND_MS * 1e3)})
+        ok = [x["rate"] for x in rows if x["sustainable"]]
+        return rows, (max(ok) if ok else None)
+
+    eng, eng_max = sweep(engine_rates, engine_s, False)
+    pl, pl_max = sweep(plain_rates, plain_s, True)
+    return {"p99_bound_ms": SERVE_P99_BOUND_MS, "engine_seconds_per_rate": engine_s,
+            "plain_seconds_per_rate": plain_s, "engine": eng, "engine_max_sustainable_req_per_s": eng_max,
+            "plain": pl, "plain_max_sustainable_req_per_s": pl_max,
+            "note": "null = not sustainable at the lowest swept rate"}
 
 
 # ---------------------------------------------------------------------------
@@ -501,8 +540,51 @@ def cpu_baseline(seed, target_s):
         el = time.perf_counter() - t0
         if el >= target_s or passes >= 200:
             break
-    return {"value": nbytes / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{CPU_SAMPLE_TEXT}; {passes} passes in {el:.1f} s"}
+    out = {"value": nbytes / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": f"{CPU_SAMPLE_TEXT}; {passes} passes in {el:.1f} s", "host": host_info()}
+    # the same sample as plain memcpy on every host core (oracle/memcpy_threads.c)
+    try:
+        from oracle.native import ThreadedMemcpy
+        cores = os.cpu_count() or 1
+        tm = ThreadedMemcpy([cm.slots[i].data for i in sorted(cm.slots)], w.ops, w.epochs)
+        tm.run(cores)
+        t0 = time.perf_counter()
+        passes = 0
+        while True:
+            tm.run(cores)
+            passes += 1
+            el = time.perf_counter() - t0
+            if el >= min(target_s, 3.0) or passes >= 200:
+                break
+        out["all_cores"] = {"value": passes * 2 * w.total_bytes / el / 1e9, "unit": "GB/s", "cores": cores,
+                            "kind": "memcpy on all host cores", "sample": f"same sample; {passes} passes in {el:.1f} s"}
+    except (OSError, subprocess.CalledProcessError) as e:
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    return out
+
+
+def nominal_hbm(h, inst):
+    """Datasheet-style HBM bandwidth (GB/s): the memory clock x bus width the
+    driver reports (the library's topology query), else the GB300 HBM3e
+    figure of about 7.9 TB/s."""
+    st, t = h.hicr_topology_query(inst)
+    if st == 0 and t.spaces[0].peak_mbps:
+        return t.spaces[0].peak_mbps / 1e3, "memory clock x bus width reported by the driver"
+    return 7900.0, "GB300 HBM3e datasheet figure (about 7.9 TB/s)"
+
+
+def host_info():
+    """Core count and CPU model of the machine that timed the CPU lines."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = f"{line.split(':', 1)[1].strip()} ({platform.machine()})"
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def run_reference(args):
@@ -556,6 +638,7 @@ def run_ours(args):
     stream_ptr = h.check(h.hicr_pu_stream(inst, 0), "pu_stream")
     stream = torch.cuda.ExternalStream(stream_ptr)
     peak, peak_src = peaks()
+    nominal, nominal_src = nominal_hbm(h, inst)
 
     w = scaled_batched(args.seed, args.scale)
     ids = setup_slots(h, inst, w, args.seed)
@@ -595,6 +678,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
+                     "nominal_peak": nominal, "nominal_source": nominal_src,
+                     "frac_of_nominal": (achieved / nominal) if achieved else None,
                      "traffic": copy_traffic(bytes_step / n_epochs),
                      "algorithmic_bytes_per_launch": bytes_step / n_epochs,
                      "kernel": "k_copy", "peak_source": f"{peak_src} hbm_gbs (copy, burst)",

@@ -96,7 +96,9 @@ typedef struct {
   uint32_t id;        /* memory-space id passed to hicr_mem_alloc */
   uint32_t kind;      /* HICR_SPACE_* */
   int32_t device;     /* CUDA device, or -1 for host memory */
-  uint32_t reserved;
+  uint32_t peak_mbps; /* device spaces: theoretical bandwidth in MB/s from the
+                         memory clock and bus width the driver reports
+                         (2 transfers per clock); 0 when unknown or host */
   uint64_t phys_size; /* physical capacity in bytes (not the virtual size) */
   uint64_t free_size; /* bytes free when queried (device spaces), else 0 */
 } hicr_memory_space_t;

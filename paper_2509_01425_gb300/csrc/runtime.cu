@@ -282,6 +282,16 @@ hicr_status hicr_topology_query(hicr_instance_t h, hicr_topology_t* out) {
   t.spaces[0].device = in->device;
   t.spaces[0].phys_size = in->prop.totalGlobalMem;
   t.spaces[0].free_size = fr;
+  {
+    int clk_khz = 0, bus_bits = 0;
+    if (cudaDeviceGetAttribute(&clk_khz, cudaDevAttrMemoryClockRate, in->device) == cudaSuccess &&
+        cudaDeviceGetAttribute(&bus_bits, cudaDevAttrGlobalMemoryBusWidth, in->device) == cudaSuccess) {
+      const unsigned long long mbps = 2ull * (unsigned long long)clk_khz * (unsigned long long)bus_bits / 8ull / 1000ull;
+      t.spaces[0].peak_mbps = mbps > 0xffffffffull ? 0u : (uint32_t)mbps;
+    } else {
+      (void)cudaGetLastError();
+    }
+  }
   t.spaces[1].id = 1;
   t.spaces[1].kind = HICR_SPACE_HOST;
   t.spaces[1].device = -1;

@@ -57,7 +57,7 @@ class hicr_op_t(C.Structure):
 
 
 class hicr_memory_space_t(C.Structure):
-    _fields_ = [("id", u32), ("kind", u32), ("device", i32), ("reserved", u32),
+    _fields_ = [("id", u32), ("kind", u32), ("device", i32), ("peak_mbps", u32),
                 ("phys_size", u64), ("free_size", u64)]
 
 

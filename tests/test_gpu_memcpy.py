@@ -49,6 +49,9 @@ def test_topology(h, inst):
     st, t = h.hicr_topology_query(inst)
     assert st == 0 and t.n_spaces == 2 and t.n_resources == 1
     assert t.spaces[0].kind == h.HICR_SPACE_HBM and t.spaces[0].phys_size > (100 << 30)
+    # theoretical HBM bandwidth from clock x bus width: 0 (unknown) or a few TB/s
+    assert t.spaces[0].peak_mbps == 0 or 1_000_000 < t.spaces[0].peak_mbps < 50_000_000
+    assert t.spaces[1].peak_mbps == 0
     assert t.resources[0].sm_count > 0
     assert h.hicr_is_root(inst) == (0, 1)
 
