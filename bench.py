@@ -37,6 +37,7 @@ from workloads import configs, splitmix  # noqa: E402
 
 METRIC = "HiCR memcpy GB/s vs HBM peak; channel msgs/s; p99 latency vs per-op plain"
 GiB = 1 << 30
+MiB = 1 << 20
 FENCE_TIMEOUT = 120_000_000_000
 
 
@@ -325,6 +326,51 @@ def bench_pingpong(h, inst):
     h.check(h.hicr_mem_free(inst, sid), "free")
     return {"workload": "ping-pong over two opposing capacity-1 SPSC channels (paper Test Case 1), "
                         "10 timed round trips after 2 warm-up, one agent = 1-64 CTAs", "curve": rows}
+
+
+def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
+    """Copies between HBM and page-locked Grace memory (the host memory
+    space) through the copy kernels over NVLink-C2C: 4 GiB per direction in
+    4 MiB ops, one device-resident batch + fence per repetition; beside it
+    the copy engine (torch copy_ of a pinned tensor, cudaMemcpyAsync) on the
+    same bytes."""
+    import torch
+    h.check(h.hicr_set_host_copies(inst, 1), "host copies on")
+    d = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, nbytes), "alloc hbm")
+    hs = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HOST, nbytes), "alloc host")
+    h.check(h.hicr_util_fill(inst, d, 0, nbytes, splitmix.fill_key_base(0, 1)), "fill")
+    h.check(h.hicr_util_fill(inst, hs, 0, nbytes, splitmix.fill_key_base(0, 2)), "fill")
+    k = nbytes // op_bytes
+    offs = np.arange(k, dtype=np.uint64) * np.uint64(op_bytes)
+    out = {"workload": f"{nbytes >> 30} GiB per direction in {op_bytes >> 20} MiB ops, batch + fence"}
+    for name, dst, src in (("hbm_to_host", hs, d), ("host_to_hbm", d, hs)):
+        ops = configs.make_ops([dst] * k, [src] * k, offs, offs, [op_bytes] * k)
+        t = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        times = []
+        for r in range(reps + 1):
+            t0 = time.perf_counter()
+            h.check(h.hicr_memcpy_batch_device(inst, t.data_ptr(), k), "batch")
+            h.check(h.hicr_fence(inst, 0), "fence")
+            if r:
+                times.append(time.perf_counter() - t0)
+        out[name + "_GB_per_s"] = nbytes / statistics.median(times) / 1e9
+    h.check(h.hicr_set_host_copies(inst, 0), "host copies off")
+    h.check(h.hicr_mem_free(inst, hs), "free")
+    h.check(h.hicr_mem_free(inst, d), "free")
+    ph = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dv = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    for name, a, b in (("copy_engine_hbm_to_host_GB_per_s", ph, dv), ("copy_engine_host_to_hbm_GB_per_s", dv, ph)):
+        times = []
+        for r in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a.copy_(b, non_blocking=True)
+            torch.cuda.synchronize()
+            if r:
+                times.append(time.perf_counter() - t0)
+        out[name] = nbytes / statistics.median(times) / 1e9
+    del ph, dv
+    return out
 
 
 def _time_mpsc(h, run, reps):
@@ -738,6 +784,7 @@ def run_ours(args):
                                                 "hicr_slot_counters_range per step"}
         side["spsc"] = bench_spsc(h, inst)
         side["pingpong"] = bench_pingpong(h, inst)
+        side["host_space"] = bench_host_space(h, inst)
         side["mpsc"] = bench_mpsc(h, inst)
         if args.serve_seconds > 0:
             h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")
