@@ -160,18 +160,23 @@ typedef struct {
  * Message (p, s) has d_sizes[p * msgs_per_producer + s] bytes (device array,
  * u64) taken from slot `staging` at byte d_src_off[p * msgs_per_producer + s]
  * (device array, u64). Each producer is one warp and reserves up to `group`
- * consecutive messages (1 .. 8) per exclusive access; each consumer is one
- * CTA that drains in ticket order, digests each payload and writes its log to
- * d_log + c * log_stride (device, at least as many entries as it receives).
+ * consecutive messages (1 .. 8) per exclusive access. Consumer c runs on
+ * `consumer_ctas` CTAs that claim successive windows of reserved tickets,
+ * digest their windows' payloads side by side and free them strictly in
+ * ticket order (a CTA frees its window once the previous one is freed); the
+ * log entry of ticket t goes to d_log + c * log_stride + (t - t0), t0 the
+ * channel's first ticket of the run (device array, at least as many entries
+ * as the consumer receives), so logs are in ticket order.
  * One cooperative grid; every wait gives up after `timeout_ns`.
  * Synchronous; `results` is a host array of n_consumers.
- * Errors: INVALID, BOUNDS (a message outside the staging slot), TOO_LARGE (a
- * message larger than its ring), DEVICE, TIMEOUT. */
+ * Errors: INVALID (also when the grid cannot be co-resident), BOUNDS (a
+ * message outside the staging slot), TOO_LARGE (a message larger than half
+ * its ring), DEVICE, TIMEOUT. */
 hicr_status hicr_mpsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
                              uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
                              const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
-                             uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
-                             hicr_mpsc_result_t* results);
+                             uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                             uint64_t log_stride, hicr_mpsc_result_t* results);
 
 /* The streaming run of hicr_mpsc_stream for non-locking channels (created
  * with hicr_mpsc_nl_create with at least ceil(n_producers / n_consumers)
@@ -184,7 +189,7 @@ hicr_status hicr_mpsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, 
  * them hold published messages. Logs are in consumption order (each
  * producer's messages in push order; the interleaving of producers is
  * arbitrary). Other arguments, results and errors as hicr_mpsc_stream
- * (cas_failures is 0); INVALID also when the grid cannot be co-resident. */
+ * (cas_failures is 0). */
 hicr_status hicr_mpsc_nl_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
                                 uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
                                 const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,

@@ -484,6 +484,9 @@ struct MpscStreamArgs {
   unsigned long long log_stride;
   hicr_mpsc_result_t* res;
   unsigned int* abort;
+  unsigned int G;                  // CTAs per consumer
+  unsigned long long* claim;       // per consumer (stride 16 words): next unclaimed ticket
+  const unsigned long long* base;  // per consumer: first ticket of the run
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
@@ -584,26 +587,31 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
   }
 }
 
-// Consumer: one CTA per channel. Each round takes a window of up to
+// Consumer c: G CTAs. Each round, a CTA claims the next window of up to
 // MPSC_WIN tickets that producers have already reserved (so every one of them
-// will be published without waiting for ring space) and
+// will be published without waiting for ring space) by advancing the
+// consumer's claim counter, and
 //   A. warps acquire the tickets' `ready` words and stage their metadata in
 //      shared memory;
 //   B. the whole CTA digests the window's payloads in 8 KiB pieces of single
 //      messages, one piece per warp at a time;
-//   C. warps write the log entries, then one thread frees every byte up to the
-//      window's last message and advances msg_tail (release stores).
+//   C. warps write the log entries (index = ticket - first ticket), then one
+//      thread waits until msg_tail reaches the window's first ticket (the
+//      previous window is freed), frees every byte up to the window's last
+//      message and advances msg_tail (release stores).
+// Windows of one consumer are digested side by side; frees stay in ticket
+// order.
 static constexpr int MPSC_WIN = 64;
 static constexpr int MPSC_PIECE = 512;  // 16-byte vectors per digest piece (8 KiB)
 
 __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline) {
-  // s_stop is written only by thread 0 before the first barrier of a round;
-  // phase-A waits that give up write s_abort_a, read after the second
-  // barrier and cleared by thread 0 at the start of the next round (after the
-  // round's last barrier), so no thread can see a flag meant for a later
-  // check and leave while others wait at a barrier.
-  __shared__ int s_stop, s_abort_a;
-  __shared__ unsigned long long s_avail, s_t0, s_bytes;
+  // s_stop / s_done are written only by thread 0 before the first barrier of
+  // a round; phase-A waits that give up write s_abort_a, read after the
+  // second barrier and cleared by thread 0 at the start of the next round
+  // (after the round's last barrier), so no thread can see a flag meant for a
+  // later check and leave while others wait at a barrier.
+  __shared__ int s_stop, s_abort_a, s_done;
+  __shared__ unsigned long long s_avail, s_t;
   __shared__ unsigned long long s_start[MPSC_WIN], s_ppre[MPSC_WIN + 1], s_dig[MPSC_WIN];
   __shared__ unsigned int s_size[MPSC_WIN], s_prod[MPSC_WIN], s_seq[MPSC_WIN];
   const MpscView v = a.chans[c];
@@ -612,25 +620,31 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
   const unsigned long long nprod = (a.n_prod > c) ? (a.n_prod - c + a.n_cons - 1) / a.n_cons : 0;
   const unsigned long long expect = nprod * a.mpp;
   const unsigned long long win_max = min((unsigned long long)MPSC_WIN, (unsigned long long)(v.M / 2 ? v.M / 2 : 1));
-  if (tid == 0) {
-    s_t0 = ld_acq(&v.st->msg_tail.v);
-    s_bytes = 0;
-    s_stop = 0;
-    s_abort_a = 0;
-  }
-  __syncthreads();
-  unsigned long long t = s_t0, consumed = 0, windows = 0;
+  const unsigned long long base = a.base[c];  // first ticket of the run
+  unsigned long long* claim = a.claim + 16ull * c;
+  if (tid == 0) s_abort_a = 0;
+  unsigned long long consumed = 0, windows = 0, bytes = 0;
   hicr_mpsc_log_t* log = a.log + a.log_stride * c;
   unsigned long long ns_a = 0, ns_b = 0, ns_c = 0, tm = 0;
-  while (consumed < expect) {
-    if (tid == 0) tm = gtime();
+  int stop_c = 0;  // thread 0: a phase-C wait gave up
+  for (;;) {
     if (tid == 0) {
-      int stop = 0;
-      unsigned long long avail = 0;
-      for (;;) {
+      tm = gtime();
+      int stop = stop_c, done = 0;
+      unsigned long long t = 0, n = 0;
+      while (!stop) {
+        t = ld_acq(claim);
+        if (t - base >= expect) {
+          done = 1;
+          break;
+        }
         const unsigned long long W = ld_acq(&v.st->reserve.v);
-        avail = ((W >> 40) - t) & MASK24;
-        if (avail) break;
+        const unsigned long long avail = ((W >> 40) - t) & MASK24;
+        if (avail) {
+          n = min(min(avail, win_max), expect - (t - base));
+          if (atomicCAS(claim, t, t + n) == t) break;
+          continue;
+        }
         if (aborted(a.abort) || gtime() > deadline) {
           stop = 1;
           atomicExch(a.abort, 1u);
@@ -638,12 +652,15 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
         }
         __nanosleep(64);
       }
-      s_avail = min(min(avail, win_max), expect - consumed);
+      s_t = t;
+      s_avail = n;
       s_stop = stop;
+      s_done = done;
       s_abort_a = 0;
     }
     __syncthreads();
-    if (s_stop) break;
+    if (s_stop || s_done) break;
+    const unsigned long long t = s_t;
     const unsigned navail = (unsigned)s_avail;
     // A. acquire and stage metadata
     for (unsigned j = warp; j < navail; j += nwarp) {
@@ -712,12 +729,12 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       const unsigned long long n = s_size[j];
       const unsigned long long nv = (n + 15) / 16;
       const unsigned long long q0 = (pc - s_ppre[j]) * MPSC_PIECE;
-      const uint4* base = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
+      const uint4* src = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
       uint4 x[MPSC_PIECE / 32];
 #pragma unroll
       for (int u = 0; u < MPSC_PIECE / 32; ++u) {
         const unsigned long long q = q0 + lane + 32 * u;
-        if (q < nv) x[u] = __ldcg(base + q);
+        if (q < nv) x[u] = __ldcg(src + q);
       }
       unsigned long long d = 0;
 #pragma unroll
@@ -741,7 +758,8 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       ns_b += x - tm;
       tm = x;
     }
-    // C. log, then free up to the window's last message
+    // C. log, then free up to the window's last message once the previous
+    // window is freed
     for (unsigned j = tid; j < navail; j += blockDim.x) {
       hicr_mpsc_log_t L;
       L.producer = s_prod[j];
@@ -750,16 +768,25 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       L.reserved = 0;
       L.offset = s_start[j] & (v.R - 1);
       L.digest = s_dig[j];
-      log[consumed + j] = L;
+      log[t - base + j] = L;
     }
     if (tid == 0) {
       unsigned long long b = 0;
       for (unsigned j = 0; j < navail; ++j) b += s_size[j];
-      s_bytes += b;
-      st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
-      st_rel(&v.st->msg_tail.v, t + navail);
+      bytes += b;
+      while (ld_acq(&v.st->msg_tail.v) != t) {
+        if (aborted(a.abort) || gtime() > deadline) {
+          stop_c = 1;
+          atomicExch(a.abort, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+      if (!stop_c) {
+        st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
+        st_rel(&v.st->msg_tail.v, t + navail);
+      }
     }
-    t += navail;
     consumed += navail;
     ++windows;
     __syncthreads();
@@ -767,13 +794,13 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
   }
   if (tid == 0) {
     hicr_mpsc_result_t* r = a.res + c;
-    r->consumed = consumed;
-    r->bytes = s_bytes;
-    r->windows = windows;
-    r->consumer_ns[0] = ns_a;
-    r->consumer_ns[1] = ns_b;
-    r->consumer_ns[2] = ns_c;
-    if (s_stop || s_abort_a) r->status = HICR_ERR_TIMEOUT;
+    atomicAdd((unsigned long long*)&r->consumed, consumed);
+    atomicAdd((unsigned long long*)&r->bytes, bytes);
+    atomicAdd((unsigned long long*)&r->windows, windows);
+    atomicAdd((unsigned long long*)&r->consumer_ns[0], ns_a);
+    atomicAdd((unsigned long long*)&r->consumer_ns[1], ns_b);
+    atomicAdd((unsigned long long*)&r->consumer_ns[2], ns_c);
+    if (s_stop || s_abort_a || stop_c) r->status = HICR_ERR_TIMEOUT;
   }
 }
 
@@ -781,12 +808,13 @@ static constexpr unsigned MPSC_THREADS = 512;
 
 __global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) {
   const unsigned long long deadline = gtime() + a.timeout_ns;
-  if (blockIdx.x < a.n_cons) {
-    mpsc_consumer(a, blockIdx.x, deadline);
+  const unsigned ncta = a.n_cons * a.G;
+  if (blockIdx.x < ncta) {
+    mpsc_consumer(a, blockIdx.x / a.G, deadline);
     return;
   }
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned p = (blockIdx.x - a.n_cons) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const unsigned p = (blockIdx.x - ncta) * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (p < a.n_prod) mpsc_producer(a, p, lane, deadline);
 }
 
@@ -1464,11 +1492,11 @@ hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
 hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
                              uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
                              const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
-                             uint64_t timeout_ns, hicr_mpsc_log_t* d_log, uint64_t log_stride,
-                             hicr_mpsc_result_t* results) {
+                             uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                             uint64_t log_stride, hicr_mpsc_result_t* results) {
   Instance* in = I(h);
   if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
-      group == 0 || group > (uint32_t)MPSC_MAX_GROUP || in->capturing)
+      group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)
     return HICR_ERR_INVALID;
   void* sp = nullptr;
   uint64_t ssize = 0;
@@ -1483,16 +1511,31 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
     views[i] = mpsc_view(c);
   }
   if (log_stride < per * msgs_per_producer) return HICR_ERR_INVALID;
+  const unsigned warps = MPSC_THREADS / 32;
+  const unsigned long long grid = (unsigned long long)n_consumers * consumer_ctas + (n_producers + warps - 1) / warps;
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpsc_stream, MPSC_THREADS, 0));
+  if (grid > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
   const size_t vb = ((sizeof(MpscView) * n_consumers + 255) / 256) * 256;
   const size_t rb = ((sizeof(hicr_mpsc_result_t) * n_consumers + 255) / 256) * 256;
+  const size_t cb = 128 * (size_t)n_consumers;  // claim counters, one 128-byte line each
+  const size_t bb = ((8 * (size_t)n_consumers + 255) / 256) * 256;
   void* buf = nullptr;
-  if ((st = dev_buffer(in, vb + rb + 256, &buf)) != HICR_OK) return st;
+  if ((st = dev_buffer(in, vb + rb + 256 + cb + bb, &buf)) != HICR_OK) return st;
   char* p = (char*)buf;
   cudaStream_t s = in->comm();
   HICR_CUDA(in, cudaMemcpyAsync(p, views.data(), sizeof(MpscView) * n_consumers, cudaMemcpyHostToDevice, s));
   HICR_CUDA(in, cudaMemsetAsync(p + vb, 0, rb + 256, s));
+  unsigned long long* claim = (unsigned long long*)(p + vb + rb + 256);
+  unsigned long long* base = (unsigned long long*)(p + vb + rb + 256 + cb);
+  // the run starts at each channel's msg_tail (the channels are empty)
+  for (uint32_t i = 0; i < n_consumers; ++i) {
+    const unsigned long long* mt = &((MpscState*)get(in, chans[i])->state)->msg_tail.v;
+    HICR_CUDA(in, cudaMemcpyAsync(claim + 16 * i, mt, 8, cudaMemcpyDeviceToDevice, s));
+    HICR_CUDA(in, cudaMemcpyAsync(base + i, mt, 8, cudaMemcpyDeviceToDevice, s));
+  }
   MpscStreamArgs a;
   a.chans = (const MpscView*)p;
   a.n_cons = n_consumers;
@@ -1507,6 +1550,9 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   a.log_stride = log_stride;
   a.res = (hicr_mpsc_result_t*)(p + vb);
   a.abort = (unsigned int*)(p + vb + rb);
+  a.G = consumer_ctas;
+  a.claim = claim;
+  a.base = base;
   int* bad = (int*)(p + vb + rb + 128);
   k_mpsc_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
   int hbad = 0;
@@ -1518,10 +1564,9 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
     MpscState* ms = (MpscState*)get(in, chans[i])->state;
     HICR_CUDA(in, cudaMemsetAsync(&ms->max_bytes, 0, sizeof(Line) * 2, s));
   }
-  const unsigned warps = MPSC_THREADS / 32;
-  const unsigned grid = n_consumers + (n_producers + warps - 1) / warps;
   void* args[] = {&a};
-  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3(grid), dim3(MPSC_THREADS), args, 0, s));
+  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3((unsigned)grid), dim3(MPSC_THREADS),
+                                            args, 0, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   for (uint32_t i = 0; i < n_consumers; ++i) {

@@ -480,7 +480,7 @@ _channel_peek = _decl("hicr_channel_peek", [H, u32, u64, C.POINTER(hicr_msg_info
 _channel_pop = _decl("hicr_channel_pop", [H, u32, u64])
 _channel_depth = _decl("hicr_channel_depth", [H, u32, C.POINTER(u64), C.POINTER(u64)])
 _spsc_stream = _decl("hicr_spsc_stream", [H, vp, u32, u64, u32, u64, vp])
-_mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u64, vp, u64, vp])
+_mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp])
 _mpsc_nl_stream = _decl("hicr_mpsc_nl_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp])
 
 
@@ -555,11 +555,12 @@ def hicr_spsc_stream(inst, chans, tokens, batch, timeout_ns=60_000_000_000):
 
 
 def hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
-                     d_log, log_stride, timeout_ns=120_000_000_000):
+                     consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000):
     arr = (u32 * len(chans))(*chans)
     res = (hicr_mpsc_result_t * len(chans))()
     st = _mpsc_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
-                      _ptr(d_src_off), staging, group, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
+                      _ptr(d_src_off), staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride,
+                      C.addressof(res))
     return st, list(res)
 
 

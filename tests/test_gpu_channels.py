@@ -183,20 +183,26 @@ def _check_mpsc(w, logs, res, ring, sample=1.0, seed=0):
             assert int(L["digest"][j]) == od.byte_digest(splitmix.mpsc_payload_bytes(p, q, sz)), (c, j)
 
 
-@pytest.mark.parametrize("P,C,M,ring,max_msgs,hi,group", [
-    (64, 4, 64, 1 << 20, 256, 16 << 10, 4),
-    (48, 3, 40, 1 << 16, 64, 4 << 10, 1),
-    (33, 5, 17, 1 << 14, 32, 2 << 10, 8),
+@pytest.mark.parametrize("P,C,M,ring,max_msgs,hi,group,ctas", [
+    (64, 4, 64, 1 << 20, 256, 16 << 10, 4, 1),
+    (48, 3, 40, 1 << 16, 64, 4 << 10, 1, 3),
+    (33, 5, 17, 1 << 14, 32, 2 << 10, 8, 2),
+    (64, 2, 100, 1 << 15, 16, 4 << 10, 2, 5),
 ])
-def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, group):
+def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, group, ctas):
     w = configs.mpsc(7, n_producers=P, n_consumers=C, msgs_per_producer=M, ring_bytes=ring, max_msgs=max_msgs,
                      hi=hi)
-    run = bench.MpscRun(h, inst, w, group=group)
+    run = bench.MpscRun(h, inst, w, group=group, consumer_ctas=ctas)
     st, res = run.run()
     assert st == 0
     _check_mpsc(w, run.logs(), res, ring)
     # the rings wrapped (skip-to-start exercised) and are empty again
     assert sum(int(r.bytes) for r in res) > ring
+    for ch in run.chans:
+        assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
+    # a second run continues from the channels' counters
+    st, res = run.run()
+    assert st == 0 and sum(int(r.consumed) for r in res) == P * M
     for ch in run.chans:
         assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
     run.free()
@@ -256,7 +262,8 @@ def test_nonlocking_host_calls_match_oracle(h, inst, seed):
     assert h.hicr_mpsc_nl_create(inst, 2, 1024, 6)[0] == h.HICR_ERR_INVALID
 
 
-def _check_mpsc_nl(w, run, res):
+def _check_mpsc_nl(w, run, res, sample=1.0, seed=0):
+    rng = np.random.default_rng(seed)
     C = w.n_consumers
     logs = run.logs()
     for c in range(C):
@@ -269,7 +276,7 @@ def _check_mpsc_nl(w, run, res):
                                      run.ring_bytes)
         assert probs == [], (c, probs[:5])
         assert int(res[c].bytes) == int(L["size"].astype(np.int64).sum())
-        for j in range(n):
+        for j in np.nonzero(rng.random(n) < sample)[0]:
             p, q, sz = int(L["producer"][j]), int(L["seq"][j]), int(L["size"][j])
             assert int(L["digest"][j]) == od.byte_digest(splitmix.mpsc_payload_bytes(p, q, sz)), (c, j)
 
@@ -306,7 +313,7 @@ def test_nonlocking_stream_rejects_bad_shapes(h, inst):
     P, M = w.sizes.shape
     args = (run.d_sizes.data_ptr(), run.d_offs.data_ptr(), run.staging)
     # the locking-mode stream does not take non-locking channels and vice versa
-    assert h.hicr_mpsc_stream(inst, run.chans, P, M, *args, 1, run.d_log.data_ptr(), run.stride)[0] == \
+    assert h.hicr_mpsc_stream(inst, run.chans, P, M, *args, 1, 1, run.d_log.data_ptr(), run.stride)[0] == \
         h.HICR_ERR_INVALID
     lock = [h.hicr_mpsc_create(inst, 4, 1 << 12, 4)[1] for _ in range(2)]
     assert h.hicr_mpsc_nl_stream(inst, lock, P, M, *args, 1, 1, run.d_log.data_ptr(), run.stride)[0] == \
