@@ -55,6 +55,8 @@ def parse_args(argv=None):
                    help="prefix of the serving trace replayed through the per-op plain form")
     p.add_argument("--scale", type=float, default=1.0,
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
+    p.add_argument("--profile-case", choices=["mpsc_small"], default=None,
+                   help="run one small side case for a profiler capture, print its timings and exit")
     return p.parse_args(argv)
 
 
@@ -818,10 +820,42 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """mpsc_small: config 4's producers and consumers with 32 messages each
+    (0.83 GB of payload) over 16 x 128 MiB locking rings, then over 64 x 2 MiB
+    non-locking rings per consumer, 5 CTAs per consumer; each mode runs once
+    untimed and once timed, so the stream kernels launch in the order
+    locking, non-locking, locking, non-locking (about 3 GB on the device)."""
+    import torch
+    from paper_2509_01425_gb300 import build
+    build.build()
+    from paper_2509_01425_gb300 import hicr as h
+    torch.cuda.set_device(0)
+    inst = h.check(h.hicr_init(0), "hicr_init")
+    w = configs.mpsc(args.seed, msgs_per_producer=32, ring_bytes=128 * MiB)
+    run = MpscRun(h, inst, w, group=4, consumer_ctas=5)
+    out = {"case": "mpsc_small", "msgs": int(w.sizes.size), "payload_bytes": int(w.total_bytes)}
+    timings = {}
+    for rep in range(2):
+        for mode in ("locking", "nonlocking"):
+            run.set_mode(mode == "nonlocking", 5)
+            t0 = time.perf_counter()
+            h.check(run.run()[0], mode)
+            if rep:
+                timings[mode + "_s"] = time.perf_counter() - t0
+    run.free()
+    out.update(timings)
+    h.check(h.hicr_finalize(inst), "finalize")
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_ours(args)
 
 
