@@ -216,7 +216,8 @@ typedef struct {
  * single-message buffer; B echoes the message into A's buffer; repeat. Each
  * buffer holds exactly one message at the consumer, so a sender never has
  * more than one message outstanding. Each agent is `ctas_per_side` CTAs (1 ..
- * 64) of one cooperative grid that copy equal shares; a side's arrival count
+ * 256, both agents co-resident) of one cooperative grid that copy equal
+ * shares; a side's arrival count
  * is the channel head the other side acquires. `warmup` untimed round trips
  * come first. After the run both buffers must hold the message (the digests
  * let the caller check). Every wait gives up after timeout_ns.

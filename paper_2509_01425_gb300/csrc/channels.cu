@@ -1669,8 +1669,11 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
 hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
                           uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out) {
   Instance* in = I(h);
-  if (!in || !out || reps == 0 || ctas_per_side == 0 || ctas_per_side > 64 || bytes == 0 || in->capturing)
+  if (!in || !out || reps == 0 || ctas_per_side == 0 || ctas_per_side > 256 || bytes == 0 || in->capturing)
     return HICR_ERR_INVALID;
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pingpong, 512, 0));
+  if (2ull * ctas_per_side > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
   void* sp = nullptr;
   uint64_t ssize = 0;
   uint32_t sspace = 0;

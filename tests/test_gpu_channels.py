@@ -208,7 +208,8 @@ def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, 
     run.free()
 
 
-@pytest.mark.parametrize("nbytes,ctas", [(1, 1), (17, 1), (4096, 2), ((1 << 20) + 3, 8), (64 << 20, 32)])
+@pytest.mark.parametrize("nbytes,ctas", [(1, 1), (17, 1), (4096, 2), ((1 << 20) + 3, 8), (64 << 20, 32),
+                                         ((64 << 20) + 5, 152)])
 def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
     """Test Case 1 restated on one GPU: after the round trips both
     single-message buffers hold exactly the message (oracle digest)."""
@@ -221,6 +222,7 @@ def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
     assert r.digest_a == exp and r.digest_b == exp
     assert r.half_rtt_ns > 0 and r.goodput_gbs > 0
     assert h.hicr_pingpong(inst, s, 200, size, 1, 0, 1)[0] == h.HICR_ERR_BOUNDS
+    assert h.hicr_pingpong(inst, s, 0, 16, 1, 0, 257)[0] == h.HICR_ERR_INVALID
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
