@@ -9,13 +9,18 @@
 //   CTA 0, warp 0   dispatcher: acquires the doorbell, copies each new request
 //                   into the per-request device table, gives it a contiguous range
 //                   of work units (memcpy: one unit per cost chunk of its
-//                   template; burst: one unit) and publishes units_pub;
+//                   template; burst: one unit per message group) and
+//                   publishes units_pub;
 //   CTAs 1..C       one MPSC consumer per channel (windowed drain as in the
 //                   channel stream kernel); completes burst requests;
 //   other CTAs      worker warps: claim the next unit, wait until it is
 //                   published, find its request and either copy one cost
 //                   chunk of the template's ops (same warp copy and chunking
-//                   as the batch path) or push the burst's messages in order.
+//                   as the batch path) or push one group of the burst's
+//                   messages: group k reserves its tickets only after group
+//                   k-1 has reserved (a per-request chain), so a burst's
+//                   messages keep their order in the channel while the groups
+//                   are copied side by side.
 // Every wait is bounded by the run deadline (%globaltimer).
 #include <stdio.h>
 #include <string.h>
@@ -45,7 +50,14 @@ struct SrvReq {
   unsigned long long done;    // completed chunks / consumed messages
   unsigned long long digest;  // burst digest accumulator
   unsigned int N, need, kind, tmpl;
+  unsigned long long gres;    // burst: message groups that have reserved their tickets
 };
+
+// A burst's messages are cut into groups of at most SRV_GROUP_MSGS
+// consecutive messages whose rounded sizes sum to at most SRV_GROUP_BYTES
+// (a larger message is a group of its own); one work unit per group.
+static constexpr unsigned SRV_GROUP_MSGS = 8;
+static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
 
 struct SrvHostDesc {
   unsigned int kind, tmpl;
@@ -76,6 +88,9 @@ struct SrvArgs {
   const unsigned long long* moffs;
   const unsigned long long* t_mbase;
   const unsigned long long* t_nmsg;
+  const unsigned long long* gstart;   // group starts (message index within the template), ng + 1 per template
+  const unsigned long long* t_gbase;  // template's first entry in gstart
+  const unsigned long long* t_ngrp;
   const uint8_t* staging;
   DevTables dt;
   const MpscView* chans;
@@ -167,13 +182,14 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
       const unsigned long long w0 = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r));
       const unsigned long long dst = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r) + 1);
       const unsigned kind = (unsigned)w0, t = (unsigned)(w0 >> 32);
-      const unsigned long long N = kind == 0 ? a.t_chunks[t] : 1ull;
+      const unsigned long long N = kind == 0 ? a.t_chunks[t] : a.t_ngrp[t];
       const unsigned long long need = kind == 0 ? a.t_chunks[t] : a.t_nmsg[t];
       e->U = U;
       e->id = r;
       e->dst = dst;
       e->done = 0;
       e->digest = 0;
+      e->gres = 0;
       e->N = (unsigned)N;
       e->need = (unsigned)need;
       e->kind = kind;
@@ -257,78 +273,86 @@ __device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   }
 }
 
-// Push every message of a burst, in order, as producer = request index.
-__device__ bool srv_push_burst(const SrvArgs& a, const ReqView& rv, unsigned lane, unsigned long long deadline) {
+// Push group k of a burst (producer = request index). Lane 0 waits until
+// group k-1 has reserved, reserves the group's tickets and ring bytes with one
+// compare-and-swap and passes the turn on; then the warp copies the messages
+// and publishes their metadata.
+__device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, unsigned long long k, unsigned lane,
+                               unsigned long long deadline) {
   const unsigned long long id = rv.id;
   const unsigned t = rv.tmpl;
   const MpscView v = a.chans[id % a.n_ch];
-  const unsigned long long mbase = a.t_mbase[t], nmsg = a.t_nmsg[t];
-  const unsigned long long half = v.R / 2;
-  unsigned long long freed = 0, mt = 0;
+  const unsigned long long mbase = a.t_mbase[t];
+  const unsigned long long* gs = a.gstart + a.t_gbase[t];
+  const unsigned long long m0 = gs[k], m1 = gs[k + 1];
+  const int cnt = (int)(m1 - m0);  // 1 .. SRV_GROUP_MSGS
+  unsigned long long r[SRV_GROUP_MSGS], st[SRV_GROUP_MSGS];
+  for (int i = 0; i < cnt; ++i) r[i] = round16(a.msizes[mbase + m0 + i]);
+  unsigned long long W = 0;
+  int stop = 0;
+  ws_set(a, WS_RESERVE);
   if (lane == 0) {
-    freed = ld_acq(&v.st->freed.v);
-    mt = ld_acq(&v.st->msg_tail.v);
+    unsigned sleep_ns = 32;
+    while (ld_acq(&e->gres) != k) {  // the previous group's turn
+      if (srv_abort(a, deadline)) {
+        stop = 1;
+        break;
+      }
+      __nanosleep(sleep_ns);
+      sleep_ns = min(sleep_ns * 2, 256u);
+    }
+    unsigned long long freed = 0, mt = 0;
+    bool fresh = false;
+    sleep_ns = 32;
+    while (!stop) {
+      W = ld_rlx(&v.st->reserve.v);
+      const unsigned long long end = mpsc_place(W, r, cnt, v.R, st);
+      const unsigned long long t0 = W >> 40;
+      if (!fresh) {
+        freed = ld_acq(&v.st->freed.v);
+        mt = ld_acq(&v.st->msg_tail.v);
+        fresh = true;
+      }
+      bool room = ((end - freed) & MASK40) <= v.R && (((t0 + cnt) - mt) & MASK24) <= v.M;
+      if (!room) {
+        freed = ld_acq(&v.st->freed.v);
+        mt = ld_acq(&v.st->msg_tail.v);
+        room = ((end - freed) & MASK40) <= v.R && (((t0 + cnt) - mt) & MASK24) <= v.M;
+      }
+      if (room && atomicCAS(&v.st->reserve.v, W, (((t0 + cnt) & MASK24) << 40) | end) == W) break;
+      if (srv_abort(a, deadline)) {
+        stop = 1;
+        break;
+      }
+      if (!room) {
+        __nanosleep(sleep_ns);
+        sleep_ns = min(sleep_ns * 2, 4096u);
+      }
+    }
+    if (!stop) st_rel(&e->gres, k + 1);
   }
-  for (unsigned long long s = 0; s < nmsg;) {
-    unsigned long long r[8], st[8];
-    int k = 0;
-    unsigned long long sum = 0;
-    for (; k < 8 && s + k < nmsg; ++k) {
-      const unsigned long long rk = round16(a.msizes[mbase + s + k]);
-      if (k > 0 && sum + rk > half) break;
-      r[k] = rk;
-      sum += rk;
+  if (__shfl_sync(FULLM, stop, 0)) return false;
+  ws_set(a, WS_PUSH);
+  W = __shfl_sync(FULLM, W, 0);
+  const unsigned long long t0 = W >> 40;
+  for (int i = 0; i < cnt; ++i) {
+    const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+    warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.moffs[mbase + m0 + i], a.msizes[mbase + m0 + i], lane);
+  }
+  __threadfence();
+  __syncwarp();
+  for (int i = 0; i < cnt; ++i) {
+    const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
+    if (lane == (unsigned)i) {
+      const unsigned long long tk = t0 + i;
+      MpscMeta* m = v.meta + (tk & (v.M - 1));
+      m->start = si;
+      m->size = (unsigned int)a.msizes[mbase + m0 + i];
+      m->producer = (unsigned int)id;
+      m->seq = (unsigned int)(m0 + i);
+      m->flags = 0;
+      st_rel(&m->ready, (tk & MASK24) + 1);
     }
-    unsigned long long W = 0;
-    int stop = 0;
-    ws_set(a, WS_RESERVE);
-    if (lane == 0) {
-      unsigned sleep_ns = 32;
-      for (;;) {
-        W = ld_rlx(&v.st->reserve.v);
-        const unsigned long long end = mpsc_place(W, r, k, v.R, st);
-        const unsigned long long t0 = W >> 40;
-        bool room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
-        if (!room) {
-          freed = ld_acq(&v.st->freed.v);
-          mt = ld_acq(&v.st->msg_tail.v);
-          room = ((end - freed) & MASK40) <= v.R && (((t0 + k) - mt) & MASK24) <= v.M;
-        }
-        if (room && atomicCAS(&v.st->reserve.v, W, (((t0 + k) & MASK24) << 40) | end) == W) break;
-        if (srv_abort(a, deadline)) {
-          stop = 1;
-          break;
-        }
-        if (!room) {
-          __nanosleep(sleep_ns);
-          sleep_ns = min(sleep_ns * 2, 4096u);
-        }
-      }
-    }
-    if (__shfl_sync(FULLM, stop, 0)) return false;
-    ws_set(a, WS_PUSH);
-    W = __shfl_sync(FULLM, W, 0);
-    const unsigned long long t0 = W >> 40;
-    for (int i = 0; i < k; ++i) {
-      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
-      warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.moffs[mbase + s + i], a.msizes[mbase + s + i], lane);
-    }
-    __threadfence();
-    __syncwarp();
-    for (int i = 0; i < k; ++i) {
-      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
-      if (lane == (unsigned)i) {
-        const unsigned long long tk = t0 + i;
-        MpscMeta* m = v.meta + (tk & (v.M - 1));
-        m->start = si;
-        m->size = (unsigned int)a.msizes[mbase + s + i];
-        m->producer = (unsigned int)id;
-        m->seq = (unsigned int)(s + i);
-        m->flags = 0;
-        st_rel(&m->ready, (tk & MASK24) + 1);
-      }
-    }
-    s += k;
   }
   return true;
 }
@@ -408,7 +432,7 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
     }
     if (rv.kind == 0) {
       srv_copy_chunk(a, e, rv, u - rv.U, lane);
-    } else if (!srv_push_burst(a, rv, lane, deadline)) {
+    } else if (!srv_push_group(a, e, rv, u - rv.U, lane, deadline)) {
       ws_set(a, WS_WORKER_DONE);
       return;
     }
@@ -669,7 +693,7 @@ struct Server {
   // templates (host copies; uploaded lazily)
   std::vector<hicr_op_t> tops;
   std::vector<unsigned long long> tcstart, t_opbase, t_nops, t_cbase, t_chunks, t_total, t_region;
-  std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg;
+  std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg, gstart, t_gbase, t_ngrp;
   hicr_slot_t staging = 0;
   bool have_staging = false;
   bool uploaded = false;
@@ -706,7 +730,9 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   if (sv->uploaded) return HICR_OK;
   if (sv->t_nops.empty()) sv->t_nops.push_back(0), sv->t_opbase.push_back(0), sv->t_cbase.push_back(0),
       sv->t_chunks.push_back(0), sv->t_total.push_back(0), sv->t_region.push_back(0), sv->tcstart.push_back(0);
-  if (sv->t_nmsg.empty()) sv->t_nmsg.push_back(0), sv->t_mbase.push_back(0);
+  if (sv->t_nmsg.empty()) sv->t_nmsg.push_back(0), sv->t_mbase.push_back(0), sv->t_gbase.push_back(0),
+      sv->t_ngrp.push_back(0);
+  if (sv->gstart.empty()) sv->gstart.push_back(0);
   if (sv->tops.empty()) sv->tops.push_back(hicr_op_t{0, 0, 0, 0, 0});
   if (sv->msizes.empty()) sv->msizes.push_back(0), sv->moffs.push_back(0);
   std::vector<const void*> dummy;
@@ -715,7 +741,8 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
                        8 * (al(sv->tcstart.size() * 8) + al(sv->t_opbase.size() * 8) + al(sv->t_nops.size() * 8) +
                             al(sv->t_cbase.size() * 8) + al(sv->t_chunks.size() * 8) + al(sv->t_total.size() * 8) +
                             al(sv->msizes.size() * 8) + al(sv->moffs.size() * 8) + al(sv->t_mbase.size() * 8) +
-                            al(sv->t_nmsg.size() * 8)) / 8;
+                            al(sv->t_nmsg.size() * 8) + al(sv->gstart.size() * 8) + al(sv->t_gbase.size() * 8) +
+                            al(sv->t_ngrp.size() * 8)) / 8;
   char* d = nullptr;
   HICR_CUDA(in, cudaMalloc(&d, bytes + 4096));
   sv->dev_tmpl = d;
@@ -741,6 +768,9 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   UP(moffs, sv->moffs);
   UP(t_mbase, sv->t_mbase);
   UP(t_nmsg, sv->t_nmsg);
+  UP(gstart, sv->gstart);
+  UP(t_gbase, sv->t_gbase);
+  UP(t_ngrp, sv->t_ngrp);
 #undef UP
   sv->uploaded = true;
   return HICR_OK;
@@ -901,6 +931,24 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, con
     mb += sizes[i];
   }
   sv->m_bytes.push_back(mb);
+  // message groups (work units): consecutive messages, at most SRV_GROUP_MSGS
+  // of them and at most SRV_GROUP_BYTES rounded bytes unless a single message
+  // is larger; every group is at most half a ring (each message is)
+  sv->t_gbase.push_back(sv->gstart.size());
+  uint64_t ng = 0, gb = 0, gm = 0;
+  for (uint64_t i = 0; i < count; ++i) {
+    const uint64_t r = round16(sizes[i]);
+    if (gm == 0 || gm == SRV_GROUP_MSGS || gb + r > SRV_GROUP_BYTES || gb + r > sv->cfg.ring_bytes / 2) {
+      sv->gstart.push_back(i);
+      ++ng;
+      gb = 0;
+      gm = 0;
+    }
+    gb += r;
+    ++gm;
+  }
+  sv->gstart.push_back(count);
+  sv->t_ngrp.push_back(ng);
   *tmpl = t;
   return HICR_OK;
 }
