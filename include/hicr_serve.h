@@ -103,7 +103,10 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t inst, hicr_serve_t srv
 /* Serve `n` requests (host array, sorted by arrival). mode 0 = by arrival
  * time (the trace), mode 1 = alone (request i+1 is admitted only after
  * request i completed). results: host array of n (may be NULL); stats may be
- * NULL. Synchronous. Errors: INVALID (unknown template, unsorted), NOMEM (a
+ * NULL. Synchronous. The engine checks itself while it runs: an entry
+ * outside the run, or a burst message consumed out of its request's order,
+ * stops it with DEVICE (stats.dev_flags bit 2; the message names the request).
+ * Errors: INVALID (unknown template, unsorted), NOMEM (a
  * request's region exceeds the arena), DEVICE, TIMEOUT (not finished within
  * timeout_ns; the engine stops, and if its kernel has not ended 10 s later
  * the call returns anyway and leaves the run's buffers allocated). */

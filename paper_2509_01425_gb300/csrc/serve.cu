@@ -570,6 +570,19 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
       if (lane == 0) atomicAdd(&s_dig[j], d);
     }
+    // self-check of the channel's order per producer: message j must be its
+    // request's next one (messages consumed in earlier windows, all of them
+    // by this consumer, plus earlier messages of the request in this window)
+    for (unsigned j = tid; j < navail; j += blockDim.x) {
+      if (s_prod[j] < a.n_req) {
+        unsigned k = 0;
+        for (unsigned i = 0; i < j; ++i) k += (s_prod[i] == s_prod[j]);
+        if (s_seq[j] != __ldcg(&a.req[s_prod[j]].done) + k) {
+          atomicCAS(&a.ctl->bad.v, 0ull, 1ull + s_prod[j]);
+          atomicExch(&a.ctl->abort.v, 1ull);
+        }
+      }
+    }
     __syncthreads();
     ws_set(a, WS_C_ACCOUNT);
     // per-request accounting: message digest weighted by its index in the burst
