@@ -365,6 +365,8 @@ struct SpscStreamArgs {
   unsigned int* abort;
 };
 
+static constexpr int SPSC_U = 8;
+
 __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   __shared__ int s_stop;
   __shared__ unsigned long long s_red[2][16];
@@ -382,6 +384,11 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   if (tid == 0) s_base = ld_acq(producer ? &v.st->head.v : &v.st->tail.v);
   __syncthreads();
   const unsigned long long base = s_base;
+  // fast layout when the vectors of a token divide the block
+  const bool fast = (blockDim.x % vpt) == 0;
+  const unsigned tpi = fast ? blockDim.x / vpt : 1;  // tokens per pass of the block
+  const unsigned jv = fast ? tid % vpt : 0, tl0 = fast ? tid / vpt : 0;
+  const unsigned long long step = tpi % v.cap;
   unsigned long long cached = base, max_occ = 0, done = 0, mism = 0, dig = 0;
   int stop = 0;
   for (unsigned long long s0 = 0; s0 < a.tokens; s0 += a.batch) {
@@ -411,28 +418,79 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
     }
     __syncthreads();
     if (s_stop) break;
-    const unsigned long long nv = k * vpt;
-    for (unsigned long long q = tid; q < nv; q += blockDim.x) {
-      const unsigned long long tok = s0 + q / vpt;
-      const unsigned long long word = tok * wpt + (q % vpt) * 2;  // index of the first 8-byte word
-      uint4* p = reinterpret_cast<uint4*>(v.ring + ((base + tok) % v.cap) * v.ts) + (q % vpt);
-      if (producer) {
-        const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
-        uint4 x;
-        x.x = (unsigned)w0;
-        x.y = (unsigned)(w0 >> 32);
-        x.z = (unsigned)w1;
-        x.w = (unsigned)(w1 >> 32);
-        *p = x;
-      } else {
-        const uint4 x = __ldcg(p);
-        const unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
-        const unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
-        mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
-        dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+    if (fast) {
+      // thread = vector column jv of tokens tl0, tl0 + tpi, ...; ring slots
+      // advance by `step` (tpi mod capacity) without a division per vector
+      unsigned long long slot = (base + s0 + tl0) % v.cap;
+      for (unsigned long long tl = tl0; tl < k; tl += (unsigned long long)SPSC_U * tpi) {
+        if (producer) {
+#pragma unroll
+          for (int u = 0; u < SPSC_U; ++u) {
+            const unsigned long long t_ = tl + (unsigned long long)u * tpi;
+            if (t_ < k) {
+              const unsigned long long word = (s0 + t_) * wpt + 2ull * jv;
+              uint4* p = reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv;
+              const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
+              uint4 x;
+              x.x = (unsigned)w0;
+              x.y = (unsigned)(w0 >> 32);
+              x.z = (unsigned)w1;
+              x.w = (unsigned)(w1 >> 32);
+              *p = x;
+            }
+            slot += step;
+            if (slot >= v.cap) slot -= v.cap;
+          }
+        } else {
+          uint4 x[SPSC_U];
+          unsigned long long sl = slot;
+#pragma unroll
+          for (int u = 0; u < SPSC_U; ++u) {
+            if (tl + (unsigned long long)u * tpi < k)
+              x[u] = __ldcg(reinterpret_cast<const uint4*>(v.ring + sl * v.ts) + jv);
+            sl += step;
+            if (sl >= v.cap) sl -= v.cap;
+          }
+          slot = sl;
+#pragma unroll
+          for (int u = 0; u < SPSC_U; ++u) {
+            const unsigned long long t_ = tl + (unsigned long long)u * tpi;
+            if (t_ < k) {
+              const unsigned long long word = (s0 + t_) * wpt + 2ull * jv;
+              const unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
+              const unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
+              mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+              dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+            }
+          }
+        }
+      }
+    } else {
+      // general token sizes: one vector per thread per step
+      const unsigned long long nv = k * vpt;
+      for (unsigned long long q = tid; q < nv; q += blockDim.x) {
+        const unsigned long long tok = s0 + q / vpt;
+        const unsigned long long word = tok * wpt + (q % vpt) * 2;  // index of the first 8-byte word
+        uint4* p = reinterpret_cast<uint4*>(v.ring + ((base + tok) % v.cap) * v.ts) + (q % vpt);
+        if (producer) {
+          const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
+          uint4 x;
+          x.x = (unsigned)w0;
+          x.y = (unsigned)(w0 >> 32);
+          x.z = (unsigned)w1;
+          x.w = (unsigned)(w1 >> 32);
+          *p = x;
+        } else {
+          const uint4 x = __ldcg(p);
+          const unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+          const unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+          mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+          dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+        }
       }
     }
-    if (producer) __threadfence();
+    // the barrier orders every thread's ring accesses before thread 0's
+    // release store, which is cumulative: no per-thread fence is needed
     __syncthreads();
     if (tid == 0) st_rel(producer ? &v.st->head.v : &v.st->tail.v, base + s0 + k);
     done = s0 + k;
@@ -1126,9 +1184,9 @@ __global__ void __launch_bounds__(512) k_pingpong(PingArgs a) {
     } else {
       cta_copy(a.buf_b + lo, a.msg + lo, hi - lo);  // send
     }
-    __threadfence();
+    // barrier, then one cumulative release by thread 0 (no per-thread fence)
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(mine, 1ull);
+    if (threadIdx.x == 0) red_add_rel(mine, 1ull);
     if (side == 0) {
       // A: wait for the echo of round k
       if (threadIdx.x == 0) {

@@ -150,6 +150,7 @@ def _spsc_expected_digest(channel, tokens, wpt=8):
     (8, 16, 64, 1003, 16),
     (4, 64, 32, 5000, 1),
     (2, 4096, 128, 70_000, 4096),
+    (3, 100, 48, 2_000, 7),          # 3 vectors per token: the general (non-divisible) layout
 ])
 def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
     chans = [h.hicr_spsc_create(inst, ts, cap)[1] for _ in range(n_ch)]
