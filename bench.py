@@ -55,16 +55,18 @@ def parse_args(argv=None):
                    help="prefix of the serving trace replayed through the per-op plain form")
     p.add_argument("--scale", type=float, default=1.0,
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
-    p.add_argument("--profile-case", choices=["mpsc_small"], default=None,
+    p.add_argument("--profile-case", choices=["mpsc_small", "copy_small"], default=None,
                    help="run one small side case for a profiler capture, print its timings and exit")
+    p.add_argument("--batch-config", default=None,
+                   help="copy_small: JSON object of batch configuration fields (default: the library's)")
     return p.parse_args(argv)
 
 
-def copy_traffic(alg_bytes_per_launch):
-    """DRAM bytes per k_copy launch scaled from the committed ncu capture, or
-    None when the kernel source changed since that capture."""
+def copy_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of the copy kernel scaled from its committed ncu
+    capture, or None when there is none or the source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_copy_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -789,9 +791,11 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None,
                      "nominal_peak": nominal, "nominal_source": nominal_src,
                      "frac_of_nominal": (achieved / nominal) if achieved else None,
-                     "traffic": copy_traffic(bytes_step / n_epochs),
+                     "traffic": copy_traffic("k_copy_tma" if tuned.get("engine") == 1 else "k_copy",
+                                             bytes_step / n_epochs),
                      "algorithmic_bytes_per_launch": bytes_step / n_epochs,
-                     "kernel": "k_copy", "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
+                     "kernel": "k_copy_tma" if tuned.get("engine") == 1 else "k_copy",
+                     "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "launches_timed": launches},
         "gpu_launches": args.steps * 2 * n_epochs,
         "clocks": clk,
@@ -803,18 +807,33 @@ def run_ours(args):
         wl = scaled_batched(args.seed, args.scale, large=True)
         assert (wl.slot_sizes == w.slot_sizes).all()
         dl = device_ops(remap(wl.ops, ids))
-        h.check(h.hicr_profile_enable(inst, 1), "profile")
-        h.check(h.hicr_profile_reset(inst), "profile")
-        gl = capture_epochs(h, inst, dl, wl.epochs)
         lsteps = max(3, args.steps // 2)
-        lms, lcopy, ln = time_graph(h, inst, stream, gl, lsteps, 2, prof=True)
-        h.check(h.hicr_profile_enable(inst, 0), "profile")
         lb = 2 * wl.total_bytes
+
+        def large_run():
+            h.check(h.hicr_profile_enable(inst, 1), "profile")
+            h.check(h.hicr_profile_reset(inst), "profile")
+            gl = capture_epochs(h, inst, dl, wl.epochs)
+            lms, lcopy, _ = time_graph(h, inst, stream, gl, lsteps, 2, prof=True)
+            h.check(h.hicr_profile_enable(inst, 0), "profile")
+            h.check(h.hicr_graph_destroy(inst, gl), "graph_destroy")
+            return {"GB_per_s": lb * lsteps / (lms * 1e-3) / 1e9,
+                    "copy_kernel_GB_per_s": lb * lsteps / (lcopy * 1e-3) / 1e9,
+                    "frac_of_peak": lb * lsteps / (lms * 1e-3) / 1e9 / peak}
+
+        headline_cfg = h.check(h.hicr_batch_get_config(inst), "get_config")
         side["large_segments"] = {"workload": "1-4 MiB aligned ops, same slots", "ops": int(len(wl.ops)),
-                                  "GB_per_s": lb * lsteps / (lms * 1e-3) / 1e9,
-                                  "copy_kernel_GB_per_s": lb * lsteps / (lcopy * 1e-3) / 1e9,
-                                  "frac_of_peak": lb * lsteps / (lms * 1e-3) / 1e9 / peak}
-        h.check(h.hicr_graph_destroy(inst, gl), "graph_destroy")
+                                  "config": tuned, **large_run()}
+        # the TMA engine (bulk copies through shared memory) on the same ops
+        tma = h.check(h.hicr_batch_get_config(inst), "get_config")
+        tma.engine, tma.tma_min_bytes, tma.threads, tma.blocks_per_sm = 1, 256 << 10, 384, 1
+        tma.chunk_bytes, tma.op_cost_bytes = 1 << 20, 4096
+        if h.hicr_batch_set_config(inst, tma) == 0:
+            side["large_segments"]["tma_engine"] = {"config": tma.as_dict(), **large_run()}
+        # what the autotuner picks for this workload (both engines are candidates)
+        ltuned, _ = autotune(h, inst, dl, wl.epochs)
+        side["large_segments"]["autotuned"] = {"config": ltuned, **large_run()}
+        h.check(h.hicr_batch_set_config(inst, headline_cfg), "set_config")
         del dl
 
         # plain form: one cudaMemcpyAsync per op, same op table, same epochs + fences
@@ -874,6 +893,48 @@ def run_ours(args):
 
 
 def run_profile_case(args):
+    if args.profile_case == "copy_small":
+        return run_copy_small(args)
+    return run_mpsc_small(args)
+
+
+def run_copy_small(args):
+    """copy_small: the batched workload at --scale (default 1/8: 32 slots,
+    2 GiB, 12,500 ops) under the configuration --batch-config, each epoch one
+    device batch + fence; two passes, so the copy kernel launches once per
+    epoch in each (the second pass is the one to capture)."""
+    import torch
+    from paper_2509_01425_gb300 import build
+    build.build()
+    from paper_2509_01425_gb300 import hicr as h
+    torch.cuda.set_device(0)
+    inst = h.check(h.hicr_init(0), "hicr_init")
+    if args.batch_config:
+        c = h.check(h.hicr_batch_get_config(inst), "get_config")
+        for k, v in json.loads(args.batch_config).items():
+            setattr(c, k, int(v))
+        h.check(h.hicr_batch_set_config(inst, c), "set_config")
+    scale = args.scale if args.scale != 1.0 else 0.125
+    w = scaled_batched(args.seed, scale)
+    ids = setup_slots(h, inst, w, args.seed)
+    dops = device_ops(remap(w.ops, ids))
+    out = {"case": "copy_small", "scale": scale, "ops": int(len(w.ops)), "epochs": len(w.epochs),
+           "config": h.check(h.hicr_batch_get_config(inst), "get_config").as_dict()}
+    for rep in range(2):
+        t0 = time.perf_counter()
+        for a, b in w.epochs:
+            h.check(h.hicr_memcpy_batch_device(inst, dops.data_ptr() + 32 * a, b - a), "batch")
+            h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+        out[f"pass{rep}_s"] = time.perf_counter() - t0
+    out["algorithmic_bytes_per_pass"] = int(2 * w.total_bytes)
+    for sid in ids:
+        h.check(h.hicr_mem_free(inst, sid), "free")
+    h.check(h.hicr_finalize(inst), "finalize")
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_mpsc_small(args):
     """mpsc_small: config 4's producers and consumers with 32 messages each
     (0.83 GB of payload) over 16 x 128 MiB locking rings, then over 64 x 2 MiB
     non-locking rings per consumer, 5 CTAs per consumer; each mode runs once

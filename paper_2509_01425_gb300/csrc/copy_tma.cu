@@ -1,0 +1,206 @@
+// The TMA engine of the batched copy (batch configuration engine = 1).
+//
+// Same work distribution as k_copy (warps claim chunks of the cost model and
+// copy the byte pieces of the ops a chunk overlaps), but a piece of at least
+// tma_min bytes whose source and destination are both in HBM and have the same
+// address residue mod 16 moves its 16-byte-aligned body through the Tensor
+// Memory Accelerator: lane 0 of the warp streams the body in TMA_STG-byte
+// pieces through TMA_NST shared-memory stages, each a bulk global->shared load
+// completed on the stage's mbarrier (cp.async.bulk ... complete_tx) followed
+// by a bulk shared->global store (cp.async.bulk ... bulk_group). A stage is
+// refilled only after the store that read it has finished reading
+// (cp.async.bulk.wait_group.read). The unaligned head and the sub-16-byte tail
+// go through the vector warp copy. Every mbarrier wait is bounded; one that
+// gives up records HICR_ERR_TIMEOUT for the op in the sticky batch error.
+#include "copy.cuh"
+#include "hicr_internal.h"
+
+namespace hicr {
+
+static constexpr unsigned FULLM_COPY = 0xffffffffu;
+static constexpr unsigned TMA_NST = 4;        // stages per warp
+static constexpr unsigned TMA_STG = 4096;     // bytes per stage
+static constexpr unsigned TMA_WARP_SMEM = TMA_NST * TMA_STG;
+static constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // bound of one mbarrier wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tma_store(void* gdst, const void* ssrc, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long tma_now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Lane 0: copy n bytes (a multiple of 16; d and s 16-byte aligned) through the
+// warp's stages. `phase` holds one parity bit per stage. Returns false when a
+// wait gave up (the copy is then incomplete).
+__device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uint8_t* stage,
+                         unsigned long long* bars, unsigned& phase) {
+  const unsigned long long np = (n + TMA_STG - 1) / TMA_STG;
+  auto piece_bytes = [&](unsigned long long p) -> unsigned {
+    const unsigned long long off = p * TMA_STG;
+    return (unsigned)(n - off < TMA_STG ? n - off : TMA_STG);
+  };
+  const unsigned long long pro = np < TMA_NST - 1 ? np : TMA_NST - 1;
+  for (unsigned long long p = 0; p < pro; ++p) {
+    const unsigned k = (unsigned)(p % TMA_NST);
+    mbar_expect_tx(bars + k, piece_bytes(p));
+    tma_load(stage + k * TMA_STG, s + p * TMA_STG, piece_bytes(p), bars + k);
+  }
+  bool ok = true;
+  for (unsigned long long p = 0; p < np; ++p) {
+    const unsigned long long q = p + TMA_NST - 1;
+    if (q < np) {
+      // stage q % NST last held piece p - 1: its store must have read it
+      tma_wait_read0();
+      const unsigned k = (unsigned)(q % TMA_NST);
+      mbar_expect_tx(bars + k, piece_bytes(q));
+      tma_load(stage + k * TMA_STG, s + q * TMA_STG, piece_bytes(q), bars + k);
+    }
+    const unsigned k = (unsigned)(p % TMA_NST);
+    const unsigned par = (phase >> k) & 1u;
+    if (!mbar_try_wait(bars + k, par)) {
+      const unsigned long long t0 = tma_now_ns();
+      while (!mbar_try_wait(bars + k, par)) {
+        if (tma_now_ns() - t0 > TMA_WAIT_NS) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (!ok) break;
+    phase ^= 1u << k;
+    tma_store(d + p * TMA_STG, stage + k * TMA_STG, piece_bytes(p));
+    tma_commit();
+  }
+  tma_wait_all();
+  // order the async-proxy writes before the generic-proxy completion signal
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  return ok;
+}
+
+__global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
+  extern __shared__ __align__(128) uint8_t tma_smem[];
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  uint8_t* stage = tma_smem + (size_t)warp * TMA_WARP_SMEM;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(tma_smem + (size_t)nwarp * TMA_WARP_SMEM) + warp * TMA_NST;
+  if (lane == 0) {
+    for (unsigned k = 0; k < TMA_NST; ++k) mbar_init(bars + k);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  unsigned phase = 0;  // lane 0: parity of each stage's next completion
+  int tma_ok = 1;      // cleared (warp-uniformly) after a wait gave up: the warp stops using its stages
+  const unsigned long long nchunks = *(volatile unsigned long long*)&a.ctrl->nchunks;
+  const unsigned long long total = *(volatile unsigned long long*)&a.ctrl->total;
+  const unsigned long long chunk = a.chunk;
+  for (;;) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(&a.ctrl->claim, 1ull);
+    c = __shfl_sync(FULLM_COPY, c, 0);
+    if (c >= nchunks) break;
+    const unsigned long long lo = c * chunk;
+    const unsigned long long hi = min(lo + chunk, total);
+    for (unsigned long long i = find_op(a.cstart, a.count, lo, lane); i < a.count; ++i) {
+      const unsigned long long cs = a.cstart[i];
+      if (cs >= hi) break;
+      const hicr_op_t op = a.ops[i];
+      const unsigned long long bs = cs + a.op_cost;
+      const unsigned long long be = bs + op.n;
+      const unsigned long long b0 = lo > bs ? lo - bs : 0ull;
+      const unsigned long long b1 = (hi < be ? hi : be) > bs ? (hi < be ? hi : be) - bs : 0ull;
+      if (b1 > b0) {
+        uint8_t* d = reinterpret_cast<uint8_t*>(a.dt.slot_base[op.dst]) + op.dst_off + b0;
+        const uint8_t* s = reinterpret_cast<const uint8_t*>(a.dt.slot_base[op.src]) + op.src_off + b0;
+        const unsigned long long n = b1 - b0;
+        const bool hbm = meta_space(a.dt.slot_meta[op.dst]) == HICR_SPACE_HBM &&
+                         meta_space(a.dt.slot_meta[op.src]) == HICR_SPACE_HBM;
+        const unsigned long long head = (16 - (reinterpret_cast<uintptr_t>(d) & 15)) & 15;
+        if (tma_ok && hbm && n >= a.tma_min && n >= head + 16 &&
+            ((reinterpret_cast<uintptr_t>(d) ^ reinterpret_cast<uintptr_t>(s)) & 15) == 0) {
+          const unsigned long long body = (n - head) & ~15ull, tail = n - head - body;
+          if (head) warp_copy(d, s, head, lane);
+          if (tail) warp_copy(d + head + body, s + head + body, tail, lane);
+          int ok = 1;
+          if (lane == 0) ok = tma_body(d + head, s + head, body, stage, bars, phase);
+          ok = __shfl_sync(FULLM_COPY, ok, 0);
+          if (!ok) {
+            tma_ok = 0;
+            if (lane == 0) atomicCAS(a.dt.sticky, 0ull, (i << 8) | (unsigned long long)(-HICR_ERR_TIMEOUT));
+          }
+        } else {
+          warp_copy(d, s, n, lane);
+        }
+      }
+      const unsigned pieces = (unsigned)((be - 1) / chunk - cs / chunk + 1);
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) {
+        const unsigned prev = atomicAdd(&a.done[i], 1u);
+        if (prev + 1 == pieces) {
+          __threadfence();
+          atomicAdd(&a.dt.sent[op.src], 1ull);
+          atomicAdd(&a.dt.recv[op.dst], 1ull);
+          const uint32_t ts = meta_tag(a.dt.slot_meta[op.src]);
+          const uint32_t td = meta_tag(a.dt.slot_meta[op.dst]);
+          atomicAdd(&a.dt.tag_ops[ts], 1ull);
+          if (td != ts) atomicAdd(&a.dt.tag_ops[td], 1ull);
+        }
+      }
+    }
+  }
+}
+
+size_t copy_tma_smem(unsigned threads) { return (size_t)(threads / 32) * (TMA_WARP_SMEM + TMA_NST * 8); }
+
+hicr_status copy_tma_prepare(Instance* in, unsigned threads, int* blocks_per_sm) {
+  const size_t smem = copy_tma_smem(threads);
+  *blocks_per_sm = 0;
+  if (smem > in->prop.sharedMemPerBlockOptin) return HICR_OK;  // cannot be resident at all
+  // allow the largest opt-in size once, so that every shape that fits can launch
+  HICR_CUDA(in, cudaFuncSetAttribute((const void*)k_copy_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)in->prop.sharedMemPerBlockOptin));
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_copy_tma, threads, smem));
+  *blocks_per_sm = per_sm;
+  return HICR_OK;
+}
+
+hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, unsigned grid, unsigned threads, cudaStream_t st) {
+  k_copy_tma<<<grid, threads, copy_tma_smem(threads), st>>>(a);
+  HICR_CUDA(in, cudaGetLastError());
+  return HICR_OK;
+}
+
+}  // namespace hicr

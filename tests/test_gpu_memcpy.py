@@ -107,10 +107,15 @@ def _corner_ops(size):
     return configs.make_ops(dst, src, doff, soff, nn)
 
 
-@pytest.mark.parametrize("path", ["batch", "device", "queue", "plain"])
+@pytest.mark.parametrize("path", ["batch", "device", "queue", "plain", "tma"])
 def test_size_and_alignment_corners(h, inst, path):
     size = 8 << 20
     ops = _corner_ops(size)
+    if path == "tma":  # the TMA engine with its smallest threshold: every co-aligned piece >= 1 KiB
+        st, c = h.hicr_batch_get_config(inst)
+        c.engine, c.tma_min_bytes, c.threads, c.blocks_per_sm, c.chunk_bytes = 1, 1024, 256, 1, 16 << 10
+        assert h.hicr_batch_set_config(inst, c) == 0
+        path = "device"
     ids = alloc_filled(h, inst, [size, size], 11)
     cm, oids = oracle_slots([size, size], 11)
     assert cm.memcpy_batch(ops) == (om.OK, None)
@@ -155,6 +160,10 @@ CONFIGS = [
     dict(chunk_bytes=4096, op_cost_bytes=4096, blocks_per_sm=2, threads=256),
     dict(chunk_bytes=64 << 10, op_cost_bytes=2048, blocks_per_sm=2, threads=512),
     dict(chunk_bytes=1 << 20, op_cost_bytes=64, blocks_per_sm=1, threads=1024),
+    # the TMA engine: small threshold (many short bodies, partial stages) and the tuned shapes
+    dict(chunk_bytes=64 << 10, op_cost_bytes=4096, blocks_per_sm=1, threads=256, engine=1, tma_min_bytes=1024),
+    dict(chunk_bytes=1 << 20, op_cost_bytes=64, blocks_per_sm=2, threads=192, engine=1, tma_min_bytes=32 << 10),
+    dict(chunk_bytes=256 << 10, op_cost_bytes=4096, blocks_per_sm=1, threads=384, engine=1, tma_min_bytes=256 << 10),
 ]
 
 
