@@ -58,7 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--profile-case", choices=["mpsc_small", "copy_small"], default=None,
                    help="run one small side case for a profiler capture, print its timings and exit")
     p.add_argument("--batch-config", default=None,
-                   help="copy_small: JSON object of batch configuration fields (default: the library's)")
+                   help="JSON object of batch configuration fields: fixes the copy kernel's configuration "
+                        "instead of autotuning (headline) or of the library default (copy_small)")
     return p.parse_args(argv)
 
 
@@ -759,7 +760,14 @@ def run_ours(args):
     lops = remap(w.ops, ids)
     dops = device_ops(lops)
     torch.cuda.synchronize()
-    tuned, tuned_ms = autotune(h, inst, dops, w.epochs)
+    if args.batch_config:  # a fixed configuration (e.g. for a profiler's launch list): no autotuning
+        c = h.check(h.hicr_batch_get_config(inst), "get_config")
+        for k, v in json.loads(args.batch_config).items():
+            setattr(c, k, int(v))
+        h.check(h.hicr_batch_set_config(inst, c), "set_config")
+        tuned, tuned_ms = c.as_dict(), None
+    else:
+        tuned, tuned_ms = autotune(h, inst, dops, w.epochs)
     h.check(h.hicr_profile_enable(inst, 1), "profile")
     g = capture_epochs(h, inst, dops, w.epochs)
     bytes_step = 2 * w.total_bytes
