@@ -69,7 +69,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB_PATH + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

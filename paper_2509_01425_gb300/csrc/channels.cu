@@ -1511,6 +1511,7 @@ hicr_status hicr_channel_depth(hicr_instance_t h, hicr_channel_t ch, uint64_t* m
 
 hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
                              uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results) {
+  hicr::NvtxRange nvtx_range("hicr_spsc_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || n == 0 || batch == 0 || in->capturing) return HICR_ERR_INVALID;
   std::vector<SpscView> views(n);
@@ -1552,6 +1553,7 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
                              const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
                              uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
                              uint64_t log_stride, hicr_mpsc_result_t* results) {
+  hicr::NvtxRange nvtx_range("hicr_mpsc_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
       group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)
@@ -1646,6 +1648,7 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
                                 const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
                                 uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
                                 uint64_t log_stride, hicr_mpsc_result_t* results) {
+  hicr::NvtxRange nvtx_range("hicr_mpsc_nl_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
       group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)

@@ -9,10 +9,21 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hicr.h"
 #include "../../include/hicr_util.h"
 
 namespace hicr {
+
+// NVTX range around a library call (visible in Nsight timelines; a no-op when
+// no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // -------------------------------------------------------------------------
 // Device-resident tables. Slot metadata word: bit 0 live, bits 1..3 memory

@@ -380,6 +380,7 @@ static hicr_status record_prof(Instance* in, cudaEvent_t ev, cudaStream_t st) {
 }
 
 hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st) {
+  hicr::NvtxRange nvtx_range("launch_batch");
   if (count == 0) return HICR_OK;
   hicr_status s = ensure_scratch(in, count);
   if (s != HICR_OK) return s;
@@ -499,6 +500,7 @@ hicr_status hicr_memcpy(hicr_instance_t h, hicr_slot_t dst, uint64_t dst_off, hi
 }
 
 hicr_status hicr_flush(hicr_instance_t h) {
+  hicr::NvtxRange nvtx_range("hicr_flush");
   Instance* in = I(h);
   if (!in) return HICR_ERR_INVALID;
   if (in->queue.empty()) return HICR_OK;
@@ -605,6 +607,7 @@ hicr_status hicr_graph_end(hicr_instance_t h, hicr_graph_t* out) {
 }
 
 hicr_status hicr_graph_launch(hicr_instance_t h, hicr_graph_t g) {
+  hicr::NvtxRange nvtx_range("hicr_graph_launch");
   Instance* in = I(h);
   if (!in || in->capturing || g == 0 || g > in->graphs.size() || !in->graphs[g - 1].live) return HICR_ERR_INVALID;
   hicr_status s = hicr_flush(h);

@@ -442,6 +442,7 @@ hicr_status hicr_slot_info(hicr_instance_t h, hicr_slot_t slot, void** ptr, uint
 }
 
 hicr_status hicr_fence(hicr_instance_t h, uint32_t tag, uint64_t timeout_ns) {
+  hicr::NvtxRange nvtx_range("hicr_fence");
   Instance* in = I(h);
   if (!in || tag >= HICR_MAX_TAGS || in->capturing) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
@@ -494,6 +495,7 @@ hicr_status hicr_tag_counter(hicr_instance_t h, uint32_t tag, uint64_t* ops) {
 
 hicr_status hicr_fence_slot(hicr_instance_t h, hicr_slot_t slot, uint64_t expect_sent, uint64_t expect_recv,
                             uint64_t timeout_ns) {
+  hicr::NvtxRange nvtx_range("hicr_fence_slot");
   Instance* in = I(h);
   if (!in || slot >= in->slots.size() || in->capturing) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);

@@ -969,6 +969,7 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, con
 hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
                            uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
                            hicr_serve_stats_t* stats) {
+  hicr::NvtxRange nvtx_range("hicr_serve_run");
   Instance* in = I(h);
   if (!in || (n && !reqs) || mode > 1 || in->capturing) return HICR_ERR_INVALID;
   Server* sv = srv_get(in, s);
