@@ -50,7 +50,12 @@ def _same(h, inst, a_ids, b_ids):
         assert h.hicr_slot_counters(inst, a)[1:] == h.hicr_slot_counters(inst, b)[1:]
 
 
-def test_noalloc_matches_device_batch_twice(h, inst):
+@pytest.mark.parametrize("engine", [0, 1])
+def test_noalloc_matches_device_batch_twice(h, inst, engine):
+    if engine == 1:  # the TMA engine (its stages are shared memory, still no allocation)
+        st, c = h.hicr_batch_get_config(inst)
+        c.engine, c.threads, c.blocks_per_sm, c.tma_min_bytes = 1, 256, 1, 4096
+        assert h.hicr_batch_set_config(inst, c) == 0
     w = configs.batched(5, n_slots=6, total_bytes=48 << 20, slot_lo=4 << 20, slot_hi=16 << 20,
                         n_ops=6000, n_lo=16, n_hi=512 << 10)
     assert len(w.epochs) >= 2
