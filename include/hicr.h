@@ -376,7 +376,10 @@ hicr_status hicr_exec_await(hicr_instance_t inst, hicr_exec_t e, uint64_t timeou
 /* ------------------------------------------------------------------------ */
 /* Diagnostics                                                               */
 /* ------------------------------------------------------------------------ */
-/* Copy the last CUDA error text recorded by this instance into buf. */
+/* Copy the last error text recorded by this instance (a CUDA error, a
+ * serving-engine timeout or self-check) into buf. With the environment
+ * variable HICR_LOG set (to anything but "0"), every such message is also
+ * printed to stderr when it is recorded. */
 hicr_status hicr_last_error_string(hicr_instance_t inst, char* buf, uint64_t len);
 
 #ifdef __cplusplus

@@ -184,6 +184,9 @@ hicr_status check_config(const Instance* in, const hicr_batch_config_t* c);
 
 // channels.cu
 void destroy_channels(Instance* in);
+void destroy_servers(Instance* in);  // serve.cu
+// Records the instance's last error message (and prints it when HICR_LOG is set).
+void log_error(Instance* in, const std::string& msg);
 
 // dataobject.cu
 void forget_data_objects(const Instance* in);

@@ -16,10 +16,22 @@ namespace hicr {
 const void* builtin_fill_kernel();
 const void* builtin_digest_kernel();
 
-hicr_status cuda_fail(Instance* in, cudaError_t e, const char* what) {
-  if (in) {
-    in->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+// HICR_LOG set (to anything but "0") in the environment: every recorded
+// error is also printed to stderr as it happens.
+void log_error(Instance* in, const std::string& msg) {
+  if (in) in->last_err = msg;
+  static const bool on = [] {
+    const char* v = getenv("HICR_LOG");
+    return v && *v && strcmp(v, "0") != 0;
+  }();
+  if (on) {
+    fprintf(stderr, "hicr: %s\n", msg.c_str());
+    fflush(stderr);
   }
+}
+
+hicr_status cuda_fail(Instance* in, cudaError_t e, const char* what) {
+  log_error(in, std::string(what) + ": " + cudaGetErrorString(e));
   (void)cudaGetLastError();  // clear a non-sticky error
   return HICR_ERR_DEVICE;
 }
@@ -234,6 +246,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
   }
   cudaDeviceSynchronize();
   destroy_channels(in);
+  destroy_servers(in);
   forget_data_objects(in);
   for (auto& g : in->graphs) {
     if (g.exec) cudaGraphExecDestroy(g.exec);

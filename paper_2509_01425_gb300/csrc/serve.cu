@@ -732,6 +732,20 @@ static Server* srv_get(Instance* in, hicr_serve_t s) {
   return (v && v->live) ? v : nullptr;
 }
 
+// Called by hicr_finalize: release every engine the caller did not destroy.
+// The arena is an owned slot and is freed with the instance's slots.
+void destroy_servers(Instance* in) {
+  auto it = g_servers.find(in);
+  if (it == g_servers.end()) return;
+  for (Server* sv : it->second) {
+    if (!sv) continue;
+    if (sv->rings) cudaFree(sv->rings);
+    if (sv->dev_tmpl) cudaFree(sv->dev_tmpl);
+    delete sv;
+  }
+  g_servers.erase(it);
+}
+
 template <class T>
 static char* put(char* p, const std::vector<T>& v, const T** dst) {
   const size_t n = v.size() * sizeof(T);
@@ -1199,7 +1213,7 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
       msg += " [r" + std::to_string(inflight[i]) + " kind " + std::to_string(stuck_req[i].kind) + " done " +
              std::to_string(stuck_req[i].done) + "/" + std::to_string(stuck_req[i].need) + " units " +
              std::to_string(stuck_req[i].U) + "+" + std::to_string(stuck_req[i].N) + "]";
-    in->last_err = msg;
+    log_error(in, msg);
     fprintf(stderr, "hicr_serve_run: %s\n", msg.c_str());
     fflush(stderr);
   }
@@ -1223,7 +1237,7 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   }
   const unsigned long long bad = dv[5];
   if (bad) {
-    in->last_err = "serving engine self-check failed at request " + std::to_string(bad - 1);
+    log_error(in, "serving engine self-check failed at request " + std::to_string(bad - 1));
     result = HICR_ERR_DEVICE;
   }
   if (stats) {

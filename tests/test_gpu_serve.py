@@ -95,3 +95,19 @@ def test_serve_rejects_bad_requests(h, inst):
     reqs["arrival_ns"] = [10, 5]
     assert h.hicr_serve_run(inst, ss.srv, reqs, 0, T)[0] == h.HICR_ERR_INVALID
     ss.free()
+
+
+def test_finalize_releases_an_engine_left_alive(h):
+    """An engine the caller never destroys is released with its instance:
+    its arena and rings (here 8 GiB) return to the device."""
+    import torch
+    torch.cuda.synchronize()
+    st, i2 = h.hicr_init(0)
+    assert st == 0
+    free0 = torch.cuda.mem_get_info()[0]
+    cfg = dict(budget_bytes=8 << 30, n_channels=4, max_msgs=1024, ring_bytes=256 << 20, chunk_bytes=64 << 10,
+               op_cost_bytes=2048, verify=0)
+    h.check(h.hicr_serve_create(i2, cfg), "serve_create")
+    assert torch.cuda.mem_get_info()[0] < free0 - (7 << 30)
+    assert h.hicr_finalize(i2) == 0
+    assert torch.cuda.mem_get_info()[0] > free0 - (256 << 20)
