@@ -304,7 +304,13 @@ hicr_status hicr_batch_set_config(hicr_instance_t inst, const hicr_batch_config_
  * safe to execute repeatedly: hazard-free, sources not written) and install
  * the fastest. Each candidate is run `reps` times after one warm-up; the
  * median is compared. *best (may be NULL) receives the winner, *best_ms its
- * median time (may be NULL). */
+ * median time (may be NULL). Candidates cover both copy engines.
+ * Tuning cache: with the environment variable HICR_TUNE_CACHE naming a file,
+ * the call first runs the table once with the current configuration to learn
+ * its payload bytes. It then looks up the key (device name, SM count,
+ * floor(log2(ops)), floor(log2(bytes))) in that file, one JSON object per
+ * line. On a hit it installs the cached configuration without trials; on a
+ * miss it tunes and appends a line. */
 hicr_status hicr_batch_autotune(hicr_instance_t inst, const hicr_op_t* d_ops, uint64_t count,
                                 uint32_t reps, hicr_batch_config_t* best, float* best_ms);
 

@@ -20,6 +20,8 @@
 // ops are cut into many chunks that different warps copy in parallel, runs of
 // small ops are packed into one chunk, and the per-op charge keeps a warp
 // from being handed too many tiny ops at once.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -655,6 +657,53 @@ hicr_status hicr_profile_read(hicr_instance_t h, float* copy_ms, uint32_t* launc
   return HICR_OK;
 }
 
+namespace {
+// One line of the tuning cache: a JSON object with a fixed field order.
+const char* TUNE_FMT =
+    "{\"device\":\"%127[^\"]\",\"sms\":%d,\"ops_log2\":%d,\"bytes_log2\":%d,\"chunk_bytes\":%u,"
+    "\"op_cost_bytes\":%u,\"blocks_per_sm\":%u,\"threads\":%u,\"engine\":%u,\"tma_min_bytes\":%u,\"ms\":%f}";
+
+int ilog2(unsigned long long x) {
+  int k = -1;
+  while (x) {
+    x >>= 1;
+    ++k;
+  }
+  return k;
+}
+
+bool tune_lookup(const char* path, const char* dev, int sms, int ol, int bl, hicr_batch_config_t* c, float* ms) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[1024];
+  bool hit = false;
+  while (fgets(line, sizeof line, f)) {
+    char d[128];
+    int s2, o2, b2;
+    hicr_batch_config_t x = *c;
+    float t = 0;
+    if (sscanf(line, TUNE_FMT, d, &s2, &o2, &b2, &x.chunk_bytes, &x.op_cost_bytes, &x.blocks_per_sm, &x.threads,
+               &x.engine, &x.tma_min_bytes, &t) == 11 &&
+        strcmp(d, dev) == 0 && s2 == sms && o2 == ol && b2 == bl) {
+      *c = x;  // the last matching line wins
+      *ms = t;
+      hit = true;
+    }
+  }
+  fclose(f);
+  return hit;
+}
+
+void tune_store(const char* path, const char* dev, int sms, int ol, int bl, const hicr_batch_config_t& c, float ms) {
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, TUNE_FMT, dev, sms, ol, bl, c.chunk_bytes, c.op_cost_bytes, c.blocks_per_sm, c.threads, c.engine,
+          c.tma_min_bytes, (double)ms);
+  fputc('\n', f);
+  fclose(f);
+}
+}  // namespace
+
 hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint64_t count, uint32_t reps,
                                 hicr_batch_config_t* best, float* best_ms) {
   Instance* in = I(h);
@@ -663,6 +712,31 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
   if (s != HICR_OK) return s;
   if ((s = ensure_scratch(in, count)) != HICR_OK) return s;
   const hicr_batch_config_t base = in->cfg;
+  // tuning cache: the key needs the table's payload bytes, which one run with
+  // the current configuration leaves in the batch control block
+  const char* cache = getenv("HICR_TUNE_CACHE");
+  int key_ops = 0, key_bytes = 0;
+  if (cache && *cache) {
+    if ((s = launch_batch(in, d_ops, count, in->comm())) != HICR_OK) return s;
+    BatchCtrl ctl;
+    HICR_CUDA(in, cudaMemcpyAsync(&ctl, in->scratch.ctrl, sizeof(ctl), cudaMemcpyDeviceToHost, in->comm()));
+    HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+    const unsigned long long charged = (unsigned long long)in->cfg.op_cost_bytes * count;
+    key_ops = ilog2(count);
+    key_bytes = ilog2(ctl.total > charged ? ctl.total - charged : 0ull);
+    hicr_batch_config_t c = base;
+    float ms = 0;
+    if (tune_lookup(cache, in->prop.name, in->sm_count, key_ops, key_bytes, &c, &ms) && check_config(in, &c) == HICR_OK) {
+      in->cfg = c;
+      hicr_status bst = HICR_OK;
+      uint64_t bad = 0;
+      hicr_batch_error(h, &bst, &bad);
+      if (bst != HICR_OK) return bst;
+      if (best) *best = c;
+      if (best_ms) *best_ms = ms;
+      return record_done(in);
+    }
+  }
   std::vector<hicr_batch_config_t> cands;
   const uint32_t chunks[] = {32u << 10, 64u << 10, 128u << 10, 256u << 10};
   const uint32_t shapes[][2] = {{1, 1024}, {2, 512}, {4, 256}, {2, 1024}, {4, 512}};
@@ -739,6 +813,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
   uint64_t bad = 0;
   hicr_batch_error(h, &bst, &bad);
   if (bst != HICR_OK) return bst;
+  if (cache && *cache) tune_store(cache, in->prop.name, in->sm_count, key_ops, key_bytes, best_c, best_t);
   if (best) *best = best_c;
   if (best_ms) *best_ms = best_t;
   return record_done(in);

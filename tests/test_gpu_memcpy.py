@@ -355,3 +355,29 @@ def test_bounded_device_wait_gives_up(h, inst):
     st, status, waited = h.hicr_util_wait_test(inst, 200_000_000)
     assert st == 0 and status == h.HICR_ERR_TIMEOUT
     assert 200_000_000 <= waited < 2_000_000_000
+
+
+def test_autotune_cache_round_trip(h, inst, tmp_path, monkeypatch):
+    """With HICR_TUNE_CACHE set, the first autotune appends its winner to the
+    file; a later autotune of a table with the same key installs the cached
+    configuration without trials."""
+    import json
+    path = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("HICR_TUNE_CACHE", str(path))
+    w = configs.batched_small(2)
+    ids = alloc_filled(h, inst, w.slot_sizes, 2)
+    a, b = w.epochs[0]
+    dops = to_device(remap(w.ops[a:b], ids))
+    st, c1, ms1 = h.hicr_batch_autotune(inst, dops.data_ptr(), b - a, 2)
+    assert st == 0
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1
+    rec = json.loads(lines[0])
+    assert rec["engine"] == c1.engine and rec["chunk_bytes"] == c1.chunk_bytes and rec["ops_log2"] >= 0
+    other = h.hicr_batch_get_config(inst)[1]
+    other.engine, other.chunk_bytes, other.threads, other.blocks_per_sm = 0, 4096, 64, 1
+    assert h.hicr_batch_set_config(inst, other) == 0
+    st, c2, ms2 = h.hicr_batch_autotune(inst, dops.data_ptr(), b - a, 2)
+    assert st == 0 and c2.as_dict() == c1.as_dict() and abs(ms2 - ms1) < 1e-3 * max(ms1, 1.0)
+    assert h.hicr_batch_get_config(inst)[1].as_dict() == c1.as_dict()
+    assert len(path.read_text().splitlines()) == 1
