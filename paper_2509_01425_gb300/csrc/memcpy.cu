@@ -658,7 +658,11 @@ hicr_status hicr_profile_read(hicr_instance_t h, float* copy_ms, uint32_t* launc
 }
 
 namespace {
-// One line of the tuning cache: a JSON object with a fixed field order.
+// One line of the tuning cache: a JSON object with a fixed field order
+// (TUNE_FMT reads it, TUNE_WFMT writes it: the same text, %s for the name).
+const char* TUNE_WFMT =
+    "{\"device\":\"%s\",\"sms\":%d,\"ops_log2\":%d,\"bytes_log2\":%d,\"chunk_bytes\":%u,"
+    "\"op_cost_bytes\":%u,\"blocks_per_sm\":%u,\"threads\":%u,\"engine\":%u,\"tma_min_bytes\":%u,\"ms\":%f}";
 const char* TUNE_FMT =
     "{\"device\":\"%127[^\"]\",\"sms\":%d,\"ops_log2\":%d,\"bytes_log2\":%d,\"chunk_bytes\":%u,"
     "\"op_cost_bytes\":%u,\"blocks_per_sm\":%u,\"threads\":%u,\"engine\":%u,\"tma_min_bytes\":%u,\"ms\":%f}";
@@ -697,7 +701,7 @@ bool tune_lookup(const char* path, const char* dev, int sms, int ol, int bl, hic
 void tune_store(const char* path, const char* dev, int sms, int ol, int bl, const hicr_batch_config_t& c, float ms) {
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, TUNE_FMT, dev, sms, ol, bl, c.chunk_bytes, c.op_cost_bytes, c.blocks_per_sm, c.threads, c.engine,
+  fprintf(f, TUNE_WFMT, dev, sms, ol, bl, c.chunk_bytes, c.op_cost_bytes, c.blocks_per_sm, c.threads, c.engine,
           c.tma_min_bytes, (double)ms);
   fputc('\n', f);
   fclose(f);
