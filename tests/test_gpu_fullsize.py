@@ -60,14 +60,16 @@ def test_full_size_sampled_parity(h, inst, maker):
     assert h.hicr_graph_destroy(inst, g) == 0
 
 
-def test_spsc_full_size(h, inst):
-    """64 channels x capacity 4,096 x 64 B, 10^7 tokens per channel: every word
-    checked on the device against the payload rule, exact counts, capacity
-    respected, and the whole-stream digest of two channels against the oracle."""
+@pytest.mark.parametrize("batch", [256, 1024, 2048])
+def test_spsc_full_size(h, inst, batch):
+    """64 channels x capacity 4,096 x 64 B, 10^7 tokens per channel, at the
+    hand-off batch sizes the bench chooses from: every word checked on the
+    device against the payload rule, exact counts, capacity respected, and
+    the whole-stream digest of two channels against the oracle."""
     from tests.test_gpu_channels import _spsc_expected_digest
     w = configs.SpscWorkload()
     chans = [h.hicr_spsc_create(inst, w.token_bytes, w.capacity)[1] for _ in range(w.n_channels)]
-    st, res = h.hicr_spsc_stream(inst, chans, w.tokens_per_channel, 256)
+    st, res = h.hicr_spsc_stream(inst, chans, w.tokens_per_channel, batch)
     assert st == 0
     for r in res:
         assert (r.pushed, r.popped, r.mismatches, r.status) == (w.tokens_per_channel,) * 2 + (0, 0)
@@ -76,7 +78,7 @@ def test_spsc_full_size(h, inst):
         assert res[i].digest == _spsc_expected_digest(i, w.tokens_per_channel)
 
 
-@pytest.mark.parametrize("ctas", [1, 4])
+@pytest.mark.parametrize("ctas", [1, 4, 5])
 def test_mpsc_full_size(h, inst, ctas):
     """1,024 producers -> 16 consumers, 1,024 messages each (log-uniform
     8 B - 256 KiB), 1 GiB rings, 1 or 4 CTAs per consumer (the bench's
@@ -92,7 +94,7 @@ def test_mpsc_full_size(h, inst, ctas):
     run.free()
 
 
-@pytest.mark.parametrize("ctas", [1, 4])
+@pytest.mark.parametrize("ctas", [1, 4, 5])
 def test_mpsc_nonlocking_full_size(h, inst, ctas):
     """The same messages over 64 rings of 16 MiB per consumer (non-locking
     mode at the locking mode's memory), 1 or 4 CTAs per consumer."""
