@@ -397,33 +397,32 @@ def _time_mpsc(h, run, reps):
             "algorithmic_GB_per_s": 3 * run.w.total_bytes / t / 1e9, "s_per_run": t, "capacity_respected": cap_ok}
 
 
-def bench_mpsc(h, inst, reps=3, group=4):
+def bench_mpsc(h, inst, reps=3, groups=(4, 8)):
     """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB: locking
     mode over one 1 GiB ring per consumer against non-locking mode over 64
     rings of 16 MiB per consumer (the same memory), both with 1, 2, 4 or 5
-    CTAs per consumer (5 fills the 152 SMs with the 64 producer CTAs)."""
+    CTAs per consumer (5 fills the 152 SMs with the 64 producer CTAs) and
+    reservation groups of 4 or 8 messages; the fastest shape is reported."""
     w = configs.mpsc(0)
-    run = MpscRun(h, inst, w, group=group)
-    lk = {}
-    for g in (1, 2, 4, 5):
-        run.set_mode(False, g)
-        if run.run()[0] == h.HICR_ERR_INVALID:  # grid not co-resident on this GPU
-            continue
-        lk[g] = _time_mpsc(h, run, reps)
-    best = max(lk, key=lambda g: lk[g]["msgs_per_s"])
+    run = MpscRun(h, inst, w)
+
+    def sweep(nonlocking):
+        res = {}
+        for g in (1, 2, 4, 5):
+            for grp in groups:
+                run.group = grp
+                run.set_mode(nonlocking, g)
+                if run.run()[0] == h.HICR_ERR_INVALID:  # grid not co-resident on this GPU
+                    continue
+                res[(g, grp)] = _time_mpsc(h, run, reps)
+        best = max(res, key=lambda k: res[k]["msgs_per_s"])
+        return {**res[best], "consumer_ctas": best[0], "group": best[1],
+                "msgs_per_s_by_consumer_ctas_and_group": {f"{g}x{grp}": r["msgs_per_s"] for (g, grp), r in res.items()}}
+
     out = {"workload": "1,024 producers -> 16 consumers, 1,024 msgs each, log-uniform 8 B-256 KiB, 1 GiB rings",
-           **lk[best], "group": group, "consumer_ctas": best,
-           "msgs_per_s_by_consumer_ctas": {str(g): lk[g]["msgs_per_s"] for g in lk}}
-    by = {}
-    for g in (1, 2, 4, 5):
-        run.set_mode(True, g)
-        if run.run()[0] == h.HICR_ERR_INVALID:  # grid not co-resident on this GPU
-            continue
-        by[g] = _time_mpsc(h, run, reps)
-    best = max(by, key=lambda g: by[g]["msgs_per_s"])
-    out["nonlocking"] = {"rings": f"64 x {run.ring_bytes >> 20} MiB per consumer, {run.max_msgs} msgs each",
-                         **by[best], "consumer_ctas": best,
-                         "msgs_per_s_by_consumer_ctas": {str(g): by[g]["msgs_per_s"] for g in by}}
+           **sweep(False)}
+    nl = sweep(True)
+    out["nonlocking"] = {"rings": f"64 x {run.ring_bytes >> 20} MiB per consumer, {run.max_msgs} msgs each", **nl}
     run.free()
     return out
 

@@ -102,6 +102,37 @@ hicr_status hicr_channel_pop(hicr_instance_t inst, hicr_channel_t ch, uint64_t c
  * skipped bytes, minus freed). */
 hicr_status hicr_channel_depth(hicr_instance_t inst, hicr_channel_t ch, uint64_t* msgs, uint64_t* bytes);
 
+/* Device view of a channel for kernels that push or pop on the device
+ * (the functions of hicr_device.cuh). Filled by hicr_channel_device_view,
+ * passed to a kernel by value; valid until the channel is destroyed. */
+typedef struct {
+  uint32_t kind;             /* 0 SPSC, 1 MPSC (locking mode) */
+  uint32_t token_size;       /* SPSC token bytes */
+  uint32_t capacity;         /* SPSC tokens */
+  uint32_t max_msgs;         /* MPSC metadata entries (power of two) */
+  uint64_t ring_bytes;       /* ring size in bytes */
+  uint8_t* ring;             /* the ring (the channel's ring slot) */
+  unsigned long long* head;  /* SPSC: tokens published; MPSC: reserve word */
+  unsigned long long* tail;  /* SPSC: tokens consumed; MPSC: messages freed */
+  unsigned long long* freed; /* MPSC: ring bytes freed (NULL for SPSC) */
+  void* meta;                /* MPSC: metadata ring of hicr_mpsc_meta_t (NULL for SPSC) */
+} hicr_channel_view_t;
+
+/* One MPSC metadata entry (the library's layout). `ready` holds
+ * (ticket mod 2^24) + 1 once the message of that ticket is published. */
+typedef struct {
+  unsigned long long start; /* absolute reservation start (mod 2^40) */
+  uint32_t size;
+  uint32_t producer;
+  uint32_t seq;
+  uint32_t flags;
+  unsigned long long ready;
+} hicr_mpsc_meta_t;
+
+/* Fill *out with the device view of an SPSC or MPSC (locking) channel.
+ * Errors: INVALID (unknown channel, non-locking MPSC). */
+hicr_status hicr_channel_device_view(hicr_instance_t inst, hicr_channel_t ch, hicr_channel_view_t* out);
+
 /* ------------------------------------------------------------------------ */
 /* Device-driven streaming (producers and consumers are device threads).     */
 /* ------------------------------------------------------------------------ */

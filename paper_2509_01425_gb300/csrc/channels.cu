@@ -29,6 +29,7 @@
 // mailbox. The streaming runs launch producers and consumers as one
 // cooperative grid (all CTAs resident at once); every wait is bounded by the
 // %globaltimer deadline and raises a shared abort flag on expiry.
+#include <stddef.h>
 #include <string.h>
 
 #include <vector>
@@ -241,6 +242,13 @@ struct NlMeta {
   unsigned int seq;
 };
 static_assert(sizeof(NlMeta) == 16, "non-locking metadata entry is 16 bytes");
+// the public description of a locking-mode metadata entry (hicr_channels.h)
+static_assert(sizeof(hicr_mpsc_meta_t) == sizeof(MpscMeta) && offsetof(hicr_mpsc_meta_t, start) == offsetof(MpscMeta, start) &&
+                  offsetof(hicr_mpsc_meta_t, size) == offsetof(MpscMeta, size) &&
+                  offsetof(hicr_mpsc_meta_t, producer) == offsetof(MpscMeta, producer) &&
+                  offsetof(hicr_mpsc_meta_t, seq) == offsetof(MpscMeta, seq) &&
+                  offsetof(hicr_mpsc_meta_t, ready) == offsetof(MpscMeta, ready),
+              "public MPSC metadata layout");
 struct NlView {
   uint8_t* ring;  // ring i at ring + i * R
   NlHead* head;
@@ -1395,6 +1403,35 @@ hicr_status hicr_mpsc_nl_create(hicr_instance_t h, uint32_t n_producers, uint64_
   c->seq.assign(n_producers, 0);
   return add_channel(h, c, (size_t)n_producers * ring_bytes, sizeof(NlHead) + sizeof(NlState) * (size_t)n_producers,
                      sizeof(NlMeta) * (size_t)max_msgs * n_producers, out);
+}
+
+hicr_status hicr_channel_device_view(hicr_instance_t h, hicr_channel_t ch, hicr_channel_view_t* out) {
+  Instance* in = I(h);
+  if (!in || !out) return HICR_ERR_INVALID;
+  Channel* c = get(in, ch);
+  if (!c || c->kind > 1) return HICR_ERR_INVALID;
+  hicr_channel_view_t v;
+  memset(&v, 0, sizeof(v));
+  v.kind = (uint32_t)c->kind;
+  v.ring = c->ring;
+  if (c->kind == 0) {
+    SpscState* st = (SpscState*)c->state;
+    v.token_size = c->token_size;
+    v.capacity = c->capacity;
+    v.ring_bytes = (uint64_t)c->token_size * c->capacity;
+    v.head = &st->head.v;
+    v.tail = &st->tail.v;
+  } else {
+    MpscState* st = (MpscState*)c->state;
+    v.max_msgs = c->max_msgs;
+    v.ring_bytes = c->ring_bytes;
+    v.head = &st->reserve.v;
+    v.tail = &st->msg_tail.v;
+    v.freed = &st->freed.v;
+    v.meta = c->meta;
+  }
+  *out = v;
+  return HICR_OK;
 }
 
 hicr_status hicr_channel_destroy(hicr_instance_t h, hicr_channel_t ch) {

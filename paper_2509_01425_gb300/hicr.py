@@ -517,6 +517,20 @@ def hicr_mpsc_nl_create(inst, n_producers, ring_bytes, max_msgs):
     return st, c.value
 
 
+class hicr_channel_view_t(C.Structure):
+    _fields_ = [("kind", u32), ("token_size", u32), ("capacity", u32), ("max_msgs", u32), ("ring_bytes", u64),
+                ("ring", vp), ("head", vp), ("tail", vp), ("freed", vp), ("meta", vp)]
+
+
+_channel_device_view = _decl("hicr_channel_device_view", [H, u32, C.POINTER(hicr_channel_view_t)])
+
+
+def hicr_channel_device_view(inst, ch):
+    v = hicr_channel_view_t()
+    st = _channel_device_view(inst, ch, C.byref(v))
+    return st, v
+
+
 def hicr_channel_destroy(inst, ch):
     return _channel_destroy(inst, ch)
 

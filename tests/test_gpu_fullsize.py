@@ -78,15 +78,15 @@ def test_spsc_full_size(h, inst, batch):
         assert res[i].digest == _spsc_expected_digest(i, w.tokens_per_channel)
 
 
-@pytest.mark.parametrize("ctas", [1, 4, 5])
-def test_mpsc_full_size(h, inst, ctas):
+@pytest.mark.parametrize("ctas,group", [(1, 4), (4, 4), (5, 4), (5, 8)])
+def test_mpsc_full_size(h, inst, ctas, group):
     """1,024 producers -> 16 consumers, 1,024 messages each (log-uniform
     8 B - 256 KiB), 1 GiB rings, 1 or 4 CTAs per consumer (the bench's
     launch shapes): every consumer's log passes the checker; a sample of
     payload digests matches the oracle."""
     from tests.test_gpu_channels import _check_mpsc
     w = configs.mpsc(0)
-    run = bench.MpscRun(h, inst, w, group=4, consumer_ctas=ctas)
+    run = bench.MpscRun(h, inst, w, group=group, consumer_ctas=ctas)
     st, res = run.run()
     assert st == 0
     assert sum(int(r.consumed) for r in res) == w.sizes.size
@@ -94,13 +94,13 @@ def test_mpsc_full_size(h, inst, ctas):
     run.free()
 
 
-@pytest.mark.parametrize("ctas", [1, 4, 5])
-def test_mpsc_nonlocking_full_size(h, inst, ctas):
+@pytest.mark.parametrize("ctas,group", [(1, 4), (4, 4), (5, 4), (5, 8)])
+def test_mpsc_nonlocking_full_size(h, inst, ctas, group):
     """The same messages over 64 rings of 16 MiB per consumer (non-locking
     mode at the locking mode's memory), 1 or 4 CTAs per consumer."""
     from tests.test_gpu_channels import _check_mpsc_nl
     w = configs.mpsc(0)
-    run = bench.MpscRun(h, inst, w, group=4, nonlocking=True, consumer_ctas=ctas)
+    run = bench.MpscRun(h, inst, w, group=group, nonlocking=True, consumer_ctas=ctas)
     st, res = run.run()
     assert st == 0
     assert sum(int(r.consumed) for r in res) == w.sizes.size
