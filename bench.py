@@ -382,6 +382,66 @@ def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
     return out
 
 
+def bench_latencies(h, inst, reps=2000):
+    """Host-observed latency (median and p99 over `reps` calls, microseconds)
+    of the small synchronous operations: a 16-byte memcpy + fence, an
+    execution-unit launch + await (the built-in fill on 16 bytes), a Data
+    Object get (16 bytes) + fence, and a 1-token SPSC host push + pop."""
+    import ctypes as C
+
+    def stats(f):
+        for _ in range(50):
+            f()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            f()
+            ts.append(time.perf_counter() - t0)
+        ts = np.asarray(ts) * 1e6
+        return {"p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99))}
+
+    a = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, 1 << 20), "alloc")
+    b = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, 1 << 20), "alloc")
+    out = {}
+
+    def memcpy_fence():
+        h.check(h.hicr_memcpy(inst, b, 0, a, 0, 16), "memcpy")
+        h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+    out["memcpy_16B_plus_fence"] = stats(memcpy_fence)
+
+    unit = h.check(h.hicr_exec_unit_builtin("fill_seeded"), "exec_unit")
+    ptr = h.check(h.hicr_slot_info(inst, a), "slot_info")[0]
+    pu = h.check(h.hicr_pu_create(inst), "pu")
+    args = [C.c_void_p(ptr), C.c_uint64(0), C.c_uint64(16), C.c_uint64(1)]
+
+    def launch_await():
+        e = h.check(h.hicr_exec_launch(inst, pu, unit, args), "exec_launch")
+        h.check(h.hicr_exec_await(inst, e, FENCE_TIMEOUT), "exec_await")
+    out["exec_launch_plus_await"] = stats(launch_await)
+    h.check(h.hicr_pu_destroy(inst, pu), "pu_destroy")
+
+    oid = h.check(h.hicr_dobj_publish(inst, a, 64, 16), "publish")
+    hd = h.check(h.hicr_dobj_get_handle(inst, oid), "get_handle")
+
+    def dobj_get():
+        h.check(h.hicr_dobj_get(inst, hd, b, 128), "dobj_get")
+        h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
+    out["dobj_get_16B_plus_fence"] = stats(dobj_get)
+    h.check(h.hicr_dobj_release(inst, oid), "release")
+
+    ch = h.check(h.hicr_spsc_create(inst, 64, 4096), "spsc_create")
+
+    def push_pop():
+        h.check(h.hicr_channel_push(inst, ch, 0, a, 0, 1), "push")
+        h.check(h.hicr_channel_pop(inst, ch, 1), "pop")
+    out["spsc_host_push_plus_pop"] = stats(push_pop)
+    h.check(h.hicr_channel_destroy(inst, ch), "destroy")
+    for sid in (a, b):
+        h.check(h.hicr_mem_free(inst, sid), "free")
+    out["reps"] = reps
+    return out
+
+
 def _time_mpsc(h, run, reps):
     h.check(run.run()[0], "mpsc warm-up")
     times = []
@@ -874,6 +934,7 @@ def run_ours(args):
         side["spsc"] = bench_spsc(h, inst)
         side["pingpong"] = bench_pingpong(h, inst)
         side["host_space"] = bench_host_space(h, inst)
+        side["latency"] = bench_latencies(h, inst)
         side["mpsc"] = bench_mpsc(h, inst)
         if args.serve_seconds > 0:
             h.check(h.hicr_graph_destroy(inst, g), "graph_destroy")

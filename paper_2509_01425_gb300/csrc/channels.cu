@@ -624,7 +624,7 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
     for (int i = 0; i < k; ++i) {
       const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
       const unsigned long long idx = (unsigned long long)p * a.mpp + s + i;
-      warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
+      ring_copy(v.ring + (si & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
     }
     __threadfence();
     __syncwarp();
@@ -979,7 +979,7 @@ __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, un
     for (int j = 0; j < k; ++j) {
       const unsigned long long sj = __shfl_sync(FULLM, sa[j], 0);
       const unsigned long long idx = (unsigned long long)p * a.mpp + s + j;
-      warp_copy(ring + (sj & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
+      ring_copy(ring + (sj & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
       if (lane == (unsigned)j) {
         NlMeta* e = meta + ((pub0 + j) & (v.M - 1));
         e->start = sj;

@@ -337,7 +337,7 @@ __device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   const unsigned long long t0 = W >> 40;
   for (int i = 0; i < cnt; ++i) {
     const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
-    warp_copy(v.ring + (si & (v.R - 1)), a.staging + a.moffs[mbase + m0 + i], a.msizes[mbase + m0 + i], lane);
+    ring_copy(v.ring + (si & (v.R - 1)), a.staging + a.moffs[mbase + m0 + i], a.msizes[mbase + m0 + i], lane);
   }
   __threadfence();
   __syncwarp();
