@@ -63,16 +63,34 @@ def parse_args(argv=None):
     return p.parse_args(argv)
 
 
+def kernel_source_sha(sources):
+    """sha256 over the text a kernel is compiled from: for each entry its file,
+    or the part of it from the line starting with `begin` up to the line
+    starting with `end` (exclusive)."""
+    import hashlib
+    hs = hashlib.sha256()
+    for e in sources:
+        text = open(os.path.join(ROOT, e["path"])).read()
+        if e.get("begin"):
+            lines = text.splitlines(keepends=True)
+            a = next(i for i, l in enumerate(lines) if l.startswith(e["begin"]))
+            b = next(i for i, l in enumerate(lines) if i > a and l.startswith(e["end"]))
+            text = "".join(lines[a:b])
+        hs.update(text.encode())
+    return hs.hexdigest()
+
+
 def copy_traffic(kernel, alg_bytes_per_launch):
     """DRAM bytes per launch of the copy kernel scaled from its committed ncu
-    capture, or None when there is none or the source changed since."""
-    import hashlib
+    capture, or None when there is none or the kernel's source changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    src = open(os.path.join(ROOT, d["source"]), "rb").read()
-    if hashlib.sha256(src).hexdigest() != d["source_sha256"]:
+    try:
+        if kernel_source_sha(d["sources"]) != d["source_sha256"]:
+            return None
+    except (OSError, StopIteration, KeyError):
         return None
     return d["traffic_over_algorithmic"] * alg_bytes_per_launch
 
