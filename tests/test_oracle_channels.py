@@ -269,3 +269,74 @@ def test_check_mpsc_nl_log():
     bad = [log[2], log[1], log[0], log[3]]
     assert oc.check_mpsc_nl_log(sizes, 2, 0, bad, 128)
     assert oc.check_mpsc_nl_log(sizes, 2, 0, log[:3], 128)
+
+
+def _nl_program(cls, seed=5):
+    """A random push/peek/pop program on a non-locking channel checked against
+    per-producer FIFOs (deques) and the placement rule replayed per ring;
+    returns the number of mismatches."""
+    rng = np.random.default_rng(seed)
+    P, R, M = 3, 512, 4
+    ch = cls(P, R, M)
+    refs = [deque() for _ in range(P)]
+    placed = [[] for _ in range(P)]
+    bad = 0
+    for step in range(1500):
+        if rng.random() < 0.55:
+            p = int(rng.integers(0, P))
+            n = int(rng.integers(1, 200))
+            payload = rng.integers(0, 256, n, dtype=np.uint8)
+            depth_ok = len(refs[p]) < M
+            if ch.push(p, payload) == om.OK:
+                refs[p].append(bytes(payload))
+                placed[p].append(n)
+                bad += not depth_ok
+        else:
+            flat = [(p, m) for p, r in enumerate(refs) for m in r]
+            if flat:
+                st, info = ch.peek(0)
+                if st != om.OK or bytes(ch.payload(0)) != flat[0][1] or info[2] != flat[0][0]:
+                    bad += 1
+                ch.pop(1)
+                for r in refs:
+                    if r:
+                        r.popleft()
+                        break
+    for p in range(P):  # offsets of every message a ring ever held follow the rule
+        offs = [e[0] % R for e in ch.rings[p].meta]
+        exp = oc.replay_offsets(placed[p], R)[len(placed[p]) - len(offs):] if offs else []
+        bad += offs != exp
+    return bad
+
+
+class _NLReverseDrain(oc.MpscNonLockingOracle):
+    def _locate(self, k):
+        for p in reversed(range(len(self.rings))):
+            d = self.rings[p].depth()[0]
+            if k < d:
+                return p, k
+            k -= d
+        return None
+
+
+class _NLNoSkip(oc.MpscNonLockingOracle):
+    def __init__(self, n_producers, ring_bytes, max_msgs):
+        self.rings = [_NoSkip(1, ring_bytes, max_msgs) for _ in range(n_producers)]
+
+
+class _NLLooseCapacity(oc.MpscNonLockingOracle):
+    def __init__(self, n_producers, ring_bytes, max_msgs):
+        self.rings = [oc.MpscOracle(1, ring_bytes, max_msgs + 1) for _ in range(n_producers)]
+
+
+def test_nonlocking_program_is_clean():
+    assert _nl_program(oc.MpscNonLockingOracle) == 0
+
+
+@pytest.mark.parametrize("mutant", [_NLReverseDrain, _NLNoSkip, _NLLooseCapacity])
+def test_nonlocking_planted_mistakes_are_caught(mutant):
+    try:
+        bad = _nl_program(mutant)
+    except (AssertionError, ValueError, IndexError):
+        bad = 1
+    assert bad > 0
