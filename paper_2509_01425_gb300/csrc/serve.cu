@@ -13,10 +13,13 @@
 //                   publishes units_pub;
 //   CTAs 1..C       one MPSC consumer per channel (windowed drain as in the
 //                   channel stream kernel); completes burst requests;
-//   other CTAs      worker warps: claim the next unit, wait until it is
-//                   published, find its request and either copy one cost
-//                   chunk of the template's ops (same warp copy and chunking
-//                   as the batch path) or push one group of the burst's
+//   other CTAs      worker warps share the work of the requests in flight
+//                   (processor sharing): each claim takes the next unit of a
+//                   request picked round-robin among the published requests
+//                   that still have unclaimed units, so a small request does
+//                   not wait behind the units of a large one. A unit either
+//                   copies one cost chunk of the template's ops (same warp copy
+//                   and chunking as the batch path) or pushes one group of the burst's
 //                   messages: group k reserves its tickets only after group
 //                   k-1 has reserved (a per-request chain), so a burst's
 //                   messages keep their order in the channel while the groups
@@ -51,12 +54,17 @@ struct SrvReq {
   unsigned long long digest;  // burst digest accumulator
   unsigned int N, need, kind, tmpl;
   unsigned long long gres;    // burst: message groups that have reserved their tickets
+  unsigned long long claimed; // units handed out (may pass N by failed claims)
 };
 
 // A burst's messages are cut into groups of at most SRV_GROUP_MSGS
 // consecutive messages whose rounded sizes sum to at most SRV_GROUP_BYTES
 // (a larger message is a group of its own); one work unit per group.
 static constexpr unsigned SRV_GROUP_MSGS = 8;
+// Workers share their claims round-robin among at most this many of the
+// oldest requests that may have unclaimed units (processor sharing at normal
+// load; under overload the requests behind the window wait in order).
+static constexpr unsigned long long SRV_PS_WINDOW = 16;
 static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
 
 struct SrvHostDesc {
@@ -66,6 +74,8 @@ struct SrvHostDesc {
 
 struct SrvCtl {
   Line claim, units_pub, req_pub, stop, final_units, abort, bad, exited;
+  Line lo;  // requests below lo have no unclaimed unit
+  Line rr;  // round-robin ticket of the claims
   unsigned long long final_msgs[SRV_MAX_CH];
 };
 
@@ -190,6 +200,7 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
       e->done = 0;
       e->digest = 0;
       e->gres = 0;
+      e->claimed = 0;
       e->N = (unsigned)N;
       e->need = (unsigned)need;
       e->kind = kind;
@@ -222,25 +233,6 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
     __nanosleep(sleep_ns);
     sleep_ns = min(sleep_ns * 2, 1024u);
   }
-}
-
-// Largest r in [lo, hi) with req[r].U <= u (req[lo].U <= u holds).
-__device__ __forceinline__ unsigned long long srv_find(const SrvArgs& a, unsigned long long lo, unsigned long long hi,
-                                                       unsigned long long u, unsigned lane) {
-  while (hi - lo > 32) {
-    const unsigned long long step = (hi - lo + 31) / 32;
-    const unsigned long long pos = lo + lane * step;
-    const bool le = pos < hi && ld_rlx(&a.req[pos].U) <= u;
-    const unsigned m = __ballot_sync(FULLM, le);
-    const unsigned k = 31u - __clz(m);
-    const unsigned long long nlo = lo + k * step;
-    hi = min(hi, nlo + step);
-    lo = nlo;
-  }
-  const unsigned long long pos = lo + lane;
-  const bool le = pos < hi && ld_rlx(&a.req[pos].U) <= u;
-  const unsigned m = __ballot_sync(FULLM, le);
-  return lo + (31u - __clz(m));
 }
 
 __device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, const ReqView& rv, unsigned long long k, unsigned lane) {
@@ -357,69 +349,98 @@ __device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   return true;
 }
 
-__device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
-  const unsigned lane = threadIdx.x & 31u;
-  unsigned long long hint = 0;  // request of the previous unit
-  for (;;) {
-    unsigned long long u = 0;
-    int exit_now = 0;
-    ws_set(a, WS_CLAIM);
-    if (lane == 0) {
-      u = atomicAdd(&a.ctl->claim.v, 1ull);
-      unsigned sleep_ns = 32;
-      for (;;) {
-        if (ld_acq(&a.ctl->units_pub.v) > u) break;
-        if (ld_acq(&a.ctl->stop.v) && u >= *(volatile unsigned long long*)&a.ctl->final_units.v) {
-          exit_now = 1;
-          break;
-        }
-        if (srv_abort(a, deadline)) {
-          exit_now = 1;
-          break;
-        }
-        __nanosleep(sleep_ns);
-        sleep_ns = min(sleep_ns * 2, 512u);
+// Claim one unit for the warp. Lane 0 reads the window [lo, hi) of published
+// requests that may still have unclaimed units, moves lo past exhausted
+// requests, and draws a round-robin start; the warp then scans the window from
+// there, 32 requests per step (one lane each), and claims from the first
+// request with a unit left. Returns 1 with (r, k) = (request, unit index),
+// 0 when nothing is claimable right now, 2 when the run is over (every
+// request published and claimed) or aborted. All lanes return the same value.
+__device__ int srv_claim(const SrvArgs& a, unsigned lane, unsigned long long deadline, unsigned long long& r,
+                         unsigned long long& k) {
+  unsigned long long lo = 0, hi = 0, start = 0;
+  int stop = 0;
+  if (lane == 0) {
+    if (srv_abort(a, deadline)) {
+      stop = 2;
+    } else {
+      const bool stopping = ld_acq(&a.ctl->stop.v) != 0;  // before req_pub: then hi is final
+      hi = ld_acq(&a.ctl->req_pub.v);
+      lo = ld_rlx(&a.ctl->lo.v);  // only bounds the scan: a stale (smaller) value is safe
+      // lo is read after hi, so other warps may have moved it past this hi
+      if (lo > hi) lo = hi;
+      for (int step = 0; step < 32 && lo < hi; ++step) {  // move lo past exhausted requests
+        const SrvReq* e = a.req + lo;
+        if (ld_rlx(&e->claimed) < __ldcg(&e->N)) break;
+        atomicCAS(&a.ctl->lo.v, lo, lo + 1);
+        lo = ld_rlx(&a.ctl->lo.v);
+        if (lo > hi) lo = hi;
+      }
+      if (hi > lo + SRV_PS_WINDOW) hi = lo + SRV_PS_WINDOW;  // share among the oldest requests only
+      if (lo < hi) start = atomicAdd(&a.ctl->rr.v, 1ull) % (hi - lo);
+      else if (stopping) stop = 2;
+    }
+  }
+  stop = __shfl_sync(FULLM, stop, 0);
+  if (stop) return 2;
+  lo = __shfl_sync(FULLM, lo, 0);
+  hi = __shfl_sync(FULLM, hi, 0);
+  start = __shfl_sync(FULLM, start, 0);
+  const unsigned long long w = hi - lo;
+  for (unsigned long long base = 0; base < w; base += 32) {
+    const unsigned long long off = base + lane;
+    unsigned long long cand = 0;
+    bool open = false;
+    if (off < w) {
+      cand = lo + (start + off) % w;
+      open = ld_rlx(&a.req[cand].claimed) < __ldcg(&a.req[cand].N);
+    }
+    unsigned m = __ballot_sync(FULLM, open);
+    while (m) {
+      const unsigned L = __ffs(m) - 1;
+      m &= m - 1;
+      const unsigned long long rc = __shfl_sync(FULLM, cand, L);
+      unsigned long long kk = 0;
+      int got = 0;
+      if (lane == 0) {
+        kk = atomicAdd(&a.req[rc].claimed, 1ull);
+        got = kk < __ldcg(&a.req[rc].N);
+        if (got) atomicAdd(&a.ctl->claim.v, 1ull);
+      }
+      if (__shfl_sync(FULLM, got, 0)) {
+        r = rc;
+        k = __shfl_sync(FULLM, kk, 0);
+        return 1;
       }
     }
-    if (__shfl_sync(FULLM, exit_now, 0)) {
+  }
+  return 0;
+}
+
+__device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
+  const unsigned lane = threadIdx.x & 31u;
+  unsigned sleep_ns = 32;
+  for (;;) {
+    ws_set(a, WS_CLAIM);
+    unsigned long long r = 0, k = 0;
+    const int got = srv_claim(a, lane, deadline, r, k);
+    if (got == 2) {
       ws_set(a, WS_WORKER_DONE);
       return;
     }
-    u = __shfl_sync(FULLM, u, 0);
-    ws_set(a, WS_COPY);
-    // Lane 0 alone reads the live request count and takes the decisions, then
-    // broadcasts them: lanes reading req_pub separately could see different
-    // values and split between the fast path and the warp-collective search.
-    unsigned long long hi = 0, r = 0;
-    int fast = 0;
-    if (lane == 0) {
-      hi = ld_acq(&a.ctl->req_pub.v);
-      // fast path: the same or the next request as the previous unit
-      if (hint < hi) {
-        const ReqView h0 = load_req(a.req + hint);
-        if (h0.U <= u && u < h0.U + h0.N) {
-          r = hint;
-          fast = 1;
-        }
-      }
-      if (!fast && hint + 1 < hi) {
-        const ReqView h1 = load_req(a.req + hint + 1);
-        if (h1.U <= u && u < h1.U + h1.N) {
-          r = hint + 1;
-          fast = 1;
-        }
-      }
+    if (got == 0) {
+      if (lane == 0) __nanosleep(sleep_ns);
+      __syncwarp();
+      sleep_ns = min(sleep_ns * 2, 512u);
+      continue;
     }
-    hi = __shfl_sync(FULLM, hi, 0);
-    fast = __shfl_sync(FULLM, fast, 0);
-    r = __shfl_sync(FULLM, r, 0);
-    if (!fast) r = srv_find(a, 0, hi, u, lane);  // every lane, same hi
-    const ReqView rv = load_req(a.req + r);      // published entry: the same for every lane
-    hint = r;
+    sleep_ns = 32;
+    ws_set(a, WS_COPY);
+    const ReqView rv = load_req(a.req + r);  // published entry: the same for every lane
     SrvReq* e = a.req + r;
     // self-check: a request outside this run or with an unknown template is
     // reported (ctl->bad) and stops the engine instead of being executed
-    const bool ok = r < a.n_req && rv.id == r &&
+    const bool ok = r < a.n_req && rv.id == r && k < rv.N &&
                     ((rv.kind == 0 && rv.tmpl < a.n_mt && rv.dst >= a.arena_lo && rv.dst < a.arena_hi) ||
                      (rv.kind == 1 && rv.tmpl < a.n_bt));
     if (!ok) {
@@ -431,8 +452,8 @@ __device__ void srv_worker(const SrvArgs& a, unsigned long long deadline) {
       return;
     }
     if (rv.kind == 0) {
-      srv_copy_chunk(a, e, rv, u - rv.U, lane);
-    } else if (!srv_push_group(a, e, rv, u - rv.U, lane, deadline)) {
+      srv_copy_chunk(a, e, rv, k, lane);
+    } else if (!srv_push_group(a, e, rv, k, lane, deadline)) {
       ws_set(a, WS_WORKER_DONE);
       return;
     }
