@@ -15,9 +15,10 @@
 //                   channel stream kernel); completes burst requests;
 //   other CTAs      worker warps share the work of the requests in flight
 //                   (processor sharing): each claim takes the next unit of a
-//                   request picked round-robin among the published requests
-//                   that still have unclaimed units, so a small request does
-//                   not wait behind the units of a large one. A unit either
+//                   request picked round-robin among the SRV_PS_WINDOW oldest
+//                   published requests that still have unclaimed units, so a
+//                   small request does not wait behind the units of a large
+//                   one. A unit either
 //                   copies one cost chunk of the template's ops (same warp copy
 //                   and chunking as the batch path) or pushes one group of the burst's
 //                   messages: group k reserves its tickets only after group
