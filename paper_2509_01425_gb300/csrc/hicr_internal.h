@@ -135,6 +135,7 @@ struct Instance {
   int checked = 0;
 
   cudaEvent_t done_ev = nullptr;  // recorded after the last issued work
+  unsigned long long* sticky_host = nullptr;  // page-locked copy of the sticky batch error, read by fences
   bool capturing = false;
   std::vector<GraphRec> graphs;
 

@@ -200,6 +200,8 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   pu0.live = true;
   in->pus.push_back(pu0);
   cudaEventCreateWithFlags(&in->done_ev, cudaEventDisableTiming);
+  if (cudaHostAlloc((void**)&in->sticky_host, 64, cudaHostAllocDefault) != cudaSuccess) return fail(HICR_ERR_DEVICE);
+  *in->sticky_host = 0;
   cudaEventCreateWithFlags(&in->pinned_ev[0], cudaEventDisableTiming);
   cudaEventCreateWithFlags(&in->pinned_ev[1], cudaEventDisableTiming);
   cudaEventRecord(in->done_ev, pu0.stream);
@@ -268,6 +270,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
   if (in->scratch.cost) cudaFree(in->scratch.cost);
   if (in->dt.slot_base) cudaFree(in->dt.slot_base);
   if (in->done_ev) cudaEventDestroy(in->done_ev);
+  if (in->sticky_host) cudaFreeHost(in->sticky_host);
   for (auto& p : in->pus)
     if (p.live && p.owned) cudaStreamDestroy(p.stream);
   delete h;
@@ -460,13 +463,18 @@ hicr_status hicr_fence(hicr_instance_t h, uint32_t tag, uint64_t timeout_ns) {
   if (!in || tag >= HICR_MAX_TAGS || in->capturing) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
-  // Every op is issued on the communication stream, so waiting for the last
-  // recorded event covers all earlier ops of this tag (and those of others).
+  // The sticky batch error is copied to page-locked memory behind the issued
+  // work, so one wait covers both. Every op is issued on the communication
+  // stream, so waiting for the last recorded event covers all earlier ops of
+  // this tag (and those of others).
+  HICR_CUDA(in, cudaMemcpyAsync(in->sticky_host, in->dt.sticky, 8, cudaMemcpyDeviceToHost, in->comm()));
+  if ((st = record_done(in)) != HICR_OK) return st;
   st = wait_event(in, in->done_ev, timeout_ns);
   if (st != HICR_OK) return st;
+  if (*(volatile unsigned long long*)in->sticky_host == 0) return HICR_OK;
   hicr_status bst = HICR_OK;
   uint64_t bad = 0;
-  st = hicr_batch_error(h, &bst, &bad);
+  st = hicr_batch_error(h, &bst, &bad);  // reads and clears it
   if (st != HICR_OK) return st;
   return bst;
 }
