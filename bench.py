@@ -55,7 +55,7 @@ def parse_args(argv=None):
                    help="prefix of the serving trace replayed through the per-op plain form")
     p.add_argument("--scale", type=float, default=1.0,
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
-    p.add_argument("--profile-case", choices=["mpsc_small", "copy_small"], default=None,
+    p.add_argument("--profile-case", choices=["mpsc_small", "copy_small", "side_small"], default=None,
                    help="run one small side case for a profiler capture, print its timings and exit")
     p.add_argument("--batch-config", default=None,
                    help="JSON object of batch configuration fields: fixes the copy kernel's configuration "
@@ -981,7 +981,59 @@ def run_ours(args):
 def run_profile_case(args):
     if args.profile_case == "copy_small":
         return run_copy_small(args)
+    if args.profile_case == "side_small":
+        return run_side_small(args)
     return run_mpsc_small(args)
+
+
+def run_side_small(args):
+    """side_small, for a one-pass capture (DRAM bytes and duration) of the
+    kernels that are not profiled elsewhere: an SPSC stream (64 channels x
+    10^6 tokens of 64 B, batches of 2,048), a ping-pong of 256 MiB with agents
+    of 152 CTAs (10 round trips), a 0.5 s serving trace at 20,000 req/s on
+    the bench's engine set-up, and the word digest of a 4 GiB slot. Prints
+    the algorithmic bytes of each so the capture can be read against them."""
+    import torch
+    from paper_2509_01425_gb300 import build
+    build.build()
+    from paper_2509_01425_gb300 import hicr as h
+    torch.cuda.set_device(0)
+    inst = h.check(h.hicr_init(0), "hicr_init")
+    out = {"case": "side_small"}
+    w = configs.SpscWorkload()
+    chans = [h.check(h.hicr_spsc_create(inst, w.token_bytes, w.capacity), "spsc") for _ in range(w.n_channels)]
+    h.check(h.hicr_spsc_stream(inst, chans, 1_000_000, 2048)[0], "spsc_stream")
+    out["spsc_tokens"] = w.n_channels * 1_000_000
+    out["spsc_algorithmic_bytes"] = w.n_channels * 1_000_000 * 128
+    for c in chans:
+        h.check(h.hicr_channel_destroy(inst, c), "destroy")
+    size = 256 << 20
+    sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size), "alloc")
+    h.check(h.hicr_util_fill(inst, sid, 0, size, splitmix.fill_key_base(0, 5)), "fill")
+    st, r = h.hicr_pingpong(inst, sid, 0, size, 10, 2, 152)
+    h.check(st, "pingpong")
+    out["pingpong_algorithmic_bytes"] = 12 * 2 * 2 * size  # 12 round trips x 2 one-way copies x (read + write)
+    h.check(h.hicr_mem_free(inst, sid), "free")
+    big = 4 << 30
+    sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, big), "alloc")
+    h.check(h.hicr_util_fill(inst, sid, 0, big, splitmix.fill_key_base(0, 6)), "fill")
+    h.check(h.hicr_util_digest(inst, sid, 0, big), "digest")
+    out["digest_algorithmic_bytes"] = big
+    out["fill_algorithmic_bytes"] = big
+    h.check(h.hicr_mem_free(inst, sid), "free")
+    src_w = configs.batched(args.seed)
+    tmpl = configs.serve_templates(args.seed, src_w)
+    ss = ServeSetup(h, inst, src_w, tmpl, seed=args.seed)
+    reqs = ss.requests(configs.serve_trace(args.seed, rate=20000.0, duration_s=0.5))
+    st, res, stats = h.hicr_serve_run(inst, ss.srv, reqs, 0, 120_000_000_000)
+    h.check(st, "serve_run")
+    out["serve_requests"] = int(stats.completed)
+    out["serve_bytes_moved"] = int(stats.bytes_moved)
+    out["serve_wall_s"] = stats.wall_ns / 1e9
+    ss.free()
+    h.check(h.hicr_finalize(inst), "finalize")
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_copy_small(args):
