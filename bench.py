@@ -714,11 +714,11 @@ def nominal_hbm(h, inst):
 
 
 def cpu_channels_baseline(seed, target_s=2.0):
-    """The channel oracles as they stand on bounded samples of configs 3 and 4
+    """The oracles as they stand on bounded samples of configs 1, 3 and 4
     (one core): SPSC push/pop of 64-B tokens in batches of 2,048 through a
     4,096-token ring; MPSC push/pop of config 4's first consumer's messages
     (64 producers round-robin, payloads generated beforehand) through its
-    1 GiB ring in windows of 64."""
+    1 GiB ring in windows of 64; config 1's memcpy table."""
     from oracle import channels as oc
     w3 = configs.SpscWorkload()
     ch = oc.SpscOracle(w3.token_bytes, w3.capacity)
@@ -743,9 +743,23 @@ def cpu_channels_baseline(seed, target_s=2.0):
             assert mc.pop(len(msgs[i:i + 64])) == 0
             n += len(msgs[i:i + 64])
     mpsc = n / (time.perf_counter() - t0)
-    return {"spsc_tokens_per_s": spsc, "mpsc_msgs_per_s": mpsc, "cores": 1, "kind": "oracle",
+    # config 1 (2 x 64 MiB slots, 1,024 ops): the memcpy oracle on the whole table
+    from oracle import memcpy as om
+    w1 = configs.tiny(seed)
+    cm = om.CommManager()
+    for sz in w1.slot_sizes:
+        cm.register(om.SPACE_HBM, np.ones(int(sz), dtype=np.uint8))
+    t0 = time.perf_counter()
+    passes = 0
+    while time.perf_counter() - t0 < target_s:
+        assert cm.memcpy_batch(w1.ops) == (om.OK, None)
+        passes += 1
+    tiny_gbs = passes * 2 * int(w1.ops["n"].astype(np.int64).sum()) / (time.perf_counter() - t0) / 1e9
+    return {"spsc_tokens_per_s": spsc, "mpsc_msgs_per_s": mpsc, "config1_memcpy_GB_per_s": tiny_gbs,
+            "cores": 1, "kind": "oracle",
             "sample": f"SPSC: 64-B tokens, batches of {batch}, capacity {w3.capacity}; MPSC: {len(msgs)} messages "
-                      f"of config 4's consumer 0 (64 producers), 1 GiB ring, windows of 64; about {target_s:g} s each"}
+                      f"of config 4's consumer 0 (64 producers), 1 GiB ring, windows of 64; config 1: the whole "
+                      f"1,024-op table; about {target_s:g} s each"}
 
 
 def host_info():
