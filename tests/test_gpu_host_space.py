@@ -36,8 +36,14 @@ def test_host_pairs_rejected_by_default(h, inst):
     assert h.hicr_memcpy(inst, hs, 0, a, 0, 16) == h.HICR_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("path", ["batch", "device"])
-def test_hbm_host_copies_match_oracle(h, inst, path):
+@pytest.mark.parametrize("path,engine", [("batch", 0), ("device", 0), ("device", 1)])
+def test_hbm_host_copies_match_oracle(h, inst, path, engine):
+    """engine 1: the TMA engine, which must leave pieces with a host end to the
+    vector copy (its bulk copies are for HBM pairs only)."""
+    if engine == 1:
+        st, c = h.hicr_batch_get_config(inst)
+        c.engine, c.tma_min_bytes, c.threads, c.blocks_per_sm = 1, 1024, 256, 1
+        assert h.hicr_batch_set_config(inst, c) == 0
     size = 4 << 20
     spaces = [h.HICR_SPACE_HBM, h.HICR_SPACE_HOST, h.HICR_SPACE_HBM, h.HICR_SPACE_HOST]
     ids = []
