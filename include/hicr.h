@@ -293,7 +293,9 @@ typedef struct {
   uint32_t threads;        /* threads per block (multiple of 32, <= 1024) */
   uint32_t engine;         /* 0 = vector load/store, 1 = TMA bulk for co-aligned pieces */
   uint32_t tma_min_bytes;  /* engine 1: smallest piece copied by TMA bulk */
-  uint32_t reserved[2];
+  uint32_t tma_stage_bytes; /* engine 1: bytes per shared-memory stage: 4096, 8192 or 16384 (0 = 4096) */
+  uint32_t tma_stages;      /* engine 1: stages per warp: 2, 4 or 8 (0 = 4); warps x stages x stage
+                               bytes of shared memory must fit blocks_per_sm CTAs on an SM */
 } hicr_batch_config_t;
 
 hicr_status hicr_batch_get_config(hicr_instance_t inst, hicr_batch_config_t* out);

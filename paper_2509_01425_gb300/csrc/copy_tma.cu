@@ -4,8 +4,9 @@
 // copy the byte pieces of the ops a chunk overlaps), but a piece of at least
 // tma_min bytes whose source and destination are both in HBM and have the same
 // address residue mod 16 moves its 16-byte-aligned body through the Tensor
-// Memory Accelerator: lane 0 of the warp streams the body in TMA_STG-byte
-// pieces through TMA_NST shared-memory stages, each a bulk global->shared load
+// Memory Accelerator: lane 0 of the warp streams the body in STG-byte pieces
+// through NST shared-memory stages (template parameters: 2, 4 or 8 stages of
+// 4, 8 or 16 KiB, chosen by the batch configuration), each a bulk global->shared load
 // completed on the stage's mbarrier (cp.async.bulk ... complete_tx) followed
 // by a bulk shared->global store (cp.async.bulk ... bulk_group). A stage is
 // refilled only after the store that read it has finished reading
@@ -18,9 +19,6 @@
 namespace hicr {
 
 static constexpr unsigned FULLM_COPY = 0xffffffffu;
-static constexpr unsigned TMA_NST = 4;        // stages per warp
-static constexpr unsigned TMA_STG = 4096;     // bytes per stage
-static constexpr unsigned TMA_WARP_SMEM = TMA_NST * TMA_STG;
 static constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // bound of one mbarrier wait
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -64,30 +62,31 @@ __device__ __forceinline__ unsigned long long tma_now_ns() {
 // Lane 0: copy n bytes (a multiple of 16; d and s 16-byte aligned) through the
 // warp's stages. `phase` holds one parity bit per stage. Returns false when a
 // wait gave up (the copy is then incomplete).
+template <unsigned NST, unsigned STG>
 __device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uint8_t* stage,
                          unsigned long long* bars, unsigned& phase) {
-  const unsigned long long np = (n + TMA_STG - 1) / TMA_STG;
+  const unsigned long long np = (n + STG - 1) / STG;
   auto piece_bytes = [&](unsigned long long p) -> unsigned {
-    const unsigned long long off = p * TMA_STG;
-    return (unsigned)(n - off < TMA_STG ? n - off : TMA_STG);
+    const unsigned long long off = p * STG;
+    return (unsigned)(n - off < STG ? n - off : STG);
   };
-  const unsigned long long pro = np < TMA_NST - 1 ? np : TMA_NST - 1;
+  const unsigned long long pro = np < NST - 1 ? np : NST - 1;
   for (unsigned long long p = 0; p < pro; ++p) {
-    const unsigned k = (unsigned)(p % TMA_NST);
+    const unsigned k = (unsigned)(p % NST);
     mbar_expect_tx(bars + k, piece_bytes(p));
-    tma_load(stage + k * TMA_STG, s + p * TMA_STG, piece_bytes(p), bars + k);
+    tma_load(stage + k * STG, s + p * STG, piece_bytes(p), bars + k);
   }
   bool ok = true;
   for (unsigned long long p = 0; p < np; ++p) {
-    const unsigned long long q = p + TMA_NST - 1;
+    const unsigned long long q = p + NST - 1;
     if (q < np) {
       // stage q % NST last held piece p - 1: its store must have read it
       tma_wait_read0();
-      const unsigned k = (unsigned)(q % TMA_NST);
+      const unsigned k = (unsigned)(q % NST);
       mbar_expect_tx(bars + k, piece_bytes(q));
-      tma_load(stage + k * TMA_STG, s + q * TMA_STG, piece_bytes(q), bars + k);
+      tma_load(stage + k * STG, s + q * STG, piece_bytes(q), bars + k);
     }
-    const unsigned k = (unsigned)(p % TMA_NST);
+    const unsigned k = (unsigned)(p % NST);
     const unsigned par = (phase >> k) & 1u;
     if (!mbar_try_wait(bars + k, par)) {
       const unsigned long long t0 = tma_now_ns();
@@ -100,7 +99,7 @@ __device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uin
     }
     if (!ok) break;
     phase ^= 1u << k;
-    tma_store(d + p * TMA_STG, stage + k * TMA_STG, piece_bytes(p));
+    tma_store(d + p * STG, stage + k * STG, piece_bytes(p));
     tma_commit();
   }
   tma_wait_all();
@@ -109,14 +108,15 @@ __device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uin
   return ok;
 }
 
+template <unsigned NST, unsigned STG>
 __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
   extern __shared__ __align__(128) uint8_t tma_smem[];
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  uint8_t* stage = tma_smem + (size_t)warp * TMA_WARP_SMEM;
+  uint8_t* stage = tma_smem + (size_t)warp * NST * STG;
   unsigned long long* bars =
-      reinterpret_cast<unsigned long long*>(tma_smem + (size_t)nwarp * TMA_WARP_SMEM) + warp * TMA_NST;
+      reinterpret_cast<unsigned long long*>(tma_smem + (size_t)nwarp * NST * STG) + warp * NST;
   if (lane == 0) {
-    for (unsigned k = 0; k < TMA_NST; ++k) mbar_init(bars + k);
+    for (unsigned k = 0; k < NST; ++k) mbar_init(bars + k);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
           if (head) warp_copy(d, s, head, lane);
           if (tail) warp_copy(d + head + body, s + head + body, tail, lane);
           int ok = 1;
-          if (lane == 0) ok = tma_body(d + head, s + head, body, stage, bars, phase);
+          if (lane == 0) ok = tma_body<NST, STG>(d + head, s + head, body, stage, bars, phase);
           ok = __shfl_sync(FULLM_COPY, ok, 0);
           if (!ok) {
             tma_ok = 0;
@@ -182,24 +182,59 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
   }
 }
 
-size_t copy_tma_smem(unsigned threads) { return (size_t)(threads / 32) * (TMA_WARP_SMEM + TMA_NST * 8); }
+// The stage shapes the batch configuration may ask for.
+#define HICR_TMA_SHAPES(X) X(2, 4096) X(4, 4096) X(8, 4096) X(2, 8192) X(4, 8192) X(8, 8192) X(2, 16384) X(4, 16384) X(8, 16384)
 
-hicr_status copy_tma_prepare(Instance* in, unsigned threads, int* blocks_per_sm) {
-  const size_t smem = copy_tma_smem(threads);
+static void tma_shape(const hicr_batch_config_t& c, unsigned* nst, unsigned* stg) {
+  *nst = c.tma_stages ? c.tma_stages : 4;
+  *stg = c.tma_stage_bytes ? c.tma_stage_bytes : 4096;
+}
+
+static const void* tma_kernel(unsigned nst, unsigned stg) {
+#define HICR_TMA_PICK(N, S) \
+  if (nst == N && stg == S) return (const void*)k_copy_tma<N, S>;
+  HICR_TMA_SHAPES(HICR_TMA_PICK)
+#undef HICR_TMA_PICK
+  return nullptr;
+}
+
+bool copy_tma_shape_valid(const hicr_batch_config_t& c) {
+  unsigned nst, stg;
+  tma_shape(c, &nst, &stg);
+  return tma_kernel(nst, stg) != nullptr;
+}
+
+size_t copy_tma_smem(const hicr_batch_config_t& c) {
+  unsigned nst, stg;
+  tma_shape(c, &nst, &stg);
+  return (size_t)(c.threads / 32) * ((size_t)nst * stg + nst * 8);
+}
+
+hicr_status copy_tma_prepare(Instance* in, const hicr_batch_config_t& c, int* blocks_per_sm) {
   *blocks_per_sm = 0;
-  if (smem > in->prop.sharedMemPerBlockOptin) return HICR_OK;  // cannot be resident at all
+  unsigned nst, stg;
+  tma_shape(c, &nst, &stg);
+  const void* k = tma_kernel(nst, stg);
+  const size_t smem = copy_tma_smem(c);
+  if (!k || smem > in->prop.sharedMemPerBlockOptin) return HICR_OK;  // cannot be resident at all
   // allow the largest opt-in size once, so that every shape that fits can launch
-  HICR_CUDA(in, cudaFuncSetAttribute((const void*)k_copy_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  HICR_CUDA(in, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)in->prop.sharedMemPerBlockOptin));
   int per_sm = 0;
-  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_copy_tma, threads, smem));
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, c.threads, smem));
   *blocks_per_sm = per_sm;
   return HICR_OK;
 }
 
-hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, unsigned grid, unsigned threads, cudaStream_t st) {
-  k_copy_tma<<<grid, threads, copy_tma_smem(threads), st>>>(a);
-  HICR_CUDA(in, cudaGetLastError());
+hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, const hicr_batch_config_t& c, unsigned grid,
+                            cudaStream_t st) {
+  unsigned nst, stg;
+  tma_shape(c, &nst, &stg);
+  const void* k = tma_kernel(nst, stg);
+  if (!k) return HICR_ERR_INVALID;
+  BatchArgs args = a;
+  void* params[] = {&args};
+  HICR_CUDA(in, cudaLaunchKernel(k, dim3(grid), dim3(c.threads), params, copy_tma_smem(c), st));
   return HICR_OK;
 }
 

@@ -175,9 +175,11 @@ hicr_status ensure_scratch(Instance* in, uint64_t count);
 hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st);
 // The TMA engine of the copy kernel (copy_tma.cu): dynamic shared memory per
 // CTA, one-time attribute set-up + resident CTAs per SM, launch.
-size_t copy_tma_smem(unsigned threads);
-hicr_status copy_tma_prepare(Instance* in, unsigned threads, int* blocks_per_sm);
-hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, unsigned grid, unsigned threads, cudaStream_t st);
+bool copy_tma_shape_valid(const hicr_batch_config_t& c);
+size_t copy_tma_smem(const hicr_batch_config_t& c);
+hicr_status copy_tma_prepare(Instance* in, const hicr_batch_config_t& c, int* blocks_per_sm);
+hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, const hicr_batch_config_t& c, unsigned grid,
+                            cudaStream_t st);
 hicr_status record_done(Instance* in);
 hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns);
 void default_config(Instance* in, hicr_batch_config_t* c);

@@ -303,10 +303,11 @@ hicr_status check_config(const Instance* in, const hicr_batch_config_t* c) {
   if (c->threads < 32 || c->threads > 1024 || c->threads % 32) return HICR_ERR_INVALID;
   if (c->engine > 1) return HICR_ERR_INVALID;
   if (c->tma_min_bytes < 1024) return HICR_ERR_INVALID;
+  if (!copy_tma_shape_valid(*c)) return HICR_ERR_INVALID;
   if (c->engine == 1) {
     // the TMA engine's stages must fit: blocks_per_sm CTAs resident per SM
     int per_sm = 0;
-    if (copy_tma_prepare(const_cast<Instance*>(in), c->threads, &per_sm) != HICR_OK) return HICR_ERR_DEVICE;
+    if (copy_tma_prepare(const_cast<Instance*>(in), *c, &per_sm) != HICR_OK) return HICR_ERR_DEVICE;
     if (per_sm < (int)c->blocks_per_sm) return HICR_ERR_INVALID;
   }
   return HICR_OK;
@@ -398,7 +399,7 @@ hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, c
   }
   const unsigned grid = (unsigned)in->sm_count * in->cfg.blocks_per_sm;
   if (in->cfg.engine == 1) {
-    if ((s = launch_copy_tma(in, a, grid, in->cfg.threads, st)) != HICR_OK) return s;
+    if ((s = launch_copy_tma(in, a, in->cfg, grid, st)) != HICR_OK) return s;
   } else {
     k_copy<<<grid, in->cfg.threads, 0, st>>>(a);
   }
@@ -756,18 +757,22 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
         c.engine = 0;
         cands.push_back(c);
       }
-  // the TMA engine: 16 KiB of stages per warp, so up to 12 warps per SM
-  const uint32_t tma_shapes[][2] = {{1, 256}, {1, 384}, {2, 192}};
-  for (uint32_t ch : {128u << 10, 256u << 10, 1024u << 10})
+  // the TMA engine: CTA shapes x stage shapes (stages x stage bytes per
+  // warp); candidates whose shared memory does not fit are skipped below
+  const uint32_t tma_shapes[][2] = {{1, 192}, {1, 256}, {1, 384}, {2, 192}, {1, 512}, {2, 256}, {1, 768}};
+  const uint32_t stage_shapes[][2] = {{2, 4096}, {4, 4096}, {2, 8192}, {4, 8192}, {8, 4096}, {2, 16384}};
+  for (uint32_t ch : {128u << 10, 256u << 10})
     for (auto& sh : tma_shapes)
-      for (uint32_t tm : {32u << 10, 256u << 10}) {
+      for (auto& ss : stage_shapes) {
         hicr_batch_config_t c = base;
         c.chunk_bytes = ch;
         c.blocks_per_sm = sh[0];
         c.threads = sh[1];
         c.op_cost_bytes = 4096;
         c.engine = 1;
-        c.tma_min_bytes = tm;
+        c.tma_min_bytes = 32u << 10;
+        c.tma_stages = ss[0];
+        c.tma_stage_bytes = ss[1];
         cands.push_back(c);
       }
   cudaEvent_t e0, e1;
@@ -780,7 +785,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
     // skip shapes the device cannot hold
     int per_sm = 0;
     if (c.engine == 1) {
-      if (copy_tma_prepare(in, c.threads, &per_sm) != HICR_OK) per_sm = 0;
+      if (copy_tma_prepare(in, c, &per_sm) != HICR_OK) per_sm = 0;
     } else {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_copy, c.threads, 0);
     }

@@ -106,7 +106,7 @@ extern "C" hicr_status hicr_memcpy_batch_noalloc(hicr_instance_t h, const hicr_o
   k_scan<<<1, 1024, 0, st>>>(a);
   const unsigned grid = (unsigned)in->sm_count * in->cfg.blocks_per_sm;
   if (in->cfg.engine == 1) {  // the TMA engine's stages are shared memory, not an allocation
-    if ((s = launch_copy_tma(in, a, grid, in->cfg.threads, st)) != HICR_OK) return s;
+    if ((s = launch_copy_tma(in, a, in->cfg, grid, st)) != HICR_OK) return s;
   } else {
     k_copy<<<grid, in->cfg.threads, 0, st>>>(a);
   }

@@ -75,7 +75,7 @@ class hicr_topology_t(C.Structure):
 
 class hicr_batch_config_t(C.Structure):
     _fields_ = [("chunk_bytes", u32), ("op_cost_bytes", u32), ("blocks_per_sm", u32), ("threads", u32),
-                ("engine", u32), ("tma_min_bytes", u32), ("reserved", u32 * 2)]
+                ("engine", u32), ("tma_min_bytes", u32), ("tma_stage_bytes", u32), ("tma_stages", u32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -164,6 +164,11 @@ CONFIGS = [
     dict(chunk_bytes=64 << 10, op_cost_bytes=4096, blocks_per_sm=1, threads=256, engine=1, tma_min_bytes=1024),
     dict(chunk_bytes=1 << 20, op_cost_bytes=64, blocks_per_sm=2, threads=192, engine=1, tma_min_bytes=32 << 10),
     dict(chunk_bytes=256 << 10, op_cost_bytes=4096, blocks_per_sm=1, threads=384, engine=1, tma_min_bytes=256 << 10),
+    # other stage shapes: 8 stages of 4 KiB, 2 of 16 KiB
+    dict(chunk_bytes=128 << 10, op_cost_bytes=4096, blocks_per_sm=1, threads=192, engine=1, tma_min_bytes=1024,
+         tma_stages=8, tma_stage_bytes=4096),
+    dict(chunk_bytes=256 << 10, op_cost_bytes=64, blocks_per_sm=1, threads=192, engine=1, tma_min_bytes=4096,
+         tma_stages=2, tma_stage_bytes=16384),
 ]
 
 

@@ -38,7 +38,10 @@ def _random_config(h, inst, rng):
     st, c = h.hicr_batch_get_config(inst)
     if rng.random() < 0.5:
         c.engine = 1
-        c.threads, c.blocks_per_sm = [(256, 1), (384, 1), (192, 2), (64, 1)][int(rng.integers(0, 4))]
+        # (threads, CTAs per SM, stages, stage bytes): shapes whose stages fit in shared memory
+        c.threads, c.blocks_per_sm, c.tma_stages, c.tma_stage_bytes = [
+            (256, 1, 4, 4096), (384, 1, 4, 4096), (192, 2, 4, 4096), (64, 1, 4, 4096), (192, 1, 8, 4096),
+            (192, 1, 2, 16384), (512, 1, 2, 4096), (256, 2, 2, 4096), (256, 1, 2, 8192)][int(rng.integers(0, 9))]
         c.tma_min_bytes = int(rng.choice([1024, 4096, 32 << 10]))
     else:
         c.engine = 0
