@@ -106,17 +106,37 @@ hicr_status hicr_channel_depth(hicr_instance_t inst, hicr_channel_t ch, uint64_t
  * (the functions of hicr_device.cuh). Filled by hicr_channel_device_view,
  * passed to a kernel by value; valid until the channel is destroyed. */
 typedef struct {
-  uint32_t kind;             /* 0 SPSC, 1 MPSC (locking mode) */
+  uint32_t kind;             /* 0 SPSC, 1 MPSC (locking mode), 2 MPSC (non-locking mode) */
   uint32_t token_size;       /* SPSC token bytes */
-  uint32_t capacity;         /* SPSC tokens */
-  uint32_t max_msgs;         /* MPSC metadata entries (power of two) */
-  uint64_t ring_bytes;       /* ring size in bytes */
+  uint32_t capacity;         /* SPSC tokens; non-locking: number of producer rings */
+  uint32_t max_msgs;         /* MPSC metadata entries (power of two; non-locking: per ring) */
+  uint64_t ring_bytes;       /* ring size in bytes (non-locking: per ring; ring p at ring + p * ring_bytes) */
   uint8_t* ring;             /* the ring (the channel's ring slot) */
-  unsigned long long* head;  /* SPSC: tokens published; MPSC: reserve word */
-  unsigned long long* tail;  /* SPSC: tokens consumed; MPSC: messages freed */
-  unsigned long long* freed; /* MPSC: ring bytes freed (NULL for SPSC) */
-  void* meta;                /* MPSC: metadata ring of hicr_mpsc_meta_t (NULL for SPSC) */
+  unsigned long long* head;  /* SPSC: tokens published; MPSC: reserve word; non-locking: the
+                                counter blocks, HICR_NL_STATE_WORDS words per producer ring */
+  unsigned long long* tail;  /* SPSC: tokens consumed; MPSC: messages freed (NULL for non-locking) */
+  unsigned long long* freed; /* MPSC: ring bytes freed (NULL for SPSC and non-locking) */
+  void* meta;                /* MPSC: metadata ring of hicr_mpsc_meta_t; non-locking: max_msgs
+                                hicr_nl_meta_t per ring, ring p's at meta + p * max_msgs */
 } hicr_channel_view_t;
+
+/* Non-locking counter block of producer ring p: head + p * HICR_NL_STATE_WORDS,
+ * with the bytes reserved and the messages published (written by the
+ * producer) and the bytes freed and messages consumed (written by the
+ * consumer) at these word offsets, each on its own 128-byte line. */
+#define HICR_NL_STATE_WORDS 64u
+#define HICR_NL_RESERVE 0u
+#define HICR_NL_PUB 16u
+#define HICR_NL_FREED 32u
+#define HICR_NL_CONS 48u
+
+/* One non-locking metadata entry: absolute reservation start, size and
+ * sequence number (the producer is the ring's index). */
+typedef struct {
+  unsigned long long start;
+  uint32_t size;
+  uint32_t seq;
+} hicr_nl_meta_t;
 
 /* One MPSC metadata entry (the library's layout). `ready` holds
  * (ticket mod 2^24) + 1 once the message of that ticket is published. */
@@ -129,8 +149,8 @@ typedef struct {
   unsigned long long ready;
 } hicr_mpsc_meta_t;
 
-/* Fill *out with the device view of an SPSC or MPSC (locking) channel.
- * Errors: INVALID (unknown channel, non-locking MPSC). */
+/* Fill *out with the device view of an SPSC, MPSC (locking) or MPSC
+ * (non-locking) channel. Errors: INVALID (unknown channel). */
 hicr_status hicr_channel_device_view(hicr_instance_t inst, hicr_channel_t ch, hicr_channel_view_t* out);
 
 /* ------------------------------------------------------------------------ */

@@ -17,8 +17,9 @@
  * are those of hicr_channels.h, so a channel can be filled on the device and
  * drained from the host (or the reverse), as long as each side is the only
  * producer or consumer it claims to be (SPSC: one producer agent and one
- * consumer agent at a time; MPSC: any number of producer warps, one consumer
- * agent).
+ * consumer agent at a time; MPSC locking mode: any number of producer warps,
+ * one consumer agent; non-locking mode: one producer agent per ring, one
+ * consumer agent).
  *
  * Memory: src/dst buffers are device-accessible addresses; any alignment.
  */
@@ -242,6 +243,148 @@ __device__ inline int hicr_dev_mpsc_pop(const hicr_channel_view_t& v, void* dst,
     st_release(v.tail, t + 1);
   }
   return HICR_OK;
+}
+
+/* Non-locking MPSC: producer `producer` pushes one message of n bytes into
+ * its own ring (the calling warp must be that ring's only producer). Same
+ * placement rule per ring; waits while the ring has no room. Returns
+ * HICR_OK, HICR_ERR_TOO_LARGE, HICR_ERR_INVALID or HICR_ERR_TIMEOUT. */
+__device__ inline int hicr_dev_mpsc_nl_push(const hicr_channel_view_t& v, uint32_t producer, uint32_t seq,
+                                            const void* src, uint32_t n, unsigned long long timeout_ns) {
+  using namespace hicr_dev;
+  const unsigned lane = threadIdx.x & 31u;
+  if (v.kind != 2 || producer >= v.capacity) return HICR_ERR_INVALID;
+  const unsigned long long R = v.ring_bytes, r = r16(n);
+  if (r > R) return HICR_ERR_TOO_LARGE;
+  unsigned long long* cnt = v.head + (unsigned long long)producer * HICR_NL_STATE_WORDS;
+  unsigned long long start = 0, pub = 0;
+  int st = HICR_OK;
+  if (lane == 0) {
+    const unsigned long long b = *(volatile unsigned long long*)(cnt + HICR_NL_RESERVE);
+    pub = *(volatile unsigned long long*)(cnt + HICR_NL_PUB);
+    const unsigned long long pos = b & (R - 1);
+    start = pos + r > R ? b + (R - pos) : b;
+    const unsigned long long t0 = now();
+    while (start + r - ld_acquire(cnt + HICR_NL_FREED) > R || pub + 1 - ld_acquire(cnt + HICR_NL_CONS) > v.max_msgs) {
+      if (now() - t0 > timeout_ns) {
+        st = HICR_ERR_TIMEOUT;
+        break;
+      }
+      __nanosleep(64);
+    }
+  }
+  st = __shfl_sync(0xffffffffu, st, 0);
+  if (st != HICR_OK) return st;
+  start = __shfl_sync(0xffffffffu, start, 0);
+  pub = __shfl_sync(0xffffffffu, pub, 0);
+  copy(v.ring + (unsigned long long)producer * R + (start & (R - 1)), static_cast<const uint8_t*>(src), n, lane);
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) {
+    hicr_nl_meta_t* e = static_cast<hicr_nl_meta_t*>(v.meta) + (unsigned long long)producer * v.max_msgs +
+                        (pub & (v.max_msgs - 1));
+    e->start = start;
+    e->size = n;
+    e->seq = seq;
+    *(volatile unsigned long long*)(cnt + HICR_NL_RESERVE) = start + r;
+    st_release(cnt + HICR_NL_PUB, pub + 1);
+  }
+  return HICR_OK;
+}
+
+/* Non-locking MPSC: pop the oldest message of ring `producer` into dst (at
+ * most dst_cap bytes), waiting for one; the calling warp must be that ring's
+ * only consumer. *info (if not NULL; written by lane 0) receives its ring
+ * offset, size, producer and sequence number. Returns HICR_OK,
+ * HICR_ERR_TOO_LARGE (nothing popped), HICR_ERR_INVALID or HICR_ERR_TIMEOUT. */
+__device__ inline int hicr_dev_mpsc_nl_pop(const hicr_channel_view_t& v, uint32_t producer, void* dst,
+                                           uint64_t dst_cap, hicr_msg_info_t* info, unsigned long long timeout_ns) {
+  using namespace hicr_dev;
+  const unsigned lane = threadIdx.x & 31u;
+  if (v.kind != 2 || producer >= v.capacity) return HICR_ERR_INVALID;
+  unsigned long long* cnt = v.head + (unsigned long long)producer * HICR_NL_STATE_WORDS;
+  unsigned long long c = 0, start = 0;
+  unsigned n = 0, seq = 0;
+  int st = HICR_OK;
+  if (lane == 0) {
+    c = *(volatile unsigned long long*)(cnt + HICR_NL_CONS);
+    const unsigned long long t0 = now();
+    while (ld_acquire(cnt + HICR_NL_PUB) == c) {
+      if (now() - t0 > timeout_ns) {
+        st = HICR_ERR_TIMEOUT;
+        break;
+      }
+      __nanosleep(64);
+    }
+    if (st == HICR_OK) {
+      const hicr_nl_meta_t* e = static_cast<const hicr_nl_meta_t*>(v.meta) +
+                                (unsigned long long)producer * v.max_msgs + (c & (v.max_msgs - 1));
+      start = __ldcg(&e->start);
+      n = __ldcg(&e->size);
+      seq = __ldcg(&e->seq);
+      if (n > dst_cap) st = HICR_ERR_TOO_LARGE;
+    }
+  }
+  st = __shfl_sync(0xffffffffu, st, 0);
+  if (st != HICR_OK) return st;
+  __syncwarp();
+  c = __shfl_sync(0xffffffffu, c, 0);
+  start = __shfl_sync(0xffffffffu, start, 0);
+  n = __shfl_sync(0xffffffffu, n, 0);
+  copy(static_cast<uint8_t*>(dst), v.ring + (unsigned long long)producer * v.ring_bytes + (start & (v.ring_bytes - 1)),
+       n, lane);
+  __syncwarp();
+  if (lane == 0) {
+    if (info) {
+      info->offset = start & (v.ring_bytes - 1);
+      info->size = n;
+      info->producer = producer;
+      info->reserved = 0;
+      info->seq = seq;
+    }
+    st_release(cnt + HICR_NL_FREED, start + r16(n));
+    st_release(cnt + HICR_NL_CONS, c + 1);
+  }
+  return HICR_OK;
+}
+
+/* Non-locking MPSC: pop one message from whichever ring has one, scanning
+ * the rings round-robin from *next (32 rings per step, one per lane) until
+ * one is non-empty; *next (every lane's copy) becomes the ring after the one
+ * popped. The calling warp must be the only consumer of every ring. Returns
+ * as hicr_dev_mpsc_nl_pop; HICR_ERR_TIMEOUT when every ring stayed empty. */
+__device__ inline int hicr_dev_mpsc_nl_pop_any(const hicr_channel_view_t& v, uint32_t* next, void* dst,
+                                               uint64_t dst_cap, hicr_msg_info_t* info,
+                                               unsigned long long timeout_ns) {
+  using namespace hicr_dev;
+  const unsigned lane = threadIdx.x & 31u;
+  if (v.kind != 2 || v.capacity == 0) return HICR_ERR_INVALID;
+  const unsigned P = v.capacity;
+  const unsigned long long t0 = now();
+  for (;;) {
+    const unsigned first = *next % P;
+    for (unsigned base = 0; base < P; base += 32) {
+      const unsigned off = base + lane;
+      const unsigned p = (first + off) % P;
+      bool ready = false;
+      if (off < P) {
+        const unsigned long long* cnt = v.head + (unsigned long long)p * HICR_NL_STATE_WORDS;
+        ready = ld_acquire(cnt + HICR_NL_PUB) != *(volatile const unsigned long long*)(cnt + HICR_NL_CONS);
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, ready);
+      if (m) {
+        const unsigned pick = __shfl_sync(0xffffffffu, p, __ffs(m) - 1);
+        const int st = hicr_dev_mpsc_nl_pop(v, pick, dst, dst_cap, info, timeout_ns);
+        if (st == HICR_OK) *next = (pick + 1) % P;
+        return st;
+      }
+    }
+    int give_up = 0;
+    if (lane == 0) give_up = now() - t0 > timeout_ns;
+    if (__shfl_sync(0xffffffffu, give_up, 0)) return HICR_ERR_TIMEOUT;
+    if (lane == 0) __nanosleep(64);
+    __syncwarp();
+  }
 }
 
 #endif /* __CUDACC__ */

@@ -242,6 +242,12 @@ struct NlMeta {
   unsigned int seq;
 };
 static_assert(sizeof(NlMeta) == 16, "non-locking metadata entry is 16 bytes");
+// the public description of the non-locking layout (hicr_channels.h)
+static_assert(sizeof(hicr_nl_meta_t) == sizeof(NlMeta), "public non-locking metadata layout");
+static_assert(sizeof(NlState) == 8 * HICR_NL_STATE_WORDS && offsetof(NlState, reserve) == 8 * HICR_NL_RESERVE &&
+                  offsetof(NlState, pub) == 8 * HICR_NL_PUB && offsetof(NlState, freed) == 8 * HICR_NL_FREED &&
+                  offsetof(NlState, cons) == 8 * HICR_NL_CONS,
+              "public non-locking counter layout");
 // the public description of a locking-mode metadata entry (hicr_channels.h)
 static_assert(sizeof(hicr_mpsc_meta_t) == sizeof(MpscMeta) && offsetof(hicr_mpsc_meta_t, start) == offsetof(MpscMeta, start) &&
                   offsetof(hicr_mpsc_meta_t, size) == offsetof(MpscMeta, size) &&
@@ -1409,7 +1415,7 @@ hicr_status hicr_channel_device_view(hicr_instance_t h, hicr_channel_t ch, hicr_
   Instance* in = I(h);
   if (!in || !out) return HICR_ERR_INVALID;
   Channel* c = get(in, ch);
-  if (!c || c->kind > 1) return HICR_ERR_INVALID;
+  if (!c) return HICR_ERR_INVALID;
   hicr_channel_view_t v;
   memset(&v, 0, sizeof(v));
   v.kind = (uint32_t)c->kind;
@@ -1421,7 +1427,7 @@ hicr_status hicr_channel_device_view(hicr_instance_t h, hicr_channel_t ch, hicr_
     v.ring_bytes = (uint64_t)c->token_size * c->capacity;
     v.head = &st->head.v;
     v.tail = &st->tail.v;
-  } else {
+  } else if (c->kind == 1) {
     MpscState* st = (MpscState*)c->state;
     v.max_msgs = c->max_msgs;
     v.ring_bytes = c->ring_bytes;
@@ -1429,6 +1435,13 @@ hicr_status hicr_channel_device_view(hicr_instance_t h, hicr_channel_t ch, hicr_
     v.tail = &st->msg_tail.v;
     v.freed = &st->freed.v;
     v.meta = c->meta;
+  } else {
+    const NlView nv = nl_view(c);
+    v.capacity = nv.P;
+    v.max_msgs = nv.M;
+    v.ring_bytes = nv.R;
+    v.head = &nv.st->reserve.v;
+    v.meta = nv.meta;
   }
   *out = v;
   return HICR_OK;

@@ -101,3 +101,45 @@ extern "C" int devapi_mpsc_pop(const hicr_channel_view_t* v, unsigned long long 
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? (int)cudaDeviceSynchronize() : (int)e;
 }
+
+// Non-locking MPSC. Blocks [0, P) are producers (warp 0 each), each pushing
+// its M messages into its own ring; block P (warp 0) is the consumer when
+// `consume` is set and pops P*M messages with pop_any.
+__global__ void k_nl(hicr_channel_view_t v, const uint8_t* staging, const unsigned long long* offs,
+                     const unsigned long long* sizes, unsigned P, unsigned M, int consume, uint8_t* out,
+                     unsigned long long out_stride, hicr_msg_info_t* infos, unsigned long long timeout_ns,
+                     int* status) {
+  if (threadIdx.x >= 32) return;
+  if (blockIdx.x < P) {
+    const unsigned p = blockIdx.x;
+    for (unsigned s = 0; s < M; ++s) {
+      const size_t i = (size_t)p * M + s;
+      const int st = hicr_dev_mpsc_nl_push(v, p, s, staging + offs[i], (uint32_t)sizes[i], timeout_ns);
+      if (st != HICR_OK) {
+        if (threadIdx.x == 0) atomicCAS(status, 0, st);
+        return;
+      }
+    }
+  } else if (consume) {
+    uint32_t next = 0;
+    for (unsigned long long j = 0; j < (unsigned long long)P * M; ++j) {
+      const int st = hicr_dev_mpsc_nl_pop_any(v, &next, out + j * out_stride, out_stride, infos + j, timeout_ns);
+      if (st != HICR_OK) {
+        if (threadIdx.x == 0) status[1] = st;
+        return;
+      }
+    }
+  }
+}
+
+extern "C" int devapi_nl(const hicr_channel_view_t* v, const void* staging, const unsigned long long* offs,
+                         const unsigned long long* sizes, unsigned P, unsigned M, int consume, void* out,
+                         unsigned long long out_stride, hicr_msg_info_t* infos, unsigned long long timeout_ns,
+                         int* status) {
+  hicr_channel_view_t view = *v;
+  const uint8_t* st = (const uint8_t*)staging;
+  uint8_t* o = (uint8_t*)out;
+  void* args[] = {&view, &st, &offs, &sizes, &P, &M, &consume, &o, &out_stride, &infos, &timeout_ns, &status};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_nl, dim3(P + (consume ? 1 : 0)), dim3(32), args, 0, 0);
+  return e == cudaSuccess ? (int)cudaDeviceSynchronize() : (int)e;
+}

@@ -23,7 +23,7 @@ import torch
 from oracle import channels as oc
 from oracle import memcpy as om
 from workloads import configs, splitmix
-from tests.gpu_util import h, inst  # noqa: F401
+from tests.gpu_util import device_bytes, h, inst  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -53,6 +53,7 @@ def dev():
     lib.devapi_spsc.argtypes = [vp, vp, vp, u32, u32, u64, i32, vp]
     lib.devapi_mpsc.argtypes = [vp, vp, vp, vp, u32, u32, i32, vp, u64, vp, u64, vp]
     lib.devapi_mpsc_pop.argtypes = [vp, u64, vp, u64, vp, u64, vp]
+    lib.devapi_nl.argtypes = [vp, vp, vp, vp, u32, u32, i32, vp, u64, vp, u64, vp]
     return lib
 
 
@@ -206,9 +207,80 @@ def test_device_mpsc_interoperates_with_host_calls(h, inst, dev):
     assert h.hicr_channel_destroy(inst, ch) == 0
 
 
-def test_device_view_rejects_nonlocking_channels(h, inst):
-    st, ch = h.hicr_mpsc_nl_create(inst, 2, 1 << 12, 4)
+INFO_DTYPE = np.dtype([("offset", "<u8"), ("size", "<u8"), ("producer", "<u4"), ("reserved", "<u4"), ("seq", "<u8")])
+
+
+@pytest.mark.parametrize("P,M,ring,max_msgs,hi", [(6, 30, 1 << 12, 8, 1500), (40, 5, 1 << 13, 4, 3000)])
+def test_device_nonlocking_producers_and_consumer(h, inst, dev, P, M, ring, max_msgs, hi):
+    """Producer warps push into their own rings (waiting for room as the
+    rings wrap) while one consumer warp pops with pop_any: every message once,
+    per-producer order, offsets replayed per ring, payloads exact."""
+    w, sizes, offs, staging = _mpsc_inputs(P, M, hi, 40 + P)
+    st, ch = h.hicr_mpsc_nl_create(inst, P, ring, max_msgs)
     assert st == 0
-    assert h.hicr_channel_device_view(inst, ch)[0] == h.HICR_ERR_INVALID
-    assert h.hicr_channel_device_view(inst, 12345)[0] == h.HICR_ERR_INVALID
+    v = _view(h, inst, ch)
+    assert (v.kind, v.capacity, v.ring_bytes, v.max_msgs) == (2, P, ring, max_msgs)
+    d_st = torch.from_numpy(staging).cuda()
+    d_off = torch.from_numpy(offs.view(np.int64).copy()).cuda()
+    d_sz = torch.from_numpy(sizes.view(np.int64).copy()).cuda()
+    stride = int(((sizes.max() + 15) // 16) * 16)
+    out = torch.zeros(P * M * stride, dtype=torch.uint8, device="cuda")
+    infos = torch.zeros(P * M * INFO_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    status = _status()
+    assert dev.devapi_nl(ctypes.byref(v), d_st.data_ptr(), d_off.data_ptr(), d_sz.data_ptr(), P, M, 1,
+                         out.data_ptr(), stride, infos.data_ptr(), T, status.data_ptr()) == 0
+    assert status.cpu().tolist() == [0, 0]
+    info = np.frombuffer(infos.cpu().numpy().tobytes(), dtype=INFO_DTYPE)
+    log = list(zip(info["producer"], info["seq"], info["size"], info["offset"]))
+    assert oc.check_mpsc_nl_log(w.sizes, 1, 0, log, ring) == []
+    o = out.cpu().numpy().reshape(P * M, stride)
+    for j, (p, q, n, _) in enumerate(log):
+        assert (o[j, :int(n)] == splitmix.mpsc_payload_bytes(int(p), int(q), int(n))).all(), j
+    assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
     assert h.hicr_channel_destroy(inst, ch) == 0
+
+
+def test_device_nonlocking_push_host_drain(h, inst, dev):
+    """Device producers fill their rings (no consumer); the host's peek and
+    pop see the non-locking oracle's order (producers in index order, each
+    producer's messages oldest first) with its offsets and payloads."""
+    P, M, ring = 5, 4, 1 << 14
+    w, sizes, offs, staging = _mpsc_inputs(P, M, 2000, 77)
+    st, ch = h.hicr_mpsc_nl_create(inst, P, ring, 8)
+    v = _view(h, inst, ch)
+    d_st = torch.from_numpy(staging).cuda()
+    d_off = torch.from_numpy(offs.view(np.int64).copy()).cuda()
+    d_sz = torch.from_numpy(sizes.view(np.int64).copy()).cuda()
+    status = _status()
+    assert dev.devapi_nl(ctypes.byref(v), d_st.data_ptr(), d_off.data_ptr(), d_sz.data_ptr(), P, M, 0, 0, 16, 0, T,
+                         status.data_ptr()) == 0
+    assert status.cpu().tolist() == [0, 0]
+    orc = oc.MpscNonLockingOracle(P, ring, 8)
+    for p in range(P):
+        for q in range(M):
+            i = p * M + q
+            assert orc.push(p, staging[int(offs[i]):int(offs[i]) + int(sizes[i])]) == om.OK
+    assert h.hicr_channel_depth(inst, ch)[1:] == orc.depth()
+    st, rs = h.hicr_channel_ring(inst, ch)
+    st, rptr, _, _, _ = h.hicr_slot_info(inst, rs)
+    torch.cuda.synchronize()
+    rings = device_bytes(rptr, P * ring).cpu().numpy()
+    for k in range(P * M):
+        est, einfo = orc.peek(k)
+        gst, ginfo = h.hicr_channel_peek(inst, ch, k)
+        assert gst == est == om.OK and ginfo == einfo, k
+        o, n, p, q = ginfo
+        assert (rings[p * ring + o:p * ring + o + n] == orc.payload(k)).all(), k
+    assert h.hicr_channel_pop(inst, ch, P * M) == orc.pop(P * M) == om.OK
+    assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
+    assert h.hicr_channel_destroy(inst, ch) == 0
+
+
+def test_device_view_of_every_kind(h, inst):
+    st, a = h.hicr_spsc_create(inst, 64, 16)
+    st, b = h.hicr_mpsc_create(inst, 3, 1 << 12, 8)
+    st, c = h.hicr_mpsc_nl_create(inst, 2, 1 << 12, 4)
+    assert [h.hicr_channel_device_view(inst, x)[1].kind for x in (a, b, c)] == [0, 1, 2]
+    assert h.hicr_channel_device_view(inst, 12345)[0] == h.HICR_ERR_INVALID
+    for x in (a, b, c):
+        assert h.hicr_channel_destroy(inst, x) == 0
