@@ -22,6 +22,7 @@
 // from being handed too many tiny ops at once.
 #include <stdio.h>
 #include <stdlib.h>
+#include <omp.h>
 #include <string.h>
 
 #include <algorithm>
@@ -408,6 +409,11 @@ hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, c
   return HICR_OK;
 }
 
+// Host tables of at least this many ops are validated and staged by several
+// host threads (OpenMP); smaller ones on the calling thread.
+static constexpr uint64_t PAR_OPS = 8192;
+static int host_threads() { return std::min(8, omp_get_num_procs()); }
+
 // Copy a host op table to the device through a double-buffered pinned
 // staging area and launch it.
 static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
@@ -437,7 +443,16 @@ static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_
     HICR_CUDA(in, e);
     in->d_ops_cap = cap;
   }
-  memcpy(in->pinned[k], ops, count * sizeof(hicr_op_t));
+  if (count >= PAR_OPS) {
+    const int nt = host_threads();
+#pragma omp parallel for schedule(static) num_threads(nt)
+    for (int t = 0; t < nt; ++t) {
+      const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
+      memcpy(in->pinned[k] + a, ops + a, (b - a) * sizeof(hicr_op_t));
+    }
+  } else {
+    memcpy(in->pinned[k], ops, count * sizeof(hicr_op_t));
+  }
   cudaStream_t st = in->comm();
   HICR_CUDA(in, cudaMemcpyAsync(in->d_ops, in->pinned[k], count * sizeof(hicr_op_t), cudaMemcpyHostToDevice, st));
   HICR_CUDA(in, cudaEventRecord(in->pinned_ev[k], st));
@@ -447,11 +462,23 @@ static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_
 }
 
 static hicr_status validate_all(Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
-  for (uint64_t i = 0; i < count; ++i) {
-    hicr_status s = validate_op(in, ops[i]);
-    if (s != HICR_OK) {
-      if (first_bad) *first_bad = i;
-      return s;
+  if (count >= PAR_OPS) {
+    // every op is checked; the reported one is the first invalid in issue order
+    long long first = (long long)count;
+#pragma omp parallel for schedule(static) reduction(min : first) num_threads(host_threads())
+    for (long long i = 0; i < (long long)count; ++i)
+      if (i < first && validate_op(in, ops[i]) != HICR_OK) first = i;
+    if (first < (long long)count) {
+      if (first_bad) *first_bad = (uint64_t)first;
+      return validate_op(in, ops[first]);
+    }
+  } else {
+    for (uint64_t i = 0; i < count; ++i) {
+      hicr_status s = validate_op(in, ops[i]);
+      if (s != HICR_OK) {
+        if (first_bad) *first_bad = i;
+        return s;
+      }
     }
   }
   if (in->checked) {

@@ -386,3 +386,33 @@ def test_autotune_cache_round_trip(h, inst, tmp_path, monkeypatch):
     assert st == 0 and c2.as_dict() == c1.as_dict() and abs(ms2 - ms1) < 1e-3 * max(ms1, 1.0)
     assert h.hicr_batch_get_config(inst)[1].as_dict() == c1.as_dict()
     assert len(path.read_text().splitlines()) == 1
+
+
+@pytest.mark.parametrize("n_ops,bad_at", [(20_000, 19_999), (20_000, 0), (50_000, 31_337), (8_192, 4_096)])
+def test_large_host_batch_reports_the_first_invalid_op(h, inst, n_ops, bad_at):
+    """Host tables of 8,192 ops or more are validated by several host
+    threads; the reported op is still the first invalid one in issue order,
+    nothing of the batch runs, and the same table without the bad ops runs
+    exactly as the oracle says."""
+    size = 1 << 20
+    ids = alloc_filled(h, inst, [size, size], 4)
+    cm, oids = oracle_slots([size, size], 4)
+    rng = np.random.default_rng(n_ops + bad_at)
+    n = rng.integers(0, 16, n_ops)
+    doff = np.arange(n_ops, dtype=np.uint64) * np.uint64(16)  # disjoint destinations
+    soff = rng.integers(0, size - 16, n_ops)
+    ops = configs.make_ops([1] * n_ops, [0] * n_ops, doff, soff, n)
+    bad = ops.copy()
+    bad["n"][bad_at] = size + 1                       # out of bounds
+    bad["n"][min(bad_at + 7, n_ops - 1)] = size + 1   # a later one is not the one reported
+    st, first = h.hicr_memcpy_batch(inst, remap(bad, ids))
+    assert (st, first) == (h.HICR_ERR_BOUNDS, bad_at)
+    assert cm.memcpy_batch(bad) == (om.ERR_BOUNDS, bad_at)
+    assert h.hicr_fence(inst, 0, T) == 0
+    assert h.hicr_slot_counters(inst, ids[1])[1:] == (0, 0)   # the rejected batch did nothing
+    assert h.hicr_memcpy_batch(inst, remap(ops, ids)) == (0, 0)
+    assert cm.memcpy_batch(ops) == (om.OK, None)
+    assert h.hicr_fence(inst, 0, T) == 0
+    for k in range(2):
+        assert (slot_bytes(h, inst, ids[k]) == cm.slots[oids[k]].data).all()
+    assert h.hicr_slot_counters(inst, ids[1])[1:] == (0, n_ops)
