@@ -218,8 +218,10 @@ typedef struct {
  * log entry of ticket t goes to d_log + c * log_stride + (t - t0), t0 the
  * channel's first ticket of the run (device array, at least as many entries
  * as the consumer receives), so logs are in ticket order.
- * One cooperative grid; every wait gives up after `timeout_ns`.
- * Synchronous; `results` is a host array of n_consumers.
+ * One cooperative grid: the consumer CTAs plus producer CTAs of 512
+ * threads; the producer warps are spread evenly over every CTA slot that the
+ * consumer CTAs leave free on the device. Every wait gives up after
+ * `timeout_ns`. Synchronous; `results` is a host array of n_consumers.
  * Errors: INVALID (also when the grid cannot be co-resident), BOUNDS (a
  * message outside the staging slot), TOO_LARGE (a message larger than half
  * its ring), DEVICE, TIMEOUT. */

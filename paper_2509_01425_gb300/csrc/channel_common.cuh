@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "copy.cuh"
+#include "tma.cuh"
 
 namespace hicr {
 
@@ -97,6 +98,207 @@ __device__ __forceinline__ void ring_copy(uint8_t* __restrict__ d, const uint8_t
   for (unsigned long long q = q0 + lane; q < nv; q += 32) dv[q] = __ldcs(sv + q);
   const unsigned long long tb = nv * 16;
   if (tb + lane < n) d[tb + lane] = s[tb + lane];
+}
+
+// Producer copy of a group of k (1 .. 32) messages into their ring slots
+// through the warp's NST shared-memory stages of STG bytes each (with one
+// mbarrier per stage). Lane j < k holds message j: destination d, source s, n
+// bytes. The 16-byte-aligned bodies of the messages whose source and
+// destination are both 16-byte aligned form one byte sequence that moves by
+// bulk copies: it is cut into stage fills of up to STG bytes, so that one fill
+// can carry several small messages (one bulk load each, all completing on the
+// stage's mbarrier), and every fill, once landed, leaves by one bulk store per
+// message part. NST fills are in flight at a time; a stage is refilled only
+// after the store that read it has finished reading. Sub-16-byte tails, and
+// whole messages with other alignments, use plain warp copies. Lane 0 issues
+// every bulk operation; control flow is warp-uniform. `phase` holds one parity
+// bit per stage (the same in all lanes). On return the bulk stores have
+// completed and are ordered before the caller's later generic-proxy release.
+// Returns false if an mbarrier wait gave up after wait_ns; bulk copies still in
+// flight are drained first, each wait again bounded.
+template <unsigned NST, unsigned STG>
+__device__ bool group_copy_bulk(uint8_t* d, const uint8_t* s, unsigned long long n, int k, unsigned lane,
+                                uint8_t* stage, unsigned long long* bars, unsigned& phase,
+                                unsigned long long wait_ns) {
+  const unsigned FM = 0xffffffffu;
+  const bool al =
+      lane < (unsigned)k && ((reinterpret_cast<uintptr_t>(d) | reinterpret_cast<uintptr_t>(s)) & 15u) == 0;
+  const unsigned long long B = al ? (n & ~15ull) : 0ull;
+  const unsigned long long du = reinterpret_cast<uintptr_t>(d), su = reinterpret_cast<uintptr_t>(s);
+  // the ring bytes were last read by the consumer (ordinary loads, ordered
+  // before this producer's acquire of the freed counter): order those before
+  // the bulk stores
+  if (lane == 0) fence_proxy_async_global();
+  int ci = 0;  // load cursor: message ci, byte co of its body
+  unsigned long long co = 0;
+  // one stage fill from the cursor; returns its bytes (0: nothing left)
+  auto fill = [&](unsigned st) -> unsigned {
+    int i = ci;
+    unsigned long long o = co;
+    unsigned used = 0;
+    while (i < k && used < STG) {
+      const unsigned long long b = __shfl_sync(FM, B, i);
+      if (o >= b) {
+        ++i;
+        o = 0;
+        continue;
+      }
+      const unsigned long long len = min(b - o, (unsigned long long)(STG - used));
+      used += (unsigned)len;
+      o += len;
+    }
+    if (used) {
+      if (lane == 0) mbar_expect_tx(bars + st, used);
+      unsigned off = 0;
+      while (off < used) {
+        const unsigned long long b = __shfl_sync(FM, B, ci);
+        const unsigned long long sp = __shfl_sync(FM, su, ci);
+        if (co >= b) {
+          ++ci;
+          co = 0;
+          continue;
+        }
+        const unsigned long long len = min(b - co, (unsigned long long)(used - off));
+        if (lane == 0) tma_load(stage + st * STG + off, reinterpret_cast<const uint8_t*>(sp) + co, (unsigned)len, bars + st);
+        off += (unsigned)len;
+        co += len;
+      }
+    }
+    return used;
+  };
+  // lane 0 waits (bounded) for stage st's fill; the verdict goes to all lanes
+  auto landed = [&](unsigned st) -> bool {
+    int okw = 1;
+    if (lane == 0) {
+      const unsigned par = (phase >> st) & 1u;
+      if (!mbar_try_wait(bars + st, par)) {
+        const unsigned long long t0 = tma_now_ns();
+        while (!mbar_try_wait(bars + st, par)) {
+          if (tma_now_ns() - t0 > wait_ns) {
+            okw = 0;
+            break;
+          }
+        }
+      }
+    }
+    okw = __shfl_sync(FM, okw, 0);
+    if (okw) phase ^= 1u << st;
+    return okw != 0;
+  };
+  int fi[NST];
+  unsigned long long fo[NST];
+  unsigned fu[NST];
+#pragma unroll
+  for (unsigned st = 0; st < NST; ++st) {
+    fi[st] = ci;
+    fo[st] = co;
+    fu[st] = fill(st);
+  }
+  bool ok = true;
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (unsigned st = 0; st < NST; ++st) {
+      if (!ok || fu[st] == 0) continue;
+      any = true;
+      if (!landed(st)) {
+        ok = false;
+        fu[st] = 0;
+        continue;
+      }
+      int i = fi[st];
+      unsigned long long o = fo[st];
+      unsigned off = 0;
+      while (off < fu[st]) {
+        const unsigned long long b = __shfl_sync(FM, B, i);
+        const unsigned long long dp = __shfl_sync(FM, du, i);
+        if (o >= b) {
+          ++i;
+          o = 0;
+          continue;
+        }
+        const unsigned long long len = min(b - o, (unsigned long long)(fu[st] - off));
+        if (lane == 0) tma_store(reinterpret_cast<uint8_t*>(dp) + o, stage + st * STG + off, (unsigned)len);
+        off += (unsigned)len;
+        o += len;
+      }
+      if (lane == 0) {
+        tma_commit();
+        tma_wait_read0();  // the stage may be refilled once its store has read it
+      }
+      __syncwarp();
+      fi[st] = ci;
+      fo[st] = co;
+      fu[st] = fill(st);
+    }
+    if (!any || !ok) break;
+  }
+  if (!ok) {
+    // drain the fills still in flight before the stages can be given up
+#pragma unroll
+    for (unsigned st = 0; st < NST; ++st)
+      if (fu[st]) landed(st);
+  }
+  if (lane == 0) {
+    tma_wait_all();
+    fence_proxy_async_global();
+  }
+  __syncwarp();
+  // tails and unaligned messages
+  for (int j = 0; j < k; ++j) {
+    const unsigned long long nj = __shfl_sync(FM, n, j), bj = __shfl_sync(FM, B, j);
+    const unsigned long long dj = __shfl_sync(FM, du, j), sj = __shfl_sync(FM, su, j);
+    const int aj = __shfl_sync(FM, (int)al, j);
+    uint8_t* dd = reinterpret_cast<uint8_t*>(dj);
+    const uint8_t* ss = reinterpret_cast<const uint8_t*>(sj);
+    if (!aj) warp_copy(dd, ss, nj, lane);
+    else if (bj + lane < nj) dd[bj + lane] = ss[bj + lane];
+  }
+  return ok;
+}
+
+// Word digest of one piece of a message (the 16-byte vectors
+// [q0, q0 + 32 * NU) of a message of n bytes, src = its first vector), this
+// lane's share: lane l holds vectors q = q0 + l + 32u, u < NU, and returns
+// sum over them of w0 (4q + 1) + w1 (4q + 3), where w0, w1 are the vector's
+// two little-endian words and bytes past n count as zero (so the warp sum over
+// all pieces is sum_i w_i (2i + 1) over the message's words). All NU loads
+// are issued before any arithmetic. The sum is taken in the equivalent form
+//   (4 qb + 1) S + 128 U + 2 W1,  qb = q0 + l,
+// with S = sum_u (w0 + w1), U = sum_u u (w0 + w1), W1 = sum_u w1 (all mod
+// 2^64), which needs one 64-bit product per piece instead of two per vector.
+template <int NU>
+__device__ __forceinline__ unsigned long long piece_digest(const uint4* __restrict__ src, unsigned long long q0,
+                                                           unsigned long long n, unsigned lane) {
+  const unsigned long long nv = (n + 15) / 16;
+  const unsigned long long left = nv - q0;  // > 0
+  const unsigned rem = left < 32ull * NU ? (unsigned)left : 32u * NU;
+  const uint4* sp = src + q0 + lane;
+  uint4 x[NU];
+#pragma unroll
+  for (int u = 0; u < NU; ++u)
+    if (lane + 32u * u < rem) x[u] = __ldcg(sp + 32 * u);
+  // the message's last vector (in this piece only if left <= 32 NU) keeps
+  // only the bytes below n
+  const unsigned last = left <= 32ull * NU ? rem - 1 : 0xffffffffu;
+  const unsigned tail = (unsigned)(n - 16 * (nv - 1));  // 1..16 bytes
+  unsigned long long S = 0, U = 0, W1 = 0;
+#pragma unroll
+  for (int u = NU - 1; u >= 0; --u) {
+    if (lane + 32u * u < rem) {
+      unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
+      unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
+      if (lane + 32u * u == last) {
+        if (tail < 8) w0 &= ~0ull >> (64 - 8 * tail);
+        if (tail <= 8) w1 = 0;
+        else if (tail < 16) w1 &= ~0ull >> (128 - 8 * tail);
+      }
+      S += w0 + w1;
+      W1 += w1;
+    }
+    if (u > 0) U += S;  // after the loop: U = sum_u u (w0 + w1)
+  }
+  return S * (4ull * (q0 + lane) + 1ull) + (U << 7) + (W1 << 1);
 }
 
 struct SpscView {

@@ -559,11 +559,33 @@ struct MpscStreamArgs {
   unsigned int G;                  // CTAs per consumer
   unsigned long long* claim;       // per consumer (stride 16 words): next unclaimed ticket
   const unsigned long long* base;  // per consumer: first ticket of the run
+  unsigned int pw;                 // producer warps per producer CTA
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
+// Producer warps copy their groups through PROD_NST shared-memory stages of
+// PROD_STG bytes each (bulk copies); a producer CTA holds at most PROD_WARPS
+// producer warps.
+static constexpr unsigned PROD_NST = 2, PROD_STG = 6144, PROD_WARPS = 16;
+static constexpr size_t PROD_SMEM = (size_t)PROD_WARPS * PROD_NST * (PROD_STG + 8);
+static constexpr unsigned long long PROD_WAIT_NS = 2000000000ull;  // bound of one stage wait
 
-__device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline) {
+// The warp's stages and mbarriers in the dynamic shared memory of a producer
+// CTA; lane 0 initialises the mbarriers.
+__device__ __forceinline__ void prod_stages(uint8_t* smem, unsigned warp, unsigned lane, uint8_t** stage,
+                                            unsigned long long** bars) {
+  *stage = smem + (size_t)warp * PROD_NST * PROD_STG;
+  *bars = reinterpret_cast<unsigned long long*>(smem + (size_t)PROD_WARPS * PROD_NST * PROD_STG) + warp * PROD_NST;
+  if (lane == 0) {
+    for (unsigned k = 0; k < PROD_NST; ++k) mbar_init(*bars + k);
+    mbar_init_fence();
+  }
+  __syncwarp();
+}
+
+__device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline,
+                              uint8_t* stage, unsigned long long* bars) {
+  unsigned phase = 0;
   const unsigned c = p % a.n_cons;
   const MpscView v = a.chans[c];
   const unsigned long long half = v.R / 2;
@@ -575,7 +597,7 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
   for (unsigned s = 0; s < a.mpp;) {
     // the group: up to `group` (and at most max_msgs) messages whose rounded
     // sizes sum to <= R/2, so that it always fits an emptied ring
-    unsigned long long r[MPSC_MAX_GROUP], st[MPSC_MAX_GROUP];
+    unsigned long long r[MPSC_MAX_GROUP], st[MPSC_MAX_GROUP] = {};
     int k = 0;
     unsigned long long sum = 0;
     for (; k < (int)a.group && (unsigned)k < v.M && s + k < a.mpp; ++k) {
@@ -627,25 +649,36 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
     }
     W = __shfl_sync(FULLM, W, 0);
     const unsigned long long t0 = W >> 40;
-    for (int i = 0; i < k; ++i) {
+    // lane i < k takes message i of the group
+    unsigned long long my_st = 0;
+#pragma unroll
+    for (int i = 0; i < MPSC_MAX_GROUP; ++i) {
       const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
-      const unsigned long long idx = (unsigned long long)p * a.mpp + s + i;
-      ring_copy(v.ring + (si & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
+      if (lane == (unsigned)i) my_st = si;
+    }
+    const unsigned long long idx = (unsigned long long)p * a.mpp + s + lane;
+    const bool mine = lane < (unsigned)k;
+    const unsigned long long my_n = mine ? a.sizes[idx] : 0;
+    if (!group_copy_bulk<PROD_NST, PROD_STG>(mine ? v.ring + (my_st & (v.R - 1)) : nullptr,
+                                             mine ? a.staging + a.src_off[idx] : nullptr, my_n, k, lane, stage, bars,
+                                             phase, PROD_WAIT_NS)) {
+      if (lane == 0) {
+        atomicExch(a.abort, 1u);
+        a.res[c].status = HICR_ERR_TIMEOUT;
+      }
+      return;
     }
     __threadfence();
     __syncwarp();
-    for (int i = 0; i < k; ++i) {
-      const unsigned long long si = __shfl_sync(FULLM, st[i], 0);
-      if (lane == (unsigned)i) {
-        const unsigned long long t = t0 + i;
-        MpscMeta* e = v.meta + (t & (v.M - 1));
-        e->start = si;
-        e->size = (unsigned int)a.sizes[(unsigned long long)p * a.mpp + s + i];
-        e->producer = p;
-        e->seq = s + i;
-        e->flags = 0;
-        st_rel(&e->ready, (t & MASK24) + 1);
-      }
+    if (mine) {
+      const unsigned long long t = t0 + lane;
+      MpscMeta* e = v.meta + (t & (v.M - 1));
+      e->start = my_st;
+      e->size = (unsigned int)my_n;
+      e->producer = p;
+      e->seq = s + lane;
+      e->flags = 0;
+      st_rel(&e->ready, (t & MASK24) + 1);
     }
     if (lane == 0) {
       atomicMax(&v.st->max_bytes.v, (end - freed) & MASK40);
@@ -799,28 +832,9 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       }
       const unsigned j = lo;
       const unsigned long long n = s_size[j];
-      const unsigned long long nv = (n + 15) / 16;
       const unsigned long long q0 = (pc - s_ppre[j]) * MPSC_PIECE;
       const uint4* src = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
-      uint4 x[MPSC_PIECE / 32];
-#pragma unroll
-      for (int u = 0; u < MPSC_PIECE / 32; ++u) {
-        const unsigned long long q = q0 + lane + 32 * u;
-        if (q < nv) x[u] = __ldcg(src + q);
-      }
-      unsigned long long d = 0;
-#pragma unroll
-      for (int u = 0; u < MPSC_PIECE / 32; ++u) {
-        const unsigned long long q = q0 + lane + 32 * u;
-        if (q < nv) {
-          unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
-          unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
-          const unsigned long long b0 = 16 * q;
-          if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
-          if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
-          d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
-        }
-      }
+      unsigned long long d = piece_digest<MPSC_PIECE / 32>(src, q0, n, lane);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
       if (lane == 0) atomicAdd(&s_dig[j], d);
     }
@@ -877,6 +891,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
 }
 
 static constexpr unsigned MPSC_THREADS = 512;
+static_assert(MPSC_THREADS / 32 <= PROD_WARPS, "every warp of a producer CTA needs its stages");
 
 __global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) {
   const unsigned long long deadline = gtime() + a.timeout_ns;
@@ -885,9 +900,15 @@ __global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) 
     mpsc_consumer(a, blockIdx.x / a.G, deadline);
     return;
   }
-  const unsigned lane = threadIdx.x & 31u;
-  const unsigned p = (blockIdx.x - ncta) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (p < a.n_prod) mpsc_producer(a, p, lane, deadline);
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const unsigned p = (blockIdx.x - ncta) * a.pw + warp;
+  if (warp < a.pw && p < a.n_prod) {
+    extern __shared__ __align__(128) uint8_t prod_smem[];
+    uint8_t* stage;
+    unsigned long long* bars;
+    prod_stages(prod_smem, warp, lane, &stage, &bars);
+    mpsc_producer(a, p, lane, deadline, stage, bars);
+  }
 }
 
 // Checks run before a stream: every message lies inside the staging slot and
@@ -927,9 +948,12 @@ struct NlStreamArgs {
   unsigned long long* log_count;  // per consumer
   hicr_mpsc_result_t* res;
   unsigned int* abort;
+  unsigned int pw;  // producer warps per producer CTA
 };
 
-__device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline) {
+__device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline,
+                            uint8_t* stage, unsigned long long* bars) {
+  unsigned phase = 0;
   const unsigned c = p % a.n_cons, i = p / a.n_cons;
   const NlView v = a.chans[c];
   NlState* st = v.st + i;
@@ -946,7 +970,7 @@ __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, un
     cons = ld_acq(&st->cons.v);
   }
   for (unsigned s = 0; s < a.mpp;) {
-    unsigned long long r[MPSC_MAX_GROUP], sa[MPSC_MAX_GROUP];
+    unsigned long long r[MPSC_MAX_GROUP], sa[MPSC_MAX_GROUP] = {};
     int k = 0;
     unsigned long long sum = 0;
     for (; k < (int)a.group && (unsigned)k < v.M && s + k < a.mpp; ++k) {
@@ -982,16 +1006,30 @@ __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, un
       return;
     }
     const unsigned long long pub0 = __shfl_sync(FULLM, pub, 0);
-    for (int j = 0; j < k; ++j) {
+    // lane j < k takes message j of the group
+    unsigned long long my_sa = 0;
+#pragma unroll
+    for (int j = 0; j < MPSC_MAX_GROUP; ++j) {
       const unsigned long long sj = __shfl_sync(FULLM, sa[j], 0);
-      const unsigned long long idx = (unsigned long long)p * a.mpp + s + j;
-      ring_copy(ring + (sj & (v.R - 1)), a.staging + a.src_off[idx], a.sizes[idx], lane);
-      if (lane == (unsigned)j) {
-        NlMeta* e = meta + ((pub0 + j) & (v.M - 1));
-        e->start = sj;
-        e->size = (unsigned int)a.sizes[idx];
-        e->seq = s + j;
+      if (lane == (unsigned)j) my_sa = sj;
+    }
+    const unsigned long long idx = (unsigned long long)p * a.mpp + s + lane;
+    const bool mine = lane < (unsigned)k;
+    const unsigned long long my_n = mine ? a.sizes[idx] : 0;
+    if (!group_copy_bulk<PROD_NST, PROD_STG>(mine ? ring + (my_sa & (v.R - 1)) : nullptr,
+                                             mine ? a.staging + a.src_off[idx] : nullptr, my_n, k, lane, stage, bars,
+                                             phase, PROD_WAIT_NS)) {
+      if (lane == 0) {
+        atomicExch(a.abort, 1u);
+        a.res[c].status = HICR_ERR_TIMEOUT;
       }
+      return;
+    }
+    if (mine) {
+      NlMeta* e = meta + ((pub0 + lane) & (v.M - 1));
+      e->start = my_sa;
+      e->size = (unsigned int)my_n;
+      e->seq = s + lane;
     }
     __threadfence();
     __syncwarp();
@@ -1010,6 +1048,7 @@ __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, un
   }
 }
 
+static constexpr int NL_PIECE = 384;  // 16-byte vectors per digest piece of a non-locking consumer warp
 __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw, unsigned nw, unsigned lane,
                                  unsigned long long deadline) {
   const NlView v = a.chans[c];
@@ -1067,26 +1106,7 @@ __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw,
         const uint4* src = reinterpret_cast<const uint4*>(rb + (sj & (v.R - 1)));
         const unsigned long long nv = (n + 15) / 16;
         unsigned long long d = 0;
-        for (unsigned long long q0 = 0; q0 < nv; q0 += MPSC_PIECE) {
-          uint4 x[MPSC_PIECE / 32];
-#pragma unroll
-          for (int u = 0; u < MPSC_PIECE / 32; ++u) {
-            const unsigned long long q = q0 + lane + 32 * u;
-            if (q < nv) x[u] = __ldcg(src + q);
-          }
-#pragma unroll
-          for (int u = 0; u < MPSC_PIECE / 32; ++u) {
-            const unsigned long long q = q0 + lane + 32 * u;
-            if (q < nv) {
-              unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
-              unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
-              const unsigned long long b0 = 16 * q;
-              if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
-              if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
-              d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
-            }
-          }
-        }
+        for (unsigned long long q0 = 0; q0 < nv; q0 += NL_PIECE) d += piece_digest<NL_PIECE / 32>(src, q0, n, lane);
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
         if (lane == j) {
           hicr_mpsc_log_t E;
@@ -1134,8 +1154,14 @@ __global__ void __launch_bounds__(MPSC_THREADS) k_nl_stream(NlStreamArgs a) {
     nl_consumer_warp(a, c, g * W + warp, a.G * W, lane, deadline);
     return;
   }
-  const unsigned p = (blockIdx.x - ncta) * W + warp;
-  if (p < a.n_prod) nl_producer(a, p, lane, deadline);
+  const unsigned p = (blockIdx.x - ncta) * a.pw + warp;
+  if (warp < a.pw && p < a.n_prod) {
+    extern __shared__ __align__(128) uint8_t prod_smem[];
+    uint8_t* stage;
+    unsigned long long* bars;
+    prod_stages(prod_smem, warp, lane, &stage, &bars);
+    nl_producer(a, p, lane, deadline, stage, bars);
+  }
 }
 
 // The pre-stream checks of k_mpsc_check against the per-producer rings.
@@ -1598,6 +1624,25 @@ hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   return HICR_OK;
 }
 
+// Grid of a streaming launch: the consumer CTAs first, then the producer
+// CTAs (one warp per producer), spread over every CTA slot the consumers leave
+// free, so that each SM's memory pipeline serves fewer producer warps. Sets
+// *pw to the producer warps per producer CTA; returns 0 when the producers do
+// not fit even at `warps` per CTA.
+static unsigned long long stream_grid(unsigned long long cons_ctas, unsigned long long n_prod, unsigned warps,
+                                      unsigned long long slots, unsigned* pw) {
+  const unsigned long long need = (n_prod + warps - 1) / warps;
+  if (cons_ctas + need > slots) return 0;
+  if (n_prod == 0) {
+    *pw = 1;
+    return cons_ctas;
+  }
+  unsigned long long pc = slots - cons_ctas;
+  if (pc > n_prod) pc = n_prod;
+  *pw = (unsigned)((n_prod + pc - 1) / pc);
+  return cons_ctas + (n_prod + *pw - 1) / *pw;
+}
+
 hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
                              uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
                              const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
@@ -1622,10 +1667,14 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   }
   if (log_stride < per * msgs_per_producer) return HICR_ERR_INVALID;
   const unsigned warps = MPSC_THREADS / 32;
-  const unsigned long long grid = (unsigned long long)n_consumers * consumer_ctas + (n_producers + warps - 1) / warps;
   int per_sm = 0;
-  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpsc_stream, MPSC_THREADS, 0));
-  if (grid > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaFuncSetAttribute((const void*)k_mpsc_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PROD_SMEM));
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mpsc_stream, MPSC_THREADS, PROD_SMEM));
+  unsigned pw = 0;
+  const unsigned long long grid = stream_grid(n_consumers * (unsigned long long)consumer_ctas, n_producers, warps,
+                                              (unsigned long long)per_sm * in->sm_count, &pw);
+  if (!grid) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
   const size_t vb = ((sizeof(MpscView) * n_consumers + 255) / 256) * 256;
@@ -1663,6 +1712,7 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   a.G = consumer_ctas;
   a.claim = claim;
   a.base = base;
+  a.pw = pw;
   int* bad = (int*)(p + vb + rb + 128);
   k_mpsc_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
   int hbad = 0;
@@ -1676,7 +1726,7 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   }
   void* args[] = {&a};
   HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3((unsigned)grid), dim3(MPSC_THREADS),
-                                            args, 0, s));
+                                            args, PROD_SMEM, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   for (uint32_t i = 0; i < n_consumers; ++i) {
@@ -1719,10 +1769,14 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
     views[i] = nl_view(c);
   }
   if (log_stride < per * msgs_per_producer) return HICR_ERR_INVALID;
-  const unsigned long long grid = (unsigned long long)n_consumers * consumer_ctas + (n_producers + warps - 1) / warps;
   int per_sm = 0;
-  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_stream, MPSC_THREADS, 0));
-  if (grid > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
+  HICR_CUDA(in, cudaFuncSetAttribute((const void*)k_nl_stream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PROD_SMEM));
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_nl_stream, MPSC_THREADS, PROD_SMEM));
+  unsigned pw = 0;
+  const unsigned long long grid = stream_grid(n_consumers * (unsigned long long)consumer_ctas, n_producers, warps,
+                                              (unsigned long long)per_sm * in->sm_count, &pw);
+  if (!grid) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
   const size_t vb = ((sizeof(NlView) * n_consumers + 255) / 256) * 256;
@@ -1750,6 +1804,7 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
   a.res = (hicr_mpsc_result_t*)(p + vb);
   a.log_count = (unsigned long long*)(p + vb + rb);
   a.abort = (unsigned int*)(p + vb + rb + cb);
+  a.pw = pw;
   int* bad = (int*)(p + vb + rb + cb + 128);
   k_nl_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
   int hbad = 0;
@@ -1760,7 +1815,7 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
     HICR_CUDA(in, cudaMemsetAsync(get(in, chans[i])->state, 0, sizeof(NlHead), s));
   void* args[] = {&a};
   HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_nl_stream, dim3((unsigned)grid), dim3(MPSC_THREADS), args,
-                                            0, s));
+                                            PROD_SMEM, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   for (uint32_t i = 0; i < n_consumers; ++i) {

@@ -15,49 +15,12 @@
 // gives up records HICR_ERR_TIMEOUT for the op in the sticky batch error.
 #include "copy.cuh"
 #include "hicr_internal.h"
+#include "tma.cuh"
 
 namespace hicr {
 
 static constexpr unsigned FULLM_COPY = 0xffffffffu;
 static constexpr unsigned long long TMA_WAIT_NS = 2000000000ull;  // bound of one mbarrier wait
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void tma_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(sdst)),
-               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void tma_store(void* gdst, const void* ssrc, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void tma_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void tma_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-__device__ __forceinline__ unsigned long long tma_now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Lane 0: copy n bytes (a multiple of 16; d and s 16-byte aligned) through the
 // warp's stages. `phase` holds one parity bit per stage. Returns false when a
@@ -104,7 +67,7 @@ __device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uin
   }
   tma_wait_all();
   // order the async-proxy writes before the generic-proxy completion signal
-  asm volatile("fence.proxy.async.global;" ::: "memory");
+  fence_proxy_async_global();
   return ok;
 }
 
@@ -117,7 +80,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
       reinterpret_cast<unsigned long long*>(tma_smem + (size_t)nwarp * NST * STG) + warp * NST;
   if (lane == 0) {
     for (unsigned k = 0; k < NST; ++k) mbar_init(bars + k);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncwarp();
   unsigned phase = 0;  // lane 0: parity of each stage's next completion

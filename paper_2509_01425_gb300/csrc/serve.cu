@@ -567,28 +567,10 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
         else hi = mid;
       }
       const unsigned j = lo;
-      const unsigned long long n = s_size[j], nv = (n + 15) / 16;
+      const unsigned long long n = s_size[j];
       const unsigned long long q0 = (pc - s_ppre[j]) * SRV_PIECE;
       const uint4* base = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
-      uint4 x[SRV_PIECE / 32];
-#pragma unroll
-      for (int uu = 0; uu < SRV_PIECE / 32; ++uu) {
-        const unsigned long long q = q0 + lane + 32 * uu;
-        if (q < nv) x[uu] = __ldcg(base + q);
-      }
-      unsigned long long d = 0;
-#pragma unroll
-      for (int uu = 0; uu < SRV_PIECE / 32; ++uu) {
-        const unsigned long long q = q0 + lane + 32 * uu;
-        if (q < nv) {
-          unsigned long long w0 = (unsigned long long)x[uu].x | ((unsigned long long)x[uu].y << 32);
-          unsigned long long w1 = (unsigned long long)x[uu].z | ((unsigned long long)x[uu].w << 32);
-          const unsigned long long b0 = 16 * q;
-          if (b0 + 8 > n) w0 &= (n > b0) ? (~0ull >> (64 - 8 * (n - b0))) : 0ull;
-          if (b0 + 16 > n) w1 &= (n > b0 + 8) ? (~0ull >> (64 - 8 * (n - b0 - 8))) : 0ull;
-          d += w0 * (4ull * q + 1ull) + w1 * (4ull * q + 3ull);
-        }
-      }
+      unsigned long long d = piece_digest<SRV_PIECE / 32>(base, q0, n, lane);
       for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
       if (lane == 0) atomicAdd(&s_dig[j], d);
     }
