@@ -257,6 +257,158 @@ __device__ bool group_copy_bulk(uint8_t* d, const uint8_t* s, unsigned long long
   return ok;
 }
 
+// One message as warp_digest_bulk sees it: its ring address, its body (size
+// rounded up to 16 bytes: what a bulk load may read) and its size.
+struct DigestMsg {
+  const uint8_t* addr;
+  unsigned long long body;
+  unsigned long long n;
+};
+
+// Word digest, by bulk loads, of a contiguous share of a list of messages: the
+// `bytes` bytes (a multiple of 16) of the messages' concatenated bodies that
+// start at byte o0 of message j0's body. msg(j) describes message j (ring
+// addresses 16-byte aligned); sink(j, d) receives, in every lane, a part of
+// message j's digest (sum_i w_i (2i + 1) over the part's 8-byte words, i
+// counted from the message's start, bytes past n as zero); a message's parts
+// add up to its digest. The share streams through the warp's NST stages of
+// STG bytes (one mbarrier each): a stage fill carries up to STG bytes, one bulk
+// load per message part, so that several small messages travel in one fill,
+// and NST fills are in flight while the warp digests the oldest one from
+// shared memory. Lane 0 issues the loads; control flow is warp-uniform and
+// `phase` (one parity bit per stage) is the same in all lanes. Returns false
+// if a wait gave up after wait_ns (fills in flight are drained first, each
+// wait again bounded).
+template <unsigned NST, unsigned STG, class Msg, class Sink>
+__device__ bool warp_digest_bulk(int j0, unsigned long long o0, unsigned long long bytes, Msg msg, Sink sink,
+                                 unsigned lane, uint8_t* stage, unsigned long long* bars, unsigned& phase,
+                                 unsigned long long wait_ns) {
+  const unsigned FM = 0xffffffffu;
+  int ci = j0;  // load cursor: byte co of message ci's body; `left` bytes to go
+  unsigned long long co = o0, left = bytes;
+  auto fill = [&](unsigned st) -> unsigned {
+    const unsigned used = (unsigned)min(left, (unsigned long long)STG);
+    if (used) {
+      if (lane == 0) {
+        // earlier ordinary reads of this stage come before the bulk writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bars + st, used);
+      }
+      unsigned off = 0;
+      while (off < used) {
+        const DigestMsg m = msg(ci);
+        if (co >= m.body) {
+          ++ci;
+          co = 0;
+          continue;
+        }
+        const unsigned long long len = min(m.body - co, (unsigned long long)(used - off));
+        if (lane == 0) tma_load(stage + st * STG + off, m.addr + co, (unsigned)len, bars + st);
+        off += (unsigned)len;
+        co += len;
+      }
+      left -= used;
+    }
+    return used;
+  };
+  // every lane waits (bounded) for stage st's fill: a landed fill's bytes are
+  // visible to the threads that observe its mbarrier phase complete
+  auto landed = [&](unsigned st) -> bool {
+    const unsigned par = (phase >> st) & 1u;
+    int okw = 1;
+    if (!mbar_try_wait(bars + st, par)) {
+      const unsigned long long t0 = tma_now_ns();
+      while (!mbar_try_wait(bars + st, par)) {
+        if (tma_now_ns() - t0 > wait_ns) {
+          okw = 0;
+          break;
+        }
+      }
+    }
+    okw = __all_sync(FM, okw);
+    if (okw) phase ^= 1u << st;
+    return okw != 0;
+  };
+  int fi[NST];
+  unsigned long long fo[NST];
+  unsigned fu[NST];
+#pragma unroll
+  for (unsigned st = 0; st < NST; ++st) {
+    fi[st] = ci;
+    fo[st] = co;
+    fu[st] = fill(st);
+  }
+  // the message being digested and this lane's running share of it
+  int jc = -1;
+  unsigned long long dc = 0;
+  bool ok = true;
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (unsigned st = 0; st < NST; ++st) {
+      if (!ok || fu[st] == 0) continue;
+      any = true;
+      if (!landed(st)) {
+        ok = false;
+        fu[st] = 0;
+        continue;
+      }
+      int i = fi[st];
+      unsigned long long o = fo[st];
+      unsigned off = 0;
+      while (off < fu[st]) {
+        const DigestMsg m = msg(i);
+        if (o >= m.body) {
+          ++i;
+          o = 0;
+          continue;
+        }
+        if (i != jc) {
+          if (jc >= 0) {
+            for (int x = 16; x > 0; x >>= 1) dc += __shfl_xor_sync(FM, dc, x);
+            sink(jc, dc);
+          }
+          jc = i;
+          dc = 0;
+        }
+        const unsigned len = (unsigned)min(m.body - o, (unsigned long long)(fu[st] - off));
+        const unsigned long long q0 = o / 16, nvm = (m.n + 15) / 16;
+        const unsigned tail = (unsigned)(m.n - 16 * (nvm - 1));
+        const uint4* sv = reinterpret_cast<const uint4*>(stage + st * STG + off);
+        for (unsigned v = lane; v < len / 16; v += 32) {
+          const uint4 x = sv[v];
+          unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
+          unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
+          const unsigned long long q = q0 + v;
+          if (q + 1 == nvm) {
+            if (tail < 8) w0 &= ~0ull >> (64 - 8 * tail);
+            if (tail <= 8) w1 = 0;
+            else if (tail < 16) w1 &= ~0ull >> (128 - 8 * tail);
+          }
+          dc += (w0 + w1) * (4ull * q + 1ull) + (w1 << 1);
+        }
+        off += len;
+        o += len;
+      }
+      __syncwarp();  // every lane has read the stage before it is refilled
+      fi[st] = ci;
+      fo[st] = co;
+      fu[st] = fill(st);
+    }
+    if (!any || !ok) break;
+  }
+  if (!ok) {
+#pragma unroll
+    for (unsigned st = 0; st < NST; ++st)
+      if (fu[st]) landed(st);
+  }
+  if (jc >= 0 && ok) {
+    for (int x = 16; x > 0; x >>= 1) dc += __shfl_xor_sync(FM, dc, x);
+    sink(jc, dc);
+  }
+  return ok;
+}
+
 // Word digest of one piece of a message (the 16-byte vectors
 // [q0, q0 + 32 * NU) of a message of n bytes, src = its first vector), this
 // lane's share: lane l holds vectors q = q0 + l + 32u, u < NU, and returns

@@ -698,8 +698,8 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
 // consumer's claim counter, and
 //   A. warps acquire the tickets' `ready` words and stage their metadata in
 //      shared memory;
-//   B. the whole CTA digests the window's payloads in 8 KiB pieces of single
-//      messages, one piece per warp at a time;
+//   B. each warp digests an equal share of the window's concatenated
+//      payloads, streamed through its shared-memory stages by bulk loads;
 //   C. warps write the log entries (index = ticket - first ticket), then one
 //      thread waits until msg_tail reaches the window's first ticket (the
 //      previous window is freed), frees every byte up to the window's last
@@ -707,9 +707,10 @@ __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane
 // Windows of one consumer are digested side by side; frees stay in ticket
 // order.
 static constexpr int MPSC_WIN = 64;
-static constexpr int MPSC_PIECE = 512;  // 16-byte vectors per digest piece (8 KiB)
 
-__device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline) {
+__device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long long deadline, uint8_t* stage,
+                              unsigned long long* bars) {
+  unsigned phase = 0;  // parity bits of this warp's stages
   // s_stop / s_done are written only by thread 0 before the first barrier of
   // a round; phase-A waits that give up write s_abort_a, read after the
   // second barrier and cleared by thread 0 at the start of the next round
@@ -717,7 +718,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
   // later check and leave while others wait at a barrier.
   __shared__ int s_stop, s_abort_a, s_done;
   __shared__ unsigned long long s_avail, s_t;
-  __shared__ unsigned long long s_start[MPSC_WIN], s_ppre[MPSC_WIN + 1], s_dig[MPSC_WIN];
+  __shared__ unsigned long long s_start[MPSC_WIN], s_bpre[MPSC_WIN + 1], s_dig[MPSC_WIN];
   __shared__ unsigned int s_size[MPSC_WIN], s_prod[MPSC_WIN], s_seq[MPSC_WIN];
   const MpscView v = a.chans[c];
   const unsigned tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, nwarp = blockDim.x >> 5;
@@ -800,10 +801,10 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
       tm = x;
     }
     if (warp == 0) {
-      // exclusive prefix of piece counts (navail <= 64: two values per lane)
-      const unsigned long long p0 = lane < navail ? (((unsigned long long)s_size[lane] + 15) / 16 + MPSC_PIECE - 1) / MPSC_PIECE : 0;
-      const unsigned long long p1 =
-          lane + 32 < navail ? (((unsigned long long)s_size[lane + 32] + 15) / 16 + MPSC_PIECE - 1) / MPSC_PIECE : 0;
+      // exclusive prefix of the messages' bodies (sizes rounded up to 16
+      // bytes; navail <= 64: two values per lane)
+      const unsigned long long p0 = lane < navail ? round16(s_size[lane]) : 0;
+      const unsigned long long p1 = lane + 32 < navail ? round16(s_size[lane + 32]) : 0;
       unsigned long long x0 = p0, x1 = p1;
       for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y0 = __shfl_up_sync(FULLM, x0, o), y1 = __shfl_up_sync(FULLM, x1, o);
@@ -813,32 +814,43 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
         }
       }
       const unsigned long long tot0 = __shfl_sync(FULLM, x0, 31);
-      s_ppre[lane] = x0 - p0;
-      s_ppre[lane + 32] = tot0 + x1 - p1;
-      if (lane == 31) s_ppre[64] = tot0 + x1;
+      s_bpre[lane] = x0 - p0;
+      s_bpre[lane + 32] = tot0 + x1 - p1;
+      if (lane == 31) s_bpre[64] = tot0 + x1;
     }
     __syncthreads();
-    // B. digest: each message is cut into pieces of MPSC_PIECE 16-byte vectors
-    // (one vector per lane, MPSC_PIECE / 32 loads in flight per lane); warps
-    // take pieces round-robin and add each piece's warp-reduced digest to the
-    // message's shared accumulator.
-    const unsigned long long npieces = s_ppre[navail];
-    for (unsigned long long pc = warp; pc < npieces; pc += nwarp) {
-      unsigned lo = 0, hi = navail;  // largest j < navail with s_ppre[j] <= pc
-      while (hi - lo > 1) {
-        const unsigned mid = (lo + hi) >> 1;
-        if (s_ppre[mid] <= pc) lo = mid;
-        else hi = mid;
+    // B. digest: warp w takes the w-th of nwarp equal (16-byte aligned) shares
+    // of the window's concatenated bodies and streams it through its stages
+    // by bulk loads, adding each message part's digest to the message's
+    // shared accumulator.
+    {
+      const unsigned long long T = s_bpre[navail];
+      const unsigned long long lo = (T * warp / nwarp) & ~15ull;
+      const unsigned long long hi = warp + 1 == nwarp ? T : (T * (warp + 1) / nwarp) & ~15ull;
+      if (hi > lo) {
+        unsigned jl = 0, jh = navail;  // largest j < navail with s_bpre[j] <= lo
+        while (jh - jl > 1) {
+          const unsigned mid = (jl + jh) >> 1;
+          if (s_bpre[mid] <= lo) jl = mid;
+          else jh = mid;
+        }
+        auto msg = [&](int j) {
+          return DigestMsg{v.ring + (s_start[j] & (v.R - 1)), s_bpre[j + 1] - s_bpre[j], s_size[j]};
+        };
+        auto sink = [&](int j, unsigned long long d) {
+          if (lane == 0) atomicAdd(&s_dig[j], d);
+        };
+        if (!warp_digest_bulk<PROD_NST, PROD_STG>((int)jl, lo - s_bpre[jl], hi - lo, msg, sink, lane, stage, bars,
+                                                  phase, PROD_WAIT_NS)) {
+          if (lane == 0) {
+            s_abort_a = 1;
+            atomicExch(a.abort, 1u);
+          }
+        }
       }
-      const unsigned j = lo;
-      const unsigned long long n = s_size[j];
-      const unsigned long long q0 = (pc - s_ppre[j]) * MPSC_PIECE;
-      const uint4* src = reinterpret_cast<const uint4*>(v.ring + (s_start[j] & (v.R - 1)));
-      unsigned long long d = piece_digest<MPSC_PIECE / 32>(src, q0, n, lane);
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
-      if (lane == 0) atomicAdd(&s_dig[j], d);
     }
     __syncthreads();
+    if (s_abort_a) break;
     if (tid == 0) {
       const unsigned long long x = gtime();
       ns_b += x - tm;
@@ -869,6 +881,7 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
         __nanosleep(32);
       }
       if (!stop_c) {
+        fence_proxy_async_global();  // the window's bulk reads before the free
         st_rel(&v.st->freed.v, (s_start[navail - 1] + round16(s_size[navail - 1])) & MASK40);
         st_rel(&v.st->msg_tail.v, t + navail);
       }
@@ -896,16 +909,17 @@ static_assert(MPSC_THREADS / 32 <= PROD_WARPS, "every warp of a producer CTA nee
 __global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) {
   const unsigned long long deadline = gtime() + a.timeout_ns;
   const unsigned ncta = a.n_cons * a.G;
+  extern __shared__ __align__(128) uint8_t prod_smem[];
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint8_t* stage;
+  unsigned long long* bars;
   if (blockIdx.x < ncta) {
-    mpsc_consumer(a, blockIdx.x / a.G, deadline);
+    prod_stages(prod_smem, warp, lane, &stage, &bars);
+    mpsc_consumer(a, blockIdx.x / a.G, deadline, stage, bars);
     return;
   }
-  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   const unsigned p = (blockIdx.x - ncta) * a.pw + warp;
   if (warp < a.pw && p < a.n_prod) {
-    extern __shared__ __align__(128) uint8_t prod_smem[];
-    uint8_t* stage;
-    unsigned long long* bars;
     prod_stages(prod_smem, warp, lane, &stage, &bars);
     mpsc_producer(a, p, lane, deadline, stage, bars);
   }
@@ -1048,9 +1062,9 @@ __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, un
   }
 }
 
-static constexpr int NL_PIECE = 384;  // 16-byte vectors per digest piece of a non-locking consumer warp
 __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw, unsigned nw, unsigned lane,
-                                 unsigned long long deadline) {
+                                 unsigned long long deadline, uint8_t* stage, unsigned long long* bars) {
+  unsigned phase = 0;  // parity bits of this warp's stages
   const NlView v = a.chans[c];
   const unsigned nring = a.n_prod > c ? (a.n_prod - c + a.n_cons - 1) / a.n_cons : 0;
   const unsigned owned = nring > gw ? (nring - gw + nw - 1) / nw : 0;  // <= 32 (host check)
@@ -1100,31 +1114,40 @@ __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw,
       if (lane == 0) base = atomicAdd(a.log_count + c, (unsigned long long)k);
       base = __shfl_sync(FULLM, base, 0);
       const uint8_t* rb = v.ring + (unsigned long long)ring * v.R;
-      for (unsigned j = 0; j < k; ++j) {
+      // the batch's bodies, digested by bulk loads; lane j collects message j's
+      unsigned long long total = lane < k ? round16(e_size) : 0;
+      for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(FULLM, total, o);
+      auto msg = [&](int j) {
         const unsigned long long sj = __shfl_sync(FULLM, e_start, j);
         const unsigned long long n = __shfl_sync(FULLM, e_size, j);
-        const uint4* src = reinterpret_cast<const uint4*>(rb + (sj & (v.R - 1)));
-        const unsigned long long nv = (n + 15) / 16;
-        unsigned long long d = 0;
-        for (unsigned long long q0 = 0; q0 < nv; q0 += NL_PIECE) d += piece_digest<NL_PIECE / 32>(src, q0, n, lane);
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(FULLM, d, o);
-        if (lane == j) {
-          hicr_mpsc_log_t E;
-          E.producer = ring * a.n_cons + c;
-          E.seq = e_seq;
-          E.size = e_size;
-          E.reserved = 0;
-          E.offset = e_start & (v.R - 1);
-          E.digest = d;
-          log[base + j] = E;
-          bytes += e_size;
-        }
+        return DigestMsg{rb + (sj & (v.R - 1)), round16(n), n};
+      };
+      unsigned long long my_d = 0;
+      auto sink = [&](int j, unsigned long long d) {
+        if (lane == (unsigned)j) my_d += d;
+      };
+      if (!warp_digest_bulk<PROD_NST, PROD_STG>(0, 0, total, msg, sink, lane, stage, bars, phase, PROD_WAIT_NS)) {
+        if (lane == 0) atomicExch(a.abort, 1u);
+        stop = 1;
+        break;
+      }
+      if (lane < k) {
+        hicr_mpsc_log_t E;
+        E.producer = ring * a.n_cons + c;
+        E.seq = e_seq;
+        E.size = e_size;
+        E.reserved = 0;
+        E.offset = e_start & (v.R - 1);
+        E.digest = my_d;
+        log[base + lane] = E;
+        bytes += e_size;
       }
       // free every byte up to the batch's last message
       const unsigned long long s_last = __shfl_sync(FULLM, e_start, k - 1);
       const unsigned long long n_last = __shfl_sync(FULLM, e_size, k - 1);
       __syncwarp();
       if (lane == L) {
+        fence_proxy_async_global();  // the batch's bulk reads before the free
         st_rel(&st_l->freed.v, s_last + round16(n_last));
         cons += k;
         st_rel(&st_l->cons.v, cons);
@@ -1133,6 +1156,7 @@ __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw,
       consumed += k;
       ++batches;
     }
+    if (stop) break;  // a bulk-load wait gave up
   }
   for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(FULLM, bytes, o);
   if (lane == 0) {
@@ -1149,16 +1173,17 @@ __global__ void __launch_bounds__(MPSC_THREADS) k_nl_stream(NlStreamArgs a) {
   const unsigned long long deadline = gtime() + a.timeout_ns;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const unsigned ncta = a.n_cons * a.G;
+  extern __shared__ __align__(128) uint8_t prod_smem[];
+  uint8_t* stage;
+  unsigned long long* bars;
   if (blockIdx.x < ncta) {
     const unsigned c = blockIdx.x / a.G, g = blockIdx.x % a.G;
-    nl_consumer_warp(a, c, g * W + warp, a.G * W, lane, deadline);
+    prod_stages(prod_smem, warp, lane, &stage, &bars);
+    nl_consumer_warp(a, c, g * W + warp, a.G * W, lane, deadline, stage, bars);
     return;
   }
   const unsigned p = (blockIdx.x - ncta) * a.pw + warp;
   if (warp < a.pw && p < a.n_prod) {
-    extern __shared__ __align__(128) uint8_t prod_smem[];
-    uint8_t* stage;
-    unsigned long long* bars;
     prod_stages(prod_smem, warp, lane, &stage, &bars);
     nl_producer(a, p, lane, deadline, stage, bars);
   }
