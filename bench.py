@@ -478,15 +478,15 @@ def _time_mpsc(h, run, reps):
 def bench_mpsc(h, inst, reps=3, groups=(4, 8)):
     """1,024 producers -> 16 consumers, log-uniform 8 B - 256 KiB: locking
     mode over one 1 GiB ring per consumer against non-locking mode over 64
-    rings of 16 MiB per consumer (the same memory), both with 1, 2, 4 or 5
-    CTAs per consumer (5 fills the 152 SMs with the 64 producer CTAs) and
+    rings of 16 MiB per consumer (the same memory), both with 1 to 5 CTAs per
+    consumer (the producer warps spread over the SMs left free) and
     reservation groups of 4 or 8 messages; the fastest shape is reported."""
     w = configs.mpsc(0)
     run = MpscRun(h, inst, w)
 
     def sweep(nonlocking):
         res = {}
-        for g in (1, 2, 4, 5):
+        for g in (1, 2, 3, 4, 5):
             for grp in groups:
                 run.group = grp
                 run.set_mode(nonlocking, g)
