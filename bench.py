@@ -233,17 +233,22 @@ def time_graph(h, inst, stream, g, steps, warmup, prof=False, dist=None):
 # ---------------------------------------------------------------------------
 class MpscRun:
     """Device set-up of an MPSC streaming run: staging slot with every
-    message's seeded payload (16-byte aligned, packed), device size / offset
-    tables, one channel per consumer and a device log."""
+    message's seeded payload (16-byte aligned and packed, or `stage_gap`
+    bytes apart), device size / offset tables, one channel per consumer and a
+    device log."""
 
-    def __init__(self, h, inst, w, group=4, nonlocking=False, consumer_ctas=1, ring_bytes=None, max_msgs=None):
+    def __init__(self, h, inst, w, group=4, nonlocking=False, consumer_ctas=1, ring_bytes=None, max_msgs=None,
+                 stage_gap=None):
         import torch
         self.h, self.inst, self.w, self.group = h, inst, w, group
         self.nonlocking, self.consumer_ctas = nonlocking, consumer_ctas
         P, M = w.sizes.shape
         C = w.n_consumers
         sizes = w.sizes.reshape(-1).astype(np.uint64)
-        padded = ((sizes + np.uint64(15)) // np.uint64(16)) * np.uint64(16)
+        if stage_gap is None:  # packed, each payload 16-byte aligned
+            padded = ((sizes + np.uint64(15)) // np.uint64(16)) * np.uint64(16)
+        else:  # `stage_gap` bytes between payloads: arbitrary alignments
+            padded = sizes + np.uint64(stage_gap)
         offs = np.zeros(len(sizes), dtype=np.uint64)
         offs[1:] = np.cumsum(padded)[:-1]
         self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, max(int(padded.sum()), 16)), "staging")

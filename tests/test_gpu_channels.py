@@ -209,6 +209,29 @@ def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, 
     run.free()
 
 
+@pytest.mark.parametrize("nonlocking", [False, True])
+@pytest.mark.parametrize("gap", [None, 3])
+def test_mpsc_stream_odd_staging_and_empty_messages(h, inst, nonlocking, gap):
+    """Every fifth message is empty (zero-byte bodies inside the producers'
+    group copies and the consumers' digest walks); with gap = 3 the staged
+    payloads sit at arbitrary alignments, so the producers' bulk copies fall
+    back to the warp copy for most messages of a group but not all."""
+    ring, max_msgs = 1 << 16, (8 if nonlocking else 64)
+    w = configs.mpsc(13, n_producers=40, n_consumers=4, msgs_per_producer=50, ring_bytes=ring, max_msgs=max_msgs,
+                     hi=8 << 10)
+    w.sizes[:, ::5] = 0
+    run = bench.MpscRun(h, inst, w, group=8, nonlocking=nonlocking, consumer_ctas=2, ring_bytes=ring,
+                        max_msgs=max_msgs, stage_gap=gap)
+    st, res = run.run()
+    assert st == 0
+    if nonlocking:
+        _check_mpsc_nl(w, run, res)
+    else:
+        _check_mpsc(w, run.logs(), res, ring)
+    assert sum(int(r.consumed) for r in res) == w.sizes.size
+    run.free()
+
+
 @pytest.mark.parametrize("nbytes,ctas", [(1, 1), (17, 1), (4096, 2), ((1 << 20) + 3, 8), (64 << 20, 32),
                                          ((64 << 20) + 5, 152)])
 def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
