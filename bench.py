@@ -55,7 +55,7 @@ def parse_args(argv=None):
                    help="prefix of the serving trace replayed through the per-op plain form")
     p.add_argument("--scale", type=float, default=1.0,
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
-    p.add_argument("--profile-case", choices=["mpsc_small", "copy_small", "side_small"], default=None,
+    p.add_argument("--profile-case", choices=["mpsc_small", "copy_small", "side_small", "control_small"], default=None,
                    help="run one small side case for a profiler capture, print its timings and exit")
     p.add_argument("--batch-config", default=None,
                    help="JSON object of batch configuration fields: fixes the copy kernel's configuration "
@@ -1002,7 +1002,72 @@ def run_profile_case(args):
         return run_copy_small(args)
     if args.profile_case == "side_small":
         return run_side_small(args)
+    if args.profile_case == "control_small":
+        return run_control_small(args)
     return run_mpsc_small(args)
+
+
+def run_control_small(args):
+    """control_small, for a one-pass capture (duration and DRAM bytes) of the
+    control-path kernels: slot registration (k_set_slot); host-side channel
+    calls, 16 rounds each of push, peek and pop on an SPSC channel (64 B
+    tokens), a locking MPSC and a non-locking MPSC channel (messages of
+    100 B-64 KiB) (k_*_push_host, k_*_ctl); the seeded staging fill and the
+    pre-checks of both MPSC streams on a 64 -> 4 producer x 16 message table
+    (k_fill_segments, k_mpsc_check, k_nl_check, and the two stream kernels);
+    two allocation-free batches of 10,000 ops (k_plan, k_scan, k_copy); and a
+    1 ms bounded device wait (k_wait_test)."""
+    import torch
+    from paper_2509_01425_gb300 import build
+    build.build()
+    from paper_2509_01425_gb300 import hicr as h
+    torch.cuda.set_device(0)
+    inst = h.check(h.hicr_init(0), "hicr_init")
+    size = 64 * MiB
+    a = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size), "alloc")
+    h.check(h.hicr_util_fill(inst, a, 0, size, splitmix.fill_key_base(args.seed, 1)), "fill")
+    t = torch.zeros(1 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(4):
+        r = h.check(h.hicr_slot_register(inst, h.HICR_SPACE_HBM, t.data_ptr(), t.numel()), "register")
+        h.check(h.hicr_slot_deregister(inst, r), "deregister")
+    spsc = h.check(h.hicr_spsc_create(inst, 64, 4096), "spsc_create")
+    lock = h.check(h.hicr_mpsc_create(inst, 4, 1 << 20, 64), "mpsc_create")
+    nl = h.check(h.hicr_mpsc_nl_create(inst, 4, 1 << 20, 64), "nl_create")
+    for i in range(16):
+        h.check(h.hicr_channel_push(inst, spsc, 0, a, 4096 * i, 16), "spsc push")
+        h.check(h.hicr_channel_peek(inst, spsc, 0)[0], "spsc peek")
+        h.check(h.hicr_channel_pop(inst, spsc, 16), "spsc pop")
+        n = (100, 4096, 65536)[i % 3]
+        for ch in (lock, nl):
+            h.check(h.hicr_channel_push(inst, ch, i % 4, a, 65536 * i, n), "mpsc push")
+            h.check(h.hicr_channel_peek(inst, ch, 0)[0], "mpsc peek")
+            h.check(h.hicr_channel_pop(inst, ch, 1), "mpsc pop")
+    for ch in (spsc, lock, nl):
+        h.check(h.hicr_channel_destroy(inst, ch), "destroy")
+    w = configs.mpsc(args.seed, n_producers=64, n_consumers=4, msgs_per_producer=16, ring_bytes=1 << 20,
+                     max_msgs=256, hi=16 << 10)
+    run = MpscRun(h, inst, w, group=4, consumer_ctas=2)
+    h.check(run.run()[0], "mpsc stream")
+    run.set_mode(True, 2, 1 << 16, 16)
+    h.check(run.run()[0], "nl stream")
+    run.free()
+    n_ops = 10_000
+    rng = np.random.default_rng(args.seed)
+    n = rng.integers(16, 2048, n_ops).astype(np.uint64)
+    dst = np.arange(n_ops, dtype=np.uint64) * np.uint64(2048)
+    src = np.uint64(32 * MiB) + dst
+    b = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size), "alloc")
+    ops = configs.make_ops([b] * n_ops, [a] * n_ops, dst, src, n)
+    d_ops = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    h.check(h.hicr_batch_reserve(inst, n_ops), "reserve")
+    for _ in range(2):
+        h.check(h.hicr_memcpy_batch_noalloc(inst, d_ops.data_ptr(), n_ops), "noalloc")
+        h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
+    st, wst, waited = h.hicr_util_wait_test(inst, 1_000_000)
+    h.check(st, "wait_test")
+    h.check(h.hicr_finalize(inst), "finalize")
+    print(json.dumps({"case": "control_small", "wait_status": wst, "waited_ns": waited}), flush=True)
+    return 0
 
 
 def run_side_small(args):
