@@ -560,6 +560,7 @@ struct MpscStreamArgs {
   unsigned long long* claim;       // per consumer (stride 16 words): next unclaimed ticket
   const unsigned long long* base;  // per consumer: first ticket of the run
   unsigned int pw;                 // producer warps per producer CTA
+  const int* bad;                  // verdict of the pre-stream check (nonzero: the run does not start)
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
@@ -907,6 +908,7 @@ static constexpr unsigned MPSC_THREADS = 512;
 static_assert(MPSC_THREADS / 32 <= PROD_WARPS, "every warp of a producer CTA needs its stages");
 
 __global__ void __launch_bounds__(MPSC_THREADS) k_mpsc_stream(MpscStreamArgs a) {
+  if (*(volatile const int*)a.bad) return;  // the check kernel, earlier in the stream, rejected the run
   const unsigned long long deadline = gtime() + a.timeout_ns;
   const unsigned ncta = a.n_cons * a.G;
   extern __shared__ __align__(128) uint8_t prod_smem[];
@@ -938,6 +940,28 @@ __global__ void k_mpsc_check(MpscStreamArgs a, unsigned long long staging_size, 
   }
 }
 
+// Set-up and wrap-up of a locking stream, one thread per channel: before the
+// run, clear the high-water marks and start the consumer's claim counter and
+// first ticket at msg_tail (the channels are idle: stream order); after it,
+// copy the marks into the results.
+__global__ void k_mpsc_stream_prep(const MpscView* v, unsigned n, unsigned long long* claim,
+                                   unsigned long long* base) {
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    MpscState* st = v[i].st;
+    st->max_bytes.v = 0;
+    st->max_msgs.v = 0;
+    const unsigned long long mt = st->msg_tail.v;
+    claim[16ull * i] = mt;
+    base[i] = mt;
+  }
+}
+__global__ void k_mpsc_stream_marks(const MpscView* v, unsigned n, hicr_mpsc_result_t* res) {
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    res[i].max_inflight_bytes = v[i].st->max_bytes.v;
+    res[i].max_inflight_msgs = v[i].st->max_msgs.v;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Non-locking MPSC streaming: CTAs [0, n_cons * G) consume (G per channel),
 // the rest hold one producer per warp; producer p uses ring p / n_cons of
@@ -963,6 +987,7 @@ struct NlStreamArgs {
   hicr_mpsc_result_t* res;
   unsigned int* abort;
   unsigned int pw;  // producer warps per producer CTA
+  const int* bad;   // verdict of the pre-stream check (nonzero: the run does not start)
 };
 
 __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline,
@@ -1170,6 +1195,7 @@ __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw,
 }
 
 __global__ void __launch_bounds__(MPSC_THREADS) k_nl_stream(NlStreamArgs a) {
+  if (*(volatile const int*)a.bad) return;  // the check kernel, earlier in the stream, rejected the run
   const unsigned long long deadline = gtime() + a.timeout_ns;
   const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
   const unsigned ncta = a.n_cons * a.G;
@@ -1198,6 +1224,21 @@ __global__ void k_nl_check(NlStreamArgs a, unsigned long long staging_size, int*
     const unsigned c = (unsigned)((i / a.mpp) % a.n_cons);
     if (off > staging_size || n > staging_size - off) atomicCAS(bad, 0, HICR_ERR_BOUNDS);
     else if (round16(n) > a.chans[c].R / 2 || n > 0xffffffffull) atomicCAS(bad, 0, HICR_ERR_TOO_LARGE);
+  }
+}
+
+// The same set-up and wrap-up for a non-locking stream: the channel-wide
+// high-water marks live in the channel's head.
+__global__ void k_nl_stream_prep(const NlView* v, unsigned n) {
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    v[i].head->max_bytes.v = 0;
+    v[i].head->max_msgs.v = 0;
+  }
+}
+__global__ void k_nl_stream_marks(const NlView* v, unsigned n, hicr_mpsc_result_t* res) {
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    res[i].max_inflight_bytes = v[i].head->max_bytes.v;
+    res[i].max_inflight_msgs = v[i].head->max_msgs.v;
   }
 }
 
@@ -1715,11 +1756,7 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   unsigned long long* claim = (unsigned long long*)(p + vb + rb + 256);
   unsigned long long* base = (unsigned long long*)(p + vb + rb + 256 + cb);
   // the run starts at each channel's msg_tail (the channels are empty)
-  for (uint32_t i = 0; i < n_consumers; ++i) {
-    const unsigned long long* mt = &((MpscState*)get(in, chans[i])->state)->msg_tail.v;
-    HICR_CUDA(in, cudaMemcpyAsync(claim + 16 * i, mt, 8, cudaMemcpyDeviceToDevice, s));
-    HICR_CUDA(in, cudaMemcpyAsync(base + i, mt, 8, cudaMemcpyDeviceToDevice, s));
-  }
+  k_mpsc_stream_prep<<<1, 256, 0, s>>>((const MpscView*)p, n_consumers, claim, base);
   MpscStreamArgs a;
   a.chans = (const MpscView*)p;
   a.n_cons = n_consumers;
@@ -1739,29 +1776,22 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   a.base = base;
   a.pw = pw;
   int* bad = (int*)(p + vb + rb + 128);
+  a.bad = bad;
+  // the check's verdict stays on the device: a rejected run's CTAs leave at
+  // once, and the host reads the verdict with the results
   k_mpsc_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
-  int hbad = 0;
-  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HICR_CUDA(in, cudaStreamSynchronize(s));
-  if (hbad) return hbad;
-  // reset the channels' high-water marks so the results describe this run
-  for (uint32_t i = 0; i < n_consumers; ++i) {
-    MpscState* ms = (MpscState*)get(in, chans[i])->state;
-    HICR_CUDA(in, cudaMemsetAsync(&ms->max_bytes, 0, sizeof(Line) * 2, s));
-  }
   void* args[] = {&a};
   HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_mpsc_stream, dim3((unsigned)grid), dim3(MPSC_THREADS),
                                             args, PROD_SMEM, s));
-  HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
+  k_mpsc_stream_marks<<<1, 256, 0, s>>>((const MpscView*)p, n_consumers, a.res);
+  std::vector<hicr_mpsc_result_t> hres(n_consumers);
+  int hbad = 0;
+  HICR_CUDA(in, cudaMemcpyAsync(hres.data(), a.res, sizeof(hicr_mpsc_result_t) * n_consumers,
+                                cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
-  for (uint32_t i = 0; i < n_consumers; ++i) {
-    MpscState* ms = (MpscState*)get(in, chans[i])->state;
-    unsigned long long mx[2];
-    HICR_CUDA(in, cudaMemcpy(&mx[0], &ms->max_bytes.v, 8, cudaMemcpyDeviceToHost));
-    HICR_CUDA(in, cudaMemcpy(&mx[1], &ms->max_msgs.v, 8, cudaMemcpyDeviceToHost));
-    results[i].max_inflight_bytes = mx[0];
-    results[i].max_inflight_msgs = mx[1];
-  }
+  if (hbad) return hbad;
+  memcpy(results, hres.data(), sizeof(hicr_mpsc_result_t) * n_consumers);
   if ((st = record_done(in)) != HICR_OK) return st;
   for (uint32_t i = 0; i < n_consumers; ++i)
     if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
@@ -1831,26 +1861,22 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
   a.abort = (unsigned int*)(p + vb + rb + cb);
   a.pw = pw;
   int* bad = (int*)(p + vb + rb + cb + 128);
+  a.bad = bad;
+  // the check's verdict stays on the device (see hicr_mpsc_stream)
+  k_nl_stream_prep<<<1, 256, 0, s>>>((const NlView*)p, n_consumers);
   k_nl_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
-  int hbad = 0;
-  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HICR_CUDA(in, cudaStreamSynchronize(s));
-  if (hbad) return hbad;
-  for (uint32_t i = 0; i < n_consumers; ++i)
-    HICR_CUDA(in, cudaMemsetAsync(get(in, chans[i])->state, 0, sizeof(NlHead), s));
   void* args[] = {&a};
   HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_nl_stream, dim3((unsigned)grid), dim3(MPSC_THREADS), args,
                                             PROD_SMEM, s));
-  HICR_CUDA(in, cudaMemcpyAsync(results, a.res, sizeof(hicr_mpsc_result_t) * n_consumers, cudaMemcpyDeviceToHost, s));
+  k_nl_stream_marks<<<1, 256, 0, s>>>((const NlView*)p, n_consumers, a.res);
+  std::vector<hicr_mpsc_result_t> hres(n_consumers);
+  int hbad = 0;
+  HICR_CUDA(in, cudaMemcpyAsync(hres.data(), a.res, sizeof(hicr_mpsc_result_t) * n_consumers,
+                                cudaMemcpyDeviceToHost, s));
+  HICR_CUDA(in, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
-  for (uint32_t i = 0; i < n_consumers; ++i) {
-    NlHead* hd = (NlHead*)get(in, chans[i])->state;
-    unsigned long long mx[2];
-    HICR_CUDA(in, cudaMemcpy(&mx[0], &hd->max_bytes.v, 8, cudaMemcpyDeviceToHost));
-    HICR_CUDA(in, cudaMemcpy(&mx[1], &hd->max_msgs.v, 8, cudaMemcpyDeviceToHost));
-    results[i].max_inflight_bytes = mx[0];
-    results[i].max_inflight_msgs = mx[1];
-  }
+  if (hbad) return hbad;
+  memcpy(results, hres.data(), sizeof(hicr_mpsc_result_t) * n_consumers);
   if ((st = record_done(in)) != HICR_OK) return st;
   for (uint32_t i = 0; i < n_consumers; ++i)
     if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
