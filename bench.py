@@ -18,6 +18,7 @@ tables, SPSC/MPSC channel rates, and the CPU oracle baseline.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import platform
@@ -409,17 +410,24 @@ def bench_latencies(h, inst, reps=2000):
     """Host-observed latency (median and p99 over `reps` calls, microseconds)
     of the small synchronous operations: a 16-byte memcpy + fence, an
     execution-unit launch + await (the built-in fill on 16 bytes), a Data
-    Object get (16 bytes) + fence, and a 1-token SPSC host push + pop."""
+    Object get (16 bytes) + fence, and a 1-token SPSC host push + pop. Python's
+    garbage collector is off while the calls are timed."""
     import ctypes as C
 
     def stats(f):
         for _ in range(50):
             f()
         ts = []
-        for _ in range(reps):
-            t0 = time.perf_counter()
-            f()
-            ts.append(time.perf_counter() - t0)
+        gc_was = gc.isenabled()
+        gc.disable()  # as timeit does: a collection inside a call is not the library's latency
+        try:
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                f()
+                ts.append(time.perf_counter() - t0)
+        finally:
+            if gc_was:
+                gc.enable()
         ts = np.asarray(ts) * 1e6
         return {"p50_us": float(np.percentile(ts, 50)), "p99_us": float(np.percentile(ts, 99))}
 

@@ -140,6 +140,7 @@ struct Instance {
   std::vector<GraphRec> graphs;
 
   std::unordered_map<uint64_t, cudaEvent_t> execs;
+  std::vector<cudaEvent_t> exec_events;  // completion events of awaited executions, reused
   uint64_t next_exec = 1;
 
   bool prof = false;

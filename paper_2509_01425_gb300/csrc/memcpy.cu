@@ -409,6 +409,68 @@ hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, c
   return HICR_OK;
 }
 
+// Host-validated batches of at most SMALL_OPS ops of at most SMALL_BYTES bytes
+// each (single memcpys before a fence, small tables) skip the op-table upload
+// and the plan/scan: the ops travel as kernel parameters, one CTA per op
+// copies it with all its warps and then bumps the op's counters.
+static constexpr uint32_t SMALL_OPS = 8;
+static constexpr uint64_t SMALL_BYTES = 256u << 10;
+struct SmallBatch {
+  unsigned long long dst[SMALL_OPS], src[SMALL_OPS], n[SMALL_OPS];  // device-usable addresses, bytes
+  uint32_t dslot[SMALL_OPS], sslot[SMALL_OPS], dtag[SMALL_OPS], stag[SMALL_OPS];
+  unsigned long long* sent;
+  unsigned long long* recv;
+  unsigned long long* tag_ops;
+};
+
+__global__ void __launch_bounds__(512) k_copy_small(SmallBatch b) {
+  const unsigned i = blockIdx.x;
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long n = b.n[i];
+  const unsigned long long lo = n * w / nw, hi = n * (w + 1) / nw;
+  if (hi > lo)
+    warp_copy(reinterpret_cast<uint8_t*>(b.dst[i]) + lo, reinterpret_cast<const uint8_t*>(b.src[i]) + lo, hi - lo,
+              lane);
+  // the barrier, then one cumulative fence by thread 0 before the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(&b.sent[b.sslot[i]], 1ull);
+    atomicAdd(&b.recv[b.dslot[i]], 1ull);
+    atomicAdd(&b.tag_ops[b.stag[i]], 1ull);
+    if (b.dtag[i] != b.stag[i]) atomicAdd(&b.tag_ops[b.dtag[i]], 1ull);
+  }
+}
+
+static bool small_batch(const Instance* in, const hicr_op_t* ops, uint64_t count) {
+  if (count == 0 || count > SMALL_OPS || in->prof) return false;
+  for (uint64_t i = 0; i < count; ++i)
+    if (ops[i].n > SMALL_BYTES) return false;
+  return true;
+}
+
+static hicr_status launch_small(Instance* in, const hicr_op_t* ops, uint64_t count) {
+  SmallBatch b;
+  memset(&b, 0, sizeof(b));
+  for (uint64_t i = 0; i < count; ++i) {
+    const HostSlot& d = in->slots[ops[i].dst];
+    const HostSlot& sl = in->slots[ops[i].src];
+    b.dst[i] = d.base + ops[i].dst_off;
+    b.src[i] = sl.base + ops[i].src_off;
+    b.n[i] = ops[i].n;
+    b.dslot[i] = ops[i].dst;
+    b.sslot[i] = ops[i].src;
+    b.dtag[i] = d.tag;
+    b.stag[i] = sl.tag;
+  }
+  b.sent = in->dt.sent;
+  b.recv = in->dt.recv;
+  b.tag_ops = in->dt.tag_ops;
+  k_copy_small<<<(unsigned)count, 512, 0, in->comm()>>>(b);
+  HICR_CUDA(in, cudaGetLastError());
+  return record_done(in);
+}
+
 // Host tables of at least this many ops are validated and staged by several
 // host threads (OpenMP); smaller ones on the calling thread.
 static constexpr uint64_t PAR_OPS = 8192;
@@ -417,6 +479,7 @@ static int host_threads() { return std::min(8, omp_get_num_procs()); }
 // Copy a host op table to the device through a double-buffered pinned
 // staging area and launch it.
 static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
+  if (small_batch(in, ops, count)) return launch_small(in, ops, count);
   const int k = in->pinned_idx;
   in->pinned_idx ^= 1;
   // the staging buffer may still feed an earlier upload

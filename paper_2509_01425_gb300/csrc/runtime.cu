@@ -261,6 +261,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
     }
   }
   for (auto& kv : in->execs) cudaEventDestroy(kv.second);
+  for (cudaEvent_t ev : in->exec_events) cudaEventDestroy(ev);
   for (auto e : in->prof_ev) cudaEventDestroy(e);
   for (int k = 0; k < 2; ++k) {
     if (in->pinned[k]) cudaFreeHost(in->pinned[k]);
@@ -658,8 +659,14 @@ hicr_status hicr_exec_launch(hicr_instance_t h, hicr_pu_t pu, const hicr_exec_un
   cudaStream_t st = in->pus[pu].stream;
   HICR_CUDA(in, cudaLaunchKernel(u->func, dim3(u->grid[0], u->grid[1], u->grid[2]),
                                  dim3(u->block[0], u->block[1], u->block[2]), args, u->smem_bytes, st));
+  // completion event: one returned by an earlier await, else a new one
   cudaEvent_t ev;
-  HICR_CUDA(in, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  if (!in->exec_events.empty()) {
+    ev = in->exec_events.back();
+    in->exec_events.pop_back();
+  } else {
+    HICR_CUDA(in, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  }
   cudaError_t e = cudaEventRecord(ev, st);
   if (e != cudaSuccess) {
     cudaEventDestroy(ev);
@@ -693,7 +700,7 @@ hicr_status hicr_exec_await(hicr_instance_t h, hicr_exec_t e, uint64_t timeout_n
   if (it == in->execs.end()) return HICR_ERR_INVALID;
   hicr_status st = wait_event(in, it->second, timeout_ns);
   if (st != HICR_OK) return st;
-  cudaEventDestroy(it->second);
+  in->exec_events.push_back(it->second);
   in->execs.erase(it);
   return HICR_OK;
 }

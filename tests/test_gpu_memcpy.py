@@ -139,6 +139,57 @@ def test_size_and_alignment_corners(h, inst, path):
         assert h.hicr_slot_counters(inst, ids[1])[1:] == (0, len(ops))
 
 
+@pytest.mark.parametrize("sizes", [
+    [16],
+    [0, 1, 17],
+    [4099, 65536, 33, 262144, 5, 100_000, 2, 7],   # eight ops, one at the 256 KiB limit
+    [4099, 65536, 33, 262145],                      # one op over the limit: the regular path
+    [64] * 9,                                       # nine ops: the regular path
+])
+def test_small_batches_match_oracle(h, inst, sizes):
+    """Host batches of at most 8 ops of at most 256 KiB travel as kernel
+    parameters (one CTA per op, no op-table upload, no plan/scan); larger
+    ones take the regular path. Both must leave the oracle's bytes and exact
+    slot and tag counters, through single memcpys + fence and through
+    hicr_memcpy_batch."""
+    size = 4 << 20
+    ids = []
+    for s, tag in enumerate((3, 5)):
+        st, sid = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size, tag)
+        assert st == 0 and h.hicr_util_fill(inst, sid, 0, size, fill_key(23, s)) == 0
+        ids.append(sid)
+    cm, oids = oracle_slots([size, size], 23)
+    rng = np.random.default_rng(len(sizes) * 31 + sum(sizes) % 97)
+    c0 = [h.hicr_slot_counters(inst, i)[1:] for i in ids]
+    t0 = [h.hicr_tag_counter(inst, t)[1] for t in (3, 5)]
+    for rnd, path in enumerate(("queue", "batch")):
+        cursor = rnd * (size // 2)
+        dst, src, doff, soff = [], [], [], []
+        for n in sizes:
+            d = cursor + int(rng.integers(0, 16))
+            cursor = d + n + 1
+            dst.append(1), src.append(0), doff.append(d), soff.append(int(rng.integers(0, size - n)))
+        assert cursor <= (rnd + 1) * (size // 2)
+        ops = configs.make_ops(dst, src, doff, soff, sizes)
+        assert cm.memcpy_batch(ops) == (om.OK, None)
+        dops = remap(ops, ids)
+        if path == "queue":
+            for o in dops:
+                assert h.hicr_memcpy(inst, int(o["dst"]), int(o["dst_off"]), int(o["src"]), int(o["src_off"]),
+                                     int(o["n"])) == 0
+        else:
+            assert h.hicr_memcpy_batch(inst, dops) == (0, 0)
+        assert h.hicr_fence(inst, 0, T) == 0
+        for k in range(2):
+            assert (slot_bytes(h, inst, ids[k]) == cm.slots[oids[k]].data).all(), (path, k)
+        m = (rnd + 1) * len(sizes)
+        assert h.hicr_slot_counters(inst, ids[0])[1:] == (c0[0][0] + m, c0[0][1])
+        assert h.hicr_slot_counters(inst, ids[1])[1:] == (c0[1][0], c0[1][1] + m)
+        assert [h.hicr_tag_counter(inst, t)[1] for t in (3, 5)] == [t0[0] + m, t0[1] + m]
+    for i in ids:
+        assert h.hicr_mem_free(inst, i) == 0
+
+
 def test_tiny_config_bit_exact(h, inst):
     w = configs.tiny(0)
     ids = alloc_filled(h, inst, w.slot_sizes, 0)
