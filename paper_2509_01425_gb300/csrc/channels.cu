@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
               const unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
               const unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
               mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
-              dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+              // w0 (2 word + 1) + w1 (2 word + 3) with one product
+              dig += (w0 + w1) * (2ull * word + 1ull) + (w1 << 1);
             }
           }
         }
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
           const unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
           const unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
           mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
-          dig += w0 * (2ull * word + 1ull) + w1 * (2ull * word + 3ull);
+          dig += (w0 + w1) * (2ull * word + 1ull) + (w1 << 1);
         }
       }
     }
