@@ -466,18 +466,27 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
             if (sl >= v.cap) sl -= v.cap;
           }
           slot = sl;
+          // Vector u of this pass starts at word W0 + u D (D = tpi wpt), so
+          // its digest term w0 (2 word + 1) + w1 (2 word + 3) sums over the
+          // pass to (2 W0 + 1) S + 2 D U + 2 W1, with S = sum_u (w0 + w1),
+          // U = sum_u u (w0 + w1) (suffix sums, u descending), W1 = sum_u w1
+          // (mod 2^64): two products per pass instead of one per vector.
+          const unsigned long long W0 = (s0 + tl) * wpt + 2ull * jv;
+          unsigned long long S = 0, U = 0, W1 = 0;
 #pragma unroll
-          for (int u = 0; u < SPSC_U; ++u) {
+          for (int u = SPSC_U - 1; u >= 0; --u) {
             const unsigned long long t_ = tl + (unsigned long long)u * tpi;
             if (t_ < k) {
-              const unsigned long long word = (s0 + t_) * wpt + 2ull * jv;
+              const unsigned long long word = W0 + (unsigned long long)u * tpi * wpt;
               const unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
               const unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
               mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
-              // w0 (2 word + 1) + w1 (2 word + 3) with one product
-              dig += (w0 + w1) * (2ull * word + 1ull) + (w1 << 1);
+              S += w0 + w1;
+              W1 += w1;
             }
+            if (u > 0) U += S;
           }
+          dig += S * (2ull * W0 + 1ull) + U * (2ull * tpi * wpt) + (W1 << 1);
         }
       }
     } else {
