@@ -1022,9 +1022,11 @@ def run_control_small(args):
     tokens), a locking MPSC and a non-locking MPSC channel (messages of
     100 B-64 KiB) (k_*_push_host, k_*_ctl); the seeded staging fill and the
     pre-checks of both MPSC streams on a 64 -> 4 producer x 16 message table
-    (k_fill_segments, k_mpsc_check, k_nl_check, and the two stream kernels);
-    two allocation-free batches of 10,000 ops (k_plan, k_scan, k_copy); and a
-    1 ms bounded device wait (k_wait_test)."""
+    (k_fill_segments, k_mpsc_check, k_nl_check, the streams' set-up and
+    wrap-up kernels, and the two stream kernels); two allocation-free batches
+    of 10,000 ops (k_plan, k_scan, k_copy); four single memcpys, each
+    followed by a fence (k_copy_small); and a 1 ms bounded device wait
+    (k_wait_test)."""
     import torch
     from paper_2509_01425_gb300 import build
     build.build()
@@ -1070,6 +1072,9 @@ def run_control_small(args):
     h.check(h.hicr_batch_reserve(inst, n_ops), "reserve")
     for _ in range(2):
         h.check(h.hicr_memcpy_batch_noalloc(inst, d_ops.data_ptr(), n_ops), "noalloc")
+        h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
+    for i in range(4):  # single memcpys before a fence: the small-batch kernel
+        h.check(h.hicr_memcpy(inst, b, 40 * MiB + 64 * i, a, 64 * i, 16 << i), "memcpy")
         h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
     st, wst, waited = h.hicr_util_wait_test(inst, 1_000_000)
     h.check(st, "wait_test")
