@@ -43,6 +43,14 @@ struct Mailbox {
   unsigned long long v[6];
 };
 
+// A host-call kernel's last act: everything it wrote before (results in v[],
+// ring bytes, counters) becomes visible system-wide, then the status word,
+// which the host polls in mapped memory.
+__device__ __forceinline__ void mb_post(Mailbox* mb, int st) {
+  __threadfence_system();
+  *(volatile int*)&mb->status = st;
+}
+
 
 // ---------------------------------------------------------------------------
 // Device primitives.

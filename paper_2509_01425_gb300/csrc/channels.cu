@@ -32,6 +32,7 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <thread>
 #include <vector>
 
 #include "../../include/hicr_channels.h"
@@ -75,7 +76,7 @@ __global__ void k_spsc_push_host(SpscView v, const uint8_t* src, unsigned long l
   }
   __syncthreads();
   if (!s_ok) {
-    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
     return;
   }
   // at most two contiguous runs: up to the ring end, then from its start
@@ -88,7 +89,7 @@ __global__ void k_spsc_push_host(SpscView v, const uint8_t* src, unsigned long l
   if (threadIdx.x == 0) {
     st_rel(&v.st->head.v, s_head + k);
     mb->v[0] = s_head;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   }
 }
 
@@ -99,24 +100,24 @@ __global__ void k_spsc_ctl(SpscView v, int op, unsigned long long k, Mailbox* mb
   if (op == 2) {
     mb->v[0] = depth;
     mb->v[1] = depth * v.ts;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   } else if (op == 0) {
     if (k >= depth) {
-      mb->status = HICR_ERR_EMPTY;
+      mb_post(mb, HICR_ERR_EMPTY);
       return;
     }
     mb->v[0] = ((t + k) % v.cap) * v.ts;
     mb->v[1] = v.ts;
     mb->v[2] = 0;
     mb->v[3] = t + k;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   } else {
     if (k > depth) {
-      mb->status = HICR_ERR_EMPTY;
+      mb_post(mb, HICR_ERR_EMPTY);
       return;
     }
     st_rel(&v.st->tail.v, t + k);
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   }
 }
 
@@ -151,7 +152,7 @@ __global__ void k_mpsc_push_host(MpscView v, unsigned int producer, unsigned int
   }
   __syncthreads();
   if (!s_ok) {
-    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
     return;
   }
   cta_copy(v.ring + (s_start & (v.R - 1)), src, n);
@@ -167,7 +168,7 @@ __global__ void k_mpsc_push_host(MpscView v, unsigned int producer, unsigned int
     st_rel(&e->ready, (s_ticket & MASK24) + 1);
     mb->v[0] = s_start & (v.R - 1);
     mb->v[1] = s_ticket;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   }
 }
 
@@ -180,39 +181,39 @@ __global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb
   if (op == 2) {
     mb->v[0] = depth;
     mb->v[1] = ((W & MASK40) - freed) & MASK40;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
     return;
   }
   if (op == 0) {
     if (k >= depth) {
-      mb->status = HICR_ERR_EMPTY;
+      mb_post(mb, HICR_ERR_EMPTY);
       return;
     }
     const unsigned long long t = mt + k;
     MpscMeta* e = v.meta + (t & (v.M - 1));
     if (ld_acq(&e->ready) != (t & MASK24) + 1) {
-      mb->status = HICR_ERR_EMPTY;
+      mb_post(mb, HICR_ERR_EMPTY);
       return;
     }
     mb->v[0] = __ldcg(&e->start) & (v.R - 1);
     mb->v[1] = __ldcg(&e->size);
     mb->v[2] = __ldcg(&e->producer);
     mb->v[3] = __ldcg(&e->seq);
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
     return;
   }
   if (k > depth) {
-    mb->status = HICR_ERR_EMPTY;
+    mb_post(mb, HICR_ERR_EMPTY);
     return;
   }
   if (k == 0) {
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
     return;
   }
   for (unsigned long long i = 0; i < k; ++i) {
     const unsigned long long t = mt + i;
     if (ld_acq(&v.meta[t & (v.M - 1)].ready) != (t & MASK24) + 1) {
-      mb->status = HICR_ERR_EMPTY;
+      mb_post(mb, HICR_ERR_EMPTY);
       return;
     }
   }
@@ -220,7 +221,7 @@ __global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb
   const unsigned long long end = (__ldcg(&last->start) + round16(__ldcg(&last->size))) & MASK40;
   st_rel(&v.st->freed.v, end);
   st_rel(&v.st->msg_tail.v, mt + k);
-  mb->status = HICR_OK;
+  mb_post(mb, HICR_OK);
 }
 
 // ---------------------------------------------------------------------------
@@ -295,7 +296,7 @@ __global__ void k_nl_push_host(NlView v, unsigned int producer, unsigned int seq
   }
   __syncthreads();
   if (!s_ok) {
-    if (threadIdx.x == 0) mb->status = HICR_ERR_FULL;
+    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
     return;
   }
   uint8_t* ring = v.ring + (unsigned long long)producer * v.R;
@@ -312,7 +313,7 @@ __global__ void k_nl_push_host(NlView v, unsigned int producer, unsigned int seq
     st_rel(&st->pub.v, s_pub + 1);
     mb->v[0] = s_start & (v.R - 1);
     mb->v[1] = s_pub;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
   }
 }
 
@@ -328,11 +329,11 @@ __global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) {
   if (op == 2) {
     mb->v[0] = msgs;
     mb->v[1] = bytes;
-    mb->status = HICR_OK;
+    mb_post(mb, HICR_OK);
     return;
   }
   if (op == 0 ? k >= msgs : k > msgs) {
-    mb->status = HICR_ERR_EMPTY;
+    mb_post(mb, HICR_ERR_EMPTY);
     return;
   }
   unsigned long long left = k;
@@ -348,7 +349,7 @@ __global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) {
         mb->v[1] = __ldcg(&e->size);
         mb->v[2] = p;
         mb->v[3] = __ldcg(&e->seq);
-        mb->status = HICR_OK;
+        mb_post(mb, HICR_OK);
         return;
       }
       left -= d;
@@ -363,7 +364,7 @@ __global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) {
       if (!left) break;
     }
   }
-  mb->status = HICR_OK;
+  mb_post(mb, HICR_OK);
 }
 
 // ---------------------------------------------------------------------------
@@ -1348,9 +1349,23 @@ static hicr_status mailbox(Instance* in, Mailbox** host, Mailbox** dev) {
 
 static hicr_status finish(Instance* in, Mailbox* mh) {
   HICR_CUDA(in, cudaGetLastError());
-  HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
-  if (mh->status == 1) return HICR_ERR_DEVICE;
-  return mh->status;
+  // The kernel posts its status last, behind a system-scope fence, so a
+  // posted status means its work is visible. Poll the mapped word; query the
+  // stream now and then, so a kernel that failed (status never posted) ends
+  // the wait with its error.
+  volatile int* st = &mh->status;
+  for (uint64_t i = 0;; ++i) {
+    if (*st != 1) return *st;
+    if ((i & 255) == 255) {
+      const cudaError_t e = cudaStreamQuery(in->comm());
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorNotReady) return cuda_fail(in, e, "host channel call");
+      if (i > (1u << 20)) std::this_thread::yield();
+    }
+  }
+  // the stream is idle: the status word is final
+  if (*st == 1) return HICR_ERR_DEVICE;
+  return *st;
 }
 
 static hicr_status dev_buffer(Instance* in, size_t bytes, void** out) {
