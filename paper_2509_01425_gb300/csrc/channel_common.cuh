@@ -81,11 +81,12 @@ __device__ __forceinline__ bool aborted(const unsigned int* abort) {
 }
 __host__ __device__ __forceinline__ unsigned long long round16(unsigned long long n) { return (n + 15) & ~15ull; }
 
-// Producer copy into a channel ring: when source and destination are both
-// 16-byte aligned (staged payloads and ring positions always are), every lane
-// keeps 16 vector loads in flight (8 KiB per warp) and the ring is written
-// with default-cached stores, so that the consumer, which reads the message
-// soon after, can find it in L2. Other alignments use the general warp copy.
+// Register-staged producer copy into a channel ring (the serving engine's
+// burst producers; the streaming kernels use group_copy_bulk below): when
+// source and destination are both 16-byte aligned, every lane keeps 16 vector
+// loads in flight (8 KiB per warp) and the ring is written with
+// default-cached stores, so that the consumer, which reads the message soon
+// after, can find it in L2. Other alignments use the general warp copy.
 __device__ __forceinline__ void ring_copy(uint8_t* __restrict__ d, const uint8_t* __restrict__ s,
                                           unsigned long long n, unsigned lane) {
   if ((((uintptr_t)d | (uintptr_t)s) & 15u) != 0) {
