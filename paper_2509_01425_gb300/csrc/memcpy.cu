@@ -1,6 +1,7 @@
 // Batched local-to-local memcpy between memory slots (HiCR paper Sec. 3.1.4,
-// "memcpy" and "fence"; Fig. 5). One batch = three kernels on the
-// communication stream:
+// "memcpy" and "fence"; Fig. 5). One batch = these steps on the
+// communication stream (k_plan_scan fuses the first two on the main path;
+// the allocation-free entry runs them as two kernels):
 //
 //   k_plan  (grid over ops)  validate each op against the device slot table
 //                            with the same rules as the host, charge it
@@ -8,7 +9,8 @@
 //   k_scan  (one CTA)        exclusive prefix sum of the costs, chunk count,
 //                            first bad op -> the batch copies nothing and the
 //                            error is left for the next fence;
-//   k_copy  (persistent)     every warp repeatedly claims a chunk of
+//   k_copy  (persistent)     (or k_copy_tma, the bulk-copy engine)
+//                            every warp repeatedly claims a chunk of
 //                            `chunk` cost units, finds the op holding its
 //                            first unit by a 32-ary search of the prefix sums,
 //                            and copies the byte pieces of every op the chunk
@@ -20,6 +22,9 @@
 // ops are cut into many chunks that different warps copy in parallel, runs of
 // small ops are packed into one chunk, and the per-op charge keeps a warp
 // from being handed too many tiny ops at once.
+//
+// Host-validated batches of a few small ops skip all of this: k_copy_small
+// takes them as kernel parameters (see SMALL_OPS).
 #include <stdio.h>
 #include <stdlib.h>
 #include <omp.h>
