@@ -1,8 +1,10 @@
 // Device-side layout and synchronisation primitives of the channels, shared
 // by the channel kernels and the serving engine.
 #pragma once
+#include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/hicr_channels.h"
 #include "copy.cuh"
 #include "tma.cuh"
 
@@ -486,6 +488,68 @@ __device__ __forceinline__ unsigned long long mpsc_place(unsigned long long W, c
     if (pos + r[i] > R) b = (b + (R - pos)) & MASK40;
     start[i] = b;
     b = (b + r[i]) & MASK40;
+  }
+  return b;
+}
+
+// Copy n bytes with every warp of the CTA taking an equal share.
+__device__ __forceinline__ void cta_copy(uint8_t* d, const uint8_t* s, unsigned long long n) {
+  const unsigned lane = threadIdx.x & 31u, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long a = n * w / nw, b = n * (w + 1) / nw;
+  if (b > a) warp_copy(d + a, s + a, b - a, lane);
+}
+
+// ---------------------------------------------------------------------------
+// Non-locking MPSC layout.
+// ---------------------------------------------------------------------------
+struct NlState {
+  Line reserve;  // bytes reserved (absolute, including skipped bytes); producer
+  Line pub;      // messages published; producer
+  Line freed;    // bytes freed; consumer
+  Line cons;     // messages consumed; consumer
+};
+struct NlHead {
+  Line max_bytes;  // high-water marks of reserved-minus-freed / in-flight
+  Line max_msgs;   // messages over the channel's rings (streaming runs)
+};
+struct NlMeta {
+  unsigned long long start;  // absolute reservation start
+  unsigned int size;
+  unsigned int seq;
+};
+static_assert(sizeof(NlMeta) == 16, "non-locking metadata entry is 16 bytes");
+// the public description of the non-locking layout (hicr_channels.h)
+static_assert(sizeof(hicr_nl_meta_t) == sizeof(NlMeta), "public non-locking metadata layout");
+static_assert(sizeof(NlState) == 8 * HICR_NL_STATE_WORDS && offsetof(NlState, reserve) == 8 * HICR_NL_RESERVE &&
+                  offsetof(NlState, pub) == 8 * HICR_NL_PUB && offsetof(NlState, freed) == 8 * HICR_NL_FREED &&
+                  offsetof(NlState, cons) == 8 * HICR_NL_CONS,
+              "public non-locking counter layout");
+// the public description of a locking-mode metadata entry (hicr_channels.h)
+static_assert(sizeof(hicr_mpsc_meta_t) == sizeof(MpscMeta) && offsetof(hicr_mpsc_meta_t, start) == offsetof(MpscMeta, start) &&
+                  offsetof(hicr_mpsc_meta_t, size) == offsetof(MpscMeta, size) &&
+                  offsetof(hicr_mpsc_meta_t, producer) == offsetof(MpscMeta, producer) &&
+                  offsetof(hicr_mpsc_meta_t, seq) == offsetof(MpscMeta, seq) &&
+                  offsetof(hicr_mpsc_meta_t, ready) == offsetof(MpscMeta, ready),
+              "public MPSC metadata layout");
+struct NlView {
+  uint8_t* ring;  // ring i at ring + i * R
+  NlHead* head;
+  NlState* st;    // st[i]
+  NlMeta* meta;   // ring i's entries at meta + i * M
+  unsigned long long R;
+  unsigned int M;
+  unsigned int P;
+};
+
+// Placement of k messages with rounded sizes r[] from absolute position b
+// (the locking mode's rule on one ring, without the ticket packing).
+__device__ __forceinline__ unsigned long long nl_place(unsigned long long b, const unsigned long long* r, int k,
+                                                        unsigned long long R, unsigned long long* start) {
+  for (int i = 0; i < k; ++i) {
+    const unsigned long long pos = b & (R - 1);
+    if (pos + r[i] > R) b += R - pos;
+    start[i] = b;
+    b += r[i];
   }
   return b;
 }

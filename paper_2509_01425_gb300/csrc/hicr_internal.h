@@ -108,7 +108,7 @@ struct GraphRec {
   bool live = false;
 };
 
-struct Channel;  // channels.cu
+struct Channel;  // channel_host.h
 
 struct Instance {
   int device = 0;

@@ -1,0 +1,175 @@
+// The paper's Test Case 1 (Sec. 5.1) restated on one GPU: two agents, each a
+// group of CTAs of one cooperative grid, exchange a single message through
+// two buffers; the round-trip time gives the one-way latency and goodput.
+#include <stddef.h>
+#include <string.h>
+
+#include "../../include/hicr_channels.h"
+#include "../../include/hicr_util.h"
+#include "channel_host.h"
+
+namespace hicr {
+
+// ---------------------------------------------------------------------------
+// Ping-pong: CTAs [0, G) are agent A, [G, 2G) agent B. Round k: A's CTAs copy
+// their share of the message into B's buffer and count themselves in
+// (arrive_a); B's CTAs wait for arrive_a >= k*G, echo their share into A's
+// buffer and count in (arrive_b); A waits for arrive_b >= k*G.
+// ---------------------------------------------------------------------------
+struct PingArgs {
+  const uint8_t* msg;
+  uint8_t* buf_a;
+  uint8_t* buf_b;
+  unsigned long long bytes;
+  unsigned int G;
+  unsigned int rounds;   // warm-up + timed
+  unsigned int warmup;
+  unsigned long long timeout_ns;
+  unsigned long long* arrive;  // [0] A, [16] B (separate lines)
+  unsigned long long* times;   // [0] start of the first timed round, [1] end of the last
+  unsigned int* abort;
+};
+
+__global__ void __launch_bounds__(512) k_pingpong(PingArgs a) {
+  __shared__ int s_stop;
+  const unsigned side = blockIdx.x / a.G, g = blockIdx.x % a.G;
+  const unsigned long long lo = a.bytes * g / a.G, hi = a.bytes * (g + 1) / a.G;
+  unsigned long long* mine = a.arrive + (side ? 16 : 0);
+  unsigned long long* peer = a.arrive + (side ? 0 : 16);
+  const unsigned long long deadline = gtime() + a.timeout_ns;
+  for (unsigned k = 1; k <= a.rounds; ++k) {
+    if (side == 0 && g == 0 && threadIdx.x == 0 && k == a.warmup + 1) a.times[0] = gtime();
+    if (side == 1) {
+      // B: wait for A's k-th message
+      if (threadIdx.x == 0) {
+        int stop = 0;
+        while (ld_acq(peer) < (unsigned long long)k * a.G) {
+          if (aborted(a.abort) || gtime() > deadline) {
+            stop = 1;
+            atomicExch(a.abort, 1u);
+            break;
+          }
+        }
+        s_stop = stop;
+      }
+      __syncthreads();
+      if (s_stop) return;
+      cta_copy(a.buf_a + lo, a.buf_b + lo, hi - lo);  // echo
+    } else {
+      cta_copy(a.buf_b + lo, a.msg + lo, hi - lo);  // send
+    }
+    // barrier, then one cumulative release by thread 0 (no per-thread fence)
+    __syncthreads();
+    if (threadIdx.x == 0) red_add_rel(mine, 1ull);
+    if (side == 0) {
+      // A: wait for the echo of round k
+      if (threadIdx.x == 0) {
+        int stop = 0;
+        while (ld_acq(peer) < (unsigned long long)k * a.G) {
+          if (aborted(a.abort) || gtime() > deadline) {
+            stop = 1;
+            atomicExch(a.abort, 1u);
+            break;
+          }
+        }
+        s_stop = stop;
+      }
+      __syncthreads();
+      if (s_stop) return;
+    }
+  }
+  if (side == 0 && g == 0 && threadIdx.x == 0) a.times[1] = gtime();
+}
+
+}  // namespace hicr
+
+using namespace hicr;
+
+extern "C" {
+
+hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
+                          uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out) {
+  Instance* in = I(h);
+  if (!in || !out || reps == 0 || ctas_per_side == 0 || ctas_per_side > 256 || bytes == 0 || in->capturing)
+    return HICR_ERR_INVALID;
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pingpong, 512, 0));
+  if (2ull * ctas_per_side > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
+  void* sp = nullptr;
+  uint64_t ssize = 0;
+  uint32_t sspace = 0;
+  if (hicr_slot_info(h, src, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+  if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+  if (src_off > ssize || bytes > ssize - src_off) return HICR_ERR_BOUNDS;
+  hicr_status st = hicr_flush(h);
+  if (st != HICR_OK) return st;
+  // the two single-message buffers (one allocation, freed at the end)
+  uint8_t* bufs = nullptr;
+  const uint64_t half = (bytes + 255) & ~255ull;
+  cudaError_t e = cudaMalloc(&bufs, 2 * half);
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    return HICR_ERR_NOMEM;
+  }
+  HICR_CUDA(in, e);
+  void* buf = nullptr;
+  st = dev_buffer(in, 65536, &buf);
+  if (st != HICR_OK) {
+    cudaFree(bufs);
+    return st;
+  }
+  cudaStream_t cs = in->comm();
+  unsigned long long* arrive = (unsigned long long*)buf;  // [0], [16]
+  unsigned long long* times = arrive + 32;
+  unsigned int* abort_flag = (unsigned int*)(times + 4);
+  e = cudaMemsetAsync(buf, 0, 512, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bufs, 0, 2 * half, cs);
+  PingArgs a;
+  a.msg = (const uint8_t*)sp + src_off;
+  a.buf_a = bufs;
+  a.buf_b = bufs + half;
+  a.bytes = bytes;
+  a.G = ctas_per_side;
+  a.rounds = reps + warmup;
+  a.warmup = warmup;
+  a.timeout_ns = timeout_ns;
+  a.arrive = arrive;
+  a.times = times;
+  a.abort = abort_flag;
+  void* args[] = {&a};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void*)k_pingpong, dim3(2 * ctas_per_side), dim3(512), args, 0, cs);
+  unsigned long long ht[2] = {0, 0};
+  unsigned int hab = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ht, times, 16, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hab, abort_flag, 4, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) {
+    cudaFree(bufs);
+    return cuda_fail(in, e, "pingpong");
+  }
+  // digests of both buffers with the library's digest kernel
+  hicr_pingpong_result_t r;
+  memset(&r, 0, sizeof(r));
+  r.bytes = bytes;
+  r.reps = reps;
+  r.ctas_per_side = ctas_per_side;
+  r.status = hab ? HICR_ERR_TIMEOUT : HICR_OK;
+  const double dt = (double)(ht[1] - ht[0]);
+  r.half_rtt_ns = hab ? 0.0 : dt / (2.0 * reps);
+  r.goodput_gbs = r.half_rtt_ns > 0 ? (double)bytes / r.half_rtt_ns : 0.0;
+  hicr_slot_t sa = 0, sb = 0;
+  st = hicr_slot_register(h, HICR_SPACE_HBM, bufs, bytes, 0, &sa);
+  if (st == HICR_OK) st = hicr_slot_register(h, HICR_SPACE_HBM, bufs + half, bytes, 0, &sb);
+  if (st == HICR_OK) st = hicr_util_digest(h, sa, 0, bytes, &r.digest_a);
+  if (st == HICR_OK) st = hicr_util_digest(h, sb, 0, bytes, &r.digest_b);
+  cudaStreamSynchronize(cs);
+  hicr_slot_deregister(h, sa);
+  hicr_slot_deregister(h, sb);
+  cudaFree(bufs);
+  if (st != HICR_OK) return st;
+  *out = r;
+  return r.status;
+}
+
+}  // extern "C"
