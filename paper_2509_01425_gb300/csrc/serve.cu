@@ -1147,10 +1147,12 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
       }
     }
     if (completed == n) break;
-    if (next_admit < n && wait_head == waiting.size() && mode == 0 && next_arrival < n) {
-      const uint64_t gap = reqs[next_arrival].arrival_ns > now ? reqs[next_arrival].arrival_ns - now : 0;
-      if (gap > 50000 && inflight.empty()) std::this_thread::sleep_for(std::chrono::nanoseconds(gap - 20000));
-    }
+    // Idle until the next arrival: yield rather than sleep. A timed sleep on
+    // Linux wakes up to a timer-slack late (tens of microseconds, sometimes
+    // milliseconds), and that delay went straight into the next request's
+    // admission time.
+    if (next_admit < n && wait_head == waiting.size() && mode == 0 && next_arrival < n && inflight.empty())
+      std::this_thread::yield();
   }
   hstop->store(1, std::memory_order_release);
   // Wait for the engine with a bound: its own deadline ends every device
