@@ -15,11 +15,12 @@
  *  - admitted requests are published through a doorbell in mapped host memory;
  *    a dispatcher warp moves them into a device-side request table and cuts
  *    them into work units (memcpy: cost chunks; burst: groups of up to 8
- *    messages); worker warps claim units round-robin among the 16 oldest
- *    requests that still have unclaimed units (continuous batching with
- *    processor sharing: work of requests admitted at different times overlaps
- *    on the device, and a small request is not queued behind all the units of
- *    a large one);
+ *    messages); worker warps claim units from the 16 oldest requests that
+ *    still have unclaimed units, taking the one with the fewest unclaimed
+ *    units first (continuous batching with shortest-remaining-first order
+ *    inside that window: work of requests admitted at different times
+ *    overlaps on the device, and a small request is not queued behind the
+ *    units of a large one);
  *  - the unit that finishes a request writes its completion into mapped host
  *    memory; the host frees the request's region and records the latency from
  *    arrival to the moment it saw the completion.

@@ -14,8 +14,8 @@
 //   CTAs 1..C       one MPSC consumer per channel (windowed drain as in the
 //                   channel stream kernel); completes burst requests;
 //   other CTAs      worker warps share the work of the requests in flight
-//                   (processor sharing): each claim takes the next unit of a
-//                   request picked round-robin among the SRV_PS_WINDOW oldest
+//                   (shortest remaining first): each claim takes the next unit of the
+//                   request with the fewest unclaimed units among the SRV_PS_WINDOW oldest
 //                   published requests that still have unclaimed units, so a
 //                   small request does not wait behind the units of a large
 //                   one. A unit either
@@ -62,9 +62,9 @@ struct SrvReq {
 // consecutive messages whose rounded sizes sum to at most SRV_GROUP_BYTES
 // (a larger message is a group of its own); one work unit per group.
 static constexpr unsigned SRV_GROUP_MSGS = 8;
-// Workers share their claims round-robin among at most this many of the
-// oldest requests that may have unclaimed units (processor sharing at normal
-// load; under overload the requests behind the window wait in order).
+// Workers claim among at most this many of the oldest requests that may have
+// unclaimed units, the one with the fewest unclaimed units first (under
+// overload the requests behind the window wait in order).
 static constexpr unsigned long long SRV_PS_WINDOW = 16;
 static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
 
@@ -353,8 +353,9 @@ __device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
 // Claim one unit for the warp. Lane 0 reads the window [lo, hi) of published
 // requests that may still have unclaimed units, moves lo past exhausted
 // requests, and draws a round-robin start; the warp then scans the window from
-// there, 32 requests per step (one lane each), and claims from the first
-// request with a unit left. Returns 1 with (r, k) = (request, unit index),
+// there, 32 requests per step (one lane each), and claims from the request
+// with the fewest unclaimed units (ties: scan order), trying the next fewest
+// when another warp took the last one. Returns 1 with (r, k) = (request, unit index),
 // 0 when nothing is claimable right now, 2 when the run is over (every
 // request published and claimed) or aborted. All lanes return the same value.
 __device__ int srv_claim(const SrvArgs& a, unsigned lane, unsigned long long deadline, unsigned long long& r,
@@ -392,14 +393,19 @@ __device__ int srv_claim(const SrvArgs& a, unsigned lane, unsigned long long dea
     const unsigned long long off = base + lane;
     unsigned long long cand = 0;
     bool open = false;
+    unsigned left = 0xffffffffu;  // unclaimed units (capped), for the shortest-remaining choice
     if (off < w) {
       cand = lo + (start + off) % w;
-      open = ld_rlx(&a.req[cand].claimed) < __ldcg(&a.req[cand].N);
+      const unsigned long long c = ld_rlx(&a.req[cand].claimed), n = __ldcg(&a.req[cand].N);
+      open = c < n;
+      if (open) left = (unsigned)min(n - c, 0xfffffffeull);
     }
     unsigned m = __ballot_sync(FULLM, open);
     while (m) {
-      const unsigned L = __ffs(m) - 1;
-      m &= m - 1;
+      // the open request with the fewest unclaimed units (ties: scan order)
+      const unsigned best = __reduce_min_sync(FULLM, (m >> lane) & 1u ? left : 0xffffffffu);
+      const unsigned L = __ffs(__ballot_sync(FULLM, ((m >> lane) & 1u) && left == best)) - 1;
+      m &= ~(1u << L);
       const unsigned long long rc = __shfl_sync(FULLM, cand, L);
       unsigned long long kk = 0;
       int got = 0;
