@@ -15,7 +15,7 @@
  *  - admitted requests are published through a doorbell in mapped host memory;
  *    a dispatcher warp moves them into a device-side request table and cuts
  *    them into work units (memcpy: cost chunks; burst: groups of up to 8
- *    messages); worker warps claim units from the 16 oldest requests that
+ *    messages); worker warps claim units from the 32 oldest requests that
  *    still have unclaimed units, taking the one with the fewest unclaimed
  *    units first (continuous batching with shortest-remaining-first order
  *    inside that window: work of requests admitted at different times

@@ -65,7 +65,7 @@ static constexpr unsigned SRV_GROUP_MSGS = 8;
 // Workers claim among at most this many of the oldest requests that may have
 // unclaimed units, the one with the fewest unclaimed units first (under
 // overload the requests behind the window wait in order).
-static constexpr unsigned long long SRV_PS_WINDOW = 16;
+static constexpr unsigned long long SRV_PS_WINDOW = 32;
 static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
 
 struct SrvHostDesc {
