@@ -200,7 +200,8 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// MPSC streaming: CTAs [0, n_cons) consume, the rest hold one producer per
+// MPSC streaming (locking mode): CTAs [0, n_cons * G) consume (G per
+// consumer); the rest hold the producers, pw warps each, one producer per
 // warp; producer p feeds consumer p mod n_cons.
 // ---------------------------------------------------------------------------
 struct MpscStreamArgs {
