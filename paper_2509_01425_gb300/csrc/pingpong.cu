@@ -81,6 +81,76 @@ __global__ void __launch_bounds__(512) k_pingpong(PingArgs a) {
   if (side == 0 && g == 0 && threadIdx.x == 0) a.times[1] = gtime();
 }
 
+// The same exchange for large messages when each agent has at most half the
+// SMs: every CTA then has an SM to itself and takes PING_SMEM of shared memory
+// for two bulk-copy stages per warp, and each warp moves its (16-byte-aligned)
+// share of the CTA's part by bulk copies through them (group_copy_bulk). A
+// wait on a stage that gives up raises the abort flag; the CTA leaves after
+// its barrier.
+static constexpr unsigned PING_NST = 2, PING_STG = 6144, PING_WARPS = 16;
+static constexpr size_t PING_SMEM = (size_t)PING_WARPS * PING_NST * (PING_STG + 8);
+static constexpr unsigned long long PING_WAIT_NS = 2000000000ull;  // bound of one stage wait
+static constexpr unsigned long long PING_BULK_MIN = 64u << 10;     // smallest warp share for the bulk form
+
+__global__ void __launch_bounds__(512, 1) k_pingpong_bulk(PingArgs a) {
+  extern __shared__ __align__(128) uint8_t ping_smem[];
+  __shared__ int s_stop, s_fail;
+  const unsigned side = blockIdx.x / a.G, g = blockIdx.x % a.G;
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned long long lo = g == 0 ? 0 : (a.bytes * g / a.G) & ~15ull;
+  const unsigned long long hi = g + 1 == a.G ? a.bytes : (a.bytes * (g + 1) / a.G) & ~15ull;
+  const unsigned long long n = hi - lo;
+  const unsigned long long wa = warp == 0 ? 0 : (n * warp / nw) & ~15ull;
+  const unsigned long long wb = warp + 1 == nw ? n : (n * (warp + 1) / nw) & ~15ull;
+  uint8_t* stage = ping_smem + (size_t)warp * PING_NST * PING_STG;
+  unsigned long long* bars =
+      reinterpret_cast<unsigned long long*>(ping_smem + (size_t)PING_WARPS * PING_NST * PING_STG) + warp * PING_NST;
+  if (lane == 0) {
+    for (unsigned k = 0; k < PING_NST; ++k) mbar_init(bars + k);
+    mbar_init_fence();
+  }
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  unsigned phase = 0;
+  unsigned long long* mine = a.arrive + (side ? 16 : 0);
+  unsigned long long* peer = a.arrive + (side ? 0 : 16);
+  const unsigned long long deadline = gtime() + a.timeout_ns;
+  auto wait_peer = [&](unsigned k) -> bool {
+    if (threadIdx.x == 0) {
+      int stop = 0;
+      while (ld_acq(peer) < (unsigned long long)k * a.G) {
+        if (aborted(a.abort) || gtime() > deadline) {
+          stop = 1;
+          atomicExch(a.abort, 1u);
+          break;
+        }
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    return s_stop == 0;
+  };
+  for (unsigned k = 1; k <= a.rounds; ++k) {
+    if (side == 0 && g == 0 && threadIdx.x == 0 && k == a.warmup + 1) a.times[0] = gtime();
+    if (side == 1 && !wait_peer(k)) return;  // B: wait for A's k-th message
+    uint8_t* d = (side ? a.buf_a : a.buf_b) + lo;
+    const uint8_t* s = (side ? a.buf_b : a.msg) + lo;
+    if (wb > wa && !group_copy_bulk<PING_NST, PING_STG>(d + wa, s + wa, wb - wa, 1, lane, stage, bars, phase,
+                                                        PING_WAIT_NS)) {
+      if (lane == 0) s_fail = 1;
+    }
+    // barrier, then one cumulative release by thread 0 (no per-thread fence)
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0) atomicExch(a.abort, 1u);
+      return;
+    }
+    if (threadIdx.x == 0) red_add_rel(mine, 1ull);
+    if (side == 0 && !wait_peer(k)) return;  // A: wait for the echo of round k
+  }
+  if (side == 0 && g == 0 && threadIdx.x == 0) a.times[1] = gtime();
+}
+
 }  // namespace hicr
 
 using namespace hicr;
@@ -95,6 +165,16 @@ hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, 
   int per_sm = 0;
   HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pingpong, 512, 0));
   if (2ull * ctas_per_side > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
+  // large messages, agents of at most half the SMs: the bulk-copy form
+  bool bulk = 2ull * ctas_per_side <= (unsigned long long)in->sm_count &&
+              bytes / (16ull * ctas_per_side) >= PING_BULK_MIN;
+  if (bulk) {
+    int per_sm_b = 0;
+    HICR_CUDA(in, cudaFuncSetAttribute((const void*)k_pingpong_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)PING_SMEM));
+    HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, k_pingpong_bulk, 512, PING_SMEM));
+    bulk = 2ull * ctas_per_side <= (unsigned long long)per_sm_b * in->sm_count;
+  }
   void* sp = nullptr;
   uint64_t ssize = 0;
   uint32_t sspace = 0;
@@ -138,7 +218,9 @@ hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, 
   a.abort = abort_flag;
   void* args[] = {&a};
   if (e == cudaSuccess)
-    e = cudaLaunchCooperativeKernel((const void*)k_pingpong, dim3(2 * ctas_per_side), dim3(512), args, 0, cs);
+    e = bulk ? cudaLaunchCooperativeKernel((const void*)k_pingpong_bulk, dim3(2 * ctas_per_side), dim3(512), args,
+                                           PING_SMEM, cs)
+             : cudaLaunchCooperativeKernel((const void*)k_pingpong, dim3(2 * ctas_per_side), dim3(512), args, 0, cs);
   unsigned long long ht[2] = {0, 0};
   unsigned int hab = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(ht, times, 16, cudaMemcpyDeviceToHost, cs);

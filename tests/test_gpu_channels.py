@@ -232,21 +232,26 @@ def test_mpsc_stream_odd_staging_and_empty_messages(h, inst, nonlocking, gap):
     run.free()
 
 
-@pytest.mark.parametrize("nbytes,ctas", [(1, 1), (17, 1), (4096, 2), ((1 << 20) + 3, 8), (64 << 20, 32),
-                                         ((64 << 20) + 5, 152)])
-def test_pingpong_delivers_the_message(h, inst, nbytes, ctas):
+@pytest.mark.parametrize("nbytes,ctas,off", [
+    (1, 1, 7), (17, 1, 7), (4096, 2, 7), ((1 << 20) + 3, 8, 7), ((64 << 20) + 5, 152, 7),
+    # agents of at most half the SMs with >= 64 KiB per warp: the bulk-copy form
+    # (from an unaligned source the send falls back to the warp copy, the echo does not)
+    (64 << 20, 32, 7), ((128 << 20) + 9, 64, 0), ((96 << 20) + 1, 76, 16),
+])
+def test_pingpong_delivers_the_message(h, inst, nbytes, ctas, off):
     """Test Case 1 restated on one GPU: after the round trips both
     single-message buffers hold exactly the message (oracle digest)."""
     size = nbytes + 100
     st, s = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
     assert h.hicr_util_fill(inst, s, 0, size, splitmix.fill_key_base(5, 1)) == 0
-    st, r = h.hicr_pingpong(inst, s, 7, nbytes, reps=10, warmup=2, ctas_per_side=ctas)
+    st, r = h.hicr_pingpong(inst, s, off, nbytes, reps=10, warmup=2, ctas_per_side=ctas)
     assert st == 0 and r.status == 0
-    exp = od.byte_digest(splitmix.fill_bytes(5, 1, 7, nbytes))
+    exp = od.byte_digest(splitmix.fill_bytes(5, 1, off, nbytes))
     assert r.digest_a == exp and r.digest_b == exp
     assert r.half_rtt_ns > 0 and r.goodput_gbs > 0
     assert h.hicr_pingpong(inst, s, 200, size, 1, 0, 1)[0] == h.HICR_ERR_BOUNDS
     assert h.hicr_pingpong(inst, s, 0, 16, 1, 0, 257)[0] == h.HICR_ERR_INVALID
+    assert h.hicr_mem_free(inst, s) == 0
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
