@@ -1037,8 +1037,9 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
     cudaFreeHost(hp);
     return cuda_fail(in, ce, "cudaMalloc(requests)");
   }
-  HICR_CUDA(in, cudaMemset(dreq, 0, sizeof(SrvReq) * (n + 1)));
-  HICR_CUDA(in, cudaMemset(sv->ctl, 0, sizeof(SrvCtl)));
+  // on the communication stream, so that the engine launched there sees them
+  HICR_CUDA(in, cudaMemsetAsync(dreq, 0, sizeof(SrvReq) * (n + 1), in->comm()));
+  HICR_CUDA(in, cudaMemsetAsync(sv->ctl, 0, sizeof(SrvCtl), in->comm()));
   SrvArgs a = sv->base;
   a.ctl = sv->ctl;
   a.req = dreq;
@@ -1064,7 +1065,7 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   const size_t n_warps = (size_t)grid * (SRV_THREADS / 32);
   unsigned int* wstate = nullptr;
   HICR_CUDA(in, cudaMalloc(&wstate, 4 * n_warps));
-  HICR_CUDA(in, cudaMemset(wstate, 0, 4 * n_warps));
+  HICR_CUDA(in, cudaMemsetAsync(wstate, 0, 4 * n_warps, in->comm()));
   a.wstate = wstate;
   if (grid < a.n_ch + 2) {
     cudaFreeHost(hp);
