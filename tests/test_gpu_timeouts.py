@@ -56,13 +56,14 @@ def test_mpsc_stream_gives_up_and_recovers(h, inst, nonlocking):
     run.free()
 
 
-def test_pingpong_gives_up_and_recovers(h, inst):
-    size = 1 << 20
+@pytest.mark.parametrize("size,ctas", [(1 << 20, 1), (128 << 20, 64)])  # vector form, bulk-copy form
+def test_pingpong_gives_up_and_recovers(h, inst, size, ctas):
     st, s = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
     assert h.hicr_util_fill(inst, s, 0, size, splitmix.fill_key_base(8, 1)) == 0
-    st, r = h.hicr_pingpong(inst, s, 0, size, 1000, 0, 1, TINY)
+    st, r = h.hicr_pingpong(inst, s, 0, size, 1000, 0, ctas, TINY)
     assert st == h.HICR_ERR_TIMEOUT
-    st, r = h.hicr_pingpong(inst, s, 0, size, 4, 1, 4)
+    st, r = h.hicr_pingpong(inst, s, 0, size, 4, 1, max(ctas, 4))
     assert st == 0 and r.status == 0
     exp = od.byte_digest(splitmix.fill_bytes(8, 1, 0, size))
     assert r.digest_a == exp and r.digest_b == exp
+    assert h.hicr_mem_free(inst, s) == 0
