@@ -1087,7 +1087,8 @@ def run_side_small(args):
     """side_small, for a one-pass capture (DRAM bytes and duration) of the
     kernels that are not profiled elsewhere: an SPSC stream (64 channels x
     10^6 tokens of 64 B, batches of 2,048), a ping-pong of 256 MiB with agents
-    of 152 CTAs (10 round trips), a 0.5 s serving trace at 20,000 req/s on
+    of 152 CTAs and one of 1 GiB with agents of 76 CTAs (the bulk-copy form;
+    10 round trips each), a 0.5 s serving trace at 20,000 req/s on
     the bench's engine set-up, and the word digest of a 4 GiB slot. Prints
     the algorithmic bytes of each so the capture can be read against them."""
     import torch
@@ -1110,6 +1111,13 @@ def run_side_small(args):
     st, r = h.hicr_pingpong(inst, sid, 0, size, 10, 2, 152)
     h.check(st, "pingpong")
     out["pingpong_algorithmic_bytes"] = 12 * 2 * 2 * size  # 12 round trips x 2 one-way copies x (read + write)
+    h.check(h.hicr_mem_free(inst, sid), "free")
+    size = 1 << 30  # the bulk-copy form: agents of 76 CTAs, one per SM
+    sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size), "alloc")
+    h.check(h.hicr_util_fill(inst, sid, 0, size, splitmix.fill_key_base(0, 7)), "fill")
+    st, r = h.hicr_pingpong(inst, sid, 0, size, 10, 2, 76)
+    h.check(st, "pingpong bulk")
+    out["pingpong_bulk_algorithmic_bytes"] = 12 * 2 * 2 * size
     h.check(h.hicr_mem_free(inst, sid), "free")
     big = 4 << 30
     sid = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, big), "alloc")
