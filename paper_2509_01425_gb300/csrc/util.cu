@@ -8,44 +8,90 @@
 namespace hicr {
 
 // Byte i of the slot (i in [off, off+n)) = byte (i mod 8), little endian, of
-// first_output(key_base + i/8). Whole 8-byte words are stored at once when
-// the slot base is 8-byte aligned.
-__global__ void k_fill(uint8_t* base, unsigned long long off, unsigned long long n, unsigned long long key_base) {
-  const unsigned long long end = off + n;
-  const unsigned long long w0 = off >> 3, w1 = (end + 7) >> 3;
+// first_output(key_base + i/8), written over the words that overlap [a, b) by
+// threads t, t + st, ...: whole 8-byte words at once when the base is 8-byte
+// aligned, bytes elsewhere.
+__device__ __forceinline__ void fill_words(uint8_t* base, unsigned long long a, unsigned long long b,
+                                           unsigned long long key_base, unsigned long long t, unsigned long long st) {
   const bool aligned = ((uintptr_t)base & 7u) == 0;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long w = w0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += stride) {
+  for (unsigned long long w = (a >> 3) + t; w < ((b + 7) >> 3); w += st) {
     const uint64_t v = sm64_first_output(key_base + w);
-    const unsigned long long b = w << 3;
-    if (aligned && b >= off && b + 8 <= end) {
-      *reinterpret_cast<uint64_t*>(base + b) = v;
+    const unsigned long long bw = w << 3;
+    if (aligned && bw >= a && bw + 8 <= b) {
+      *reinterpret_cast<uint64_t*>(base + bw) = v;
     } else {
       for (int k = 0; k < 8; ++k) {
-        const unsigned long long i = b + k;
-        if (i >= off && i < end) base[i] = (uint8_t)(v >> (8 * k));
+        const unsigned long long i = bw + k;
+        if (i >= a && i < b) base[i] = (uint8_t)(v >> (8 * k));
       }
     }
   }
 }
 
+// The fill of [off, off+n). With a 16-byte-aligned base, the 16-byte units
+// inside the range are written by one vector store each (words 2u and 2u + 1)
+// and two threads write the head and tail bytes around them.
+__global__ void k_fill(uint8_t* base, unsigned long long off, unsigned long long n, unsigned long long key_base) {
+  const unsigned long long end = off + n;
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long u0 = (off + 15) >> 4, u1 = end >> 4;  // full units inside the range
+  if (((uintptr_t)base & 15u) != 0 || u1 <= u0) {
+    fill_words(base, off, end, key_base, tid, stride);
+    return;
+  }
+  uint4* vb = reinterpret_cast<uint4*>(base);
+  for (unsigned long long u = u0 + tid; u < u1; u += stride) {
+    const uint64_t lo = sm64_first_output(key_base + 2 * u), hi = sm64_first_output(key_base + 2 * u + 1);
+    vb[u] = make_uint4((unsigned)lo, (unsigned)(lo >> 32), (unsigned)hi, (unsigned)(hi >> 32));
+  }
+  if (tid == 0) fill_words(base, off, u0 << 4, key_base, 0, 1);
+  if (tid == 1) fill_words(base, u1 << 4, end, key_base, 0, 1);
+}
+
 // out += sum_j w_j * (2j + 1) over the little-endian words of p[0, n), the
-// last word zero-padded (*out must start at zero).
+// last word zero-padded (*out must start at zero). With a 16-byte-aligned p,
+// threads read 16-byte vectors, four independent loads at a time; vector q
+// holds words 2q and 2q + 1, whose terms are (w0 + w1)(4q + 1) + 2 w1. The
+// words past the last full vector (at most two) go to thread 0.
 __global__ void k_digest(const uint8_t* p, unsigned long long n, unsigned long long* out) {
   const unsigned long long nw = (n + 7) >> 3;
-  const bool aligned = ((uintptr_t)p & 7u) == 0;
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   unsigned long long acc = 0;
-  for (unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; j < nw; j += stride) {
-    uint64_t w = 0;
+  auto word = [&](unsigned long long j) -> uint64_t {  // word j, zero-padded past n
     const unsigned long long b = j << 3;
-    if (aligned && b + 8 <= n) {
+    uint64_t w = 0;
+    if ((((uintptr_t)p & 7u) == 0) && b + 8 <= n) {
       w = *reinterpret_cast<const uint64_t*>(p + b);
     } else {
       for (int k = 0; k < 8; ++k)
         if (b + k < n) w |= (uint64_t)p[b + k] << (8 * k);
     }
-    acc += w * (2ull * j + 1ull);
+    return w;
+  };
+  if (((uintptr_t)p & 15u) == 0) {
+    const unsigned long long nv = n >> 4;
+    const uint4* pv = reinterpret_cast<const uint4*>(p);
+    for (unsigned long long q = tid; q < nv; q += 4 * stride) {
+      uint4 x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q + u * stride < nv) x[u] = __ldcs(pv + q + u * stride);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const unsigned long long qq = q + u * stride;
+        if (qq < nv) {
+          const uint64_t w0 = (uint64_t)x[u].x | ((uint64_t)x[u].y << 32);
+          const uint64_t w1 = (uint64_t)x[u].z | ((uint64_t)x[u].w << 32);
+          acc += (w0 + w1) * (4ull * qq + 1ull) + (w1 << 1);
+        }
+      }
+    }
+    if (tid == 0)
+      for (unsigned long long j = 2 * nv; j < nw; ++j) acc += word(j) * (2ull * j + 1ull);
+  } else {
+    for (unsigned long long j = tid; j < nw; j += stride) acc += word(j) * (2ull * j + 1ull);
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
