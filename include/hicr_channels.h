@@ -270,8 +270,10 @@ typedef struct {
  * buffer holds exactly one message at the consumer, so a sender never has
  * more than one message outstanding. Each agent is `ctas_per_side` CTAs (1 ..
  * 256, both agents co-resident) of one cooperative grid that copy equal
- * shares; a side's arrival count
- * is the channel head the other side acquires. `warmup` untimed round trips
+ * shares with vector loads and stores; when each agent has at most half the
+ * SMs and every warp's share is at least 64 KiB, the CTAs run one per SM and
+ * copy by bulk copies (TMA) through shared memory instead. A side's arrival
+ * count is the channel head the other side acquires. `warmup` untimed round trips
  * come first. After the run both buffers must hold the message (the digests
  * let the caller check). Every wait gives up after timeout_ns.
  * Errors: INVALID, BOUNDS, NOMEM, DEVICE, TIMEOUT. */
