@@ -1,5 +1,5 @@
 /*
- * CPU baseline for batched memcpy on all host cores -- TEST AND BASELINE
+ * CPU baseline for batched memcpy on all host cores -- TEST AND CPU-BASELINE
  * INFRASTRUCTURE ONLY (never part of the library's product path).
  *
  * What it computes: the local-to-local memcpy of the HiCR communication

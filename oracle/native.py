@@ -1,4 +1,4 @@
-"""Build and load the oracle's plain C parts -- TEST AND BASELINE
+"""Build and load the oracle's plain C parts -- TEST AND CPU-BASELINE
 INFRASTRUCTURE ONLY.
 
 ``memcpy_threads.c`` is the all-cores CPU memcpy baseline (see its header).
