@@ -22,7 +22,7 @@ LIB_NAME = "libhicr_gb300.so"
 LIB_PATH = os.path.join(HERE, LIB_NAME)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-fopenmp", "--expt-relaxed-constexpr",
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-pthread", "--expt-relaxed-constexpr",
               "-I", INCLUDE, "-I", CSRC]
 
 
@@ -69,7 +69,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
             sys.stderr.write(log)
     objs = [o for o, _ in results]
     tmp = LIB_PATH + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lcuda", "-ldl", "-lgomp"]
+    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-pthread", "-o", tmp, *objs, "-lcuda", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

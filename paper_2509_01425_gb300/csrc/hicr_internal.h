@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <chrono>
+#include <memory>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -13,6 +14,7 @@
 
 #include "../../include/hicr.h"
 #include "../../include/hicr_util.h"
+#include "host_pool.h"
 
 namespace hicr {
 
@@ -123,6 +125,7 @@ struct Instance {
 
   // hicr_memcpy queue and host-batch upload
   std::vector<hicr_op_t> queue;
+  std::unique_ptr<HostPool> pool;  // host workers for large op tables (created on first use)
   hicr_op_t* pinned[2] = {nullptr, nullptr};
   uint64_t pinned_cap[2] = {0, 0};
   cudaEvent_t pinned_ev[2] = {nullptr, nullptr};

@@ -27,7 +27,6 @@
 // takes them as kernel parameters (see SMALL_OPS).
 #include <stdio.h>
 #include <stdlib.h>
-#include <omp.h>
 #include <string.h>
 
 #include <algorithm>
@@ -476,18 +475,23 @@ static hicr_status launch_small(Instance* in, const hicr_op_t* ops, uint64_t cou
   return record_done(in);
 }
 
-// Host tables of at least this many ops are validated and staged by several
-// host threads (OpenMP); smaller ones on the calling thread.
+// Host tables of at least this many ops are validated and staged by the
+// instance's host worker pool (HostPool, up to 8 threads with the caller);
+// smaller ones on the calling thread.
 static constexpr uint64_t PAR_OPS = 8192;
-static int host_threads() { return std::min(8, omp_get_num_procs()); }
 
-// Copy a host op table to the device through a double-buffered pinned
-// staging area and launch it.
-static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
-  if (small_batch(in, ops, count)) return launch_small(in, ops, count);
-  const int k = in->pinned_idx;
-  in->pinned_idx ^= 1;
-  // the staging buffer may still feed an earlier upload
+static HostPool& host_pool(Instance* in) {
+  if (!in->pool) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    in->pool.reset(new HostPool((int)std::min(8u, hw ? hw : 1u)));
+  }
+  return *in->pool;
+}
+
+// Staging buffer k (pinned host memory) and the device op table, grown to
+// hold `count` ops; buffer k may still feed an earlier upload, so its last
+// upload is waited for first.
+static hicr_status stage_prepare(Instance* in, uint64_t count, int k) {
   HICR_CUDA(in, cudaEventSynchronize(in->pinned_ev[k]));
   if (in->pinned_cap[k] < count) {
     if (in->pinned[k]) cudaFreeHost(in->pinned[k]);
@@ -511,16 +515,12 @@ static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_
     HICR_CUDA(in, e);
     in->d_ops_cap = cap;
   }
-  if (count >= PAR_OPS) {
-    const int nt = host_threads();
-#pragma omp parallel for schedule(static) num_threads(nt)
-    for (int t = 0; t < nt; ++t) {
-      const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
-      memcpy(in->pinned[k] + a, ops + a, (b - a) * sizeof(hicr_op_t));
-    }
-  } else {
-    memcpy(in->pinned[k], ops, count * sizeof(hicr_op_t));
-  }
+  return HICR_OK;
+}
+
+// Upload the ops staged in buffer k and launch the batch on them.
+static hicr_status launch_staged(Instance* in, uint64_t count, int k) {
+  in->pinned_idx = k ^ 1;
   cudaStream_t st = in->comm();
   HICR_CUDA(in, cudaMemcpyAsync(in->d_ops, in->pinned[k], count * sizeof(hicr_op_t), cudaMemcpyHostToDevice, st));
   HICR_CUDA(in, cudaEventRecord(in->pinned_ev[k], st));
@@ -529,25 +529,56 @@ static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_
   return record_done(in);
 }
 
-static hicr_status validate_all(Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
+// Copy a host op table to the device through a double-buffered pinned
+// staging area and launch it.
+static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
+  if (small_batch(in, ops, count)) return launch_small(in, ops, count);
+  const int k = in->pinned_idx;
+  hicr_status s = stage_prepare(in, count, k);
+  if (s != HICR_OK) return s;
+  hicr_op_t* dst = in->pinned[k];
   if (count >= PAR_OPS) {
-    // every op is checked; the reported one is the first invalid in issue order
-    long long first = (long long)count;
-#pragma omp parallel for schedule(static) reduction(min : first) num_threads(host_threads())
-    for (long long i = 0; i < (long long)count; ++i)
-      if (i < first && validate_op(in, ops[i]) != HICR_OK) first = i;
-    if (first < (long long)count) {
-      if (first_bad) *first_bad = (uint64_t)first;
-      return validate_op(in, ops[first]);
-    }
+    host_pool(in).run([&](int t, int nt) {
+      const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
+      memcpy(dst + a, ops + a, (b - a) * sizeof(hicr_op_t));
+    });
   } else {
-    for (uint64_t i = 0; i < count; ++i) {
-      hicr_status s = validate_op(in, ops[i]);
-      if (s != HICR_OK) {
-        if (first_bad) *first_bad = i;
-        return s;
-      }
-    }
+    memcpy(dst, ops, count * sizeof(hicr_op_t));
+  }
+  return launch_staged(in, count, k);
+}
+
+// Index of the first invalid op of ops[a, b) (b when all are valid); with
+// `stage` the range is also copied there.
+static uint64_t validate_range(const Instance* in, const hicr_op_t* ops, uint64_t a, uint64_t b, hicr_op_t* stage) {
+  for (uint64_t i = a; i < b; ++i)
+    if (validate_op(in, ops[i]) != HICR_OK) return i;
+  if (stage) memcpy(stage + a, ops + a, (b - a) * sizeof(hicr_op_t));
+  return b;
+}
+
+// Validate every op (and, with `stage`, copy the table there) on the pool;
+// returns the index of the first invalid op in issue order, or count.
+static uint64_t validate_par(Instance* in, const hicr_op_t* ops, uint64_t count, hicr_op_t* stage) {
+  HostPool& pool = host_pool(in);
+  std::vector<uint64_t> first((size_t)pool.size(), count);
+  pool.run([&](int t, int nt) {
+    const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
+    const uint64_t f = validate_range(in, ops, a, b, stage);
+    first[t] = f < b ? f : count;
+  });
+  uint64_t f = count;
+  for (uint64_t x : first) f = std::min(f, x);
+  return f;
+}
+
+static hicr_status validate_all(Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
+  // every op is checked; the reported one is the first invalid in issue order
+  const uint64_t first = count >= PAR_OPS ? validate_par(in, ops, count, nullptr)
+                                          : validate_range(in, ops, 0, count, nullptr);
+  if (first < count) {
+    if (first_bad) *first_bad = first;
+    return validate_op(in, ops[first]);
   }
   if (in->checked) {
     uint64_t bad = 0;
@@ -611,6 +642,19 @@ hicr_status hicr_flush(hicr_instance_t h) {
 hicr_status hicr_memcpy_batch(hicr_instance_t h, const hicr_op_t* ops, uint64_t count, uint64_t* first_bad) {
   Instance* in = I(h);
   if (!in || (count && !ops) || in->capturing) return HICR_ERR_INVALID;
+  if (count >= PAR_OPS && !in->checked && in->queue.empty()) {
+    // one pass of the host workers validates the table and stages it for
+    // upload; nothing is launched unless every op is valid
+    const int k = in->pinned_idx;
+    hicr_status s = stage_prepare(in, count, k);
+    if (s != HICR_OK) return s;
+    const uint64_t first = validate_par(in, ops, count, in->pinned[k]);
+    if (first < count) {
+      if (first_bad) *first_bad = first;
+      return validate_op(in, ops[first]);
+    }
+    return launch_staged(in, count, k);
+  }
   hicr_status s = validate_all(in, ops, count, first_bad);
   if (s != HICR_OK) return s;
   if (count == 0) return HICR_OK;
