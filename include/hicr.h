@@ -192,7 +192,11 @@ hicr_status hicr_flush(hicr_instance_t inst);
  * batch (persistent size-binned copy kernel). On a validation error nothing is
  * launched and *first_bad (if not NULL) receives the index of the first bad op.
  * With checked mode on (hicr_set_checked) cross-op hazards are rejected too
- * (HAZARD). The op array may be reused when the call returns. */
+ * (HAZARD). The op array may be reused when the call returns. Tables of
+ * 8,192 ops or more are validated and staged by the instance's host worker
+ * threads (up to 8 with the caller, started on first use); they spin, yielding,
+ * for up to 5 ms after each such call before they block, so that batches
+ * issued one fence apart find them awake. */
 hicr_status hicr_memcpy_batch(hicr_instance_t inst, const hicr_op_t* ops, uint64_t count,
                               uint64_t* first_bad);
 
