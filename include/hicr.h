@@ -224,9 +224,10 @@ hicr_status hicr_memcpy_batch_device(hicr_instance_t inst, const hicr_op_t* d_op
  *    that every GPU which loads the library holds until the process exits.
  *  - count <= HICR_NOALLOC_MAX_OPS, otherwise HICR_ERR_TOO_LARGE and nothing
  *    is launched.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress, with the instance's device current); make that
- *    first call before any stream capture begins.
+ *  - hicr_init looks up the array's device address (cudaGetSymbolAddress,
+ *    with the instance's device current) and loads the kernels this call
+ *    launches, so that under lazy module loading neither the array's
+ *    placement nor a kernel load falls on a call of this function.
  *  - Every call, from every instance on the device, shares the one array,
  *    which keeps the last call's contents: calls whose work overlaps on the
  *    GPU race. Issue them on one stream, or order them with events.

@@ -13,8 +13,11 @@ path (the C-ABI library and its Python binding) must never call into it.
 Modules
   memcpy    -- memory slots, memcpy(dst, dOff, src, sOff, n), fence and the
                sent/received message counters (HiCR paper Sec. 3.1.3-3.1.4, Fig. 5).
-  channels  -- SPSC and MPSC (locking mode) circular-buffer channels
+  channels  -- SPSC and MPSC (locking and non-locking mode) circular-buffer
+               channels and the interleaving-agnostic log checkers
                (HiCR paper Sec. 4.3, Channels frontend).
+  dataobject -- the Data Object frontend: publish / getHandle / get
+               (HiCR paper Sec. 4.3).
   digest    -- the position-weighted word digest the checkers compare.
-  serving   -- expected per-request results of the serving loop.
+  native    -- builds memcpy_threads.c, the all-cores CPU memcpy baseline.
 """

@@ -12,7 +12,12 @@
 // refilled only after the store that read it has finished reading
 // (cp.async.bulk.wait_group.read). The unaligned head and the sub-16-byte tail
 // go through the vector warp copy. Every mbarrier wait is bounded; one that
-// gives up records HICR_ERR_TIMEOUT for the op in the sticky batch error.
+// gives up records HICR_ERR_TIMEOUT for the op in the sticky batch error,
+// first waits (each wait bounded again) for the warp's loads still in flight
+// so that no bulk copy writes into the stages after the warp has left them,
+// and leaves the op uncounted: its sent/recv/tag counters are not bumped and
+// its destination bytes are undefined, which the next fence reports as
+// TIMEOUT.
 #include "copy.cuh"
 #include "hicr_internal.h"
 #include "tma.cuh"
@@ -60,7 +65,20 @@ __device__ bool tma_body(uint8_t* d, const uint8_t* s, unsigned long long n, uin
         }
       }
     }
-    if (!ok) break;
+    if (!ok) {
+      // Pieces p .. last_issued have loads in flight, one per stage; wait
+      // for each (bounded) before the stages can be left behind.
+      const unsigned long long last = (p + NST - 1 < np ? p + NST - 1 : np - 1);
+      for (unsigned long long r = p; r <= last; ++r) {
+        const unsigned kr = (unsigned)(r % NST);
+        const unsigned long long t1 = tma_now_ns();
+        while (!mbar_try_wait(bars + kr, (phase >> kr) & 1u)) {
+          if (tma_now_ns() - t1 > TMA_WAIT_NS) break;
+        }
+        phase ^= 1u << kr;
+      }
+      break;
+    }
     phase ^= 1u << k;
     tma_store(d + p * STG, stage + k * STG, piece_bytes(p));
     tma_commit();
@@ -103,6 +121,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
       const unsigned long long be = bs + op.n;
       const unsigned long long b0 = lo > bs ? lo - bs : 0ull;
       const unsigned long long b1 = (hi < be ? hi : be) > bs ? (hi < be ? hi : be) - bs : 0ull;
+      int piece_done = 1;  // cleared (warp-uniformly) when this piece's bulk copy gave up
       if (b1 > b0) {
         uint8_t* d = reinterpret_cast<uint8_t*>(a.dt.slot_base[op.dst]) + op.dst_off + b0;
         const uint8_t* s = reinterpret_cast<const uint8_t*>(a.dt.slot_base[op.src]) + op.src_off + b0;
@@ -120,6 +139,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
           ok = __shfl_sync(FULLM_COPY, ok, 0);
           if (!ok) {
             tma_ok = 0;
+            piece_done = 0;
             if (lane == 0) atomicCAS(a.dt.sticky, 0ull, (i << 8) | (unsigned long long)(-HICR_ERR_TIMEOUT));
           }
         } else {
@@ -129,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
       const unsigned pieces = (unsigned)((be - 1) / chunk - cs / chunk + 1);
       __threadfence();
       __syncwarp();
-      if (lane == 0) {
+      if (lane == 0 && piece_done) {
         const unsigned prev = atomicAdd(&a.done[i], 1u);
         if (prev + 1 == pieces) {
           __threadfence();
@@ -159,6 +179,14 @@ static const void* tma_kernel(unsigned nst, unsigned stg) {
   HICR_TMA_SHAPES(HICR_TMA_PICK)
 #undef HICR_TMA_PICK
   return nullptr;
+}
+
+hicr_status copy_tma_load_all(Instance* in) {
+  cudaFuncAttributes fa;
+#define HICR_TMA_LOAD(N, S) HICR_CUDA(in, cudaFuncGetAttributes(&fa, (const void*)k_copy_tma<N, S>));
+  HICR_TMA_SHAPES(HICR_TMA_LOAD)
+#undef HICR_TMA_LOAD
+  return HICR_OK;
 }
 
 bool copy_tma_shape_valid(const hicr_batch_config_t& c) {

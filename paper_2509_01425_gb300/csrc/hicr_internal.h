@@ -184,6 +184,11 @@ size_t copy_tma_smem(const hicr_batch_config_t& c);
 hicr_status copy_tma_prepare(Instance* in, const hicr_batch_config_t& c, int* blocks_per_sm);
 hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, const hicr_batch_config_t& c, unsigned grid,
                             cudaStream_t st);
+// Loads every stage shape of the TMA engine (cudaFuncGetAttributes).
+hicr_status copy_tma_load_all(Instance* in);
+// memcpy_noalloc.cu: per-device set-up of the allocation-free entry point
+// (device address of its static scratch array, kernels loaded); hicr_init.
+hicr_status noalloc_setup(Instance* in);
 hicr_status record_done(Instance* in);
 hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns);
 void default_config(Instance* in, hicr_batch_config_t* c);

@@ -45,22 +45,40 @@ static constexpr int NA_MAX_DEVICES = 64;
 static unsigned long long* g_na_ptr[NA_MAX_DEVICES] = {nullptr};
 static std::mutex g_na_mutex;
 
-static hicr_status noalloc_scratch(Instance* in, unsigned long long** out) {
+// Set-up, called by hicr_init with the instance's device current: look up
+// the array's device address once per device. Under lazy module loading this
+// lookup is what loads the module and places the array, so it must not wait
+// for the entry point's first call. The kernels the entry point launches are
+// loaded here too (cudaFuncGetAttributes loads a function), so that no call
+// of it has to load code either.
+hicr_status noalloc_setup(Instance* in) {
   if (in->device < 0 || in->device >= NA_MAX_DEVICES) return HICR_ERR_INVALID;
   std::lock_guard<std::mutex> lock(g_na_mutex);
   if (!g_na_ptr[in->device]) {
-    int prev = 0;
-    HICR_CUDA(in, cudaGetDevice(&prev));
-    HICR_CUDA(in, cudaSetDevice(in->device));
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, hicr_noalloc_scratch);
-    cudaError_t e2 = cudaSetDevice(prev);
     if (e != cudaSuccess) return cuda_fail(in, e, "cudaGetSymbolAddress(hicr_noalloc_scratch)");
-    if (e2 != cudaSuccess) return cuda_fail(in, e2, "cudaSetDevice");
     if (!p) return HICR_ERR_DEVICE;
+    cudaFuncAttributes fa;
+    const void* fns[] = {(const void*)k_plan, (const void*)k_scan, (const void*)k_copy};
+    for (const void* f : fns) HICR_CUDA(in, cudaFuncGetAttributes(&fa, f));
+    hicr_status s = copy_tma_load_all(in);
+    if (s != HICR_OK) return s;
     g_na_ptr[in->device] = (unsigned long long*)p;
   }
-  *out = g_na_ptr[in->device];
+  return HICR_OK;
+}
+
+static hicr_status noalloc_scratch(Instance* in, unsigned long long** out) {
+  if (in->device < 0 || in->device >= NA_MAX_DEVICES) return HICR_ERR_INVALID;
+  unsigned long long* p = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    p = g_na_ptr[in->device];
+  }
+  // hicr_init resolved it; an instance whose set-up failed never reaches here
+  if (!p) return HICR_ERR_INVALID;
+  *out = p;
   return HICR_OK;
 }
 

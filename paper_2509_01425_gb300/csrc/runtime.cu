@@ -208,6 +208,12 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   cudaEventRecord(in->pinned_ev[0], pu0.stream);
   cudaEventRecord(in->pinned_ev[1], pu0.stream);
   default_config(in, &in->cfg);
+  if (noalloc_setup(in) != HICR_OK) {
+    cudaFreeHost(in->sticky_host);
+    cudaStreamDestroy(pu0.stream);
+    cudaFree(in->dt.slot_base);
+    return fail(HICR_ERR_DEVICE);
+  }
   if (cudaDeviceSynchronize() != cudaSuccess) return fail(HICR_ERR_DEVICE);
   *out = h;
   return HICR_OK;

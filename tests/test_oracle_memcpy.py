@@ -124,6 +124,65 @@ def test_batch_all_or_nothing():
     assert cm.memcpy_batch(ops[:1], checked=True) == (om.OK, None)
 
 
+def _touch_sets(op):
+    """The (slot, byte) pairs an op writes and reads, spelled out byte by byte."""
+    dst, doff, src, soff, n = op
+    return {(dst, doff + i) for i in range(n)}, {(src, soff + i) for i in range(n)}
+
+
+def _first_hazard_plain(ops):
+    """Two ops conflict iff some byte written by one is read or written by the
+    other; the answer is the first op (issue order) that conflicts with an
+    earlier one."""
+    sets = [_touch_sets(o) for o in ops]
+    for j in range(len(ops)):
+        wj, rj = sets[j]
+        for i in range(j):
+            wi, ri = sets[i]
+            if wi & (wj | rj) or wj & ri:
+                return j
+    return None
+
+
+def _as_table(ops):
+    return configs.make_ops([o[0] for o in ops], [o[2] for o in ops], [o[1] for o in ops],
+                            [o[3] for o in ops], [o[4] for o in ops])
+
+
+def test_first_hazard_equals_the_byte_set_construction():
+    """first_hazard pinned in both directions: every hazard the byte sets show
+    is reported (none missed) and nothing else is (no src/src overlap, no
+    adjacent-but-disjoint ranges, no zero-size op counts). All ordered pairs
+    of ops on two 32-byte slots with offsets and sizes at the interesting
+    corners, then random triples over every offset and size."""
+    size = 32
+    offs = [0, 1, 7, 15, 16, 17, 24, 31]
+    ns = [0, 1, 2, 8, 15, 16, 17]
+    singles = [(d, do, s, so, n) for d in (0, 1) for s in (0, 1) for n in ns for do in offs for so in offs
+               if do + n <= size and so + n <= size]
+    rng = np.random.default_rng(11)
+    pairs = [(singles[a], singles[b]) for a, b in rng.integers(0, len(singles), size=(12000, 2))]
+    hits = 0
+    for ops in pairs:
+        exp = _first_hazard_plain(ops)
+        hits += exp is not None
+        assert om.first_hazard(_as_table(ops)) == exp, ops
+    assert 0.1 * len(pairs) < hits < 0.9 * len(pairs)
+    for _ in range(3000):
+        ops = []
+        for _ in range(3):
+            n = int(rng.integers(0, 12))
+            ops.append((int(rng.integers(0, 2)), int(rng.integers(0, size - n + 1)), int(rng.integers(0, 2)),
+                        int(rng.integers(0, size - n + 1)), n))
+        assert om.first_hazard(_as_table(ops)) == _first_hazard_plain(ops), ops
+    # the corners an over-strict checker would flag
+    assert om.first_hazard(_as_table([(1, 0, 0, 0, 8), (1, 8, 0, 0, 8)])) is None     # adjacent dsts, shared src
+    assert om.first_hazard(_as_table([(1, 0, 0, 4, 8), (1, 8, 0, 8, 8)])) is None     # overlapping srcs only
+    assert om.first_hazard(_as_table([(1, 0, 0, 0, 8), (0, 8, 1, 8, 4)])) is None     # dst next to a src
+    assert om.first_hazard(_as_table([(1, 4, 0, 0, 0), (1, 0, 0, 0, 8)])) is None     # zero-size op inside
+    assert om.first_hazard(_as_table([(1, 0, 0, 0, 8), (0, 0, 1, 7, 1)])) == 1        # one-byte read of a dst
+
+
 def _hazard_free_sets(rng, k, size=64):
     while True:
         ops = []

@@ -6,8 +6,11 @@ cannot absorb cudaMalloc's implicit synchronisation). They use
 hicr_memcpy_batch_noalloc, whose scratch is a static device array instead of
 cudaMalloc'd memory. Here both entry points run the same op tables on two
 identically filled sets of slots and must leave identical bytes and counters,
-on two calls in a row; an oversized batch is rejected, and an invalid batch
-reports its error without disturbing the next call.
+on two calls in a row, and both must equal the CPU oracle byte for byte; a
+batch of exactly the maximum op count runs, an oversized batch is rejected,
+an invalid batch (also one whose bad op is the last of a maximum-size table)
+reports its error and index without disturbing the next call, and repeated
+calls leave the device's free memory unchanged.
 
 This file is collected last so a run that stops at the first failure has
 already run every other test; it also passes on its own in a fresh process.
@@ -16,8 +19,9 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import memcpy as om
 from workloads import configs, splitmix
-from tests.gpu_util import device_bytes, h, inst  # noqa: F401
+from tests.gpu_util import device_bytes, h, inst, slot_bytes  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +45,19 @@ def _table(ops, ids):
     return torch.from_numpy(o.view(np.uint8).copy()).cuda()
 
 
+def _oracle(w, seed):
+    cm = om.CommManager()
+    for s, sz in enumerate(w.slot_sizes):
+        assert cm.register(om.SPACE_HBM, splitmix.fill_bytes(seed, s, 0, int(sz))) == s
+    return cm
+
+
+def _matches_oracle(h, inst, ids, cm):
+    for k, sid in enumerate(ids):
+        assert (slot_bytes(h, inst, sid) == cm.slots[k].data).all(), f"slot {k} differs from the oracle"
+        assert h.hicr_slot_counters(inst, sid)[1:] == cm.counters(k), k
+
+
 def _same(h, inst, a_ids, b_ids):
     for a, b in zip(a_ids, b_ids):
         _, pa, na, _, _ = h.hicr_slot_info(inst, a)
@@ -61,6 +78,7 @@ def test_noalloc_matches_device_batch_twice(h, inst, engine):
     assert len(w.epochs) >= 2
     a_ids = _slots(h, inst, w, 5)   # written by the no-allocation entry point
     b_ids = _slots(h, inst, w, 5)   # written by hicr_memcpy_batch_device
+    cm = _oracle(w, 5)
     for call, (lo, hi) in enumerate(w.epochs[:2]):
         count = min(hi - lo, h.HICR_NOALLOC_MAX_OPS)
         ta, tb = _table(w.ops[lo:lo + count], a_ids), _table(w.ops[lo:lo + count], b_ids)
@@ -69,8 +87,54 @@ def test_noalloc_matches_device_batch_twice(h, inst, engine):
         assert h.hicr_memcpy_batch_device(inst, tb.data_ptr(), count) == 0
         assert h.hicr_fence(inst, 0, T) == 0
         _same(h, inst, a_ids, b_ids)
+        assert cm.memcpy_batch(w.ops[lo:lo + count]) == (om.OK, None)
+        _matches_oracle(h, inst, a_ids, cm)
         s, r = h.hicr_slot_counters_range(inst, a_ids[0], len(a_ids))[1:]
         assert int(s.sum()) == int(r.sum()) > 0
+
+
+def test_noalloc_at_the_op_limit(h, inst):
+    """Exactly HICR_NOALLOC_MAX_OPS ops: the last words of the static array's
+    regions (prefix sums, piece counters) are in use, and the single-CTA scan
+    runs full per-thread runs. A bad op at the last index is reported with
+    that index and copies nothing; the good table then equals the oracle."""
+    n = h.HICR_NOALLOC_MAX_OPS
+    w = configs.tiny(9, slot_bytes=2 << 20, n_ops=n, max_n=48)
+    assert len(w.ops) == n
+    ids = _slots(h, inst, w, 9)
+    cm = _oracle(w, 9)
+    bad = w.ops.copy()
+    bad["n"][n - 1] = int(w.slot_sizes[bad["src"][n - 1]]) + 1
+    tbad = _table(bad, ids)
+    assert h.hicr_memcpy_batch_noalloc(inst, tbad.data_ptr(), n) == 0
+    assert h.hicr_batch_error(inst) == (0, h.HICR_ERR_BOUNDS, n - 1)
+    assert h.hicr_fence(inst, 0, T) == 0
+    _matches_oracle(h, inst, ids, cm)  # nothing copied, counters untouched
+    t = _table(w.ops, ids)
+    for _ in range(2):
+        assert h.hicr_memcpy_batch_noalloc(inst, t.data_ptr(), n) == 0
+        assert h.hicr_fence(inst, 0, T) == 0
+        assert cm.memcpy_batch(w.ops) == (om.OK, None)
+        _matches_oracle(h, inst, ids, cm)
+
+
+def test_noalloc_calls_leave_device_memory_untouched(h, inst):
+    """The point of the entry point: after a first call, further calls (and
+    the fences that complete them) do not change the device's free memory."""
+    w = configs.batched(8, n_slots=4, total_bytes=32 << 20, slot_lo=4 << 20, slot_hi=16 << 20,
+                        n_ops=3000, n_lo=16, n_hi=256 << 10)
+    ids = _slots(h, inst, w, 8)
+    lo, hi = w.epochs[0]
+    t = _table(w.ops[lo:hi], ids)
+    assert h.hicr_memcpy_batch_noalloc(inst, t.data_ptr(), hi - lo) == 0
+    assert h.hicr_fence(inst, 0, T) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        assert h.hicr_memcpy_batch_noalloc(inst, t.data_ptr(), hi - lo) == 0
+        assert h.hicr_fence(inst, 0, T) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
 
 
 def test_noalloc_rejects_oversize_and_recovers_from_a_bad_batch(h, inst):
