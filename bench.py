@@ -252,7 +252,10 @@ class MpscRun:
             padded = sizes + np.uint64(stage_gap)
         offs = np.zeros(len(sizes), dtype=np.uint64)
         offs[1:] = np.cumsum(padded)[:-1]
-        self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, max(int(padded.sum()), 16)), "staging")
+        self.staging_bytes = max(int(padded.sum()), 16)
+        self.offs = offs
+        self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, self.staging_bytes), "staging")
+        self.capture = None
         p = np.repeat(np.arange(P, dtype=np.uint64), M)
         q = np.tile(np.arange(M, dtype=np.uint64), P)
         keys = (np.uint64(1) << np.uint64(63)) | (p << np.uint64(40)) | (q << np.uint64(16))
@@ -285,15 +288,23 @@ class MpscRun:
         self.chans = [h.check(create(self.inst, per, self.ring_bytes, self.max_msgs), "mpsc_create")
                       for _ in range(w.n_consumers)]
 
-    def run(self, timeout_ns=60_000_000_000):
+    def run(self, timeout_ns=60_000_000_000, capture=False):
+        """One streaming run. With capture=True the consumers also copy every
+        message they consumed into ``self.capture`` (zeroed first), message
+        (p, s) at the same offset as its staged payload."""
+        import torch
         P, M = self.w.sizes.shape
+        kw = {}
+        if capture:
+            self.capture = torch.zeros(self.staging_bytes, dtype=torch.uint8, device="cuda")
+            kw = dict(d_capture=self.capture.data_ptr(), d_cap_off=self.d_offs.data_ptr())
         if self.nonlocking:
             return self.h.hicr_mpsc_nl_stream(self.inst, self.chans, P, M, self.d_sizes.data_ptr(),
                                               self.d_offs.data_ptr(), self.staging, self.group, self.consumer_ctas,
-                                              self.d_log.data_ptr(), self.stride, timeout_ns)
+                                              self.d_log.data_ptr(), self.stride, timeout_ns, **kw)
         return self.h.hicr_mpsc_stream(self.inst, self.chans, P, M, self.d_sizes.data_ptr(), self.d_offs.data_ptr(),
                                        self.staging, self.group, self.consumer_ctas, self.d_log.data_ptr(),
-                                       self.stride, timeout_ns)
+                                       self.stride, timeout_ns, **kw)
 
     def logs(self):
         a = self.d_log.cpu().numpy().view(self.h.MPSC_LOG_DTYPE)
@@ -304,6 +315,7 @@ class MpscRun:
             self.h.check(self.h.hicr_channel_destroy(self.inst, c), "channel_destroy")
         self.h.check(self.h.hicr_mem_free(self.inst, self.staging), "mem_free")
         self.chans = []
+        self.capture = None
 
 
 def bench_spsc(h, inst, reps=3):
@@ -550,7 +562,10 @@ class ServeSetup:
         padded = ((sizes + np.uint64(15)) // np.uint64(16)) * np.uint64(16)
         offs = np.zeros(len(sizes), dtype=np.uint64)
         offs[1:] = np.cumsum(padded)[:-1]
-        self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, max(int(padded.sum()), 16)), "staging")
+        self.staging_bytes = max(int(padded.sum()), 16)
+        self.offs = offs
+        self.staging = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, self.staging_bytes), "staging")
+        self.capture = None
         nt = len(tmpl.msg_start) - 1
         tt = np.repeat(np.arange(nt, dtype=np.uint64), np.diff(tmpl.msg_start))
         mm = np.concatenate([np.arange(c, dtype=np.uint64) for c in np.diff(tmpl.msg_start)])

@@ -181,6 +181,36 @@ typedef struct {
 hicr_status hicr_spsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
                              uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results);
 
+/* Options of hicr_spsc_stream_ex. */
+typedef struct {
+  hicr_slot_t src;         /* HBM slot the producers copy tokens from (when src_tokens > 0) */
+  uint32_t reserved;
+  uint64_t src_off;        /* byte offset in src of channel 0's staged tokens (16-byte aligned address) */
+  uint64_t src_tokens;     /* tokens staged per channel: channel i's at src_off + i * src_tokens *
+                              token_size; 0 = the producers write the payload rule instead */
+  void* d_capture;         /* device buffer (16-byte aligned), or NULL: token s consumed from the
+                              i-th channel of the call is stored at d_capture + i * capture_stride +
+                              s * token_size */
+  uint64_t capture_stride; /* multiple of 16, >= tokens * token_size */
+} hicr_spsc_stream_opts_t;
+
+/* hicr_spsc_stream with two more forms, chosen by `opts`:
+ *  - copy producers (src_tokens > 0): a push is what Sec. 4.3 makes it, a
+ *    copy from a memory slot into the consumer's ring; token s of the i-th
+ *    channel is token (s mod src_tokens) of that channel's staged tokens. The
+ *    consumer does not check words against the payload rule (mismatches is
+ *    0); it digests the consumed stream as always;
+ *  - capture (d_capture != NULL): the consumer also stores every token it
+ *    consumed, in consumption order, so that a caller can compare the
+ *    delivered stream token by token (tests; it adds a write per token).
+ * All channels must have the same token size when either form is used.
+ * Errors: as hicr_spsc_stream, plus INVALID (NULL opts, unaligned or short
+ * capture area, unaligned staged tokens), UNSUPPORTED (src not in HBM), BOUNDS
+ * (staged tokens outside src). */
+hicr_status hicr_spsc_stream_ex(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                                uint32_t batch, const hicr_spsc_stream_opts_t* opts, uint64_t timeout_ns,
+                                hicr_spsc_result_t* results);
+
 /* One consumed MPSC message, as the consumer logs it in ticket order. */
 typedef struct {
   uint32_t producer;
@@ -249,6 +279,26 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t inst, const hicr_channel_t* chan
                                 uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
                                 uint64_t log_stride, hicr_mpsc_result_t* results);
 
+/* Capture forms of the two streaming runs: the same run, and each consumer
+ * also copies every message it consumed, before freeing its ring space, to
+ * d_capture + d_cap_off[p * msgs_per_producer + s] (device buffer and device
+ * array of u64 offsets chosen by the caller; message (p, s)'s bytes must fit
+ * there), so that the delivered payloads can be compared byte by byte (tests;
+ * each message is read once more). Errors: as the plain forms, plus INVALID
+ * (NULL d_capture or d_cap_off). */
+hicr_status hicr_mpsc_stream_capture(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
+                                     uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                     const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                     uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                     uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                     const uint64_t* d_cap_off);
+hicr_status hicr_mpsc_nl_stream_capture(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n_consumers,
+                                        uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                        const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                        uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                        uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                        const uint64_t* d_cap_off);
+
 /* ------------------------------------------------------------------------ */
 /* Ping-pong over two opposing single-message SPSC channels (HiCR paper      */
 /* Sec. 5.1, Test Case 1, restated for one GPU).                             */
@@ -279,6 +329,14 @@ typedef struct {
  * Errors: INVALID, BOUNDS, NOMEM, DEVICE, TIMEOUT. */
 hicr_status hicr_pingpong(hicr_instance_t inst, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
                           uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out);
+
+/* hicr_pingpong, then both agents' buffers (`bytes` each) are copied to the
+ * device buffers d_out_a and d_out_b, so that a caller can compare what each
+ * agent last received byte by byte. Errors: as hicr_pingpong, plus INVALID
+ * (a NULL output buffer). */
+hicr_status hicr_pingpong_capture(hicr_instance_t inst, hicr_slot_t src, uint64_t src_off, uint64_t bytes,
+                                  uint32_t reps, uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns,
+                                  void* d_out_a, void* d_out_b, hicr_pingpong_result_t* out);
 
 #ifdef __cplusplus
 }

@@ -83,6 +83,21 @@ __device__ __forceinline__ bool aborted(const unsigned int* abort) {
 }
 __host__ __device__ __forceinline__ unsigned long long round16(unsigned long long n) { return (n + 15) & ~15ull; }
 
+// Capture mode of the streaming consumers: copy n bytes of a consumed message
+// from the ring (written by producers on other SMs, so read at L2) to the
+// caller's capture buffer, with the whole warp.
+__device__ __forceinline__ void capture_copy(uint8_t* __restrict__ d, const uint8_t* __restrict__ s,
+                                             unsigned long long n, unsigned lane) {
+  unsigned long long q0 = 0;
+  if ((((uintptr_t)d | (uintptr_t)s) & 15u) == 0) {
+    const unsigned long long nv = n / 16;
+    for (unsigned long long q = lane; q < nv; q += 32)
+      reinterpret_cast<uint4*>(d)[q] = __ldcg(reinterpret_cast<const uint4*>(s) + q);
+    q0 = nv * 16;
+  }
+  for (unsigned long long q = q0 + lane; q < n; q += 32) d[q] = __ldcg(s + q);
+}
+
 // Register-staged producer copy into a channel ring (the serving engine's
 // burst producers; the streaming kernels use group_copy_bulk below): when
 // source and destination are both 16-byte aligned, every lane keeps 16 vector

@@ -151,14 +151,25 @@ __global__ void __launch_bounds__(512, 1) k_pingpong_bulk(PingArgs a) {
   if (side == 0 && g == 0 && threadIdx.x == 0) a.times[1] = gtime();
 }
 
-}  // namespace hicr
+// Capture mode: copies both single-message buffers out after the run (one
+// warp per 64 KiB piece of a buffer).
+__global__ void k_pp_capture(const uint8_t* buf_a, const uint8_t* buf_b, uint8_t* out_a, uint8_t* out_b,
+                             unsigned long long bytes) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned long long piece = 64ull << 10;
+  const unsigned long long np = (bytes + piece - 1) / piece;
+  const unsigned long long nw = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  for (unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < 2 * np;
+       w += nw) {
+    const unsigned long long q = w % np, lo = q * piece, n = min(piece, bytes - lo);
+    if (w < np) warp_copy(out_a + lo, buf_a + lo, n, lane);
+    else warp_copy(out_b + lo, buf_b + lo, n, lane);
+  }
+}
 
-using namespace hicr;
-
-extern "C" {
-
-hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
-                          uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out) {
+static hicr_status pingpong_run(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
+                                uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, void* cap_a,
+                                void* cap_b, hicr_pingpong_result_t* out) {
   Instance* in = I(h);
   if (!in || !out || reps == 0 || ctas_per_side == 0 || ctas_per_side > 256 || bytes == 0 || in->capturing)
     return HICR_ERR_INVALID;
@@ -240,6 +251,14 @@ hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, 
   const double dt = (double)(ht[1] - ht[0]);
   r.half_rtt_ns = hab ? 0.0 : dt / (2.0 * reps);
   r.goodput_gbs = r.half_rtt_ns > 0 ? (double)bytes / r.half_rtt_ns : 0.0;
+  if (cap_a) {
+    k_pp_capture<<<in->sm_count * 2, 512, 0, cs>>>(bufs, bufs + half, (uint8_t*)cap_a, (uint8_t*)cap_b, bytes);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      cudaFree(bufs);
+      return cuda_fail(in, e, "pingpong capture");
+    }
+  }
   hicr_slot_t sa = 0, sb = 0;
   st = hicr_slot_register(h, HICR_SPACE_HBM, bufs, bytes, 0, &sa);
   if (st == HICR_OK) st = hicr_slot_register(h, HICR_SPACE_HBM, bufs + half, bytes, 0, &sb);
@@ -252,6 +271,24 @@ hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, 
   if (st != HICR_OK) return st;
   *out = r;
   return r.status;
+}
+
+}  // namespace hicr
+
+using namespace hicr;
+
+extern "C" {
+
+hicr_status hicr_pingpong(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
+                          uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, hicr_pingpong_result_t* out) {
+  return pingpong_run(h, src, src_off, bytes, reps, warmup, ctas_per_side, timeout_ns, nullptr, nullptr, out);
+}
+
+hicr_status hicr_pingpong_capture(hicr_instance_t h, hicr_slot_t src, uint64_t src_off, uint64_t bytes, uint32_t reps,
+                                  uint32_t warmup, uint32_t ctas_per_side, uint64_t timeout_ns, void* d_out_a,
+                                  void* d_out_b, hicr_pingpong_result_t* out) {
+  if (!d_out_a || !d_out_b) return HICR_ERR_INVALID;
+  return pingpong_run(h, src, src_off, bytes, reps, warmup, ctas_per_side, timeout_ns, d_out_a, d_out_b, out);
 }
 
 }  // extern "C"

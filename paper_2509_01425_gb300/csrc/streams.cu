@@ -19,6 +19,16 @@ namespace hicr {
 
 // ---------------------------------------------------------------------------
 // SPSC streaming: CTA 2i produces into channel i, CTA 2i+1 consumes it.
+// Template switches:
+//   COPY     the producer pushes by copying token s of channel i from the
+//            staging area (token s mod src_tokens of the channel's staged
+//            tokens), the channel push the paper defines (a memcpy into the
+//            consumer's buffer); otherwise it writes the payload rule's words;
+//   VERIFY   the consumer compares every word with the payload rule;
+//   CAPTURE  the consumer also stores every token it consumed, in order, to
+//            the capture area (token s of channel i at cap + i * cap_stride +
+//            s * token_size), so that the tokens can be compared one by one.
+// The consumer always folds the consumed words into the digest.
 // ---------------------------------------------------------------------------
 struct SpscStreamArgs {
   const SpscView* chans;
@@ -28,10 +38,24 @@ struct SpscStreamArgs {
   unsigned long long timeout_ns;
   hicr_spsc_result_t* res;
   unsigned int* abort;
+  const uint8_t* src;              // COPY: channel i's staged tokens at src + i * src_tokens * ts
+  unsigned long long src_tokens;
+  uint8_t* cap;                    // CAPTURE
+  unsigned long long cap_stride;
 };
 
 static constexpr int SPSC_U = 8;
 
+__device__ __forceinline__ uint4 words_to_vec(unsigned long long w0, unsigned long long w1) {
+  uint4 x;
+  x.x = (unsigned)w0;
+  x.y = (unsigned)(w0 >> 32);
+  x.z = (unsigned)w1;
+  x.w = (unsigned)(w1 >> 32);
+  return x;
+}
+
+template <bool COPY, bool VERIFY, bool CAPTURE>
 __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   __shared__ int s_stop;
   __shared__ unsigned long long s_red[2][16];
@@ -43,6 +67,9 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   const unsigned long long key0 = (unsigned long long)ci << 40;
   const unsigned long long deadline = gtime() + a.timeout_ns;
   const unsigned tid = threadIdx.x;
+  const uint8_t* src = COPY ? a.src + (unsigned long long)ci * a.src_tokens * v.ts : nullptr;
+  uint8_t* cap = CAPTURE ? a.cap + (unsigned long long)ci * a.cap_stride : nullptr;
+  const unsigned long long W = COPY ? a.src_tokens : 1;
   // The channel starts empty (head == tail); token s of this run has counter
   // value base + s and ring slot (base + s) mod capacity.
   __shared__ unsigned long long s_base;
@@ -54,6 +81,7 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   const unsigned tpi = fast ? blockDim.x / vpt : 1;  // tokens per pass of the block
   const unsigned jv = fast ? tid % vpt : 0, tl0 = fast ? tid / vpt : 0;
   const unsigned long long step = tpi % v.cap;
+  const unsigned long long sstep = tpi % W;
   unsigned long long cached = base, max_occ = 0, done = 0, mism = 0, dig = 0;
   int stop = 0;
   for (unsigned long long s0 = 0; s0 < a.tokens; s0 += a.batch) {
@@ -85,26 +113,40 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
     if (s_stop) break;
     if (fast) {
       // thread = vector column jv of tokens tl0, tl0 + tpi, ...; ring slots
-      // advance by `step` (tpi mod capacity) without a division per vector
+      // (and staged positions) advance by `step` (`sstep`) without a
+      // division per vector
       unsigned long long slot = (base + s0 + tl0) % v.cap;
+      unsigned long long sp = COPY ? (s0 + tl0) % W : 0;
       for (unsigned long long tl = tl0; tl < k; tl += (unsigned long long)SPSC_U * tpi) {
         if (producer) {
+          if (COPY) {
+            uint4 x[SPSC_U];
+            unsigned long long q = sp;
 #pragma unroll
-          for (int u = 0; u < SPSC_U; ++u) {
-            const unsigned long long t_ = tl + (unsigned long long)u * tpi;
-            if (t_ < k) {
-              const unsigned long long word = (s0 + t_) * wpt + 2ull * jv;
-              uint4* p = reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv;
-              const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
-              uint4 x;
-              x.x = (unsigned)w0;
-              x.y = (unsigned)(w0 >> 32);
-              x.z = (unsigned)w1;
-              x.w = (unsigned)(w1 >> 32);
-              *p = x;
+            for (int u = 0; u < SPSC_U; ++u) {
+              if (tl + (unsigned long long)u * tpi < k) x[u] = __ldcg(reinterpret_cast<const uint4*>(src + q * v.ts) + jv);
+              q += sstep;
+              if (q >= W) q -= W;
             }
-            slot += step;
-            if (slot >= v.cap) slot -= v.cap;
+            sp = q;
+#pragma unroll
+            for (int u = 0; u < SPSC_U; ++u) {
+              if (tl + (unsigned long long)u * tpi < k) *(reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv) = x[u];
+              slot += step;
+              if (slot >= v.cap) slot -= v.cap;
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < SPSC_U; ++u) {
+              const unsigned long long t_ = tl + (unsigned long long)u * tpi;
+              if (t_ < k) {
+                const unsigned long long word = (s0 + t_) * wpt + 2ull * jv;
+                uint4* p = reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv;
+                *p = words_to_vec(sm64_first_output(key0 + word), sm64_first_output(key0 + word + 1));
+              }
+              slot += step;
+              if (slot >= v.cap) slot -= v.cap;
+            }
           }
         } else {
           uint4 x[SPSC_U];
@@ -117,6 +159,13 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
             if (sl >= v.cap) sl -= v.cap;
           }
           slot = sl;
+          if (CAPTURE) {
+#pragma unroll
+            for (int u = 0; u < SPSC_U; ++u) {
+              const unsigned long long t_ = tl + (unsigned long long)u * tpi;
+              if (t_ < k) *(reinterpret_cast<uint4*>(cap + (s0 + t_) * v.ts) + jv) = x[u];
+            }
+          }
           // Vector u of this pass starts at word W0 + u D (D = tpi wpt), so
           // its digest term w0 (2 word + 1) + w1 (2 word + 3) sums over the
           // pass to (2 W0 + 1) S + 2 D U + 2 W1, with S = sum_u (w0 + w1),
@@ -128,10 +177,12 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
           for (int u = SPSC_U - 1; u >= 0; --u) {
             const unsigned long long t_ = tl + (unsigned long long)u * tpi;
             if (t_ < k) {
-              const unsigned long long word = W0 + (unsigned long long)u * tpi * wpt;
               const unsigned long long w0 = (unsigned long long)x[u].x | ((unsigned long long)x[u].y << 32);
               const unsigned long long w1 = (unsigned long long)x[u].z | ((unsigned long long)x[u].w << 32);
-              mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+              if (VERIFY) {
+                const unsigned long long word = W0 + (unsigned long long)u * tpi * wpt;
+                mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+              }
               S += w0 + w1;
               W1 += w1;
             }
@@ -148,18 +199,14 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
         const unsigned long long word = tok * wpt + (q % vpt) * 2;  // index of the first 8-byte word
         uint4* p = reinterpret_cast<uint4*>(v.ring + ((base + tok) % v.cap) * v.ts) + (q % vpt);
         if (producer) {
-          const unsigned long long w0 = sm64_first_output(key0 + word), w1 = sm64_first_output(key0 + word + 1);
-          uint4 x;
-          x.x = (unsigned)w0;
-          x.y = (unsigned)(w0 >> 32);
-          x.z = (unsigned)w1;
-          x.w = (unsigned)(w1 >> 32);
-          *p = x;
+          if (COPY) *p = __ldcg(reinterpret_cast<const uint4*>(src + (tok % W) * v.ts) + (q % vpt));
+          else *p = words_to_vec(sm64_first_output(key0 + word), sm64_first_output(key0 + word + 1));
         } else {
           const uint4 x = __ldcg(p);
+          if (CAPTURE) *(reinterpret_cast<uint4*>(cap + tok * v.ts) + (q % vpt)) = x;
           const unsigned long long w0 = (unsigned long long)x.x | ((unsigned long long)x.y << 32);
           const unsigned long long w1 = (unsigned long long)x.z | ((unsigned long long)x.w << 32);
-          mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
+          if (VERIFY) mism += (w0 != sm64_first_output(key0 + word)) + (w1 != sm64_first_output(key0 + word + 1));
           dig += (w0 + w1) * (2ull * word + 1ull) + (w1 << 1);
         }
       }
@@ -223,6 +270,8 @@ struct MpscStreamArgs {
   const unsigned long long* base;  // per consumer: first ticket of the run
   unsigned int pw;                 // producer warps per producer CTA
   const int* bad;                  // verdict of the pre-stream check (nonzero: the run does not start)
+  uint8_t* cap;                    // capture mode: message (p, s) is copied to cap + cap_off[p * mpp + s]
+  const unsigned long long* cap_off;
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
@@ -511,6 +560,17 @@ __device__ void mpsc_consumer(const MpscStreamArgs& a, unsigned c, unsigned long
           }
         }
       }
+      // capture mode: warp w copies messages w, w + nwarp, ... of the window
+      // out of the ring (they are freed only after the barrier below); an
+      // entry naming no message of the run is skipped (the log shows it)
+      if (a.cap) {
+        for (unsigned j = warp; j < navail; j += nwarp) {
+          if (s_prod[j] >= a.n_prod || s_seq[j] >= a.mpp) continue;
+          const unsigned long long idx = (unsigned long long)s_prod[j] * a.mpp + s_seq[j];
+          capture_copy(a.cap + a.cap_off[idx], v.ring + (s_start[j] & (v.R - 1)),
+                       min((unsigned long long)s_size[j], a.sizes[idx]), lane);
+        }
+      }
     }
     __syncthreads();
     if (s_abort_a) break;
@@ -650,6 +710,8 @@ struct NlStreamArgs {
   unsigned int* abort;
   unsigned int pw;  // producer warps per producer CTA
   const int* bad;   // verdict of the pre-stream check (nonzero: the run does not start)
+  uint8_t* cap;     // capture mode, as in MpscStreamArgs
+  const unsigned long long* cap_off;
 };
 
 __device__ void nl_producer(const NlStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline,
@@ -818,6 +880,17 @@ __device__ void nl_consumer_warp(const NlStreamArgs& a, unsigned c, unsigned gw,
         stop = 1;
         break;
       }
+      if (a.cap) {  // capture mode: copy the batch's messages out before they are freed
+        const unsigned long long p = (unsigned long long)ring * a.n_cons + c;
+        for (unsigned j = 0; j < k; ++j) {
+          const unsigned long long sj = __shfl_sync(FULLM, e_start, j);
+          const unsigned long long nj = __shfl_sync(FULLM, (unsigned long long)e_size, j);
+          const unsigned long long qj = __shfl_sync(FULLM, (unsigned long long)e_seq, j);
+          if (p >= a.n_prod || qj >= a.mpp) continue;
+          const unsigned long long idx = p * a.mpp + qj;
+          capture_copy(a.cap + a.cap_off[idx], rb + (sj & (v.R - 1)), min(nj, a.sizes[idx]), lane);
+        }
+      }
       if (lane < k) {
         hicr_mpsc_log_t E;
         E.producer = ring * a.n_cons + c;
@@ -908,18 +981,44 @@ __global__ void k_nl_stream_marks(const NlView* v, unsigned n, hicr_mpsc_result_
 
 using namespace hicr;
 
-extern "C" {
+namespace hicr {
 
-hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
-                             uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results) {
+// One SPSC streaming run; opts == nullptr is the generate-and-verify form.
+static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                                   uint32_t batch, const hicr_spsc_stream_opts_t* opts, uint64_t timeout_ns,
+                                   hicr_spsc_result_t* results) {
   hicr::NvtxRange nvtx_range("hicr_spsc_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || n == 0 || batch == 0 || in->capturing) return HICR_ERR_INVALID;
   std::vector<SpscView> views(n);
+  uint32_t ts = 0;
   for (uint32_t i = 0; i < n; ++i) {
     Channel* c = get(in, chans[i]);
     if (!c || c->kind != 0 || c->token_size % 16 || batch > c->capacity) return HICR_ERR_INVALID;
+    if (i > 0 && c->token_size != ts && opts && (opts->src_tokens || opts->d_capture)) return HICR_ERR_INVALID;
+    ts = c->token_size;
     views[i] = spsc_view(c);
+  }
+  const bool copy = opts && opts->src_tokens > 0;
+  const bool capture = opts && opts->d_capture != nullptr;
+  const uint8_t* src = nullptr;
+  if (copy) {
+    // the staged tokens of all n channels lie inside the source slot, in HBM,
+    // 16-byte aligned (the producers load 16-byte vectors)
+    void* sp = nullptr;
+    uint64_t ssize = 0;
+    uint32_t sspace = 0;
+    if (hicr_slot_info(h, opts->src, &sp, &ssize, &sspace, nullptr) != HICR_OK) return HICR_ERR_INVALID;
+    if (sspace != HICR_SPACE_HBM) return HICR_ERR_UNSUPPORTED;
+    const unsigned __int128 need = (unsigned __int128)opts->src_tokens * ts * n;
+    if (opts->src_off > ssize || need > (unsigned __int128)(ssize - opts->src_off)) return HICR_ERR_BOUNDS;
+    src = (const uint8_t*)sp + opts->src_off;
+    if ((uintptr_t)src & 15u) return HICR_ERR_INVALID;
+  }
+  if (capture) {
+    if (((uintptr_t)opts->d_capture & 15u) || (opts->capture_stride & 15u) ||
+        (unsigned __int128)tokens * ts > (unsigned __int128)opts->capture_stride)
+      return HICR_ERR_INVALID;
   }
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
@@ -939,8 +1038,15 @@ hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   a.timeout_ns = timeout_ns;
   a.res = (hicr_spsc_result_t*)(p + vb);
   a.abort = (unsigned int*)(p + vb + rb);
+  a.src = src;
+  a.src_tokens = copy ? opts->src_tokens : 0;
+  a.cap = capture ? (uint8_t*)opts->d_capture : nullptr;
+  a.cap_stride = capture ? opts->capture_stride : 0;
+  const void* k;
+  if (copy) k = capture ? (const void*)k_spsc_stream<true, false, true> : (const void*)k_spsc_stream<true, false, false>;
+  else k = capture ? (const void*)k_spsc_stream<false, true, true> : (const void*)k_spsc_stream<false, true, false>;
   void* args[] = {&a};
-  HICR_CUDA(in, cudaLaunchCooperativeKernel((const void*)k_spsc_stream, dim3(2 * n), dim3(512), args, 0, s));
+  HICR_CUDA(in, cudaLaunchCooperativeKernel(k, dim3(2 * n), dim3(512), args, 0, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, rb, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   if ((st = record_done(in)) != HICR_OK) return st;
@@ -948,6 +1054,26 @@ hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
     if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
   return HICR_OK;
 }
+
+}  // namespace hicr
+
+extern "C" {
+
+hicr_status hicr_spsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                             uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results) {
+  return spsc_stream_run(h, chans, n, tokens, batch, nullptr, timeout_ns, results);
+}
+
+hicr_status hicr_spsc_stream_ex(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
+                                uint32_t batch, const hicr_spsc_stream_opts_t* opts, uint64_t timeout_ns,
+                                hicr_spsc_result_t* results) {
+  if (!opts) return HICR_ERR_INVALID;
+  return spsc_stream_run(h, chans, n, tokens, batch, opts, timeout_ns, results);
+}
+
+}  // extern "C"
+
+namespace hicr {
 
 // Grid of a streaming launch: the consumer CTAs first, then the producer
 // CTAs (one warp per producer), spread over every CTA slot the consumers leave
@@ -968,16 +1094,18 @@ static unsigned long long stream_grid(unsigned long long cons_ctas, unsigned lon
   return cons_ctas + (n_prod + *pw - 1) / *pw;
 }
 
-hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
-                             uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
-                             const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
-                             uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
-                             uint64_t log_stride, hicr_mpsc_result_t* results) {
+static hicr_status mpsc_stream_run(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                   uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                   const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                   uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                   uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                   const uint64_t* d_cap_off) {
   hicr::NvtxRange nvtx_range("hicr_mpsc_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
       group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)
     return HICR_ERR_INVALID;
+  if (d_capture && !d_cap_off) return HICR_ERR_INVALID;
   void* sp = nullptr;
   uint64_t ssize = 0;
   uint32_t sspace = 0;
@@ -1036,6 +1164,8 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   a.pw = pw;
   int* bad = (int*)(p + vb + rb + 128);
   a.bad = bad;
+  a.cap = (uint8_t*)d_capture;
+  a.cap_off = (const unsigned long long*)d_cap_off;
   // the check's verdict stays on the device: a rejected run's CTAs leave at
   // once, and the host reads the verdict with the results
   k_mpsc_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
@@ -1057,16 +1187,18 @@ hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uin
   return HICR_OK;
 }
 
-hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
-                                uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
-                                const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
-                                uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
-                                uint64_t log_stride, hicr_mpsc_result_t* results) {
+static hicr_status nl_stream_run(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                 uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                 const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                 uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                 uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                 const uint64_t* d_cap_off) {
   hicr::NvtxRange nvtx_range("hicr_mpsc_nl_stream");
   Instance* in = I(h);
   if (!in || !chans || !results || !d_sizes || !d_src_off || !d_log || n_consumers == 0 || n_producers == 0 ||
       group == 0 || group > (uint32_t)MPSC_MAX_GROUP || consumer_ctas == 0 || in->capturing)
     return HICR_ERR_INVALID;
+  if (d_capture && !d_cap_off) return HICR_ERR_INVALID;
   void* sp = nullptr;
   uint64_t ssize = 0;
   uint32_t sspace = 0;
@@ -1121,6 +1253,8 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
   a.pw = pw;
   int* bad = (int*)(p + vb + rb + cb + 128);
   a.bad = bad;
+  a.cap = (uint8_t*)d_capture;
+  a.cap_off = (const unsigned long long*)d_cap_off;
   // the check's verdict stays on the device (see hicr_mpsc_stream)
   k_nl_stream_prep<<<1, 256, 0, s>>>((const NlView*)p, n_consumers);
   k_nl_check<<<in->sm_count * 4, 256, 0, s>>>(a, ssize, bad);
@@ -1140,6 +1274,50 @@ hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, 
   for (uint32_t i = 0; i < n_consumers; ++i)
     if (results[i].status != HICR_OK) return HICR_ERR_TIMEOUT;
   return HICR_OK;
+}
+
+}  // namespace hicr
+
+extern "C" {
+
+hicr_status hicr_mpsc_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                             uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                             const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                             uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                             uint64_t log_stride, hicr_mpsc_result_t* results) {
+  return mpsc_stream_run(h, chans, n_consumers, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                         consumer_ctas, timeout_ns, d_log, log_stride, results, nullptr, nullptr);
+}
+
+hicr_status hicr_mpsc_stream_capture(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                     uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                     const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                     uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                     uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                     const uint64_t* d_cap_off) {
+  if (!d_capture) return HICR_ERR_INVALID;
+  return mpsc_stream_run(h, chans, n_consumers, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                         consumer_ctas, timeout_ns, d_log, log_stride, results, d_capture, d_cap_off);
+}
+
+hicr_status hicr_mpsc_nl_stream(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                uint64_t log_stride, hicr_mpsc_result_t* results) {
+  return nl_stream_run(h, chans, n_consumers, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                       consumer_ctas, timeout_ns, d_log, log_stride, results, nullptr, nullptr);
+}
+
+hicr_status hicr_mpsc_nl_stream_capture(hicr_instance_t h, const hicr_channel_t* chans, uint32_t n_consumers,
+                                        uint32_t n_producers, uint32_t msgs_per_producer, const uint64_t* d_sizes,
+                                        const uint64_t* d_src_off, hicr_slot_t staging, uint32_t group,
+                                        uint32_t consumer_ctas, uint64_t timeout_ns, hicr_mpsc_log_t* d_log,
+                                        uint64_t log_stride, hicr_mpsc_result_t* results, void* d_capture,
+                                        const uint64_t* d_cap_off) {
+  if (!d_capture) return HICR_ERR_INVALID;
+  return nl_stream_run(h, chans, n_consumers, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                       consumer_ctas, timeout_ns, d_log, log_stride, results, d_capture, d_cap_off);
 }
 
 }  // extern "C"

@@ -482,6 +482,18 @@ _channel_depth = _decl("hicr_channel_depth", [H, u32, C.POINTER(u64), C.POINTER(
 _spsc_stream = _decl("hicr_spsc_stream", [H, vp, u32, u64, u32, u64, vp])
 _mpsc_stream = _decl("hicr_mpsc_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp])
 _mpsc_nl_stream = _decl("hicr_mpsc_nl_stream", [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp])
+_mpsc_stream_capture = _decl("hicr_mpsc_stream_capture",
+                             [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp, vp, vp])
+_mpsc_nl_stream_capture = _decl("hicr_mpsc_nl_stream_capture",
+                                [H, vp, u32, u32, u32, vp, vp, u32, u32, u32, u64, vp, u64, vp, vp, vp])
+
+
+class hicr_spsc_stream_opts_t(C.Structure):
+    _fields_ = [("src", u32), ("reserved", u32), ("src_off", u64), ("src_tokens", u64), ("d_capture", vp),
+                ("capture_stride", u64)]
+
+
+_spsc_stream_ex = _decl("hicr_spsc_stream_ex", [H, vp, u32, u64, u32, C.POINTER(hicr_spsc_stream_opts_t), u64, vp])
 
 
 class hicr_pingpong_result_t(C.Structure):
@@ -491,11 +503,21 @@ class hicr_pingpong_result_t(C.Structure):
 
 
 _pingpong = _decl("hicr_pingpong", [H, u32, u64, u64, u32, u32, u32, u64, C.POINTER(hicr_pingpong_result_t)])
+_pingpong_capture = _decl("hicr_pingpong_capture", [H, u32, u64, u64, u32, u32, u32, u64, vp, vp,
+                                                    C.POINTER(hicr_pingpong_result_t)])
 
 
 def hicr_pingpong(inst, src, src_off, nbytes, reps=10, warmup=2, ctas_per_side=1, timeout_ns=30_000_000_000):
     r = hicr_pingpong_result_t()
     st = _pingpong(inst, src, src_off, nbytes, reps, warmup, ctas_per_side, timeout_ns, C.byref(r))
+    return st, r
+
+
+def hicr_pingpong_capture(inst, src, src_off, nbytes, d_out_a, d_out_b, reps=10, warmup=2, ctas_per_side=1,
+                          timeout_ns=30_000_000_000):
+    r = hicr_pingpong_result_t()
+    st = _pingpong_capture(inst, src, src_off, nbytes, reps, warmup, ctas_per_side, timeout_ns, _ptr(d_out_a),
+                           _ptr(d_out_b), C.byref(r))
     return st, r
 
 
@@ -568,23 +590,41 @@ def hicr_spsc_stream(inst, chans, tokens, batch, timeout_ns=60_000_000_000):
     return st, list(res)
 
 
+def hicr_spsc_stream_ex(inst, chans, tokens, batch, src=0, src_off=0, src_tokens=0, d_capture=None,
+                        capture_stride=0, timeout_ns=60_000_000_000):
+    arr = (u32 * len(chans))(*chans)
+    res = (hicr_spsc_result_t * len(chans))()
+    o = hicr_spsc_stream_opts_t(src, 0, src_off, src_tokens, _ptr(d_capture), capture_stride)
+    st = _spsc_stream_ex(inst, C.addressof(arr), len(chans), tokens, batch, C.byref(o), timeout_ns, C.addressof(res))
+    return st, list(res)
+
+
 def hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
-                     consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000):
+                     consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000, d_capture=None, d_cap_off=None):
+    """With d_capture / d_cap_off this calls hicr_mpsc_stream_capture."""
     arr = (u32 * len(chans))(*chans)
     res = (hicr_mpsc_result_t * len(chans))()
-    st = _mpsc_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
-                      _ptr(d_src_off), staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride,
-                      C.addressof(res))
+    args = (inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes), _ptr(d_src_off),
+            staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
+    if d_capture is None:
+        st = _mpsc_stream(*args)
+    else:
+        st = _mpsc_stream_capture(*args, _ptr(d_capture), _ptr(d_cap_off))
     return st, list(res)
 
 
 def hicr_mpsc_nl_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
-                        consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000):
+                        consumer_ctas, d_log, log_stride, timeout_ns=120_000_000_000, d_capture=None,
+                        d_cap_off=None):
+    """With d_capture / d_cap_off this calls hicr_mpsc_nl_stream_capture."""
     arr = (u32 * len(chans))(*chans)
     res = (hicr_mpsc_result_t * len(chans))()
-    st = _mpsc_nl_stream(inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes),
-                         _ptr(d_src_off), staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride,
-                         C.addressof(res))
+    args = (inst, C.addressof(arr), len(chans), n_producers, msgs_per_producer, _ptr(d_sizes), _ptr(d_src_off),
+            staging, group, consumer_ctas, timeout_ns, _ptr(d_log), log_stride, C.addressof(res))
+    if d_capture is None:
+        st = _mpsc_nl_stream(*args)
+    else:
+        st = _mpsc_nl_stream_capture(*args, _ptr(d_capture), _ptr(d_cap_off))
     return st, list(res)
 
 

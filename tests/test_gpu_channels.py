@@ -3,10 +3,13 @@
 Host calls (push / peek / pop / depth) are deterministic and must match the
 oracle exactly: statuses, ring offsets, sizes, producers, sequence numbers
 and payload bytes. Device streaming runs interleave producers freely: the
-SPSC stream must deliver the exact token stream (digest of every word), the
-MPSC stream must pass the interleaving-agnostic checker (multiset, per-
-producer order, sizes, ring offsets replayed from the placement rule) and
-carry the exact payloads (digests), without ever exceeding capacity.
+SPSC stream must deliver the exact token stream, the MPSC stream must pass
+the interleaving-agnostic checker (multiset, per-producer order, sizes, ring
+offsets replayed from the placement rule) without ever exceeding capacity.
+What the consumers received is compared with what the oracle delivers byte
+by byte: the streams' capture forms store every consumed token or message,
+and the ping-pong's capture form both agents' buffers. The digests are
+checked as well, as an extra.
 """
 import numpy as np
 import pytest
@@ -145,6 +148,25 @@ def _spsc_expected_digest(channel, tokens, wpt=8):
     return d
 
 
+def _spsc_through_oracle(stream: np.ndarray, ts: int, cap: int) -> np.ndarray:
+    """Push the tokens of `stream` through the SPSC oracle (capacity `cap`) in
+    batches of up to `cap` tokens, popping each batch: the bytes the oracle
+    delivers, in order."""
+    orc = oc.SpscOracle(ts, cap)
+    out = []
+    n = len(stream) // ts
+    for t0 in range(0, n, cap):
+        k = min(cap, n - t0)
+        assert orc.push(stream[t0 * ts:(t0 + k) * ts]) == om.OK
+        out.extend(orc.token(j) for j in range(k))
+        assert orc.pop(k) == om.OK
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.uint8)
+
+
+def _rule_stream(channel, tokens, ts):
+    return splitmix.spsc_token_words(channel, 0, tokens, ts // 8).astype("<u8").view(np.uint8)
+
+
 @pytest.mark.parametrize("n_ch,cap,ts,tokens,batch", [
     (64, 4096, 64, 100_000, 256),
     (8, 16, 64, 1003, 16),
@@ -153,17 +175,113 @@ def _spsc_expected_digest(channel, tokens, wpt=8):
     (3, 100, 48, 2_000, 7),          # 3 vectors per token: the general (non-divisible) layout
 ])
 def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
+    """The consumers' captured streams equal, token by token, the payload-rule
+    stream pushed through the SPSC oracle (every channel of the small cases;
+    the first and last channel of the 64-channel case, whose other channels
+    are compared with the payload rule's words directly)."""
     chans = [h.hicr_spsc_create(inst, ts, cap)[1] for _ in range(n_ch)]
-    st, res = h.hicr_spsc_stream(inst, chans, tokens, batch)
+    cap_buf = torch.zeros(n_ch * tokens * ts, dtype=torch.uint8, device="cuda")
+    st, res = h.hicr_spsc_stream_ex(inst, chans, tokens, batch, d_capture=cap_buf.data_ptr(),
+                                    capture_stride=tokens * ts)
     assert st == 0
+    got = cap_buf.cpu().numpy().reshape(n_ch, tokens * ts)
     for i, r in enumerate(res):
         assert (r.pushed, r.popped, r.mismatches, r.status) == (tokens, tokens, 0, 0)
         assert 0 < r.max_occupancy <= cap
         assert r.digest == _spsc_expected_digest(i, tokens, ts // 8), i
         assert h.hicr_channel_depth(inst, chans[i])[1] == 0
+        exp = _rule_stream(i, tokens, ts)
+        if n_ch <= 8 or i in (0, n_ch - 1):
+            exp = _spsc_through_oracle(exp, ts, cap)
+        bad = np.nonzero(got[i] != exp)[0]
+        assert len(bad) == 0, f"channel {i}: {len(bad)} bytes differ, first in token {bad[0] // ts}"
     # a second run continues from the channels' counters
     st, res2 = h.hicr_spsc_stream(inst, chans[:1], 100, min(batch, 100))
     assert st == 0 and res2[0].digest == _spsc_expected_digest(0, 100, ts // 8)
+
+
+@pytest.mark.parametrize("n_ch,cap,ts,tokens,batch,staged", [
+    (16, 4096, 64, 50_000, 256, 4096),
+    (4, 16, 64, 1003, 16, 7),
+    (3, 64, 32, 5000, 1, 64),
+    (2, 100, 48, 2_000, 7, 33),      # the general layout
+    (1, 8, 16, 333, 8, 1),
+])
+def test_spsc_copy_producers_deliver_the_staged_tokens(h, inst, n_ch, cap, ts, tokens, batch, staged):
+    """Producers that push by copying from a memory slot (Sec. 4.3): token s
+    of channel i is staged token (s mod staged) of that channel; the captured
+    stream equals that sequence pushed through the SPSC oracle, and the digest
+    equals the oracle digest of those words."""
+    rng = np.random.default_rng(ts * 1000 + n_ch)
+    pool = rng.integers(0, 256, n_ch * staged * ts + 16, dtype=np.uint8)
+    s, keep = src_slot(h, inst, pool)
+    chans = [h.hicr_spsc_create(inst, ts, cap)[1] for _ in range(n_ch)]
+    cap_buf = torch.zeros(n_ch * tokens * ts, dtype=torch.uint8, device="cuda")
+    st, res = h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=16, src_tokens=staged,
+                                    d_capture=cap_buf.data_ptr(), capture_stride=tokens * ts)
+    assert st == 0
+    got = cap_buf.cpu().numpy().reshape(n_ch, tokens * ts)
+    for i, r in enumerate(res):
+        assert (r.pushed, r.popped, r.mismatches, r.status) == (tokens, tokens, 0, 0)
+        mine = pool[16 + i * staged * ts:16 + (i + 1) * staged * ts].reshape(staged, ts)
+        pushed = mine[np.arange(tokens) % staged].reshape(-1)
+        exp = _spsc_through_oracle(pushed, ts, cap) if tokens * n_ch <= 200_000 else pushed
+        assert (got[i] == exp).all(), i
+        assert r.digest == od.byte_digest(exp), i
+    # without capture the same run gives the same digests
+    st, res2 = h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=16, src_tokens=staged)
+    assert st == 0 and [r.digest for r in res2] == [r.digest for r in res]
+    # staged tokens outside the slot, and an unaligned staging address
+    assert h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=32, src_tokens=staged)[0] == \
+        h.HICR_ERR_BOUNDS
+    assert h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=8, src_tokens=staged)[0] == \
+        h.HICR_ERR_INVALID
+
+
+def _oracle_deliveries(w, ring, max_msgs, nonlocking):
+    """What the channel oracle delivers, message by message: for each consumer
+    c, its producers (c, c + C, ...) push their messages round-robin into one
+    oracle channel (locking: MpscOracle, one shared ring; non-locking:
+    MpscNonLockingOracle, a ring per producer); whenever a push finds no room
+    the consumer pops everything buffered, and it drains the channel at the
+    end. Returns {(producer, seq): the payload bytes popped}."""
+    P, M = w.sizes.shape
+    out = {}
+    for c in range(w.n_consumers):
+        prods = list(range(c, P, w.n_consumers))
+        orc = (oc.MpscNonLockingOracle if nonlocking else oc.MpscOracle)(len(prods), ring, max_msgs)
+
+        def drain():
+            while orc.depth()[0]:
+                st, (_, n, k, s) = orc.peek(0)
+                out[(prods[k], s)] = orc.payload(0)
+                assert len(out[(prods[k], s)]) == n and orc.pop(1) == om.OK
+
+        for s in range(M):
+            for k, p in enumerate(prods):
+                data = splitmix.mpsc_payload_bytes(p, s, int(w.sizes[p, s]))
+                st = orc.push(k, data)
+                if st == om.ERR_FULL:
+                    drain()
+                    st = orc.push(k, data)
+                assert st == om.OK, (c, p, s, st)
+        drain()
+    return out
+
+
+def _check_capture(w, run, deliveries):
+    """The capture buffer holds every message the GPU consumers received at
+    its staging offset, and zeros elsewhere: compare it with the oracle's
+    deliveries byte by byte."""
+    got = run.capture.cpu().numpy()
+    exp = np.zeros_like(got)
+    P, M = w.sizes.shape
+    assert len(deliveries) == P * M
+    for (p, s), data in deliveries.items():
+        o = int(run.offs[p * M + s])
+        exp[o:o + len(data)] = data
+    bad = np.nonzero(got != exp)[0]
+    assert len(bad) == 0, f"{len(bad)} captured bytes differ from the oracle's deliveries, first at {bad[0]}"
 
 
 def _check_mpsc(w, logs, res, ring, sample=1.0, seed=0):
@@ -194,9 +312,10 @@ def test_mpsc_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs, hi, 
     w = configs.mpsc(7, n_producers=P, n_consumers=C, msgs_per_producer=M, ring_bytes=ring, max_msgs=max_msgs,
                      hi=hi)
     run = bench.MpscRun(h, inst, w, group=group, consumer_ctas=ctas)
-    st, res = run.run()
+    st, res = run.run(capture=True)
     assert st == 0
     _check_mpsc(w, run.logs(), res, ring)
+    _check_capture(w, run, _oracle_deliveries(w, ring, max_msgs, False))
     # the rings wrapped (skip-to-start exercised) and are empty again
     assert sum(int(r.bytes) for r in res) > ring
     for ch in run.chans:
@@ -222,12 +341,13 @@ def test_mpsc_stream_odd_staging_and_empty_messages(h, inst, nonlocking, gap):
     w.sizes[:, ::5] = 0
     run = bench.MpscRun(h, inst, w, group=8, nonlocking=nonlocking, consumer_ctas=2, ring_bytes=ring,
                         max_msgs=max_msgs, stage_gap=gap)
-    st, res = run.run()
+    st, res = run.run(capture=True)
     assert st == 0
     if nonlocking:
         _check_mpsc_nl(w, run, res)
     else:
         _check_mpsc(w, run.logs(), res, ring)
+    _check_capture(w, run, _oracle_deliveries(w, ring, max_msgs, nonlocking))
     assert sum(int(r.consumed) for r in res) == w.sizes.size
     run.free()
 
@@ -244,9 +364,24 @@ def test_pingpong_delivers_the_message(h, inst, nbytes, ctas, off):
     size = nbytes + 100
     st, s = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
     assert h.hicr_util_fill(inst, s, 0, size, splitmix.fill_key_base(5, 1)) == 0
-    st, r = h.hicr_pingpong(inst, s, off, nbytes, reps=10, warmup=2, ctas_per_side=ctas)
+    out_a = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    out_b = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")
+    st, r = h.hicr_pingpong_capture(inst, s, off, nbytes, out_a.data_ptr(), out_b.data_ptr(), reps=10, warmup=2,
+                                    ctas_per_side=ctas)
     assert st == 0 and r.status == 0
-    exp = od.byte_digest(splitmix.fill_bytes(5, 1, off, nbytes))
+    # the oracle: A pushes the message into B's single-message channel, B pops
+    # it and pushes it back into A's, A pops it (two rounds suffice: every
+    # round leaves the same bytes)
+    msg = splitmix.fill_bytes(5, 1, off, nbytes)
+    ab, ba = oc.SpscOracle(nbytes, 1), oc.SpscOracle(nbytes, 1)
+    for _ in range(2):
+        assert ab.push(msg) == om.OK
+        got_b = ab.token(0)
+        assert ab.pop(1) == om.OK and ba.push(got_b) == om.OK
+        got_a = ba.token(0)
+        assert ba.pop(1) == om.OK
+    assert (out_b.cpu().numpy() == got_b).all() and (out_a.cpu().numpy() == got_a).all()
+    exp = od.byte_digest(msg)
     assert r.digest_a == exp and r.digest_b == exp
     assert r.half_rtt_ns > 0 and r.goodput_gbs > 0
     assert h.hicr_pingpong(inst, s, 200, size, 1, 0, 1)[0] == h.HICR_ERR_BOUNDS
@@ -323,9 +458,10 @@ def test_nonlocking_stream_checker_and_payloads(h, inst, P, C, M, ring, max_msgs
                      hi=hi)
     run = bench.MpscRun(h, inst, w, group=group, nonlocking=True, consumer_ctas=ctas, ring_bytes=ring,
                         max_msgs=max_msgs)
-    st, res = run.run()
+    st, res = run.run(capture=True)
     assert st == 0
     _check_mpsc_nl(w, run, res)
+    _check_capture(w, run, _oracle_deliveries(w, ring, max_msgs, True))
     # some rings wrapped (skip-to-start exercised) and all are empty again
     assert (((w.sizes + 15) // 16 * 16).sum(1) > ring).any()
     for ch in run.chans:

@@ -6,15 +6,17 @@ message fits half a ring), a reservation group size, consumer CTAs, whether
 the staged payloads are packed 16-byte aligned or `gap` bytes apart (so the
 producers' bulk copies meet every alignment and fall back where they must),
 and which messages are empty. The streams' logs must pass the oracle's
-interleaving-agnostic checker and every payload digest must equal the
-oracle's; a second run continues from the channels' counters."""
+interleaving-agnostic checker, every message the consumers received (the
+capture form) must equal the oracle's delivery byte by byte, and every
+payload digest must equal the oracle's; a second run continues from the
+channels' counters."""
 import numpy as np
 import pytest
 
 import bench
 from workloads import configs
 from tests.gpu_util import h, inst  # noqa: F401
-from tests.test_gpu_channels import _check_mpsc, _check_mpsc_nl
+from tests.test_gpu_channels import _check_capture, _check_mpsc, _check_mpsc_nl, _oracle_deliveries
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +49,7 @@ def test_random_stream_shapes(h, inst, seed, nonlocking):
     run = bench.MpscRun(h, inst, w, group=group, nonlocking=nonlocking, consumer_ctas=ctas, ring_bytes=ring,
                         max_msgs=max_msgs, stage_gap=gap)
     for rnd in range(2):
-        st, res = run.run()
+        st, res = run.run(capture=True)
         assert st == 0, (seed, rnd)
         assert sum(int(r.consumed) for r in res) == w.sizes.size
         if rnd == 0:  # positions replay from the first ticket only on the first run
@@ -55,6 +57,8 @@ def test_random_stream_shapes(h, inst, seed, nonlocking):
                 _check_mpsc_nl(w, run, res)
             else:
                 _check_mpsc(w, run.logs(), res, ring)
+            deliveries = _oracle_deliveries(w, ring, max_msgs, nonlocking)
+        _check_capture(w, run, deliveries)
     for ch in run.chans:
         assert h.hicr_channel_depth(inst, ch)[1:] == (0, 0)
     run.free()
