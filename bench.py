@@ -58,6 +58,8 @@ def parse_args(argv=None):
                    help="fraction of the batched workload (slots, bytes, ops); 1.0 = 16 GiB / 100,000 ops")
     p.add_argument("--profile-case", choices=["mpsc_small", "copy_small", "side_small", "control_small"], default=None,
                    help="run one small side case for a profiler capture, print its timings and exit")
+    p.add_argument("--copy-scale", type=float, default=0.125,
+                   help="copy_small: fraction of the batched workload to run (1.0 = the full 16 GiB / 100,000 ops)")
     p.add_argument("--batch-config", default=None,
                    help="JSON object of batch configuration fields: fixes the copy kernel's configuration "
                         "instead of autotuning (headline) or of the library default (copy_small)")
@@ -82,8 +84,11 @@ def kernel_source_sha(sources):
 
 
 def copy_traffic(kernel, alg_bytes_per_launch):
-    """DRAM bytes per launch of the copy kernel scaled from its committed ncu
-    capture, or None when there is none or the kernel's source changed since."""
+    """DRAM bytes per launch of the copy kernel: the DRAM-to-algorithmic ratio
+    of its committed ncu capture (taken on the full-size workload, whose
+    launches are the ones timed here) times the algorithmic bytes of a
+    launch; None when there is no capture or the kernel's source changed
+    since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     if not os.path.exists(path):
         return None
@@ -336,15 +341,49 @@ def bench_spsc(h, inst, reps=3):
         times.append(time.perf_counter() - t0)
         h.check(st, "spsc_stream")
         assert all(r.mismatches == 0 and r.popped == w.tokens_per_channel for r in res)
-    for c in chans:
-        h.check(h.hicr_channel_destroy(inst, c), "channel_destroy")
     t = statistics.median(times)
     tokens = w.n_channels * w.tokens_per_channel
+    # the channel as the paper defines a push (a copy from a memory slot into
+    # the consumer's ring): producers copy staged tokens (4,096 per channel,
+    # 16 MiB in all), consumers only digest
+    staged = w.capacity
+    stg = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, w.n_channels * staged * w.token_bytes), "staging")
+    h.check(h.hicr_util_fill(inst, stg, 0, w.n_channels * staged * w.token_bytes, splitmix.fill_key_base(0, 77)),
+            "fill staging")
+    ctimes = []
+    for r in range(reps + 1):
+        t0 = time.perf_counter()
+        st, res = h.hicr_spsc_stream_ex(inst, chans, w.tokens_per_channel, batch, src=stg, src_tokens=staged)
+        if r:
+            ctimes.append(time.perf_counter() - t0)
+        h.check(st, "spsc_stream copy")
+        assert all(x.popped == w.tokens_per_channel for x in res)
+    for c in chans:
+        h.check(h.hicr_channel_destroy(inst, c), "channel_destroy")
+    tc = statistics.median(ctimes)
+    # the L2 bound: this library's copy-loop probe over a 16 MiB working set
+    # (8 MiB copied into 8 MiB, passes repeated), best of 2, 4 and 8 CTAs per SM
+    l2 = 0.0
+    for ctas in (2, 4, 8):
+        ns = h.check(h.hicr_util_copy_loop(inst, stg, 8 * MiB, stg, 0, 8 * MiB, 2000, ctas), "copy loop")
+        l2 = max(l2, 2 * 8 * MiB * 2000 / ns)
+    h.check(h.hicr_mem_free(inst, stg), "free staging")
     return {"workload": "64 channels x capacity 4,096 x 64 B tokens, 10^7 tokens/channel, "
                         "1 producer + 1 consumer CTA per channel (cooperative grid)", "batch_tokens": batch,
             "msgs_per_s": tokens / t, "GB_per_s": tokens * 128 / t / 1e9, "s_per_run": t,
             "frac_of_hbm_peak": tokens * 128 / t / 1e9 / peaks()[0],
-            "bound": "L2 + handoff latency (rings total 16 MiB, L2-resident: the HBM fraction is context only)"}
+            "bound": "the consumers' SplitMix64 verification of every word (rings total 16 MiB, L2-resident: "
+                     "the HBM fraction is context only)",
+            "copy_producers": {
+                "workload": "the same channels; producers copy staged tokens (token s of a channel = staged token "
+                            "s mod 4,096; 16 MiB staged in all) into the ring, consumers digest only",
+                "msgs_per_s": tokens / tc, "s_per_run": tc,
+                "l2_GB_per_s": tokens * 192 / tc / 1e9,
+                "l2_bytes_per_token": 192,
+                "l2_copy_bound_GB_per_s": l2,
+                "frac_of_l2_copy_bound": tokens * 192 / tc / 1e9 / l2,
+                "note": "L2 traffic per token: staged read 64 B + ring write 64 B + ring read 64 B; bound = "
+                        "hicr_util_copy_loop's read+write rate over an L2-resident 16 MiB working set"}}
 
 
 def bench_pingpong(h, inst):
@@ -373,6 +412,12 @@ def bench_pingpong(h, inst):
                         "per size the fastest agent width of 1, 4, 16, 38, 76, 152 CTAs", "curve": rows}
 
 
+# NVIDIA's nominal NVLink-C2C bandwidth between Grace and the GPU: 900 GB/s in
+# both directions together, 450 GB/s each way (context for the host space;
+# the measured probes are the practical bound).
+NOMINAL_C2C_GBS = 450.0
+
+
 def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
     """Copies between HBM and page-locked Grace memory (the host memory
     space) through the copy kernels over NVLink-C2C: 4 GiB per direction in
@@ -399,6 +444,28 @@ def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
             if r:
                 times.append(time.perf_counter() - t0)
         out[name + "_GB_per_s"] = nbytes / statistics.median(times) / 1e9
+    # the link's practical one-way rates: this library's streaming probes
+    # reading, then writing, the host slot from every SM (best of 2, 4, 8 CTAs
+    # per SM), and its copy loop between the two spaces
+    probes = {}
+    for name, write in (("read_host", 0), ("write_host", 1)):
+        best = 0.0
+        for ctas in (2, 4, 8):
+            ns = h.check(h.hicr_util_stream(inst, hs, 0, nbytes, write, 1, ctas), "stream probe")
+            best = max(best, nbytes / ns)
+        probes[name + "_GB_per_s"] = best
+    for name, dst, src in (("copy_loop_hbm_to_host", hs, d), ("copy_loop_host_to_hbm", d, hs)):
+        best = 0.0
+        for ctas in (2, 4, 8):
+            ns = h.check(h.hicr_util_copy_loop(inst, dst, 0, src, 0, nbytes, 1, ctas), "copy loop")
+            best = max(best, nbytes / ns)
+        probes[name + "_GB_per_s"] = best
+    out["link_probes"] = probes
+    out["nominal_c2c_GB_per_s_per_direction"] = NOMINAL_C2C_GBS
+    out["frac_of_probe"] = {"hbm_to_host": out["hbm_to_host_GB_per_s"] / probes["write_host_GB_per_s"],
+                            "host_to_hbm": out["host_to_hbm_GB_per_s"] / probes["read_host_GB_per_s"]}
+    out["frac_of_nominal"] = {"hbm_to_host": out["hbm_to_host_GB_per_s"] / NOMINAL_C2C_GBS,
+                              "host_to_hbm": out["host_to_hbm_GB_per_s"] / NOMINAL_C2C_GBS}
     h.check(h.hicr_set_host_copies(inst, 0), "host copies off")
     h.check(h.hicr_mem_free(inst, hs), "free")
     h.check(h.hicr_mem_free(inst, d), "free")
@@ -482,7 +549,28 @@ def bench_latencies(h, inst, reps=2000):
     for sid in (a, b):
         h.check(h.hicr_mem_free(inst, sid), "free")
     out["reps"] = reps
+    out["from_c"] = latency_from_c(reps)
     return out
+
+
+def latency_from_c(reps=2000):
+    """The same small operations timed from C through the C ABI only
+    (paper_2509_01425_gb300/hicr_latency): no interpreter on the path."""
+    from paper_2509_01425_gb300 import build
+    exe = build.LATENCY_BIN
+    if not os.path.exists(exe):
+        build.build_latency_tool()
+    r = subprocess.run([exe, str(torch_device_index()), str(reps)], capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(f"hicr_latency failed: {r.stderr.strip()}")
+    d = json.loads(r.stdout)
+    d["reps"] = reps
+    return d
+
+
+def torch_device_index():
+    import torch
+    return torch.cuda.current_device()
 
 
 def _time_mpsc(h, run, reps):
@@ -1157,10 +1245,11 @@ def run_side_small(args):
 
 
 def run_copy_small(args):
-    """copy_small: the batched workload at --scale (default 1/8: 32 slots,
-    2 GiB, 12,500 ops) under the configuration --batch-config, each epoch one
-    device batch + fence; two passes, so the copy kernel launches once per
-    epoch in each (the second pass is the one to capture)."""
+    """copy_small: the batched workload at --copy-scale (default 1/8: 32
+    slots, 2 GiB, 12,500 ops; 1.0 is the full workload) under the
+    configuration --batch-config, each epoch one device batch + fence; two
+    passes, so the copy kernel launches once per epoch in each (the second
+    pass is the one to capture)."""
     import torch
     from paper_2509_01425_gb300 import build
     build.build()
@@ -1172,7 +1261,7 @@ def run_copy_small(args):
         for k, v in json.loads(args.batch_config).items():
             setattr(c, k, int(v))
         h.check(h.hicr_batch_set_config(inst, c), "set_config")
-    scale = args.scale if args.scale != 1.0 else 0.125
+    scale = args.copy_scale
     w = scaled_batched(args.seed, scale)
     ids = setup_slots(h, inst, w, args.seed)
     dops = device_ops(remap(w.ops, ids))

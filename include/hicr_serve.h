@@ -118,6 +118,26 @@ hicr_status hicr_serve_run(hicr_instance_t inst, hicr_serve_t srv, const hicr_se
                            uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
                            hicr_serve_stats_t* stats);
 
+/* hicr_serve_run with two checking aids (tests, sampled checks of long runs):
+ *  - keep: NULL or a host array of n flags; the destination region of every
+ *    memcpy request r with keep[r] != 0 is not reused after the request
+ *    completes (as every region is in verify mode), so that its bytes can be
+ *    read after the run (hicr_serve_arena, result dst_offset) or digested
+ *    (hicr_serve_digests). Kept regions stay taken for the rest of the run;
+ *  - d_capture, d_cap_off: NULL, or a device buffer and a device array of n
+ *    u64 offsets: the consumer copies message m of burst request r, as it
+ *    consumed it from the channel ring, to d_capture + d_cap_off[r] + (sum of
+ *    the sizes of the template's messages before m), unless d_cap_off[r] is
+ *    UINT64_MAX. The caller sizes the buffer.
+ * Errors: as hicr_serve_run, plus INVALID (d_capture without d_cap_off). */
+hicr_status hicr_serve_run_ex(hicr_instance_t inst, hicr_serve_t srv, const hicr_serve_request_t* reqs, uint64_t n,
+                              uint32_t mode, uint64_t timeout_ns, const uint8_t* keep, void* d_capture,
+                              const uint64_t* d_cap_off, hicr_serve_result_t* results, hicr_serve_stats_t* stats);
+
+/* The engine's destination arena as a (library-owned) HBM slot: the region of
+ * memcpy request r starts at result[r].dst_offset. Errors: INVALID. */
+hicr_status hicr_serve_arena(hicr_instance_t inst, hicr_serve_t srv, hicr_slot_t* out);
+
 /* The plain form on the same requests: one cudaMemcpyAsync per op (memcpy
  * requests) or per message into the channel ring space (bursts; no consumer),
  * in arrival order on one stream, with the same admission budget. Requests
@@ -126,9 +146,12 @@ hicr_status hicr_serve_run_plain(hicr_instance_t inst, hicr_serve_t srv, const h
                                  uint64_t n, uint64_t horizon_ns, uint64_t timeout_ns,
                                  hicr_serve_result_t* results, hicr_serve_stats_t* stats);
 
-/* After a verify-mode run: result[i].digest of every memcpy request i becomes
- * sum over its ops k of (2k+1) * word digest of op k's destination bytes.
- * Errors: INVALID (engine not in verify mode), DEVICE. */
+/* After a run that kept regions (verify mode, or keep flags of
+ * hicr_serve_run_ex; reqs and n as in that run): result[i].digest of every
+ * memcpy request i whose region was kept becomes sum over its ops k of
+ * (2k+1) * word digest of op k's destination bytes; other results are left
+ * as they are. Errors: INVALID (no region kept, or n differs from the last
+ * run), DEVICE. */
 hicr_status hicr_serve_digests(hicr_instance_t inst, hicr_serve_t srv, const hicr_serve_request_t* reqs,
                                uint64_t n, hicr_serve_result_t* results);
 

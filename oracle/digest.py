@@ -56,3 +56,38 @@ def byte_digest(b: np.ndarray) -> int:
 def combine(digests) -> int:
     """Ordered combination of part digests: sum_k D_k * (2k + 1) mod 2**64."""
     return word_digest(np.array([int(x) & MASK for x in digests], dtype=np.uint64))
+
+
+def block_digests(b: np.ndarray, block: int) -> np.ndarray:
+    """Byte digest of each consecutive ``block``-byte piece of ``b`` (a
+    multiple of 8; the last piece may be shorter), word positions counted
+    from each piece's start."""
+    b = np.asarray(b, dtype=np.uint8)
+    if block % 8:
+        raise ValueError("block must be a multiple of 8")
+    nfull = len(b) // block
+    out = np.zeros(nfull + (1 if len(b) % block else 0), dtype=np.uint64)
+    if nfull:
+        w = b[:nfull * block].view("<u8").reshape(nfull, block // 8)
+        j = np.uint64(2) * np.arange(block // 8, dtype=np.uint64) + np.uint64(1)
+        with np.errstate(over="ignore"):
+            out[:nfull] = (w * j).sum(axis=1, dtype=np.uint64)
+    if len(b) % block:
+        out[nfull] = np.uint64(byte_digest(b[nfull * block:]))
+    return out
+
+
+def segment_digests(words: np.ndarray, counts: np.ndarray) -> np.ndarray:
+    """Word digest of each consecutive segment of ``words`` (segment k has
+    ``counts[k]`` words; positions counted from the segment's start)."""
+    w = np.asarray(words, dtype=np.uint64)
+    counts = np.asarray(counts, dtype=np.int64)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    j = (np.arange(len(w), dtype=np.int64) - np.repeat(starts, counts)).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        terms = w * (np.uint64(2) * j + np.uint64(1))
+    out = np.zeros(len(counts), dtype=np.uint64)
+    nz = counts > 0
+    if nz.any():
+        out[nz] = np.add.reduceat(terms, starts[nz], dtype=np.uint64)
+    return out

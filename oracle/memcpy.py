@@ -237,6 +237,26 @@ def expected_bytes_at(ops: np.ndarray, epochs, slot: int, positions: np.ndarray,
     return result
 
 
+def final_slot_bytes(ops: np.ndarray, slot: int, initial: np.ndarray, source_bytes) -> np.ndarray:
+    """Content of ``slot`` after every op of ``ops`` in issue order, for a
+    table in which no slot is both read and written (the batched workload's
+    read-only source half): start from ``initial`` (the slot's bytes before
+    the table) and, for each op whose destination is ``slot``, in issue
+    order, set bytes [dst_off, dst_off + n) to ``source_bytes(src, src_off,
+    n)``. This is CommManager.memcpy_batch seen from one destination slot;
+    it is exact here because no op reads a byte that another op writes, so
+    every source byte keeps its initial value."""
+    if np.intersect1d(ops["dst"], ops["src"]).size:
+        raise ValueError("a slot is both read and written")
+    out = np.array(initial, dtype=np.uint8, copy=True)
+    for o in ops[ops["dst"] == slot]:  # a boolean selection keeps issue order
+        n = int(o["n"])
+        if n:
+            d = int(o["dst_off"])
+            out[d:d + n] = source_bytes(int(o["src"]), int(o["src_off"]), n)
+    return out
+
+
 def counters_from_ops(ops: np.ndarray, n_slots: int):
     """sent[s] = #ops reading slot s, recv[s] = #ops writing slot s."""
     sent = np.bincount(ops["src"].astype(np.int64), minlength=n_slots).astype(np.uint64)

@@ -39,12 +39,13 @@ def sources():
 
 def _newest_input() -> float:
     files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) \
-        + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
+        + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__), LATENCY_SRC]
     return max(os.path.getmtime(f) for f in files)
 
 
 def up_to_date() -> bool:
-    return os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _newest_input()
+    return (os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= _newest_input()
+            and os.path.exists(LATENCY_BIN))
 
 
 def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
@@ -74,7 +75,25 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB_PATH)
+    build_latency_tool()
     return LIB_PATH
+
+
+LATENCY_SRC = os.path.join(HERE, "hicr_latency.c")
+LATENCY_BIN = os.path.join(HERE, "hicr_latency")
+
+
+def build_latency_tool() -> str:
+    """The C latency harness (hicr_latency.c), linked against the library."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler for hicr_latency.c")
+    cmd = [cc, "-O2", "-std=gnu11", "-Wall", LATENCY_SRC, "-I", INCLUDE, "-L", HERE, "-lhicr_gb300",
+           "-Wl,-rpath,$ORIGIN", "-o", LATENCY_BIN]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"hicr_latency build failed:\n{r.stdout}\n{r.stderr}")
+    return LATENCY_BIN
 
 
 if __name__ == "__main__":

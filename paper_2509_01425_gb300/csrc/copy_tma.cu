@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(1024) k_copy_tma(BatchArgs a) {
       }
     }
   }
+  copy_exit(a, lane);
 }
 
 // The stage shapes the batch configuration may ask for.

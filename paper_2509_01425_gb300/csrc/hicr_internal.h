@@ -39,7 +39,24 @@ struct DevTables {
   unsigned long long* recv;        // [HICR_MAX_SLOTS]
   unsigned long long* tag_ops;     // [HICR_MAX_TAGS]
   unsigned long long* sticky;      // [2]: packed (first_bad << 8 | -status), 0 = none
+  unsigned long long* sig;         // [2]: completion signals emitted, CTA tickets of the small-batch kernel
+  unsigned long long* sig_host;    // device address of the mapped host mirror: [0] last signal, [1] sticky then
 };
+
+// Completion signal of one memcpy launch (a batch's copy kernel, a small
+// batch): called once, by the thread that finished the launch's last piece
+// of work after every other thread had finished (an exit counter). It counts
+// the signal on the device and writes its number, after the sticky batch
+// error as of now, into mapped host memory, where fences poll it. Launches
+// on the one communication stream finish in order, so the mirrored number
+// only grows.
+__device__ __forceinline__ void emit_signal(const DevTables& dt) {
+  __threadfence();
+  const unsigned long long v = atomicAdd(&dt.sig[0], 1ull) + 1ull;
+  const unsigned long long sticky = atomicAdd(dt.sticky, 0ull);
+  asm volatile("st.relaxed.sys.global.u64 [%0], %1;" ::"l"(dt.sig_host + 1), "l"(sticky) : "memory");
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(dt.sig_host), "l"(v) : "memory");
+}
 
 __host__ __device__ inline uint32_t meta_pack(uint32_t live, uint32_t space, uint32_t tag) {
   return (live & 1u) | ((space & 7u) << 1) | (tag << 8);
@@ -59,6 +76,7 @@ struct BatchCtrl {
   unsigned long long nchunks;    // chunks in this batch (0 when invalid)
   unsigned long long total;      // summed cost
   unsigned long long bad;        // packed (index << 8 | -status) of the first bad op; ~0 = none
+  unsigned long long exited;     // copy-kernel warps that have finished (the last one signals)
 };
 
 // Per-batch scratch, sized for `cap` ops.
@@ -88,6 +106,18 @@ struct BatchArgs {
   unsigned int tma_stage;
 };
 
+// The end of a copy-kernel warp (k_copy, k_copy_tma): the last warp of the
+// launch to finish emits the batch's completion signal; every op completed
+// in the launch is counted by then.
+__device__ __forceinline__ void copy_exit(const BatchArgs& a, unsigned lane) {
+  __syncwarp();
+  if (lane == 0) {
+    __threadfence();
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(&a.ctrl->exited, 1ull) + 1 == warps) emit_signal(a.dt);
+  }
+}
+
 struct HostSlot {
   uint64_t base = 0;     // device-usable address
   void* host_ptr = nullptr;
@@ -108,6 +138,7 @@ struct GraphRec {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool live = false;
+  uint64_t sigs = 0;  // completion signals one launch of the graph emits
 };
 
 struct Channel;  // channel_host.h
@@ -138,7 +169,15 @@ struct Instance {
   int checked = 0;
 
   cudaEvent_t done_ev = nullptr;  // recorded after the last issued work
-  unsigned long long* sticky_host = nullptr;  // page-locked copy of the sticky batch error, read by fences
+  // Completion signals (fence): every memcpy launch emits one; sig_mirror is
+  // the mapped host pair the device writes (last signal, sticky error then).
+  unsigned long long* sig_mirror = nullptr;
+  uint64_t sig_issued = 0;      // signals of the launches issued so far
+  uint64_t any_sig = 0;         // signal of the last launch whose tags the host does not know
+  uint64_t small_tickets = 0;   // CTAs of the small-batch kernel launched so far
+  uint64_t cap_sigs = 0;        // signals of the graph being captured
+  std::vector<uint64_t> tag_sig;  // per tag: signal of the last launch with an op of that tag
+  bool opaque = false;          // other work issued on the communication stream since the last full wait
   bool capturing = false;
   std::vector<GraphRec> graphs;
 
@@ -176,7 +215,9 @@ hicr_status first_hazard(const Instance* in, const hicr_op_t* ops, uint64_t coun
 
 // memcpy.cu
 hicr_status ensure_scratch(Instance* in, uint64_t count);
-hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st);
+// `tags`: HICR_MAX_TAGS bits of the ops' tags, or nullptr when unknown.
+hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st,
+                         const uint64_t* tags);
 // The TMA engine of the copy kernel (copy_tma.cu): dynamic shared memory per
 // CTA, one-time attribute set-up + resident CTAs per SM, launch.
 bool copy_tma_shape_valid(const hicr_batch_config_t& c);
@@ -189,7 +230,17 @@ hicr_status copy_tma_load_all(Instance* in);
 // memcpy_noalloc.cu: per-device set-up of the allocation-free entry point
 // (device address of its static scratch array, kernels loaded); hicr_init.
 hicr_status noalloc_setup(Instance* in);
+// Record the instance's done event after work on the communication stream
+// that emits no completion signal (fences then wait for all of it once).
 hicr_status record_done(Instance* in);
+// The same after a memcpy launch accounted for by note_signal.
+hicr_status record_signalled(Instance* in);
+// One more completion signal issued; `mask` (HICR_MAX_TAGS bits) holds the
+// tags of the launch's ops, or nullptr when the host does not know them.
+void note_signal(Instance* in, const uint64_t* mask);
+// Sets the bits of both slots' tags of ops[0, count) in mask (validated ops).
+void tag_mask(const Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* mask);
+static constexpr int TAG_WORDS = HICR_MAX_TAGS / 64;
 hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns);
 void default_config(Instance* in, hicr_batch_config_t* c);
 hicr_status check_config(const Instance* in, const hicr_batch_config_t* c);

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(1024) k_scan(BatchArgs a) {
     const unsigned long long bad = a.ctrl->bad;
     a.ctrl->total = total;
     a.ctrl->claim = 0;
+    a.ctrl->exited = 0;
     if (bad != NO_BAD) {
       a.ctrl->nchunks = 0;
       // keep the first failure until a fence reads it
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(PS_THREADS) k_plan_scan(BatchArgs a, unsigned 
     const unsigned long long bad = atomicAdd(&a.ctrl->bad, 0ull);
     a.ctrl->total = total;
     a.ctrl->claim = 0;
+    a.ctrl->exited = 0;
     if (bad != NO_BAD) {
       a.ctrl->nchunks = 0;
       atomicCAS(a.dt.sticky, 0ull, bad);
@@ -283,6 +285,7 @@ __global__ void __launch_bounds__(1024) k_copy(BatchArgs a) {
       }
     }
   }
+  copy_exit(a, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -349,6 +352,7 @@ hicr_status ensure_scratch(Instance* in, uint64_t count) {
   init.nchunks = 0;
   init.total = 0;
   init.bad = NO_BAD;
+  init.exited = 0;
   HICR_CUDA(in, cudaMemcpy(in->scratch.ctrl, &init, sizeof(init), cudaMemcpyHostToDevice));
   return HICR_OK;
 }
@@ -387,7 +391,8 @@ static hicr_status record_prof(Instance* in, cudaEvent_t ev, cudaStream_t st) {
   return HICR_OK;
 }
 
-hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st) {
+hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, cudaStream_t st,
+                         const uint64_t* tags) {
   hicr::NvtxRange nvtx_range("launch_batch");
   if (count == 0) return HICR_OK;
   hicr_status s = ensure_scratch(in, count);
@@ -408,8 +413,9 @@ hicr_status launch_batch(Instance* in, const hicr_op_t* d_ops, uint64_t count, c
   } else {
     k_copy<<<grid, in->cfg.threads, 0, st>>>(a);
   }
-  if (in->prof && (s = record_prof(in, e1, st)) != HICR_OK) return s;
   HICR_CUDA(in, cudaGetLastError());
+  note_signal(in, tags);  // the copy kernel is launched: its last warp will signal
+  if (in->prof && (s = record_prof(in, e1, st)) != HICR_OK) return s;
   return HICR_OK;
 }
 
@@ -425,6 +431,8 @@ struct SmallBatch {
   unsigned long long* sent;
   unsigned long long* recv;
   unsigned long long* tag_ops;
+  DevTables dt;                    // completion signal
+  unsigned long long ticket_end;   // small-batch CTA ticket of this launch's last CTA, plus one
 };
 
 __global__ void __launch_bounds__(512) k_copy_small(SmallBatch b) {
@@ -443,6 +451,10 @@ __global__ void __launch_bounds__(512) k_copy_small(SmallBatch b) {
     atomicAdd(&b.recv[b.dslot[i]], 1ull);
     atomicAdd(&b.tag_ops[b.stag[i]], 1ull);
     if (b.dtag[i] != b.stag[i]) atomicAdd(&b.tag_ops[b.dtag[i]], 1ull);
+    // CTAs draw tickets from a counter that runs across launches; the one
+    // drawing this launch's last ticket finishes it
+    __threadfence();
+    if (atomicAdd(&b.dt.sig[1], 1ull) + 1 == b.ticket_end) emit_signal(b.dt);
   }
 }
 
@@ -470,9 +482,15 @@ static hicr_status launch_small(Instance* in, const hicr_op_t* ops, uint64_t cou
   b.sent = in->dt.sent;
   b.recv = in->dt.recv;
   b.tag_ops = in->dt.tag_ops;
+  b.dt = in->dt;
+  b.ticket_end = in->small_tickets + count;
   k_copy_small<<<(unsigned)count, 512, 0, in->comm()>>>(b);
   HICR_CUDA(in, cudaGetLastError());
-  return record_done(in);
+  in->small_tickets += count;
+  uint64_t mask[TAG_WORDS] = {};
+  tag_mask(in, ops, count, mask);
+  note_signal(in, mask);
+  return record_signalled(in);
 }
 
 // Host tables of at least this many ops are validated and staged by the
@@ -519,14 +537,14 @@ static hicr_status stage_prepare(Instance* in, uint64_t count, int k) {
 }
 
 // Upload the ops staged in buffer k and launch the batch on them.
-static hicr_status launch_staged(Instance* in, uint64_t count, int k) {
+static hicr_status launch_staged(Instance* in, uint64_t count, int k, const uint64_t* tags) {
   in->pinned_idx = k ^ 1;
   cudaStream_t st = in->comm();
   HICR_CUDA(in, cudaMemcpyAsync(in->d_ops, in->pinned[k], count * sizeof(hicr_op_t), cudaMemcpyHostToDevice, st));
   HICR_CUDA(in, cudaEventRecord(in->pinned_ev[k], st));
-  hicr_status s = launch_batch(in, in->d_ops, count, st);
+  hicr_status s = launch_batch(in, in->d_ops, count, st, tags);
   if (s != HICR_OK) return s;
-  return record_done(in);
+  return record_signalled(in);
 }
 
 // Copy a host op table to the device through a double-buffered pinned
@@ -537,38 +555,54 @@ static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_
   hicr_status s = stage_prepare(in, count, k);
   if (s != HICR_OK) return s;
   hicr_op_t* dst = in->pinned[k];
+  uint64_t mask[TAG_WORDS] = {};
   if (count >= PAR_OPS) {
-    host_pool(in).run([&](int t, int nt) {
+    HostPool& pool = host_pool(in);
+    std::vector<uint64_t> masks((size_t)pool.size() * TAG_WORDS, 0);
+    pool.run([&](int t, int nt) {
       const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
       memcpy(dst + a, ops + a, (b - a) * sizeof(hicr_op_t));
+      tag_mask(in, ops + a, b - a, masks.data() + (size_t)t * TAG_WORDS);
     });
+    for (size_t t = 0; t < (size_t)pool.size(); ++t)
+      for (int w = 0; w < TAG_WORDS; ++w) mask[w] |= masks[t * TAG_WORDS + w];
   } else {
     memcpy(dst, ops, count * sizeof(hicr_op_t));
+    tag_mask(in, ops, count, mask);
   }
-  return launch_staged(in, count, k);
+  return launch_staged(in, count, k, mask);
 }
 
 // Index of the first invalid op of ops[a, b) (b when all are valid); with
-// `stage` the range is also copied there.
-static uint64_t validate_range(const Instance* in, const hicr_op_t* ops, uint64_t a, uint64_t b, hicr_op_t* stage) {
+// `stage` the range is also copied there, and with `mask` the tags of its
+// ops are added to it.
+static uint64_t validate_range(const Instance* in, const hicr_op_t* ops, uint64_t a, uint64_t b, hicr_op_t* stage,
+                               uint64_t* mask = nullptr) {
   for (uint64_t i = a; i < b; ++i)
     if (validate_op(in, ops[i]) != HICR_OK) return i;
   if (stage) memcpy(stage + a, ops + a, (b - a) * sizeof(hicr_op_t));
+  if (mask) tag_mask(in, ops + a, b - a, mask);
   return b;
 }
 
-// Validate every op (and, with `stage`, copy the table there) on the pool;
-// returns the index of the first invalid op in issue order, or count.
-static uint64_t validate_par(Instance* in, const hicr_op_t* ops, uint64_t count, hicr_op_t* stage) {
+// Validate every op (and, with `stage`, copy the table there and collect the
+// ops' tags in `mask`) on the pool; returns the index of the first invalid op
+// in issue order, or count.
+static uint64_t validate_par(Instance* in, const hicr_op_t* ops, uint64_t count, hicr_op_t* stage,
+                             uint64_t* mask = nullptr) {
   HostPool& pool = host_pool(in);
   std::vector<uint64_t> first((size_t)pool.size(), count);
+  std::vector<uint64_t> masks(mask ? (size_t)pool.size() * TAG_WORDS : 0, 0);
   pool.run([&](int t, int nt) {
     const uint64_t a = count * t / nt, b = count * (t + 1) / nt;
-    const uint64_t f = validate_range(in, ops, a, b, stage);
+    const uint64_t f = validate_range(in, ops, a, b, stage, mask ? masks.data() + (size_t)t * TAG_WORDS : nullptr);
     first[t] = f < b ? f : count;
   });
   uint64_t f = count;
   for (uint64_t x : first) f = std::min(f, x);
+  if (mask)
+    for (size_t t = 0; t < (size_t)pool.size(); ++t)
+      for (int w = 0; w < TAG_WORDS; ++w) mask[w] |= masks[t * TAG_WORDS + w];
   return f;
 }
 
@@ -648,12 +682,13 @@ hicr_status hicr_memcpy_batch(hicr_instance_t h, const hicr_op_t* ops, uint64_t 
     const int k = in->pinned_idx;
     hicr_status s = stage_prepare(in, count, k);
     if (s != HICR_OK) return s;
-    const uint64_t first = validate_par(in, ops, count, in->pinned[k]);
+    uint64_t mask[TAG_WORDS] = {};
+    const uint64_t first = validate_par(in, ops, count, in->pinned[k], mask);
     if (first < count) {
       if (first_bad) *first_bad = first;
       return validate_op(in, ops[first]);
     }
-    return launch_staged(in, count, k);
+    return launch_staged(in, count, k, mask);
   }
   hicr_status s = validate_all(in, ops, count, first_bad);
   if (s != HICR_OK) return s;
@@ -670,9 +705,9 @@ hicr_status hicr_memcpy_batch_device(hicr_instance_t h, const hicr_op_t* d_ops, 
   if (in->capturing && count > in->scratch.cap) return HICR_ERR_INVALID;
   hicr_status s = hicr_flush(h);
   if (s != HICR_OK) return s;
-  s = launch_batch(in, d_ops, count, in->comm());
+  s = launch_batch(in, d_ops, count, in->comm(), nullptr);  // the host does not read the table: tags unknown
   if (s != HICR_OK) return s;
-  return record_done(in);
+  return record_signalled(in);
 }
 
 hicr_status hicr_batch_reserve(hicr_instance_t h, uint64_t max_ops) {
@@ -721,6 +756,7 @@ hicr_status hicr_graph_begin(hicr_instance_t h) {
   if (s != HICR_OK) return s;
   HICR_CUDA(in, cudaStreamBeginCapture(in->comm(), cudaStreamCaptureModeThreadLocal));
   in->capturing = true;
+  in->cap_sigs = 0;
   return HICR_OK;
 }
 
@@ -736,6 +772,7 @@ hicr_status hicr_graph_end(hicr_instance_t h, hicr_graph_t* out) {
     return cuda_fail(in, e, "cudaGraphInstantiate");
   }
   g.live = true;
+  g.sigs = in->cap_sigs;
   for (size_t i = 0; i < in->graphs.size(); ++i) {
     if (!in->graphs[i].live) {
       in->graphs[i] = g;
@@ -755,7 +792,8 @@ hicr_status hicr_graph_launch(hicr_instance_t h, hicr_graph_t g) {
   hicr_status s = hicr_flush(h);
   if (s != HICR_OK) return s;
   HICR_CUDA(in, cudaGraphLaunch(in->graphs[g - 1].exec, in->comm()));
-  return record_done(in);
+  for (uint64_t k = 0; k < in->graphs[g - 1].sigs; ++k) note_signal(in, nullptr);
+  return record_signalled(in);
 }
 
 hicr_status hicr_graph_destroy(hicr_instance_t h, hicr_graph_t g) {
@@ -861,7 +899,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
   const char* cache = getenv("HICR_TUNE_CACHE");
   int key_ops = 0, key_bytes = 0;
   if (cache && *cache) {
-    if ((s = launch_batch(in, d_ops, count, in->comm())) != HICR_OK) return s;
+    if ((s = launch_batch(in, d_ops, count, in->comm(), nullptr)) != HICR_OK) return s;
     BatchCtrl ctl;
     HICR_CUDA(in, cudaMemcpyAsync(&ctl, in->scratch.ctrl, sizeof(ctl), cudaMemcpyDeviceToHost, in->comm()));
     HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
@@ -878,7 +916,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
       if (bst != HICR_OK) return bst;
       if (best) *best = c;
       if (best_ms) *best_ms = ms;
-      return record_done(in);
+      return record_signalled(in);
     }
   }
   std::vector<hicr_batch_config_t> cands;
@@ -933,7 +971,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
     std::vector<float> ts;
     for (uint32_t r = 0; r <= reps; ++r) {
       cudaEventRecord(e0, st);
-      s = launch_batch(in, d_ops, count, st);
+      s = launch_batch(in, d_ops, count, st, nullptr);
       if (s != HICR_OK) break;
       cudaEventRecord(e1, st);
       cudaError_t e = cudaEventSynchronize(e1);
@@ -964,7 +1002,7 @@ hicr_status hicr_batch_autotune(hicr_instance_t h, const hicr_op_t* d_ops, uint6
   if (cache && *cache) tune_store(cache, in->prop.name, in->sm_count, key_ops, key_bytes, best_c, best_t);
   if (best) *best = best_c;
   if (best_ms) *best_ms = best_t;
-  return record_done(in);
+  return record_signalled(in);
 }
 
 }  // extern "C"

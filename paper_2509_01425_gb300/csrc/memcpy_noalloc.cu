@@ -129,5 +129,6 @@ extern "C" hicr_status hicr_memcpy_batch_noalloc(hicr_instance_t h, const hicr_o
     k_copy<<<grid, in->cfg.threads, 0, st>>>(a);
   }
   HICR_CUDA(in, cudaGetLastError());
-  return record_done(in);
+  note_signal(in, nullptr);  // the copy kernel's last warp signals; the table's tags are not read here
+  return record_signalled(in);
 }

@@ -7,6 +7,7 @@
 #include <map>
 
 #include <algorithm>
+#include <atomic>
 #include <thread>
 
 #include "hicr_internal.h"
@@ -53,8 +54,55 @@ static hicr_status push_slot(Instance* in, uint32_t id) {
 
 hicr_status record_done(Instance* in) {
   if (in->capturing) return HICR_OK;
+  in->opaque = true;
   HICR_CUDA(in, cudaEventRecord(in->done_ev, in->comm()));
   return HICR_OK;
+}
+
+hicr_status record_signalled(Instance* in) {
+  if (in->capturing) return HICR_OK;
+  HICR_CUDA(in, cudaEventRecord(in->done_ev, in->comm()));
+  return HICR_OK;
+}
+
+void note_signal(Instance* in, const uint64_t* mask) {
+  if (in->capturing) {
+    ++in->cap_sigs;
+    return;
+  }
+  const uint64_t v = ++in->sig_issued;
+  if (!mask) {
+    in->any_sig = v;
+    return;
+  }
+  for (int w = 0; w < TAG_WORDS; ++w)
+    for (uint64_t m = mask[w]; m; m &= m - 1) in->tag_sig[w * 64 + __builtin_ctzll(m)] = v;
+}
+
+void tag_mask(const Instance* in, const hicr_op_t* ops, uint64_t count, uint64_t* mask) {
+  for (uint64_t i = 0; i < count; ++i) {
+    const uint32_t a = in->slots[ops[i].dst].tag, b = in->slots[ops[i].src].tag;
+    mask[a >> 6] |= 1ull << (a & 63);
+    mask[b >> 6] |= 1ull << (b & 63);
+  }
+}
+
+// Wait until the device has emitted completion signal `target` (mapped host
+// memory, written by the launch's last thread), or timeout. Spins first,
+// then yields, then sleeps in short steps.
+static hicr_status wait_signal(Instance* in, uint64_t target, uint64_t timeout_ns) {
+  volatile unsigned long long* m = in->sig_mirror;
+  if (*m >= target) return HICR_OK;
+  const uint64_t t0 = now_ns();
+  for (uint32_t spins = 0;; ++spins) {
+    if (*m >= target) return HICR_OK;
+    if ((spins & 63) == 0) {
+      const uint64_t dt = now_ns() - t0;
+      if (dt >= timeout_ns) return *m >= target ? HICR_OK : HICR_ERR_TIMEOUT;
+      if (dt > 2000000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (dt > 50000) std::this_thread::yield();
+    }
+  }
 }
 
 hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns) {
@@ -179,7 +227,7 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
 
   // one allocation for all device tables
   const size_t S = HICR_MAX_SLOTS;
-  size_t bytes = S * 8 * 2 + S * 4 + S * 8 * 2 + HICR_MAX_TAGS * 8 + 2 * 8;
+  size_t bytes = S * 8 * 2 + S * 4 + S * 8 * 2 + HICR_MAX_TAGS * 8 + 2 * 8 + 2 * 8;
   char* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) return fail(HICR_ERR_NOMEM);
   if (cudaMemset(p, 0, bytes) != cudaSuccess) { cudaFree(p); return fail(HICR_ERR_DEVICE); }
@@ -189,7 +237,9 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   in->dt.recv = (unsigned long long*)p; p += S * 8;
   in->dt.tag_ops = (unsigned long long*)p; p += HICR_MAX_TAGS * 8;
   in->dt.sticky = (unsigned long long*)p; p += 2 * 8;
+  in->dt.sig = (unsigned long long*)p; p += 2 * 8;
   in->dt.slot_meta = (uint32_t*)p;
+  in->tag_sig.assign(HICR_MAX_TAGS, 0);
 
   Pu pu0;
   if (cudaStreamCreateWithFlags(&pu0.stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -200,8 +250,10 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   pu0.live = true;
   in->pus.push_back(pu0);
   cudaEventCreateWithFlags(&in->done_ev, cudaEventDisableTiming);
-  if (cudaHostAlloc((void**)&in->sticky_host, 64, cudaHostAllocDefault) != cudaSuccess) return fail(HICR_ERR_DEVICE);
-  *in->sticky_host = 0;
+  if (cudaHostAlloc((void**)&in->sig_mirror, 64, cudaHostAllocMapped) != cudaSuccess ||
+      cudaHostGetDevicePointer((void**)&in->dt.sig_host, in->sig_mirror, 0) != cudaSuccess)
+    return fail(HICR_ERR_DEVICE);
+  memset(in->sig_mirror, 0, 64);
   cudaEventCreateWithFlags(&in->pinned_ev[0], cudaEventDisableTiming);
   cudaEventCreateWithFlags(&in->pinned_ev[1], cudaEventDisableTiming);
   cudaEventRecord(in->done_ev, pu0.stream);
@@ -209,7 +261,7 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   cudaEventRecord(in->pinned_ev[1], pu0.stream);
   default_config(in, &in->cfg);
   if (noalloc_setup(in) != HICR_OK) {
-    cudaFreeHost(in->sticky_host);
+    cudaFreeHost(in->sig_mirror);
     cudaStreamDestroy(pu0.stream);
     cudaFree(in->dt.slot_base);
     return fail(HICR_ERR_DEVICE);
@@ -277,7 +329,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
   if (in->scratch.cost) cudaFree(in->scratch.cost);
   if (in->dt.slot_base) cudaFree(in->dt.slot_base);
   if (in->done_ev) cudaEventDestroy(in->done_ev);
-  if (in->sticky_host) cudaFreeHost(in->sticky_host);
+  if (in->sig_mirror) cudaFreeHost(in->sig_mirror);
   for (auto& p : in->pus)
     if (p.live && p.owned) cudaStreamDestroy(p.stream);
   delete h;
@@ -444,6 +496,11 @@ hicr_status hicr_slot_deregister(hicr_instance_t h, hicr_slot_t slot) {
   if (!in || in->capturing || !valid_slot(in, slot) || in->slots[slot].owned) return HICR_ERR_INVALID;
   if (!in->queue.empty()) return HICR_ERR_BUSY;
   cudaError_t e = cudaEventQuery(in->done_ev);
+  // A fence returns at the completion signal, which the last thread of a
+  // launch writes just before the kernel ends: when every signal issued is
+  // in and nothing else is pending, the done event follows within moments.
+  if (e == cudaErrorNotReady && !in->opaque && *(volatile unsigned long long*)in->sig_mirror >= in->sig_issued)
+    e = cudaEventSynchronize(in->done_ev);
   if (e == cudaErrorNotReady) return HICR_ERR_BUSY;
   HICR_CUDA(in, e);
   in->slots[slot] = HostSlot();
@@ -464,26 +521,40 @@ hicr_status hicr_slot_info(hicr_instance_t h, hicr_slot_t slot, void** ptr, uint
   return HICR_OK;
 }
 
+// Wait for the work fences must cover: when work without completion signals
+// was issued on the communication stream since the last full wait, the done
+// event covers everything once; then completion signal `target`. Returns the
+// sticky batch error the device mirrored with the last signal, if any.
+static hicr_status fence_wait(hicr_instance_t h, Instance* in, uint64_t target, uint64_t timeout_ns) {
+  const uint64_t t0 = now_ns();
+  if (in->opaque) {
+    HICR_CUDA(in, cudaEventRecord(in->done_ev, in->comm()));
+    hicr_status st = wait_event(in, in->done_ev, timeout_ns);
+    if (st != HICR_OK) return st;
+    in->opaque = false;
+  }
+  const uint64_t used = now_ns() - t0;
+  hicr_status st = wait_signal(in, target, timeout_ns > used ? timeout_ns - used : 0);
+  if (st != HICR_OK) return st;
+  std::atomic_thread_fence(std::memory_order_acquire);
+  if (*(volatile unsigned long long*)(in->sig_mirror + 1) == 0) return HICR_OK;
+  hicr_status bst = HICR_OK;
+  uint64_t bad = 0;
+  st = hicr_batch_error(h, &bst, &bad);  // reads and clears it
+  if (st != HICR_OK) return st;
+  return bst;
+}
+
 hicr_status hicr_fence(hicr_instance_t h, uint32_t tag, uint64_t timeout_ns) {
   hicr::NvtxRange nvtx_range("hicr_fence");
   Instance* in = I(h);
   if (!in || tag >= HICR_MAX_TAGS || in->capturing) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
-  // The sticky batch error is copied to page-locked memory behind the issued
-  // work, so one wait covers both. Every op is issued on the communication
-  // stream, so waiting for the last recorded event covers all earlier ops of
-  // this tag (and those of others).
-  HICR_CUDA(in, cudaMemcpyAsync(in->sticky_host, in->dt.sticky, 8, cudaMemcpyDeviceToHost, in->comm()));
-  if ((st = record_done(in)) != HICR_OK) return st;
-  st = wait_event(in, in->done_ev, timeout_ns);
-  if (st != HICR_OK) return st;
-  if (*(volatile unsigned long long*)in->sticky_host == 0) return HICR_OK;
-  hicr_status bst = HICR_OK;
-  uint64_t bad = 0;
-  st = hicr_batch_error(h, &bst, &bad);  // reads and clears it
-  if (st != HICR_OK) return st;
-  return bst;
+  // Every memcpy launch ends with a completion signal; the host knows the
+  // signal of the last launch with an op of this tag (or of unknown tags).
+  // Later launches of other tags are not waited for.
+  return fence_wait(h, in, std::max(in->tag_sig[tag], in->any_sig), timeout_ns);
 }
 
 static hicr_status read_u64_pair(Instance* in, const unsigned long long* a, const unsigned long long* b,
@@ -528,15 +599,16 @@ hicr_status hicr_fence_slot(hicr_instance_t h, hicr_slot_t slot, uint64_t expect
   if (!in || slot >= in->slots.size() || in->capturing) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
-  const uint64_t t0 = now_ns();
-  for (;;) {
-    uint64_t s = 0, r = 0;
-    st = hicr_slot_counters(h, slot, &s, &r);
-    if (st != HICR_OK) return st;
-    if (s >= expect_sent && r >= expect_recv) return HICR_OK;
-    if (now_ns() - t0 >= timeout_ns) return HICR_ERR_TIMEOUT;
-    std::this_thread::sleep_for(std::chrono::microseconds(10));
-  }
+  // Only launches with an op of the slot's tag can move its counters: wait
+  // for the last of them (polling mapped host memory), then read the
+  // counters once. If they fall short, no issued op can still raise them.
+  const uint64_t target = std::max(in->tag_sig[in->slots[slot].tag], in->any_sig);
+  st = fence_wait(h, in, target, timeout_ns);
+  if (st != HICR_OK) return st;
+  uint64_t s = 0, r = 0;
+  st = hicr_slot_counters(h, slot, &s, &r);
+  if (st != HICR_OK) return st;
+  return (s >= expect_sent && r >= expect_recv) ? HICR_OK : HICR_ERR_TIMEOUT;
 }
 
 hicr_status hicr_batch_error(hicr_instance_t h, hicr_status* status, uint64_t* first_bad) {
@@ -549,6 +621,8 @@ hicr_status hicr_batch_error(hicr_instance_t h, hicr_status* status, uint64_t* f
     unsigned long long z = 0;
     HICR_CUDA(in, cudaMemcpy(in->dt.sticky, &z, 8, cudaMemcpyHostToDevice));
   }
+  // the stream is idle: no signal can be writing the mirror now
+  *(volatile unsigned long long*)(in->sig_mirror + 1) = 0;
   if (status) *status = v ? -(hicr_status)(v & 0xFF) : HICR_OK;
   if (first_bad) *first_bad = v ? (v >> 8) : 0;
   return HICR_OK;
@@ -663,6 +737,7 @@ hicr_status hicr_exec_launch(hicr_instance_t h, hicr_pu_t pu, const hicr_exec_un
     return HICR_ERR_INVALID;
   if (u->n_args > 0 && !args) return HICR_ERR_INVALID;
   cudaStream_t st = in->pus[pu].stream;
+  if (pu == in->comm_pu) in->opaque = true;  // fences on this stream wait for it once
   HICR_CUDA(in, cudaLaunchKernel(u->func, dim3(u->grid[0], u->grid[1], u->grid[2]),
                                  dim3(u->block[0], u->block[1], u->block[2]), args, u->smem_bytes, st));
   // completion event: one returned by an earlier await, else a new one

@@ -113,6 +113,12 @@ struct SrvArgs {
   unsigned int n_mt, n_bt;    // memcpy / burst templates
   unsigned long long arena_lo, arena_hi;
   unsigned int* wstate;       // per warp: where it is (diagnostics)
+  // capture of consumed burst messages (tests and sampled checks): message m
+  // of burst request r goes to cap + cap_off[r] + mcap[t_mbase[tmpl] + m]
+  // unless cap_off[r] is ~0
+  uint8_t* cap;
+  const unsigned long long* cap_off;
+  const unsigned long long* mcap;  // per template message: offset within the burst's captured bytes
 };
 
 // Warp states recorded in SrvArgs::wstate (diagnostics of a stuck run).
@@ -593,6 +599,20 @@ __device__ void srv_consumer(const SrvArgs& a, unsigned c, unsigned long long de
         }
       }
     }
+    // capture: warp w copies messages w, w + nwarp, ... of the window out of
+    // the ring before the window is freed (after the barrier below)
+    if (a.cap) {
+      for (unsigned j = warp; j < navail; j += nwarp) {
+        if (s_prod[j] >= a.n_req) continue;  // the self-check reports it
+        const unsigned long long co = __ldcg(&a.cap_off[s_prod[j]]);
+        if (co == ~0ull) continue;
+        const unsigned tm = __ldcg(&a.req[s_prod[j]].tmpl);
+        if (tm >= a.n_bt || s_seq[j] >= a.t_nmsg[tm]) continue;
+        const unsigned long long mi = a.t_mbase[tm] + s_seq[j];
+        capture_copy(a.cap + co + a.mcap[mi], v.ring + (s_start[j] & (v.R - 1)),
+                     min((unsigned long long)s_size[j], a.msizes[mi]), lane);
+      }
+    }
     __syncthreads();
     ws_set(a, WS_C_ACCOUNT);
     // per-request accounting: message digest weighted by its index in the burst
@@ -725,6 +745,8 @@ struct Server {
   SrvCtl* ctl = nullptr;
   MpscView* d_views = nullptr;
   std::vector<unsigned long long> t_bytes, m_bytes;  // payload bytes per template
+  std::vector<unsigned long long> mcap;              // per template message: exclusive prefix of sizes
+  std::vector<uint8_t> kept;  // last run: memcpy requests whose region was not reused
 };
 
 static Server* srv_get(Instance* in, hicr_serve_t s);
@@ -771,7 +793,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
       sv->t_ngrp.push_back(0);
   if (sv->gstart.empty()) sv->gstart.push_back(0);
   if (sv->tops.empty()) sv->tops.push_back(hicr_op_t{0, 0, 0, 0, 0});
-  if (sv->msizes.empty()) sv->msizes.push_back(0), sv->moffs.push_back(0);
+  if (sv->msizes.empty()) sv->msizes.push_back(0), sv->moffs.push_back(0), sv->mcap.push_back(0);
   std::vector<const void*> dummy;
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t bytes = al(sv->tops.size() * sizeof(hicr_op_t)) +
@@ -779,7 +801,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
                             al(sv->t_cbase.size() * 8) + al(sv->t_chunks.size() * 8) + al(sv->t_total.size() * 8) +
                             al(sv->msizes.size() * 8) + al(sv->moffs.size() * 8) + al(sv->t_mbase.size() * 8) +
                             al(sv->t_nmsg.size() * 8) + al(sv->gstart.size() * 8) + al(sv->t_gbase.size() * 8) +
-                            al(sv->t_ngrp.size() * 8)) / 8;
+                            al(sv->t_ngrp.size() * 8) + al(sv->mcap.size() * 8)) / 8;
   char* d = nullptr;
   HICR_CUDA(in, cudaMalloc(&d, bytes + 4096));
   sv->dev_tmpl = d;
@@ -808,6 +830,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   UP(gstart, sv->gstart);
   UP(t_gbase, sv->t_gbase);
   UP(t_ngrp, sv->t_ngrp);
+  UP(mcap, sv->mcap);
 #undef UP
   sv->uploaded = true;
   return HICR_OK;
@@ -965,6 +988,7 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, con
   for (uint64_t i = 0; i < count; ++i) {
     sv->msizes.push_back(sizes[i]);
     sv->moffs.push_back(staging_off[i]);
+    sv->mcap.push_back(mb);
     mb += sizes[i];
   }
   sv->m_bytes.push_back(mb);
@@ -990,12 +1014,16 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, con
   return HICR_OK;
 }
 
-hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
-                           uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
-                           hicr_serve_stats_t* stats) {
+}  // extern "C"
+
+namespace hicr {
+
+static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                             uint32_t mode, uint64_t timeout_ns, const uint8_t* keep, void* d_capture,
+                             const uint64_t* d_cap_off, hicr_serve_result_t* results, hicr_serve_stats_t* stats) {
   hicr::NvtxRange nvtx_range("hicr_serve_run");
   Instance* in = I(h);
-  if (!in || (n && !reqs) || mode > 1 || in->capturing) return HICR_ERR_INVALID;
+  if (!in || (n && !reqs) || mode > 1 || in->capturing || (d_capture && !d_cap_off)) return HICR_ERR_INVALID;
   Server* sv = srv_get(in, s);
   if (!sv) return HICR_ERR_INVALID;
   for (uint64_t i = 0; i < n; ++i) {
@@ -1059,6 +1087,11 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   a.n_bt = (unsigned)sv->t_nmsg.size();
   a.arena_lo = (unsigned long long)sv->arena;
   a.arena_hi = (unsigned long long)sv->arena + (sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
+  a.cap = (uint8_t*)d_capture;
+  a.cap_off = (const unsigned long long*)d_cap_off;
+  sv->kept.assign(n, sv->cfg.verify ? 1 : 0);
+  if (keep)
+    for (uint64_t r = 0; r < n; ++r) sv->kept[r] |= keep[r] ? 1 : 0;
   int per_sm = 0;
   HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_serve, SRV_THREADS, 0));
   const unsigned grid = (unsigned)(in->sm_count * std::max(1, per_sm));
@@ -1141,7 +1174,7 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
         }
         if (reqs[r].kind == 0) {
           bytes += sv->t_bytes[reqs[r].tmpl];
-          if (!sv->cfg.verify) arena.release(region_off[r], region_len[r]);
+          if (!sv->kept[r]) arena.release(region_off[r], region_len[r]);
         } else {
           bytes += sv->m_bytes[reqs[r].tmpl];
         }
@@ -1266,6 +1299,31 @@ hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_r
   return result;
 }
 
+}  // namespace hicr
+
+extern "C" {
+
+hicr_status hicr_serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                           uint32_t mode, uint64_t timeout_ns, hicr_serve_result_t* results,
+                           hicr_serve_stats_t* stats) {
+  return serve_run(h, s, reqs, n, mode, timeout_ns, nullptr, nullptr, nullptr, results, stats);
+}
+
+hicr_status hicr_serve_run_ex(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
+                              uint32_t mode, uint64_t timeout_ns, const uint8_t* keep, void* d_capture,
+                              const uint64_t* d_cap_off, hicr_serve_result_t* results, hicr_serve_stats_t* stats) {
+  return serve_run(h, s, reqs, n, mode, timeout_ns, keep, d_capture, d_cap_off, results, stats);
+}
+
+hicr_status hicr_serve_arena(hicr_instance_t h, hicr_serve_t s, hicr_slot_t* out) {
+  Instance* in = I(h);
+  if (!in || !out) return HICR_ERR_INVALID;
+  Server* sv = srv_get(in, s);
+  if (!sv) return HICR_ERR_INVALID;
+  *out = sv->arena_slot;
+  return HICR_OK;
+}
+
 hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_serve_request_t* reqs, uint64_t n,
                                  uint64_t horizon_ns, uint64_t timeout_ns, hicr_serve_result_t* results,
                                  hicr_serve_stats_t* stats) {
@@ -1373,10 +1431,13 @@ hicr_status hicr_serve_digests(hicr_instance_t h, hicr_serve_t s, const hicr_ser
   Instance* in = I(h);
   if (!in || (n && (!reqs || !results))) return HICR_ERR_INVALID;
   Server* sv = srv_get(in, s);
-  if (!sv || !sv->cfg.verify) return HICR_ERR_INVALID;
+  if (!sv || sv->kept.size() != n) return HICR_ERR_INVALID;
+  bool any = false;
+  for (uint64_t r = 0; r < n; ++r) any = any || (reqs[r].kind == 0 && sv->kept[r]);
+  if (!any && !sv->cfg.verify) return HICR_ERR_INVALID;
   std::vector<VerifyItem> items;
   for (uint64_t r = 0; r < n; ++r) {
-    if (reqs[r].kind != 0) continue;
+    if (reqs[r].kind != 0 || !sv->kept[r]) continue;
     const unsigned t = reqs[r].tmpl;
     if (t >= sv->t_nops.size()) return HICR_ERR_INVALID;
     for (uint64_t k = 0; k < sv->t_nops[t]; ++k) {
@@ -1406,7 +1467,7 @@ hicr_status hicr_serve_digests(hicr_instance_t h, hicr_serve_t s, const hicr_ser
   cudaFree(d_out);
   if (e != cudaSuccess) return cuda_fail(in, e, "serve digests");
   for (uint64_t r = 0; r < n; ++r)
-    if (reqs[r].kind == 0) results[r].digest = out[r];
+    if (reqs[r].kind == 0 && sv->kept[r]) results[r].digest = out[r];
   return HICR_OK;
 }
 

@@ -137,6 +137,59 @@ __global__ void k_wait_test(unsigned long long* flag, unsigned long long timeout
   out[1] = gtime() - t0;
 }
 
+// Bandwidth probes (no counterpart in the paper): the bounds the channel and
+// host-space measurements are read against. Every thread owns the 16-byte
+// vectors tid, tid + stride, ... of the range and keeps U of them in flight;
+// loads go to L2 (ld.global.cg), so a range re-read by the same SM is not
+// served from its L1.
+static constexpr int PROBE_U = 8;
+
+// `reps` passes of dst[0, nv) = src[0, nv) (16-byte vectors).
+__global__ void k_copy_loop(uint4* __restrict__ dst, const uint4* __restrict__ src, unsigned long long nv,
+                            unsigned reps) {
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned r = 0; r < reps; ++r) {
+    for (unsigned long long q = tid; q < nv; q += PROBE_U * stride) {
+      uint4 x[PROBE_U];
+#pragma unroll
+      for (int u = 0; u < PROBE_U; ++u)
+        if (q + u * stride < nv) x[u] = __ldcg(src + q + u * stride);
+#pragma unroll
+      for (int u = 0; u < PROBE_U; ++u)
+        if (q + u * stride < nv) dst[q + u * stride] = x[u];
+    }
+  }
+}
+
+// `reps` passes reading p[0, nv) (write = 0) or writing it (write = 1); a
+// reading thread folds what it read into one word and stores it only when it
+// equals a value no input makes likely, which keeps the loads alive.
+__global__ void k_stream(uint4* __restrict__ p, unsigned long long nv, unsigned reps, int write,
+                         unsigned long long* sink) {
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long acc = 0;
+  for (unsigned r = 0; r < reps; ++r) {
+    for (unsigned long long q = tid; q < nv; q += PROBE_U * stride) {
+      if (write) {
+#pragma unroll
+        for (int u = 0; u < PROBE_U; ++u)
+          if (q + u * stride < nv) __stcs(p + q + u * stride, make_uint4((unsigned)q, u, r, 0x5a5a5a5au));
+      } else {
+        uint4 x[PROBE_U];
+#pragma unroll
+        for (int u = 0; u < PROBE_U; ++u)
+          if (q + u * stride < nv) x[u] = __ldcg(p + q + u * stride);
+#pragma unroll
+        for (int u = 0; u < PROBE_U; ++u)
+          if (q + u * stride < nv) acc ^= ((unsigned long long)x[u].x << 32 | x[u].y) + x[u].z + x[u].w;
+      }
+    }
+  }
+  if (acc == 0x0123456789abcdefull) *sink = acc;
+}
+
 const void* builtin_fill_kernel() { return (const void*)k_fill; }
 const void* builtin_digest_kernel() { return (const void*)k_digest; }
 
@@ -212,6 +265,85 @@ hicr_status hicr_util_digest(hicr_instance_t h, hicr_slot_t slot, uint64_t off, 
   HICR_CUDA(in, cudaStreamSynchronize(cs));
   *out = v;
   return record_done(in);
+}
+
+}  // extern "C"
+
+namespace hicr {
+
+static hicr_status probe_range(Instance* in, hicr_slot_t slot, uint64_t off, uint64_t n, uint8_t** p) {
+  if (slot >= in->slots.size() || !in->slots[slot].live) return HICR_ERR_INVALID;
+  const HostSlot& s = in->slots[slot];
+  if (off > s.size || n > s.size - off) return HICR_ERR_BOUNDS;
+  *p = (uint8_t*)s.base + off;
+  if (((uintptr_t)*p & 15u) || (n & 15u)) return HICR_ERR_INVALID;
+  return HICR_OK;
+}
+
+// Runs `launch` between two events on the communication stream, waits, and
+// returns the device time.
+template <class F>
+static hicr_status probe_time(Instance* in, F launch, uint64_t* device_ns) {
+  cudaStream_t cs = in->comm();
+  cudaEvent_t e0, e1;
+  HICR_CUDA(in, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(in, e, "cudaEventCreate");
+  }
+  e = cudaEventRecord(e0, cs);
+  if (e == cudaSuccess) {
+    launch(cs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(in, e, "bandwidth probe");
+  *device_ns = (uint64_t)((double)ms * 1e6);
+  return record_done(in);
+}
+
+}  // namespace hicr
+
+extern "C" {
+
+hicr_status hicr_util_copy_loop(hicr_instance_t h, hicr_slot_t dst, uint64_t dst_off, hicr_slot_t src,
+                                uint64_t src_off, uint64_t n, uint32_t reps, uint32_t ctas_per_sm,
+                                uint64_t* device_ns) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || !device_ns || reps == 0 || ctas_per_sm == 0 || ctas_per_sm > 8 || in->capturing)
+    return HICR_ERR_INVALID;
+  uint8_t *d = nullptr, *s = nullptr;
+  hicr_status st = probe_range(in, dst, dst_off, n, &d);
+  if (st == HICR_OK) st = probe_range(in, src, src_off, n, &s);
+  if (st != HICR_OK) return st;
+  if (dst == src && dst_off < src_off + n && src_off < dst_off + n) return HICR_ERR_OVERLAP;
+  if ((st = hicr_flush(h)) != HICR_OK) return st;
+  const unsigned grid = (unsigned)in->sm_count * ctas_per_sm;
+  return probe_time(
+      in, [&](cudaStream_t cs) { k_copy_loop<<<grid, 256, 0, cs>>>((uint4*)d, (const uint4*)s, n / 16, reps); },
+      device_ns);
+}
+
+hicr_status hicr_util_stream(hicr_instance_t h, hicr_slot_t slot, uint64_t off, uint64_t n, int32_t write,
+                             uint32_t reps, uint32_t ctas_per_sm, uint64_t* device_ns) {
+  Instance* in = h ? &h->impl : nullptr;
+  if (!in || !device_ns || reps == 0 || ctas_per_sm == 0 || ctas_per_sm > 8 || in->capturing)
+    return HICR_ERR_INVALID;
+  uint8_t* p = nullptr;
+  hicr_status st = probe_range(in, slot, off, n, &p);
+  if (st != HICR_OK) return st;
+  if ((st = hicr_flush(h)) != HICR_OK) return st;
+  unsigned long long* sink = in->dt.sticky + 1;  // spare word next to the sticky error (never written in practice)
+  const unsigned grid = (unsigned)in->sm_count * ctas_per_sm;
+  return probe_time(
+      in, [&](cudaStream_t cs) { k_stream<<<grid, 256, 0, cs>>>((uint4*)p, n / 16, reps, write ? 1 : 0, sink); },
+      device_ns);
 }
 
 }  // extern "C"

@@ -163,6 +163,8 @@ _util_fill = _decl("hicr_util_fill", [H, u32, u64, u64, u64])
 _util_fill_segments = _decl("hicr_util_fill_segments", [H, u32, vp, u64])
 _util_wait_test = _decl("hicr_util_wait_test", [H, u64, C.POINTER(i32), C.POINTER(u64)])
 _util_digest = _decl("hicr_util_digest", [H, u32, u64, u64, C.POINTER(u64)])
+_util_copy_loop = _decl("hicr_util_copy_loop", [H, u32, u64, u32, u64, u64, u32, u32, C.POINTER(u64)])
+_util_stream = _decl("hicr_util_stream", [H, u32, u64, u64, i32, u32, u32, C.POINTER(u64)])
 
 
 def hicr_status_str(s: int) -> str:
@@ -437,6 +439,18 @@ def hicr_util_wait_test(inst, timeout_ns):
     return st, st_.value, w.value
 
 
+def hicr_util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas_per_sm=4):
+    v = u64()
+    st = _util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas_per_sm, C.byref(v))
+    return st, v.value
+
+
+def hicr_util_stream(inst, slot, off, n, write, reps, ctas_per_sm=4):
+    v = u64()
+    st = _util_stream(inst, slot, off, n, 1 if write else 0, reps, ctas_per_sm, C.byref(v))
+    return st, v.value
+
+
 def hicr_util_digest(inst, slot, off, n):
     v = u64()
     st = _util_digest(inst, slot, off, n, C.byref(v))
@@ -655,6 +669,9 @@ _serve_add_burst = _decl("hicr_serve_add_burst_template", [H, u64, vp, vp, u64, 
 _serve_run = _decl("hicr_serve_run", [H, u64, vp, u64, u32, u64, vp, C.POINTER(hicr_serve_stats_t)])
 _serve_run_plain = _decl("hicr_serve_run_plain", [H, u64, vp, u64, u64, u64, vp, C.POINTER(hicr_serve_stats_t)])
 _serve_digests = _decl("hicr_serve_digests", [H, u64, vp, u64, vp])
+_serve_run_ex = _decl("hicr_serve_run_ex", [H, u64, vp, u64, u32, u64, vp, vp, vp, vp,
+                                            C.POINTER(hicr_serve_stats_t)])
+_serve_arena = _decl("hicr_serve_arena", [H, u64, C.POINTER(u32)])
 
 
 def hicr_serve_create(inst, cfg):
@@ -693,6 +710,26 @@ def hicr_serve_run(inst, srv, reqs, mode=0, timeout_ns=300_000_000_000):
     stats = hicr_serve_stats_t()
     st = _serve_run(inst, srv, reqs.ctypes.data, len(reqs), mode, timeout_ns, res.ctypes.data, C.byref(stats))
     return st, res, stats
+
+
+def hicr_serve_run_ex(inst, srv, reqs, mode=0, timeout_ns=300_000_000_000, keep=None, d_capture=None,
+                      d_cap_off=None):
+    """keep: None or a uint8 array of len(reqs); d_capture / d_cap_off: device
+    buffer and device u64 array (addresses or tensors)."""
+    reqs = np.ascontiguousarray(reqs, dtype=SERVE_REQ_DTYPE)
+    res = np.zeros(len(reqs), dtype=SERVE_RES_DTYPE)
+    stats = hicr_serve_stats_t()
+    k = None if keep is None else np.ascontiguousarray(keep, dtype=np.uint8)
+    st = _serve_run_ex(inst, srv, reqs.ctypes.data, len(reqs), mode, timeout_ns,
+                       None if k is None else k.ctypes.data, _ptr(d_capture), _ptr(d_cap_off), res.ctypes.data,
+                       C.byref(stats))
+    return st, res, stats
+
+
+def hicr_serve_arena(inst, srv):
+    s = u32()
+    st = _serve_arena(inst, srv, C.byref(s))
+    return st, s.value
 
 
 def hicr_serve_run_plain(inst, srv, reqs, horizon_ns, timeout_ns=300_000_000_000):

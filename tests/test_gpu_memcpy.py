@@ -179,7 +179,7 @@ def test_small_batches_match_oracle(h, inst, sizes):
                                      int(o["n"])) == 0
         else:
             assert h.hicr_memcpy_batch(inst, dops) == (0, 0)
-        assert h.hicr_fence(inst, 0, T) == 0
+        assert h.hicr_fence(inst, 3, T) == 0  # every op touches tags 3 and 5
         for k in range(2):
             assert (slot_bytes(h, inst, ids[k]) == cm.slots[oids[k]].data).all(), (path, k)
         m = (rnd + 1) * len(sizes)

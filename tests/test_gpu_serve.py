@@ -6,14 +6,22 @@ of the word digests of its ops' destination bytes; burst: ordered combination
 of the consumed messages' digests) must be bit-identical when the requests
 run one at a time and when they arrive together and overlap on the device,
 and both must equal the digest the oracle computes from the seeded sources.
+In the mix, every request's delivered bytes are also compared with the
+oracle's byte by byte: each memcpy request's destination region (kept after
+the run and read from the arena) against the memcpy oracle applying the
+template's ops, and every burst message as the consumer took it from the
+channel (the capture form) against the channel oracle's delivery.
 """
 import numpy as np
 import pytest
+import torch
 
 import bench
+from oracle import channels as oc
 from oracle import digest as od
+from oracle import memcpy as om
 from workloads import configs, splitmix
-from tests.gpu_util import h, inst  # noqa: F401
+from tests.gpu_util import device_bytes, h, inst  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +73,87 @@ def test_alone_equals_mix_equals_oracle(h, inst):
             cache[key] = expected_digest(tmpl, *key)
         assert int(mix["digest"][i]) == cache[key], (i, key)
     assert (mix["latency_ns"] > 0).all()
+    ss.free()
+
+
+def _oracle_region(src_w, tmpl, t):
+    """The memcpy oracle applies template t's ops to a fresh region slot: the
+    expected bytes of every op's destination range."""
+    a, b = int(tmpl.op_start[t]), int(tmpl.op_start[t + 1])
+    cm = om.CommManager()
+    ids = {}
+    for o in tmpl.ops[a:b]:
+        sl = int(o["src"])
+        if sl not in ids:
+            ids[sl] = cm.register(om.SPACE_HBM, splitmix.fill_bytes(SEED, sl, 0, int(src_w.slot_sizes[sl])))
+    dst = cm.register(om.SPACE_HBM, np.zeros(max(int(tmpl.region_bytes[t]), 1), dtype=np.uint8))
+    ops = tmpl.ops[a:b].copy()
+    ops["dst"] = dst
+    ops["src"] = [ids[int(x)] for x in tmpl.ops[a:b]["src"]]
+    assert cm.memcpy_batch(ops) == (om.OK, None)
+    return cm.slots[dst].data
+
+
+def _oracle_burst(tmpl, t, ring=8 << 20, max_msgs=1024):
+    """The channel oracle's delivery of burst template t: its messages pushed
+    in order by one producer into an MPSC channel and popped one by one."""
+    a, b = int(tmpl.msg_start[t]), int(tmpl.msg_start[t + 1])
+    orc = oc.MpscOracle(1, ring, max_msgs)
+    out = []
+    for m in range(b - a):
+        data = splitmix.mpsc_payload_bytes(t, m, int(tmpl.msg_sizes[a + m]))
+        if orc.push(0, data) == om.ERR_FULL:
+            while orc.depth()[0]:
+                out.append(orc.payload(0))
+                orc.pop(1)
+            assert orc.push(0, data) == om.OK
+    while orc.depth()[0]:
+        out.append(orc.payload(0))
+        orc.pop(1)
+    return np.concatenate(out) if out else np.zeros(0, dtype=np.uint8)
+
+
+def test_mix_delivers_the_oracle_bytes(h, inst):
+    src_w, tmpl, ss = small_setup(h, inst, verify=False, budget=2 << 30)  # room for every kept region
+    tr = configs.serve_trace(SEED + 2, rate=200_000.0, duration_s=0.002, n_templates=16)
+    reqs = ss.requests(tr)
+    burst = reqs["kind"] == 1
+    assert burst.any() and (~burst).any()
+    bbytes = np.array([int(tmpl.msg_sizes[tmpl.msg_start[t]:tmpl.msg_start[t + 1]].sum()) for t in range(16)])
+    cap_off = np.full(len(reqs), np.iinfo(np.uint64).max, dtype=np.uint64)
+    sizes = np.where(burst, bbytes[reqs["tmpl"]], 0).astype(np.uint64)
+    cap_off[burst] = (np.cumsum(sizes) - sizes)[burst]
+    cap = torch.zeros(max(int(sizes.sum()), 16), dtype=torch.uint8, device="cuda")
+    d_off = torch.from_numpy(cap_off.view(np.int64).copy()).cuda()
+    keep = (~burst).astype(np.uint8)
+    st, res, stats = h.hicr_serve_run_ex(inst, ss.srv, reqs, 0, T, keep=keep, d_capture=cap, d_cap_off=d_off)
+    assert st == 0 and stats.completed == len(reqs), (st, stats.as_dict(), h.hicr_last_error_string(inst))
+    assert stats.max_inflight > 1
+    st, arena = h.hicr_serve_arena(inst, ss.srv)
+    st, aptr, asize, _, _ = h.hicr_slot_info(inst, arena)
+    torch.cuda.synchronize()
+    got_cap = cap.cpu().numpy()
+    regions, bursts = {}, {}
+    for i, r in enumerate(reqs):
+        t = int(r["tmpl"])
+        if r["kind"] == 0:
+            if t not in regions:
+                regions[t] = _oracle_region(src_w, tmpl, t)
+            n = int(tmpl.region_bytes[t])
+            got = device_bytes(aptr + int(res["dst_offset"][i]), n).cpu().numpy()
+            a, b = int(tmpl.op_start[t]), int(tmpl.op_start[t + 1])
+            for o in tmpl.ops[a:b]:
+                d0, k = int(o["dst_off"]), int(o["n"])
+                assert (got[d0:d0 + k] == regions[t][d0:d0 + k]).all(), (i, t, d0)
+        else:
+            if t not in bursts:
+                bursts[t] = _oracle_burst(tmpl, t)
+            o = int(cap_off[i])
+            assert (got_cap[o:o + len(bursts[t])] == bursts[t]).all(), (i, t)
+    # the digests agree with the bytes
+    assert h.hicr_serve_digests(inst, ss.srv, reqs, res) == 0
+    for i, r in enumerate(reqs):
+        assert int(res["digest"][i]) == expected_digest(tmpl, int(r["kind"]), int(r["tmpl"])), i
     ss.free()
 
 
