@@ -260,12 +260,23 @@ hicr_status hicr_set_checked(hicr_instance_t inst, int32_t on);
  * call that touches a slot of `tag` has completed, or `timeout_ns` elapsed
  * (TIMEOUT; the work keeps running and a later fence can succeed). When a
  * device-validated batch failed, returns its error (INVALID/BOUNDS/...).
- * On success the slot counters are final for those ops. */
+ * On success the slot counters are final for those ops.
+ * Only those ops are waited for: each memcpy launch ends with a completion
+ * signal that the device writes into mapped host memory, and the fence polls
+ * for the signal of the last launch holding an op of `tag`, so copies of
+ * other tags issued later may still run when it returns. Device-resident
+ * batches and graph launches (whose tables the host does not read) count as
+ * holding every tag; other work issued on the communication stream since the
+ * last fence (fills, channel calls, launches on that processing unit) is
+ * waited for in full by the next fence, whatever its tag. */
 hicr_status hicr_fence(hicr_instance_t inst, uint32_t tag, uint64_t timeout_ns);
 
 /* Wait until slot's sent counter >= expect_sent and received counter >=
  * expect_recv ("the expected number of incoming and outgoing transfers",
- * Sec. 3.1.4), polling the device counters, or TIMEOUT. */
+ * Sec. 3.1.4), or TIMEOUT. It waits, as hicr_fence does, for the ops of the
+ * slot's tag issued before the call, then reads the counters once; counts
+ * that are still short then cannot be reached by any issued op, and the
+ * call returns TIMEOUT at once. */
 hicr_status hicr_fence_slot(hicr_instance_t inst, hicr_slot_t slot, uint64_t expect_sent,
                             uint64_t expect_recv, uint64_t timeout_ns);
 
