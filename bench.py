@@ -362,11 +362,17 @@ def bench_spsc(h, inst, reps=3):
         h.check(h.hicr_channel_destroy(inst, c), "channel_destroy")
     tc = statistics.median(ctimes)
     # the L2 bound: this library's copy-loop probe over a 16 MiB working set
-    # (8 MiB copied into 8 MiB, passes repeated), best of 2, 4 and 8 CTAs per SM
+    # (8 MiB copied into 8 MiB, passes repeated), best of 2, 4 and 8 CTAs per
+    # SM; and the same probe on as many SMs as the channels' producers hold
+    # (one CTA each), the rate the producer side can reach
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     l2 = 0.0
-    for ctas in (2, 4, 8):
-        ns = h.check(h.hicr_util_copy_loop(inst, stg, 8 * MiB, stg, 0, 8 * MiB, 2000, ctas), "copy loop")
+    for per in (2, 4, 8):
+        ns = h.check(h.hicr_util_copy_loop(inst, stg, 8 * MiB, stg, 0, 8 * MiB, 2000, per * sms), "copy loop")
         l2 = max(l2, 2 * 8 * MiB * 2000 / ns)
+    ns = h.check(h.hicr_util_copy_loop(inst, stg, 8 * MiB, stg, 0, 8 * MiB, 500, w.n_channels), "copy loop")
+    l2_prod = 2 * 8 * MiB * 500 / ns
     h.check(h.hicr_mem_free(inst, stg), "free staging")
     return {"workload": "64 channels x capacity 4,096 x 64 B tokens, 10^7 tokens/channel, "
                         "1 producer + 1 consumer CTA per channel (cooperative grid)", "batch_tokens": batch,
@@ -382,8 +388,13 @@ def bench_spsc(h, inst, reps=3):
                 "l2_bytes_per_token": 192,
                 "l2_copy_bound_GB_per_s": l2,
                 "frac_of_l2_copy_bound": tokens * 192 / tc / 1e9 / l2,
-                "note": "L2 traffic per token: staged read 64 B + ring write 64 B + ring read 64 B; bound = "
-                        "hicr_util_copy_loop's read+write rate over an L2-resident 16 MiB working set"}}
+                "producer_l2_GB_per_s": tokens * 128 / tc / 1e9,
+                "l2_copy_bound_on_producer_sms_GB_per_s": l2_prod,
+                "producer_frac_of_that_bound": tokens * 128 / tc / 1e9 / l2_prod,
+                "note": "L2 traffic per token: staged read 64 B + ring write 64 B (producer SM) + ring read 64 B "
+                        "(consumer SM); bounds = hicr_util_copy_loop's read+write rate over an L2-resident 16 MiB "
+                        f"working set on the whole GPU ({sms} SMs x 2-8 CTAs) and on {w.n_channels} CTAs, one SM "
+                        "each, as many as the producers hold"}}
 
 
 def bench_pingpong(h, inst):
@@ -447,19 +458,27 @@ def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
     # the link's practical one-way rates: this library's streaming probes
     # reading, then writing, the host slot from every SM (best of 2, 4, 8 CTAs
     # per SM), and its copy loop between the two spaces
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     probes = {}
     for name, write in (("read_host", 0), ("write_host", 1)):
         best = 0.0
-        for ctas in (2, 4, 8):
-            ns = h.check(h.hicr_util_stream(inst, hs, 0, nbytes, write, 1, ctas), "stream probe")
+        for per in (2, 4, 8):
+            ns = h.check(h.hicr_util_stream(inst, hs, 0, nbytes, write, 1, per * sms), "stream probe")
             best = max(best, nbytes / ns)
         probes[name + "_GB_per_s"] = best
     for name, dst, src in (("copy_loop_hbm_to_host", hs, d), ("copy_loop_host_to_hbm", d, hs)):
         best = 0.0
-        for ctas in (2, 4, 8):
-            ns = h.check(h.hicr_util_copy_loop(inst, dst, 0, src, 0, nbytes, 1, ctas), "copy loop")
+        for per in (2, 4, 8):
+            ns = h.check(h.hicr_util_copy_loop(inst, dst, 0, src, 0, nbytes, 1, per * sms), "copy loop")
             best = max(best, nbytes / ns)
         probes[name + "_GB_per_s"] = best
+    # both directions at once: a copy inside the host slot reads and writes
+    # the link together (the bytes crossing it, both ways, per second)
+    best = 0.0
+    for per in (2, 4, 8):
+        ns = h.check(h.hicr_util_copy_loop(inst, hs, nbytes // 2, hs, 0, nbytes // 2, 1, per * sms), "copy loop")
+        best = max(best, nbytes / ns)
+    probes["copy_loop_host_to_host_both_ways_GB_per_s"] = best
     out["link_probes"] = probes
     out["nominal_c2c_GB_per_s_per_direction"] = NOMINAL_C2C_GBS
     out["frac_of_probe"] = {"hbm_to_host": out["hbm_to_host_GB_per_s"] / probes["write_host_GB_per_s"],
@@ -487,7 +506,8 @@ def bench_host_space(h, inst, nbytes=4 * GiB, op_bytes=4 * MiB, reps=5):
 
 def bench_latencies(h, inst, reps=2000):
     """Host-observed latency (median and p99 over `reps` calls, microseconds)
-    of the small synchronous operations: a 16-byte memcpy + fence, an
+    of the small synchronous operations: a 16-byte memcpy + fence (also in
+    latency mode, where a persistent server kernel takes the copy), an
     execution-unit launch + await (the built-in fill on 16 bytes), a Data
     Object get (16 bytes) + fence, and a 1-token SPSC host push + pop. Python's
     garbage collector is off while the calls are timed."""
@@ -518,6 +538,9 @@ def bench_latencies(h, inst, reps=2000):
         h.check(h.hicr_memcpy(inst, b, 0, a, 0, 16), "memcpy")
         h.check(h.hicr_fence(inst, 0, FENCE_TIMEOUT), "fence")
     out["memcpy_16B_plus_fence"] = stats(memcpy_fence)
+    h.check(h.hicr_set_latency_mode(inst, 2000), "latency mode on")
+    out["memcpy_16B_plus_fence_latency_mode"] = stats(memcpy_fence)
+    h.check(h.hicr_set_latency_mode(inst, 0), "latency mode off")
 
     unit = h.check(h.hicr_exec_unit_builtin("fill_seeded"), "exec_unit")
     ptr = h.check(h.hicr_slot_info(inst, a), "slot_info")[0]

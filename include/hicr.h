@@ -252,6 +252,21 @@ hicr_status hicr_batch_reserve(hicr_instance_t inst, uint64_t max_ops);
  * kernels over NVLink-C2C) is accepted. Errors: INVALID. */
 hicr_status hicr_set_host_copies(hicr_instance_t inst, int32_t on);
 
+/* Latency mode for small synchronous copies. With idle_us > 0, host
+ * batches of at most 8 ops of at most 256 KiB each (what single hicr_memcpy
+ * calls before a fence, Data Object gets and small hicr_memcpy_batch tables
+ * give) are not launched as kernels: a persistent server kernel of one CTA,
+ * on a stream of its own, takes them from a ring in mapped host memory and
+ * publishes their completion there, where fences poll it. The server ends
+ * after idle_us microseconds without work (at most 1 s) and the next small
+ * batch starts a new one; while it runs it holds one CTA slot of one SM, and
+ * device-wide synchronisations (cudaDeviceSynchronize, cudaFree) wait for it
+ * to end. The ops keep the model's semantics: unordered within an epoch,
+ * complete at the fence of their tag, counters exact. idle_us = 0 (the
+ * default) turns the mode off after the server's pending ops complete.
+ * Errors: INVALID (idle_us > 1,000,000 or capturing), DEVICE, TIMEOUT. */
+hicr_status hicr_set_latency_mode(hicr_instance_t inst, uint32_t idle_us);
+
 /* Checked mode: hicr_memcpy_batch and the hicr_memcpy queue also reject
  * cross-op hazards within one epoch (O(k log k) host check). Default off. */
 hicr_status hicr_set_checked(hicr_instance_t inst, int32_t on);

@@ -53,10 +53,11 @@ hicr_status hicr_util_wait_test(hicr_instance_t inst, uint64_t timeout_ns, hicr_
                                 uint64_t* waited_ns);
 
 /* Bandwidth probes: the bounds that channel and host-space measurements are
- * read against. Both run a grid of ctas_per_sm (1 .. 8) CTAs of 256 threads
- * per SM on the communication stream, each thread with eight 16-byte
- * accesses in flight, loads at L2 (bypassing L1), and return the device time
- * (CUDA events) in *device_ns. Synchronous. Ranges are 16-byte aligned with
+ * read against. Both run `ctas` CTAs of 256 threads (1 .. 8 per SM of the
+ * device in all; the scheduler spreads them over the SMs) on the
+ * communication stream, each thread with eight 16-byte accesses in flight,
+ * loads at L2 (bypassing L1), and return the device time (CUDA events) in
+ * *device_ns. Synchronous. Ranges are 16-byte aligned with
  * n a multiple of 16; slots of either memory space (host slots through
  * their device-visible address).
  *  - hicr_util_copy_loop: `reps` passes copying n bytes from src to dst
@@ -64,13 +65,12 @@ hicr_status hicr_util_wait_test(hicr_instance_t inst, uint64_t timeout_ns, hicr_
  *    MiB each way) gives the L2 copy rate;
  *  - hicr_util_stream: `reps` passes reading (write == 0) or writing
  *    (write != 0) n bytes; on a host slot, the link's one-way rate.
- * Errors: INVALID (bad slot, alignment, reps or ctas_per_sm), BOUNDS,
+ * Errors: INVALID (bad slot, alignment, reps or ctas), BOUNDS,
  * OVERLAP (copy ranges of one slot intersect), DEVICE. */
 hicr_status hicr_util_copy_loop(hicr_instance_t inst, hicr_slot_t dst, uint64_t dst_off, hicr_slot_t src,
-                                uint64_t src_off, uint64_t n, uint32_t reps, uint32_t ctas_per_sm,
-                                uint64_t* device_ns);
+                                uint64_t src_off, uint64_t n, uint32_t reps, uint32_t ctas, uint64_t* device_ns);
 hicr_status hicr_util_stream(hicr_instance_t inst, hicr_slot_t slot, uint64_t off, uint64_t n, int32_t write,
-                             uint32_t reps, uint32_t ctas_per_sm, uint64_t* device_ns);
+                             uint32_t reps, uint32_t ctas, uint64_t* device_ns);
 
 #ifdef __cplusplus
 }

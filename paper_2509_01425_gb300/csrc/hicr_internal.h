@@ -141,6 +141,22 @@ struct GraphRec {
   uint64_t sigs = 0;  // completion signals one launch of the graph emits
 };
 
+// Latency mode (latency.cu): the ring of small-batch ops a short-lived
+// persistent server kernel takes from mapped host memory. head is written by
+// the host, done and exit_epoch by the server, stop by the host.
+static constexpr unsigned LAT_RING_OPS = 256;
+struct LatOp {
+  unsigned long long dst, src, n;  // device-usable addresses, bytes
+  uint32_t dslot, sslot, dtag, stag;
+};
+struct LatRing {
+  alignas(128) unsigned long long head;        // ops published
+  alignas(128) unsigned long long done;        // ops completed (counters bumped)
+  alignas(128) unsigned long long exit_epoch;  // epoch of the last server that announced its exit
+  alignas(128) unsigned long long stop;        // ask a running server to end
+  alignas(128) LatOp ops[LAT_RING_OPS];
+};
+
 struct Channel;  // channel_host.h
 
 struct Instance {
@@ -178,6 +194,12 @@ struct Instance {
   uint64_t cap_sigs = 0;        // signals of the graph being captured
   std::vector<uint64_t> tag_sig;  // per tag: signal of the last launch with an op of that tag
   bool opaque = false;          // other work issued on the communication stream since the last full wait
+  // latency mode (latency.cu)
+  LatRing* lat_ring = nullptr;      // mapped host ring
+  LatRing* lat_ring_dev = nullptr;  // its device address
+  cudaStream_t lat_stream = nullptr;
+  uint64_t lat_head = 0, lat_epoch = 0, lat_idle_ns = 0;  // idle_ns 0 = latency mode off
+  std::vector<uint64_t> tag_lat;    // per tag: server op count to wait for
   bool capturing = false;
   std::vector<GraphRec> graphs;
 
@@ -227,6 +249,12 @@ hicr_status launch_copy_tma(Instance* in, const BatchArgs& a, const hicr_batch_c
                             cudaStream_t st);
 // Loads every stage shape of the TMA engine (cudaFuncGetAttributes).
 hicr_status copy_tma_load_all(Instance* in);
+// latency.cu: submit validated small ops to the server (launching one when
+// needed), wait until it has completed `target` ops, stop it, free it.
+hicr_status lat_submit(Instance* in, const hicr_op_t* ops, uint64_t count);
+hicr_status lat_wait(Instance* in, uint64_t target, uint64_t timeout_ns);
+hicr_status lat_stop(Instance* in);
+void lat_destroy(Instance* in);
 // memcpy_noalloc.cu: per-device set-up of the allocation-free entry point
 // (device address of its static scratch array, kernels loaded); hicr_init.
 hicr_status noalloc_setup(Instance* in);

@@ -550,7 +550,7 @@ static hicr_status launch_staged(Instance* in, uint64_t count, int k, const uint
 // Copy a host op table to the device through a double-buffered pinned
 // staging area and launch it.
 static hicr_status upload_and_launch(Instance* in, const hicr_op_t* ops, uint64_t count) {
-  if (small_batch(in, ops, count)) return launch_small(in, ops, count);
+  if (small_batch(in, ops, count)) return in->lat_idle_ns ? lat_submit(in, ops, count) : launch_small(in, ops, count);
   const int k = in->pinned_idx;
   hicr_status s = stage_prepare(in, count, k);
   if (s != HICR_OK) return s;

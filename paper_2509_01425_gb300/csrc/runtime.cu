@@ -240,6 +240,7 @@ hicr_status hicr_init(int cuda_device, hicr_instance_t* out) {
   in->dt.sig = (unsigned long long*)p; p += 2 * 8;
   in->dt.slot_meta = (uint32_t*)p;
   in->tag_sig.assign(HICR_MAX_TAGS, 0);
+  in->tag_lat.assign(HICR_MAX_TAGS, 0);
 
   Pu pu0;
   if (cudaStreamCreateWithFlags(&pu0.stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -304,6 +305,7 @@ hicr_status hicr_finalize(hicr_instance_t h) {
       return HICR_ERR_BUSY;
     }
   }
+  lat_destroy(in);
   cudaDeviceSynchronize();
   destroy_channels(in);
   destroy_servers(in);
@@ -455,6 +457,13 @@ hicr_status hicr_mem_free(hicr_instance_t h, hicr_slot_t slot) {
   Instance* in = I(h);
   if (!in || in->capturing || !valid_slot(in, slot) || !in->slots[slot].owned) return HICR_ERR_INVALID;
   HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
+  if (in->lat_ring) {
+    // ops the latency-mode server still holds may touch the slot; a stopped
+    // server does not keep the device synchronisation below waiting
+    hicr_status ls = lat_wait(in, in->lat_head, 60ull * 1000000000ull);
+    if (ls == HICR_OK) ls = lat_stop(in);
+    if (ls != HICR_OK) return ls;
+  }
   HICR_CUDA(in, cudaDeviceSynchronize());
   HostSlot& s = in->slots[slot];
   if (s.space == HICR_SPACE_HOST) cudaFreeHost(s.host_ptr);
@@ -495,6 +504,7 @@ hicr_status hicr_slot_deregister(hicr_instance_t h, hicr_slot_t slot) {
   Instance* in = I(h);
   if (!in || in->capturing || !valid_slot(in, slot) || in->slots[slot].owned) return HICR_ERR_INVALID;
   if (!in->queue.empty()) return HICR_ERR_BUSY;
+  if (in->lat_ring && *(volatile unsigned long long*)&in->lat_ring->done < in->lat_head) return HICR_ERR_BUSY;
   cudaError_t e = cudaEventQuery(in->done_ev);
   // A fence returns at the completion signal, which the last thread of a
   // launch writes just before the kernel ends: when every signal issued is
@@ -554,7 +564,11 @@ hicr_status hicr_fence(hicr_instance_t h, uint32_t tag, uint64_t timeout_ns) {
   // Every memcpy launch ends with a completion signal; the host knows the
   // signal of the last launch with an op of this tag (or of unknown tags).
   // Later launches of other tags are not waited for.
-  return fence_wait(h, in, std::max(in->tag_sig[tag], in->any_sig), timeout_ns);
+  const uint64_t t0 = now_ns();
+  st = lat_wait(in, in->tag_lat[tag], timeout_ns);  // small batches the latency-mode server took
+  if (st != HICR_OK) return st;
+  const uint64_t used = now_ns() - t0;
+  return fence_wait(h, in, std::max(in->tag_sig[tag], in->any_sig), timeout_ns > used ? timeout_ns - used : 0);
 }
 
 static hicr_status read_u64_pair(Instance* in, const unsigned long long* a, const unsigned long long* b,
@@ -602,8 +616,9 @@ hicr_status hicr_fence_slot(hicr_instance_t h, hicr_slot_t slot, uint64_t expect
   // Only launches with an op of the slot's tag can move its counters: wait
   // for the last of them (polling mapped host memory), then read the
   // counters once. If they fall short, no issued op can still raise them.
-  const uint64_t target = std::max(in->tag_sig[in->slots[slot].tag], in->any_sig);
-  st = fence_wait(h, in, target, timeout_ns);
+  const uint32_t tag = in->slots[slot].tag;
+  if ((st = lat_wait(in, in->tag_lat[tag], timeout_ns)) != HICR_OK) return st;
+  st = fence_wait(h, in, std::max(in->tag_sig[tag], in->any_sig), timeout_ns);
   if (st != HICR_OK) return st;
   uint64_t s = 0, r = 0;
   st = hicr_slot_counters(h, slot, &s, &r);

@@ -313,10 +313,9 @@ static hicr_status probe_time(Instance* in, F launch, uint64_t* device_ns) {
 extern "C" {
 
 hicr_status hicr_util_copy_loop(hicr_instance_t h, hicr_slot_t dst, uint64_t dst_off, hicr_slot_t src,
-                                uint64_t src_off, uint64_t n, uint32_t reps, uint32_t ctas_per_sm,
-                                uint64_t* device_ns) {
+                                uint64_t src_off, uint64_t n, uint32_t reps, uint32_t ctas, uint64_t* device_ns) {
   Instance* in = h ? &h->impl : nullptr;
-  if (!in || !device_ns || reps == 0 || ctas_per_sm == 0 || ctas_per_sm > 8 || in->capturing)
+  if (!in || !device_ns || reps == 0 || ctas == 0 || ctas > 8u * (uint32_t)in->sm_count || in->capturing)
     return HICR_ERR_INVALID;
   uint8_t *d = nullptr, *s = nullptr;
   hicr_status st = probe_range(in, dst, dst_off, n, &d);
@@ -324,25 +323,23 @@ hicr_status hicr_util_copy_loop(hicr_instance_t h, hicr_slot_t dst, uint64_t dst
   if (st != HICR_OK) return st;
   if (dst == src && dst_off < src_off + n && src_off < dst_off + n) return HICR_ERR_OVERLAP;
   if ((st = hicr_flush(h)) != HICR_OK) return st;
-  const unsigned grid = (unsigned)in->sm_count * ctas_per_sm;
   return probe_time(
-      in, [&](cudaStream_t cs) { k_copy_loop<<<grid, 256, 0, cs>>>((uint4*)d, (const uint4*)s, n / 16, reps); },
+      in, [&](cudaStream_t cs) { k_copy_loop<<<ctas, 256, 0, cs>>>((uint4*)d, (const uint4*)s, n / 16, reps); },
       device_ns);
 }
 
 hicr_status hicr_util_stream(hicr_instance_t h, hicr_slot_t slot, uint64_t off, uint64_t n, int32_t write,
-                             uint32_t reps, uint32_t ctas_per_sm, uint64_t* device_ns) {
+                             uint32_t reps, uint32_t ctas, uint64_t* device_ns) {
   Instance* in = h ? &h->impl : nullptr;
-  if (!in || !device_ns || reps == 0 || ctas_per_sm == 0 || ctas_per_sm > 8 || in->capturing)
+  if (!in || !device_ns || reps == 0 || ctas == 0 || ctas > 8u * (uint32_t)in->sm_count || in->capturing)
     return HICR_ERR_INVALID;
   uint8_t* p = nullptr;
   hicr_status st = probe_range(in, slot, off, n, &p);
   if (st != HICR_OK) return st;
   if ((st = hicr_flush(h)) != HICR_OK) return st;
   unsigned long long* sink = in->dt.sticky + 1;  // spare word next to the sticky error (never written in practice)
-  const unsigned grid = (unsigned)in->sm_count * ctas_per_sm;
   return probe_time(
-      in, [&](cudaStream_t cs) { k_stream<<<grid, 256, 0, cs>>>((uint4*)p, n / 16, reps, write ? 1 : 0, sink); },
+      in, [&](cudaStream_t cs) { k_stream<<<ctas, 256, 0, cs>>>((uint4*)p, n / 16, reps, write ? 1 : 0, sink); },
       device_ns);
 }
 

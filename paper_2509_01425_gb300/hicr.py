@@ -133,6 +133,7 @@ _batch_error = _decl("hicr_batch_error", [H, C.POINTER(i32), C.POINTER(u64)])
 _batch_reserve = _decl("hicr_batch_reserve", [H, u64])
 _set_checked = _decl("hicr_set_checked", [H, i32])
 _set_host_copies = _decl("hicr_set_host_copies", [H, i32])
+_set_latency_mode = _decl("hicr_set_latency_mode", [H, u32])
 _fence = _decl("hicr_fence", [H, u32, u64])
 _fence_slot = _decl("hicr_fence_slot", [H, u32, u64, u64, u64])
 _slot_counters = _decl("hicr_slot_counters", [H, u32, C.POINTER(u64), C.POINTER(u64)])
@@ -273,6 +274,10 @@ def hicr_batch_reserve(inst, max_ops):
 
 def hicr_set_checked(inst, on):
     return _set_checked(inst, 1 if on else 0)
+
+
+def hicr_set_latency_mode(inst, idle_us):
+    return _set_latency_mode(inst, idle_us)
 
 
 def hicr_set_host_copies(inst, on):
@@ -439,15 +444,15 @@ def hicr_util_wait_test(inst, timeout_ns):
     return st, st_.value, w.value
 
 
-def hicr_util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas_per_sm=4):
+def hicr_util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas):
     v = u64()
-    st = _util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas_per_sm, C.byref(v))
+    st = _util_copy_loop(inst, dst, dst_off, src, src_off, n, reps, ctas, C.byref(v))
     return st, v.value
 
 
-def hicr_util_stream(inst, slot, off, n, write, reps, ctas_per_sm=4):
+def hicr_util_stream(inst, slot, off, n, write, reps, ctas):
     v = u64()
-    st = _util_stream(inst, slot, off, n, 1 if write else 0, reps, ctas_per_sm, C.byref(v))
+    st = _util_stream(inst, slot, off, n, 1 if write else 0, reps, ctas, C.byref(v))
     return st, v.value
 
 

@@ -12,7 +12,10 @@
  *                   bytes (1 CTA), then hicr_exec_await;
  *   spsc_push_pop   hicr_channel_push of one 64-byte token, then
  *                   hicr_channel_pop of it;
- *   dobj_get_fence  hicr_dobj_get of a 16-byte Data Object, then hicr_fence.
+ *   dobj_get_fence  hicr_dobj_get of a 16-byte Data Object, then hicr_fence;
+ *   memcpy16_fence_latency_mode, dobj_get_fence_latency_mode
+ *                   the same two with hicr_set_latency_mode on (a persistent
+ *                   server kernel takes the small copies; no launch per call).
  * Exit status 0 on success, 1 on any library error (its name is printed).
  */
 #include <stdint.h>
@@ -130,7 +133,24 @@ int main(int argc, char** argv) {
       CHECK(hicr_fence(inst, 0, fence_to));
       if (i >= 0) t[i] = now_ns() - t0;
     }
-    report("dobj_get_fence", t, reps, 1);
+    report("dobj_get_fence", t, reps, 0);
+
+    CHECK(hicr_set_latency_mode(inst, 2000));
+    for (int i = -warm; i < reps; ++i) {
+      const uint64_t t0 = now_ns();
+      CHECK(hicr_memcpy(inst, b, 64 * (uint64_t)(i & 1023), a, 16 * (uint64_t)(i & 4095), 16));
+      CHECK(hicr_fence(inst, 0, fence_to));
+      if (i >= 0) t[i] = now_ns() - t0;
+    }
+    report("memcpy16_fence_latency_mode", t, reps, 0);
+    for (int i = -warm; i < reps; ++i) {
+      const uint64_t t0 = now_ns();
+      CHECK(hicr_dobj_get(inst, &hd, b, 16 * (uint64_t)(i & 4095)));
+      CHECK(hicr_fence(inst, 0, fence_to));
+      if (i >= 0) t[i] = now_ns() - t0;
+    }
+    report("dobj_get_fence_latency_mode", t, reps, 1);
+    CHECK(hicr_set_latency_mode(inst, 0));
     CHECK(hicr_dobj_release(inst, id));
   }
   printf("}\n");

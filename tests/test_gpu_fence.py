@@ -184,5 +184,86 @@ def test_c_latency_harness(h, inst):
     assert r.returncode == 0, r.stderr
     d = json.loads(r.stdout)
     print(d, flush=True)
-    for k in ("memcpy16_fence", "fence_idle", "exec_await", "spsc_push_pop", "dobj_get_fence"):
+    for k in ("memcpy16_fence", "fence_idle", "exec_await", "spsc_push_pop", "dobj_get_fence",
+              "memcpy16_fence_latency_mode", "dobj_get_fence_latency_mode"):
         assert 0 < d[k]["p50_us"] <= d[k]["p99_us"] <= d[k]["max_us"]
+
+
+@pytest.mark.parametrize("idle_us", [50, 5000])
+def test_latency_mode_matches_the_oracle(h, inst, idle_us):
+    """Latency mode: small host batches go to the persistent server (which
+    ends after idle_us without work, so the short window also exercises its
+    relaunch), large ones to the stream; fences on each tag, slot
+    deregistration and freeing interleave with them. Bytes (read without
+    device-wide synchronisation) and counters equal the oracle's after every
+    fence; at the end the mode is turned off and everything still matches.
+    The server runs beside the stream, so the program respects the model's
+    rule that ops not separated by a fence of their tag are unordered: no
+    destination byte is written twice between two fences on all tags."""
+    rng = np.random.default_rng(idle_us)
+    assert h.hicr_set_latency_mode(inst, idle_us) == 0
+    tags = [0, 1, 2, 0, 1, 2]
+    size = 4 << 20
+    ids = []
+    cm = om.CommManager()
+    for s_, tg in enumerate(tags):
+        st, sid = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size, tg)
+        assert st == 0 and h.hicr_util_fill(inst, sid, 0, size, splitmix.fill_key_base(6, s_)) == 0
+        ids.append(sid)
+        cm.register(om.SPACE_HBM, splitmix.fill_bytes(6, s_, 0, size), tg)
+    cursor = {}  # per slot: destination bytes below it were written since the last fence on all tags
+    for rnd in range(60):
+        big = rnd % 7 == 3
+        n_ops = int(rng.integers(9, 30)) if big else int(rng.integers(1, 9))
+        if max(cursor.values(), default=0) > size // 4:
+            for tg in range(3):
+                assert h.hicr_fence(inst, tg, T) == 0
+            cursor = {}
+        dst, src, doff, soff, n = [], [], [], [], []
+        for _ in range(n_ops):
+            d, s_ = rng.choice(len(tags), 2, replace=False)
+            k = int(rng.integers(0, 300_000 if big else 70_000))
+            c = cursor.get(int(d), 0)
+            if c + k > size // 2:
+                continue
+            dst.append(int(d)), src.append(int(s_)), doff.append(c), n.append(k)
+            soff.append(size // 2 + int(rng.integers(0, size // 2 - k)))
+            cursor[int(d)] = c + k + int(rng.integers(0, 64))
+        if not n:
+            continue
+        ops = configs.make_ops(dst, src, doff, soff, n)
+        assert cm.memcpy_batch(ops) == (om.OK, None)
+        g = ops.copy()
+        g["dst"] = np.asarray(ids, dtype=np.uint32)[ops["dst"]]
+        g["src"] = np.asarray(ids, dtype=np.uint32)[ops["src"]]
+        if rnd % 2:
+            assert h.hicr_memcpy_batch(inst, g) == (0, 0)
+        else:
+            for o in g:
+                assert h.hicr_memcpy(inst, int(o["dst"]), int(o["dst_off"]), int(o["src"]), int(o["src_off"]),
+                                     int(o["n"])) == 0
+        if rnd % 3 == 0:
+            time.sleep(0.002)  # sometimes longer than the idle window: the server ends and restarts
+        tag = int(rng.integers(0, 3))
+        assert h.hicr_fence(inst, tag, T) == 0
+        for k, sid in enumerate(ids):
+            if tags[k] != tag:
+                continue
+            st, ptr, sz, _, _ = h.hicr_slot_info(inst, sid)
+            assert (device_bytes(ptr, sz).cpu().numpy() == cm.slots[k].data).all(), (rnd, k)
+            assert h.hicr_slot_counters(inst, sid)[1:] == cm.counters(k), (rnd, k)
+    for tg in range(3):
+        assert h.hicr_fence(inst, tg, T) == 0
+        assert h.hicr_tag_counter(inst, tg) == (0, cm.tag_ops.get(tg, 0))
+    # a registered slot leaves only when the server has finished with it
+    t = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    st, r = h.hicr_slot_register(inst, h.HICR_SPACE_HBM, t.data_ptr(), 4096, 0)
+    assert st == 0 and h.hicr_memcpy(inst, r, 0, ids[0], 0, 4096) == 0 and h.hicr_flush(inst) == 0
+    assert h.hicr_fence(inst, 0, T) == 0 and h.hicr_slot_deregister(inst, r) == 0
+    assert (t.cpu().numpy() == cm.slots[0].data[:4096]).all()
+    assert h.hicr_set_latency_mode(inst, 0) == 0
+    for k, sid in enumerate(ids):
+        assert (slot_bytes(h, inst, sid) == cm.slots[k].data).all(), k
+        assert h.hicr_slot_counters(inst, sid)[1:] == cm.counters(k), k
+        assert h.hicr_mem_free(inst, sid) == 0
+    assert h.hicr_set_latency_mode(inst, 2_000_000) == h.HICR_ERR_INVALID
