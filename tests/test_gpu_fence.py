@@ -258,9 +258,11 @@ def test_latency_mode_matches_the_oracle(h, inst, idle_us):
     # a registered slot leaves only when the server has finished with it
     t = torch.zeros(4096, dtype=torch.uint8, device="cuda")
     st, r = h.hicr_slot_register(inst, h.HICR_SPACE_HBM, t.data_ptr(), 4096, 0)
+    ro = cm.register(om.SPACE_HBM, np.zeros(4096, dtype=np.uint8), 0)
+    assert cm.memcpy(ro, 0, 0, 0, 4096) == om.OK
     assert st == 0 and h.hicr_memcpy(inst, r, 0, ids[0], 0, 4096) == 0 and h.hicr_flush(inst) == 0
     assert h.hicr_fence(inst, 0, T) == 0 and h.hicr_slot_deregister(inst, r) == 0
-    assert (t.cpu().numpy() == cm.slots[0].data[:4096]).all()
+    assert (t.cpu().numpy() == cm.slots[ro].data).all()
     assert h.hicr_set_latency_mode(inst, 0) == 0
     for k, sid in enumerate(ids):
         assert (slot_bytes(h, inst, sid) == cm.slots[k].data).all(), k
