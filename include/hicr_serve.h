@@ -80,6 +80,9 @@ typedef struct {
   uint64_t dev_flags;        /* bit 0 stop seen, bit 1 abort (deadline), bit 2 self-check */
   int32_t status;            /* HICR_OK or HICR_ERR_TIMEOUT */
   uint32_t reserved;
+  uint64_t burst_bytes;      /* the burst part of bytes_moved (the rest is memcpy payload): each burst
+                                byte is read from staging, written to a ring and read by the consumer
+                                (3 bytes of traffic), each memcpy byte read and written once (2) */
 } hicr_serve_stats_t;
 
 /* Create a serving engine: allocates the destination arena and the channel

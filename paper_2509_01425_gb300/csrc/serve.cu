@@ -1120,7 +1120,7 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
   arena.reset(sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
   std::vector<uint64_t> region_off(n, 0), region_len(n, 0), admit_t(n, 0);
   std::vector<uint64_t> inflight;
-  uint64_t next_arrival = 0, next_admit = 0, completed = 0, max_inflight = 0, bytes = 0;
+  uint64_t next_arrival = 0, next_admit = 0, completed = 0, max_inflight = 0, bytes = 0, burst_bytes = 0;
   std::vector<uint64_t> waiting;  // arrived, not admitted (FIFO)
   size_t wait_head = 0;
   const uint64_t t0 = now_ns();
@@ -1177,6 +1177,7 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
           if (!sv->kept[r]) arena.release(region_off[r], region_len[r]);
         } else {
           bytes += sv->m_bytes[reqs[r].tmpl];
+          burst_bytes += sv->m_bytes[reqs[r].tmpl];
         }
         ++completed;
         last_done = tnow;
@@ -1289,6 +1290,7 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
   if (stats) {
     stats->completed = completed;
     stats->bytes_moved = bytes;
+    stats->burst_bytes = burst_bytes;
     stats->wall_ns = last_done - t0 - (n && mode == 0 ? std::min<uint64_t>(last_done - t0, reqs[0].arrival_ns) : 0);
     stats->max_inflight = max_inflight;
     stats->max_region_bytes = arena.high;
@@ -1346,7 +1348,7 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
   arena.reset(sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
   std::vector<uint64_t> region_off(m, 0), region_len(m, 0);
   std::vector<uint64_t> ring_pos(sv->cfg.n_channels, 0);
-  uint64_t next = 0, head = 0, completed = 0, bytes = 0, max_inflight = 0;  // in-flight = [head, next)
+  uint64_t next = 0, head = 0, completed = 0, bytes = 0, burst_bytes = 0, max_inflight = 0;  // in-flight = [head, next)
   const uint64_t t0 = now_ns();
   uint64_t last_done = t0;
   hicr_status result = HICR_OK;
@@ -1402,6 +1404,7 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
         arena.release(region_off[head], region_len[head]);
       } else {
         bytes += sv->m_bytes[q.tmpl];
+        burst_bytes += sv->m_bytes[q.tmpl];
       }
       ++completed;
       ++head;
@@ -1418,6 +1421,7 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
   if (stats) {
     stats->completed = completed;
     stats->bytes_moved = bytes;
+    stats->burst_bytes = burst_bytes;
     stats->wall_ns = last_done - t0 - (m ? std::min<uint64_t>(last_done - t0, reqs[0].arrival_ns) : 0);
     stats->max_inflight = max_inflight;
     stats->max_region_bytes = arena.high;

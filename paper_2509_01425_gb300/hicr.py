@@ -658,7 +658,8 @@ class hicr_serve_config_t(C.Structure):
 class hicr_serve_stats_t(C.Structure):
     _fields_ = [("completed", u64), ("bytes_moved", u64), ("wall_ns", u64), ("max_inflight", u64),
                 ("max_region_bytes", u64), ("admitted", u64), ("dev_units", u64), ("dev_claimed", u64),
-                ("dev_requests", u64), ("dev_flags", u64), ("status", i32), ("reserved", u32)]
+                ("dev_requests", u64), ("dev_flags", u64), ("status", i32), ("reserved", u32),
+                ("burst_bytes", u64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
