@@ -350,10 +350,18 @@ def bench_spsc(h, inst, reps=3):
     stg = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, w.n_channels * staged * w.token_bytes), "staging")
     h.check(h.hicr_util_fill(inst, stg, 0, w.n_channels * staged * w.token_bytes, splitmix.fill_key_base(0, 77)),
             "fill staging")
+    # tokens per head/tail update for this form, tuned the same way
+    ctune = {}
+    for b in (256, 512, 1024, 2048):
+        t0 = time.perf_counter()
+        h.check(h.hicr_spsc_stream_ex(inst, chans, w.tokens_per_channel // 10, b, src=stg, src_tokens=staged)[0],
+                "spsc copy tune")
+        ctune[b] = time.perf_counter() - t0
+    cbatch = min(ctune, key=ctune.get)
     ctimes = []
     for r in range(reps + 1):
         t0 = time.perf_counter()
-        st, res = h.hicr_spsc_stream_ex(inst, chans, w.tokens_per_channel, batch, src=stg, src_tokens=staged)
+        st, res = h.hicr_spsc_stream_ex(inst, chans, w.tokens_per_channel, cbatch, src=stg, src_tokens=staged)
         if r:
             ctimes.append(time.perf_counter() - t0)
         h.check(st, "spsc_stream copy")
@@ -383,7 +391,7 @@ def bench_spsc(h, inst, reps=3):
             "copy_producers": {
                 "workload": "the same channels; producers copy staged tokens (token s of a channel = staged token "
                             "s mod 4,096; 16 MiB staged in all) into the ring, consumers digest only",
-                "msgs_per_s": tokens / tc, "s_per_run": tc,
+                "msgs_per_s": tokens / tc, "s_per_run": tc, "batch_tokens": cbatch,
                 "l2_GB_per_s": tokens * 192 / tc / 1e9,
                 "l2_bytes_per_token": 192,
                 "l2_copy_bound_GB_per_s": l2,
