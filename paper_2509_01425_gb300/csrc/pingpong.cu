@@ -194,6 +194,8 @@ static hicr_status pingpong_run(hicr_instance_t h, hicr_slot_t src, uint64_t src
   if (src_off > ssize || bytes > ssize - src_off) return HICR_ERR_BOUNDS;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  // a cooperative grid sized for the whole device: a latency-mode server ends first
+  if ((st = lat_stop(in)) != HICR_OK) return st;
   // the two single-message buffers (one allocation, freed at the end)
   uint8_t* bufs = nullptr;
   const uint64_t half = (bytes + 255) & ~255ull;

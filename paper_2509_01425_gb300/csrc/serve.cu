@@ -1036,6 +1036,8 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
   }
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  // a cooperative grid sized for the whole device: a latency-mode server ends first
+  if ((st = lat_stop(in)) != HICR_OK) return st;
   HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
   if ((st = srv_upload(in, sv)) != HICR_OK) return st;
 

@@ -1022,6 +1022,8 @@ static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
   }
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  // a cooperative grid sized for the whole device: a latency-mode server ends first
+  if ((st = lat_stop(in)) != HICR_OK) return st;
   const size_t vb = ((sizeof(SpscView) * n + 255) / 256) * 256;
   const size_t rb = sizeof(hicr_spsc_result_t) * n;
   void* buf = nullptr;
@@ -1130,6 +1132,8 @@ static hicr_status mpsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
   if (!grid) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  // a cooperative grid sized for the whole device: a latency-mode server ends first
+  if ((st = lat_stop(in)) != HICR_OK) return st;
   const size_t vb = ((sizeof(MpscView) * n_consumers + 255) / 256) * 256;
   const size_t rb = ((sizeof(hicr_mpsc_result_t) * n_consumers + 255) / 256) * 256;
   const size_t cb = 128 * (size_t)n_consumers;  // claim counters, one 128-byte line each
@@ -1225,6 +1229,8 @@ static hicr_status nl_stream_run(hicr_instance_t h, const hicr_channel_t* chans,
   if (!grid) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  // a cooperative grid sized for the whole device: a latency-mode server ends first
+  if ((st = lat_stop(in)) != HICR_OK) return st;
   const size_t vb = ((sizeof(NlView) * n_consumers + 255) / 256) * 256;
   const size_t rb = ((sizeof(hicr_mpsc_result_t) * n_consumers + 255) / 256) * 256;
   const size_t cb = ((sizeof(unsigned long long) * n_consumers + 255) / 256) * 256;

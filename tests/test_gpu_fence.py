@@ -269,3 +269,31 @@ def test_latency_mode_matches_the_oracle(h, inst, idle_us):
         assert h.hicr_slot_counters(inst, sid)[1:] == cm.counters(k), k
         assert h.hicr_mem_free(inst, sid) == 0
     assert h.hicr_set_latency_mode(inst, 2_000_000) == h.HICR_ERR_INVALID
+
+
+def test_latency_mode_beside_cooperative_runs(h, inst):
+    """A live latency-mode server does not get in the way of this library's
+    cooperative runs (they end it first): small copies, then an SPSC stream
+    and a ping-pong, then more small copies, all correct."""
+    size = 1 << 20
+    st, a = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
+    st2, b = h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, size)
+    assert st == 0 and st2 == 0
+    assert h.hicr_util_fill(inst, a, 0, size, splitmix.fill_key_base(8, 0)) == 0
+    assert h.hicr_set_latency_mode(inst, 1_000_000) == 0  # a server that would stay for a second
+    for i in range(4):
+        assert h.hicr_memcpy(inst, b, 4096 * i, a, 4096 * i, 4096) == 0
+    assert h.hicr_fence(inst, 0, T) == 0
+    chans = [h.hicr_spsc_create(inst, 64, 256)[1] for _ in range(152)]  # one CTA per SM for each side
+    st, res = h.hicr_spsc_stream(inst, chans, 2000, 64)
+    assert st == 0 and all(r.popped == 2000 and r.mismatches == 0 for r in res)
+    st, r = h.hicr_pingpong(inst, a, 0, 1 << 16, 10, 2, 152)
+    assert st == 0 and r.status == 0
+    for i in range(4, 8):
+        assert h.hicr_memcpy(inst, b, 4096 * i, a, 4096 * i, 4096) == 0
+    assert h.hicr_fence(inst, 0, T) == 0
+    assert (slot_bytes(h, inst, b)[:8 * 4096] == splitmix.fill_bytes(8, 0, 0, 8 * 4096)).all()
+    assert h.hicr_slot_counters(inst, b)[1:] == (0, 8)
+    assert h.hicr_set_latency_mode(inst, 0) == 0
+    for c in chans:
+        assert h.hicr_channel_destroy(inst, c) == 0
