@@ -206,12 +206,17 @@ def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
     (3, 64, 32, 5000, 1, 64),
     (2, 100, 48, 2_000, 7, 33),      # the general layout
     (1, 8, 16, 333, 8, 1),
+    (1, 4096, 64, 20_000, 2048, 1),  # 128 one-token pieces per producer warp: the vector fallback
+    (80, 64, 64, 3_000, 32, 64),     # 160 CTAs do not fit with the stages: vector producers
 ])
 def test_spsc_copy_producers_deliver_the_staged_tokens(h, inst, n_ch, cap, ts, tokens, batch, staged):
     """Producers that push by copying from a memory slot (Sec. 4.3): token s
     of channel i is staged token (s mod staged) of that channel; the captured
     stream equals that sequence pushed through the SPSC oracle, and the digest
-    equals the oracle digest of those words."""
+    equals the oracle digest of those words. The producers copy by bulk
+    copies through shared memory when both sides fit on the device with their
+    stages, by vector copies otherwise (and for shares cut into more than 32
+    pieces)."""
     rng = np.random.default_rng(ts * 1000 + n_ch)
     pool = rng.integers(0, 256, n_ch * staged * ts + 16, dtype=np.uint8)
     s, keep = src_slot(h, inst, pool)
