@@ -176,8 +176,12 @@ typedef struct {
  * (1 .. capacity); the consumer checks every word, accumulates the digest and
  * releases the tail per batch. Every wait gives up after `timeout_ns`
  * (result status TIMEOUT). Synchronous; `results` is a host array of n.
- * Errors: INVALID (bad channel, token size, batch, empty list), DEVICE,
- * TIMEOUT (any channel timed out; the results say which). */
+ * Both CTAs of every channel must be resident at once: one CTA of 512
+ * threads fits an SM (about 128 registers a thread), so n is at most half
+ * the SM count (76 on a GB300).
+ * Errors: INVALID (bad channel, token size, batch, empty list, more channels
+ * than can be resident), DEVICE, TIMEOUT (any channel timed out; the results
+ * say which). */
 hicr_status hicr_spsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
                              uint32_t batch, uint64_t timeout_ns, hicr_spsc_result_t* results);
 

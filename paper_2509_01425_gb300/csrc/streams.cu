@@ -17,26 +17,6 @@
 
 namespace hicr {
 
-// Producer warps copy their groups through PROD_NST shared-memory stages of
-// PROD_STG bytes each (bulk copies); a producer CTA holds at most PROD_WARPS
-// producer warps.
-static constexpr unsigned PROD_NST = 2, PROD_STG = 6144, PROD_WARPS = 16;
-static constexpr size_t PROD_SMEM = (size_t)PROD_WARPS * PROD_NST * (PROD_STG + 8);
-static constexpr unsigned long long PROD_WAIT_NS = 2000000000ull;  // bound of one stage wait
-
-// The warp's stages and mbarriers in the dynamic shared memory of a producer
-// CTA; lane 0 initialises the mbarriers.
-__device__ __forceinline__ void prod_stages(uint8_t* smem, unsigned warp, unsigned lane, uint8_t** stage,
-                                            unsigned long long** bars) {
-  *stage = smem + (size_t)warp * PROD_NST * PROD_STG;
-  *bars = reinterpret_cast<unsigned long long*>(smem + (size_t)PROD_WARPS * PROD_NST * PROD_STG) + warp * PROD_NST;
-  if (lane == 0) {
-    for (unsigned k = 0; k < PROD_NST; ++k) mbar_init(*bars + k);
-    mbar_init_fence();
-  }
-  __syncwarp();
-}
-
 // ---------------------------------------------------------------------------
 // SPSC streaming: CTA 2i produces into channel i, CTA 2i+1 consumes it.
 // Template switches:
@@ -47,12 +27,7 @@ __device__ __forceinline__ void prod_stages(uint8_t* smem, unsigned warp, unsign
 //   VERIFY   the consumer compares every word with the payload rule;
 //   CAPTURE  the consumer also stores every token it consumed, in order, to
 //            the capture area (token s of channel i at cap + i * cap_stride +
-//            s * token_size), so that the tokens can be compared one by one;
-//   BULK     (with COPY) the producer's warps move their share of each batch
-//            by bulk copies through shared-memory stages (group_copy_bulk):
-//            a share is cut where the ring or the staged tokens wrap, and a
-//            share with more than 32 pieces (very few staged tokens) falls
-//            back to vector copies.
+//            s * token_size), so that the tokens can be compared one by one.
 // The consumer always folds the consumed words into the digest.
 // ---------------------------------------------------------------------------
 struct SpscStreamArgs {
@@ -80,10 +55,9 @@ __device__ __forceinline__ uint4 words_to_vec(unsigned long long w0, unsigned lo
   return x;
 }
 
-template <bool COPY, bool VERIFY, bool CAPTURE, bool BULK>
+template <bool COPY, bool VERIFY, bool CAPTURE>
 __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
-  __shared__ int s_stop, s_fail;
-  extern __shared__ __align__(128) uint8_t spsc_smem[];
+  __shared__ int s_stop;
   __shared__ unsigned long long s_red[2][16];
   const unsigned ci = blockIdx.x >> 1;
   const bool producer = (blockIdx.x & 1u) == 0;
@@ -96,18 +70,10 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   const uint8_t* src = COPY ? a.src + (unsigned long long)ci * a.src_tokens * v.ts : nullptr;
   uint8_t* cap = CAPTURE ? a.cap + (unsigned long long)ci * a.cap_stride : nullptr;
   const unsigned long long W = COPY ? a.src_tokens : 1;
-  const unsigned lane = tid & 31u, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  uint8_t* stage = nullptr;
-  unsigned long long* bars = nullptr;
-  unsigned phase = 0;  // the warp's stage parities (bulk producers)
-  if (BULK && producer) prod_stages(spsc_smem, warp, lane, &stage, &bars);
   // The channel starts empty (head == tail); token s of this run has counter
   // value base + s and ring slot (base + s) mod capacity.
   __shared__ unsigned long long s_base;
-  if (tid == 0) {
-    s_base = ld_acq(producer ? &v.st->head.v : &v.st->tail.v);
-    s_fail = 0;
-  }
+  if (tid == 0) s_base = ld_acq(producer ? &v.st->head.v : &v.st->tail.v);
   __syncthreads();
   const unsigned long long base = s_base;
   // fast layout when the vectors of a token divide the block
@@ -145,41 +111,7 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
     }
     __syncthreads();
     if (s_stop) break;
-    if (BULK && producer) {
-      // warp w moves tokens [lo, hi) of the batch; piece j (lane j) is a run
-      // of tokens contiguous both in the ring and among the staged tokens
-      const unsigned long long lo = k * warp / nwarp, hi = k * (warp + 1) / nwarp;
-      uint8_t* my_d = nullptr;
-      const uint8_t* my_s = nullptr;
-      unsigned long long my_n = 0;
-      int np = 0;
-      for (unsigned long long t = lo; t < hi && np <= 32;) {
-        const unsigned long long slot = (base + s0 + t) % v.cap, sp = (s0 + t) % W;
-        const unsigned long long len = min(hi - t, min(v.cap - slot, W - sp));
-        if (lane == (unsigned)np) {
-          my_d = v.ring + slot * v.ts;
-          my_s = src + sp * v.ts;
-          my_n = len * v.ts;
-        }
-        ++np;
-        t += len;
-      }
-      if (np <= 32) {
-        if (!group_copy_bulk<PROD_NST, PROD_STG>(my_d, my_s, my_n, np, lane, stage, bars, phase, PROD_WAIT_NS)) {
-          if (lane == 0) {
-            s_fail = 1;
-            atomicExch(a.abort, 1u);
-          }
-        }
-      } else {
-        for (unsigned long long q = lane; q < (hi - lo) * vpt; q += 32) {
-          const unsigned long long t = lo + q / vpt;
-          *(reinterpret_cast<uint4*>(v.ring + ((base + s0 + t) % v.cap) * v.ts) + q % vpt) =
-              __ldcg(reinterpret_cast<const uint4*>(src + ((s0 + t) % W) * v.ts) + q % vpt);
-        }
-      }
-      __threadfence();
-    } else if (fast) {
+    if (fast) {
       // thread = vector column jv of tokens tl0, tl0 + tpi, ...; ring slots
       // (and staged positions) advance by `step` (`sstep`) without a
       // division per vector
@@ -280,13 +212,8 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
       }
     }
     // the barrier orders every thread's ring accesses before thread 0's
-    // release store, which is cumulative: no per-thread fence is needed (bulk
-    // stores are ordered for it by their warp's proxy fence and fence)
+    // release store, which is cumulative: no per-thread fence is needed
     __syncthreads();
-    if (BULK && producer && s_fail) {
-      if (tid == 0) s_stop = 1;
-      break;
-    }
     if (tid == 0) st_rel(producer ? &v.st->head.v : &v.st->tail.v, base + s0 + k);
     done = s0 + k;
   }
@@ -348,6 +275,26 @@ struct MpscStreamArgs {
 };
 
 static constexpr int MPSC_MAX_GROUP = 8;
+// Producer warps copy their groups through PROD_NST shared-memory stages of
+// PROD_STG bytes each (bulk copies); a producer CTA holds at most PROD_WARPS
+// producer warps.
+static constexpr unsigned PROD_NST = 2, PROD_STG = 6144, PROD_WARPS = 16;
+static constexpr size_t PROD_SMEM = (size_t)PROD_WARPS * PROD_NST * (PROD_STG + 8);
+static constexpr unsigned long long PROD_WAIT_NS = 2000000000ull;  // bound of one stage wait
+
+// The warp's stages and mbarriers in the dynamic shared memory of a producer
+// CTA; lane 0 initialises the mbarriers.
+__device__ __forceinline__ void prod_stages(uint8_t* smem, unsigned warp, unsigned lane, uint8_t** stage,
+                                            unsigned long long** bars) {
+  *stage = smem + (size_t)warp * PROD_NST * PROD_STG;
+  *bars = reinterpret_cast<unsigned long long*>(smem + (size_t)PROD_WARPS * PROD_NST * PROD_STG) + warp * PROD_NST;
+  if (lane == 0) {
+    for (unsigned k = 0; k < PROD_NST; ++k) mbar_init(*bars + k);
+    mbar_init_fence();
+  }
+  __syncwarp();
+}
+
 __device__ void mpsc_producer(const MpscStreamArgs& a, unsigned p, unsigned lane, unsigned long long deadline,
                               uint8_t* stage, unsigned long long* bars) {
   unsigned phase = 0;
@@ -1073,6 +1020,13 @@ static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
         (unsigned __int128)tokens * ts > (unsigned __int128)opts->capture_stride)
       return HICR_ERR_INVALID;
   }
+  const void* k;
+  if (copy) k = capture ? (const void*)k_spsc_stream<true, false, true> : (const void*)k_spsc_stream<true, false, false>;
+  else k = capture ? (const void*)k_spsc_stream<false, true, true> : (const void*)k_spsc_stream<false, true, false>;
+  // both CTAs of every channel must be resident at once
+  int per_sm = 0;
+  HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 512, 0));
+  if (2ull * n > (unsigned long long)per_sm * in->sm_count) return HICR_ERR_INVALID;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
   // a cooperative grid sized for the whole device: a latency-mode server ends first
@@ -1097,29 +1051,8 @@ static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
   a.src_tokens = copy ? opts->src_tokens : 0;
   a.cap = capture ? (uint8_t*)opts->d_capture : nullptr;
   a.cap_stride = capture ? opts->capture_stride : 0;
-  const void* k;
-  size_t smem = 0;
-  if (copy) {
-    // bulk-copying producers when both sides fit with their stages (one CTA
-    // of 512 threads and the stages per SM)
-    const void* kb = capture ? (const void*)k_spsc_stream<true, false, true, true>
-                             : (const void*)k_spsc_stream<true, false, false, true>;
-    int per_sm = 0;
-    HICR_CUDA(in, cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROD_SMEM));
-    HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kb, 512, PROD_SMEM));
-    if (2ull * n <= (unsigned long long)per_sm * in->sm_count && ts % 16 == 0) {
-      k = kb;
-      smem = PROD_SMEM;
-    } else {
-      k = capture ? (const void*)k_spsc_stream<true, false, true, false>
-                  : (const void*)k_spsc_stream<true, false, false, false>;
-    }
-  } else {
-    k = capture ? (const void*)k_spsc_stream<false, true, true, false>
-                : (const void*)k_spsc_stream<false, true, false, false>;
-  }
   void* args[] = {&a};
-  HICR_CUDA(in, cudaLaunchCooperativeKernel(k, dim3(2 * n), dim3(512), args, smem, s));
+  HICR_CUDA(in, cudaLaunchCooperativeKernel(k, dim3(2 * n), dim3(512), args, 0, s));
   HICR_CUDA(in, cudaMemcpyAsync(results, a.res, rb, cudaMemcpyDeviceToHost, s));
   HICR_CUDA(in, cudaStreamSynchronize(s));
   if ((st = record_done(in)) != HICR_OK) return st;

@@ -206,17 +206,14 @@ def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
     (3, 64, 32, 5000, 1, 64),
     (2, 100, 48, 2_000, 7, 33),      # the general layout
     (1, 8, 16, 333, 8, 1),
-    (1, 4096, 64, 20_000, 2048, 1),  # 128 one-token pieces per producer warp: the vector fallback
-    (80, 64, 64, 3_000, 32, 64),     # 160 CTAs do not fit with the stages: vector producers
+    (1, 4096, 64, 20_000, 2048, 1),  # one staged token
+    (76, 64, 64, 3_000, 32, 64),     # as many channels as can be resident: one CTA on every SM
 ])
 def test_spsc_copy_producers_deliver_the_staged_tokens(h, inst, n_ch, cap, ts, tokens, batch, staged):
     """Producers that push by copying from a memory slot (Sec. 4.3): token s
     of channel i is staged token (s mod staged) of that channel; the captured
     stream equals that sequence pushed through the SPSC oracle, and the digest
-    equals the oracle digest of those words. The producers copy by bulk
-    copies through shared memory when both sides fit on the device with their
-    stages, by vector copies otherwise (and for shares cut into more than 32
-    pieces)."""
+    equals the oracle digest of those words."""
     rng = np.random.default_rng(ts * 1000 + n_ch)
     pool = rng.integers(0, 256, n_ch * staged * ts + 16, dtype=np.uint8)
     s, keep = src_slot(h, inst, pool)
@@ -241,6 +238,15 @@ def test_spsc_copy_producers_deliver_the_staged_tokens(h, inst, n_ch, cap, ts, t
         h.HICR_ERR_BOUNDS
     assert h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=8, src_tokens=staged)[0] == \
         h.HICR_ERR_INVALID
+
+
+def test_spsc_stream_rejects_more_channels_than_can_be_resident(h, inst):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    chans = [h.hicr_spsc_create(inst, 64, 64)[1] for _ in range(sms // 2 + 1)]
+    assert h.hicr_spsc_stream(inst, chans, 100, 16)[0] == h.HICR_ERR_INVALID
+    assert h.hicr_spsc_stream(inst, chans[:-1], 100, 16)[0] == h.HICR_OK
+    for c in chans:
+        assert h.hicr_channel_destroy(inst, c) == 0
 
 
 def _oracle_deliveries(w, ring, max_msgs, nonlocking):
