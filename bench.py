@@ -1165,8 +1165,9 @@ def run_control_small(args):
     (k_fill_segments, k_mpsc_check, k_nl_check, the streams' set-up and
     wrap-up kernels, and the two stream kernels); two allocation-free batches
     of 10,000 ops (k_plan, k_scan, k_copy); four single memcpys, each
-    followed by a fence (k_copy_small); and a 1 ms bounded device wait
-    (k_wait_test)."""
+    followed by a fence (k_copy_small); the same four in latency mode with a
+    100 us idle window, 1 ms apart (four k_lat_server launches); and a 1 ms
+    bounded device wait (k_wait_test)."""
     import torch
     from paper_2509_01425_gb300 import build
     build.build()
@@ -1216,6 +1217,13 @@ def run_control_small(args):
     for i in range(4):  # single memcpys before a fence: the small-batch kernel
         h.check(h.hicr_memcpy(inst, b, 40 * MiB + 64 * i, a, 64 * i, 16 << i), "memcpy")
         h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
+    # the same in latency mode: each server takes its copy, idles 100 us and ends
+    h.check(h.hicr_set_latency_mode(inst, 100), "latency mode")
+    for i in range(4):
+        h.check(h.hicr_memcpy(inst, b, 41 * MiB + 64 * i, a, 64 * i, 16 << i), "memcpy")
+        h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
+        time.sleep(0.001)
+    h.check(h.hicr_set_latency_mode(inst, 0), "latency mode off")
     st, wst, waited = h.hicr_util_wait_test(inst, 1_000_000)
     h.check(st, "wait_test")
     h.check(h.hicr_finalize(inst), "finalize")
@@ -1226,7 +1234,8 @@ def run_control_small(args):
 def run_side_small(args):
     """side_small, for a one-pass capture (DRAM bytes and duration) of the
     kernels that are not profiled elsewhere: an SPSC stream (64 channels x
-    10^6 tokens of 64 B, batches of 2,048), a ping-pong of 256 MiB with agents
+    10^6 tokens of 64 B, batches of 2,048), generating and then copying
+    staged tokens, a ping-pong of 256 MiB with agents
     of 152 CTAs and one of 1 GiB with agents of 76 CTAs (the bulk-copy form;
     10 round trips each), a 0.5 s serving trace at 20,000 req/s on
     the bench's engine set-up, and the word digest of a 4 GiB slot. Prints
@@ -1243,6 +1252,13 @@ def run_side_small(args):
     h.check(h.hicr_spsc_stream(inst, chans, 1_000_000, 2048)[0], "spsc_stream")
     out["spsc_tokens"] = w.n_channels * 1_000_000
     out["spsc_algorithmic_bytes"] = w.n_channels * 1_000_000 * 128
+    # copying producers (4,096 staged tokens per channel)
+    stg_bytes = w.n_channels * w.capacity * w.token_bytes
+    stg = h.check(h.hicr_mem_alloc(inst, h.HICR_SPACE_HBM, stg_bytes), "staging")
+    h.check(h.hicr_util_fill(inst, stg, 0, stg_bytes, splitmix.fill_key_base(0, 77)), "fill staging")
+    h.check(h.hicr_spsc_stream_ex(inst, chans, 1_000_000, 2048, src=stg, src_tokens=w.capacity)[0], "spsc copy")
+    out["spsc_copy_l2_bytes"] = w.n_channels * 1_000_000 * 192
+    h.check(h.hicr_mem_free(inst, stg), "free")
     for c in chans:
         h.check(h.hicr_channel_destroy(inst, c), "destroy")
     size = 256 << 20
