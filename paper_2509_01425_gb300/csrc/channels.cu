@@ -515,6 +515,7 @@ hicr_status hicr_channel_push(hicr_instance_t h, hicr_channel_t ch, uint32_t pro
   Mailbox *mh, *md;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
+  if ((st = lat_drain(in)) != HICR_OK) return st;
   if ((st = mailbox(in, &mh, &md)) != HICR_OK) return st;
   if (c->kind == 0) {
     if (producer != 0) return HICR_ERR_INVALID;

@@ -254,6 +254,11 @@ hicr_status copy_tma_load_all(Instance* in);
 hicr_status lat_submit(Instance* in, const hicr_op_t* ops, uint64_t count);
 hicr_status lat_wait(Instance* in, uint64_t target, uint64_t timeout_ns);
 hicr_status lat_stop(Instance* in);
+// Wait (bounded) until the server has completed every op published to it:
+// calls that read or write slot bytes on the communication stream after a
+// flush (a channel push's source, a digest) see those copies as they would
+// with the copies launched on that stream.
+hicr_status lat_drain(Instance* in);
 void lat_destroy(Instance* in);
 // memcpy_noalloc.cu: per-device set-up of the allocation-free entry point
 // (device address of its static scratch array, kernels loaded); hicr_init.

@@ -238,6 +238,11 @@ hicr_status lat_wait(Instance* in, uint64_t target, uint64_t timeout_ns) {
   }
 }
 
+hicr_status lat_drain(Instance* in) {
+  if (!in->lat_ring) return HICR_OK;
+  return lat_wait(in, in->lat_head, 60ull * 1000000000ull);
+}
+
 }  // namespace hicr
 
 using namespace hicr;

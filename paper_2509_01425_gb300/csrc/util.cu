@@ -251,6 +251,7 @@ hicr_status hicr_util_digest(hicr_instance_t h, hicr_slot_t slot, uint64_t off, 
   const HostSlot& s = in->slots[slot];
   if (off > s.size || n > s.size - off) return HICR_ERR_BOUNDS;
   hicr_status st = hicr_flush(h);
+  if (st == HICR_OK) st = lat_drain(in);
   if (st != HICR_OK) return st;
   unsigned long long* d = in->dt.sticky + 1;  // spare word next to the sticky error
   cudaStream_t cs = in->comm();
@@ -322,7 +323,7 @@ hicr_status hicr_util_copy_loop(hicr_instance_t h, hicr_slot_t dst, uint64_t dst
   if (st == HICR_OK) st = probe_range(in, src, src_off, n, &s);
   if (st != HICR_OK) return st;
   if (dst == src && dst_off < src_off + n && src_off < dst_off + n) return HICR_ERR_OVERLAP;
-  if ((st = hicr_flush(h)) != HICR_OK) return st;
+  if ((st = hicr_flush(h)) != HICR_OK || (st = lat_drain(in)) != HICR_OK) return st;
   return probe_time(
       in, [&](cudaStream_t cs) { k_copy_loop<<<ctas, 256, 0, cs>>>((uint4*)d, (const uint4*)s, n / 16, reps); },
       device_ns);
@@ -336,7 +337,7 @@ hicr_status hicr_util_stream(hicr_instance_t h, hicr_slot_t slot, uint64_t off, 
   uint8_t* p = nullptr;
   hicr_status st = probe_range(in, slot, off, n, &p);
   if (st != HICR_OK) return st;
-  if ((st = hicr_flush(h)) != HICR_OK) return st;
+  if ((st = hicr_flush(h)) != HICR_OK || (st = lat_drain(in)) != HICR_OK) return st;
   unsigned long long* sink = in->dt.sticky + 1;  // spare word next to the sticky error (never written in practice)
   return probe_time(
       in, [&](cudaStream_t cs) { k_stream<<<ctas, 256, 0, cs>>>((uint4*)p, n / 16, reps, write ? 1 : 0, sink); },
