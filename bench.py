@@ -721,6 +721,19 @@ def latency_summary(res, mask=None):
             "mean_us": float(lat.mean()) / 1e3, "max_us": float(lat.max()) / 1e3}
 
 
+def stall_summary(res, stats):
+    """Where the longest pause of a serving run happened: the host's longest
+    interval between two passes of its admission/completion loop, and the
+    longest interval between two consecutive completions on the device clock.
+    A pause that shows on the host side only was the host thread not running."""
+    dev = np.sort(res["device_done_ns"][res["device_done_ns"] > 0].astype(np.int64))
+    gap = np.diff(dev)
+    return {"host_max_poll_gap_ms": stats.max_poll_gap_ns / 1e6,
+            "host_max_poll_gap_at_s": stats.max_poll_gap_at_ns / 1e9,
+            "device_max_completion_gap_ms": float(gap.max()) / 1e6 if len(gap) else None,
+            "device_max_completion_gap_at_s": float(dev[int(np.argmax(gap)) + 1] - dev[0]) / 1e9 if len(gap) else None}
+
+
 def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
     """Config 5: Poisson 20,000 req/s, 70% memcpy batches of log-uniform 1-4,096
     ops (16 B-4 MiB) over config 2's source slots, 30% MPSC bursts of
@@ -743,7 +756,8 @@ def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
            "req_per_s": stats.completed / (stats.wall_ns / 1e9),
            "max_inflight": int(stats.max_inflight), "arena_high_water_GB": stats.max_region_bytes / 1e9,
            "latency_all": latency_summary(res), "latency_memcpy": latency_summary(res, reqs["kind"] == 0),
-           "latency_burst": latency_summary(res, reqs["kind"] == 1)}
+           "latency_burst": latency_summary(res, reqs["kind"] == 1),
+           "stalls": stall_summary(res, stats)}
     # the plain form on the first plain_seconds of the same trace
     hz = int(plain_seconds * 1e9)
     st, pres, pst = h.hicr_serve_run_plain(inst, ss.srv, reqs, hz, int((plain_seconds + 600) * 1e9))

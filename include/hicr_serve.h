@@ -65,6 +65,10 @@ typedef struct {
   uint64_t digest;      /* MPSC burst: sum over messages m of (2m+1) * word digest
                            of message m as consumed; memcpy: see hicr_serve_digests */
   uint64_t dst_offset;  /* memcpy: offset of the request's region in the arena */
+  uint64_t device_done_ns; /* engine mode: the device clock (%globaltimer, ns) when the request
+                              completed, which the host's latency_ns observes later; it shares
+                              no origin with the host clock, so only its differences mean
+                              anything. Plain mode: 0 */
 } hicr_serve_result_t;
 
 typedef struct {
@@ -83,6 +87,9 @@ typedef struct {
   uint64_t burst_bytes;      /* the burst part of bytes_moved (the rest is memcpy payload): each burst
                                 byte is read from staging, written to a ring and read by the consumer
                                 (3 bytes of traffic), each memcpy byte read and written once (2) */
+  uint64_t max_poll_gap_ns;    /* longest interval between two passes of the host's admission and
+                                  completion loop (a thread the OS did not run meanwhile shows here) */
+  uint64_t max_poll_gap_at_ns; /* when that interval ended, from the start of the run */
 } hicr_serve_stats_t;
 
 /* Create a serving engine: allocates the destination arena and the channel
@@ -109,8 +116,10 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t inst, hicr_serve_t srv
 
 /* Serve `n` requests (host array, sorted by arrival). mode 0 = by arrival
  * time (the trace), mode 1 = alone (request i+1 is admitted only after
- * request i completed). results: host array of n (may be NULL); stats may be
- * NULL. Synchronous. The engine checks itself while it runs: an entry
+ * request i completed). results: host array of n (may be NULL), zeroed
+ * before the run starts (so a freshly mapped array takes its page faults
+ * outside the run); an entry stays zero if its request did not complete.
+ * stats may be NULL. Synchronous. The engine checks itself while it runs: an entry
  * outside the run, or a burst message consumed out of its request's order,
  * stops it with DEVICE (stats.dev_flags bit 2; the message names the request).
  * Errors: INVALID (unknown template, unsorted), NOMEM (a

@@ -692,6 +692,7 @@ struct Arena {
   }
   bool alloc(uint64_t n, uint64_t* off) {
     n = std::max<uint64_t>(256, (n + 255) & ~255ull);
+    if (size - used < n) return false;  // no walk while the arena is full
     for (auto it = free_.begin(); it != free_.end(); ++it) {
       if (it->second >= n) {
         *off = it->first;
@@ -1122,28 +1123,38 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
   arena.reset(sv->cfg.budget_bytes - (uint64_t)sv->cfg.n_channels * sv->cfg.ring_bytes);
   std::vector<uint64_t> region_off(n, 0), region_len(n, 0), admit_t(n, 0);
   std::vector<uint64_t> inflight;
+  inflight.reserve(4096);
+  // requests [next_admit, next_arrival) have arrived and wait, in order, for admission
   uint64_t next_arrival = 0, next_admit = 0, completed = 0, max_inflight = 0, bytes = 0, burst_bytes = 0;
-  std::vector<uint64_t> waiting;  // arrived, not admitted (FIFO)
-  size_t wait_head = 0;
+  // Fault the results array in now: a fresh (lazily mapped) array would
+  // otherwise take its page faults inside the run, and a fault that makes the
+  // kernel zero or compact a huge page stops this thread for milliseconds.
+  if (results) memset(results, 0, sizeof(hicr_serve_result_t) * n);
   const uint64_t t0 = now_ns();
   uint64_t last_done = t0;
+  uint64_t prev_pass = 0, max_gap = 0, max_gap_at = 0;  // longest interval between two passes of this loop
   hicr_status result = HICR_OK;
   for (;;) {
     const uint64_t now = now_ns() - t0;
+    if (now - prev_pass > max_gap) {
+      max_gap = now - prev_pass;
+      max_gap_at = now;
+    }
+    prev_pass = now;
     if (now > timeout_ns) {
       result = HICR_ERR_TIMEOUT;
       break;
     }
     // arrivals
     if (mode == 0) {
-      while (next_arrival < n && reqs[next_arrival].arrival_ns <= now) waiting.push_back(next_arrival++);
-    } else if (inflight.empty() && next_arrival < n && wait_head == waiting.size()) {
-      waiting.push_back(next_arrival++);  // alone: the next request once the previous completed
+      while (next_arrival < n && reqs[next_arrival].arrival_ns <= now) ++next_arrival;
+    } else if (inflight.empty() && next_arrival < n && next_admit == next_arrival) {
+      ++next_arrival;  // alone: the next request once the previous completed
     }
     // FIFO admission under the arena budget
     bool published = false;
-    while (wait_head < waiting.size()) {
-      const uint64_t r = waiting[wait_head];
+    while (next_admit < next_arrival) {
+      const uint64_t r = next_admit;
       const hicr_serve_request_t& q = reqs[r];
       uint64_t off = 0;
       if (q.kind == 0) {
@@ -1158,7 +1169,6 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
       admit_t[r] = now_ns() - t0;
       inflight.push_back(r);
       max_inflight = std::max<uint64_t>(max_inflight, inflight.size());
-      ++wait_head;
       ++next_admit;
       published = true;
     }
@@ -1173,6 +1183,7 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
           results[r].admit_ns = mode == 0 ? admit_t[r] - std::min(admit_t[r], reqs[r].arrival_ns) : 0;
           results[r].digest = digest[r];
           results[r].dst_offset = region_off[r];
+          results[r].device_done_ns = compl_[r].load(std::memory_order_relaxed) & ~1ull;
         }
         if (reqs[r].kind == 0) {
           bytes += sv->t_bytes[reqs[r].tmpl];
@@ -1194,7 +1205,7 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
     // Linux wakes up to a timer-slack late (tens of microseconds, sometimes
     // milliseconds), and that delay went straight into the next request's
     // admission time.
-    if (next_admit < n && wait_head == waiting.size() && mode == 0 && next_arrival < n && inflight.empty())
+    if (next_admit == next_arrival && mode == 0 && next_arrival < n && inflight.empty())
       std::this_thread::yield();
   }
   hstop->store(1, std::memory_order_release);
@@ -1242,6 +1253,8 @@ static hicr_status serve_run(hicr_instance_t h, hicr_serve_t s, const hicr_serve
     (void)cudaGetLastError();
   }
   if (stats) {
+    stats->max_poll_gap_ns = max_gap;
+    stats->max_poll_gap_at_ns = max_gap_at;
     stats->admitted = next_admit;
     stats->dev_units = dv[0];
     stats->dev_claimed = dv[1];
@@ -1351,12 +1364,19 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
   std::vector<uint64_t> region_off(m, 0), region_len(m, 0);
   std::vector<uint64_t> ring_pos(sv->cfg.n_channels, 0);
   uint64_t next = 0, head = 0, completed = 0, bytes = 0, burst_bytes = 0, max_inflight = 0;  // in-flight = [head, next)
+  if (results) memset(results, 0, sizeof(hicr_serve_result_t) * m);  // faulted in before the clock starts
   const uint64_t t0 = now_ns();
   uint64_t last_done = t0;
+  uint64_t prev_pass = 0, max_gap = 0, max_gap_at = 0;
   hicr_status result = HICR_OK;
   const uint8_t* staging = sv->base.staging;
   while (completed < m) {
     const uint64_t now = now_ns() - t0;
+    if (now - prev_pass > max_gap) {
+      max_gap = now - prev_pass;
+      max_gap_at = now;
+    }
+    prev_pass = now;
     if (now > timeout_ns) {
       result = HICR_ERR_TIMEOUT;
       break;
@@ -1400,6 +1420,7 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
         results[head].admit_ns = 0;
         results[head].digest = 0;
         results[head].dst_offset = region_off[head];
+        results[head].device_done_ns = 0;
       }
       if (q.kind == 0) {
         bytes += sv->t_bytes[q.tmpl];
@@ -1427,6 +1448,8 @@ hicr_status hicr_serve_run_plain(hicr_instance_t h, hicr_serve_t s, const hicr_s
     stats->wall_ns = last_done - t0 - (m ? std::min<uint64_t>(last_done - t0, reqs[0].arrival_ns) : 0);
     stats->max_inflight = max_inflight;
     stats->max_region_bytes = arena.high;
+    stats->max_poll_gap_ns = max_gap;
+    stats->max_poll_gap_at_ns = max_gap_at;
     stats->status = result;
   }
   return result;

@@ -659,14 +659,15 @@ class hicr_serve_stats_t(C.Structure):
     _fields_ = [("completed", u64), ("bytes_moved", u64), ("wall_ns", u64), ("max_inflight", u64),
                 ("max_region_bytes", u64), ("admitted", u64), ("dev_units", u64), ("dev_claimed", u64),
                 ("dev_requests", u64), ("dev_flags", u64), ("status", i32), ("reserved", u32),
-                ("burst_bytes", u64)]
+                ("burst_bytes", u64), ("max_poll_gap_ns", u64), ("max_poll_gap_at_ns", u64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 SERVE_REQ_DTYPE = np.dtype([("arrival_ns", "<u8"), ("kind", "<u4"), ("tmpl", "<u4")])
-SERVE_RES_DTYPE = np.dtype([("latency_ns", "<u8"), ("admit_ns", "<u8"), ("digest", "<u8"), ("dst_offset", "<u8")])
+SERVE_RES_DTYPE = np.dtype([("latency_ns", "<u8"), ("admit_ns", "<u8"), ("digest", "<u8"), ("dst_offset", "<u8"),
+                            ("device_done_ns", "<u8")])
 
 _serve_create = _decl("hicr_serve_create", [H, C.POINTER(hicr_serve_config_t), C.POINTER(u64)])
 _serve_destroy = _decl("hicr_serve_destroy", [H, u64])
