@@ -517,7 +517,8 @@ def bench_latencies(h, inst, reps=2000):
     of the small synchronous operations: a 16-byte memcpy + fence (also in
     latency mode, where a persistent server kernel takes the copy), an
     execution-unit launch + await (the built-in fill on 16 bytes), a Data
-    Object get (16 bytes) + fence, and a 1-token SPSC host push + pop. Python's
+    Object get (16 bytes) + fence, and a 1-token SPSC host push + pop (also in
+    latency mode, where the server takes the channel calls). Python's
     garbage collector is off while the calls are timed."""
     import ctypes as C
 
@@ -576,6 +577,9 @@ def bench_latencies(h, inst, reps=2000):
         h.check(h.hicr_channel_push(inst, ch, 0, a, 0, 1), "push")
         h.check(h.hicr_channel_pop(inst, ch, 1), "pop")
     out["spsc_host_push_plus_pop"] = stats(push_pop)
+    h.check(h.hicr_set_latency_mode(inst, 2000), "latency mode on")
+    out["spsc_host_push_plus_pop_latency_mode"] = stats(push_pop)
+    h.check(h.hicr_set_latency_mode(inst, 0), "latency mode off")
     h.check(h.hicr_channel_destroy(inst, ch), "destroy")
     for sid in (a, b):
         h.check(h.hicr_mem_free(inst, sid), "free")
@@ -721,17 +725,66 @@ def latency_summary(res, mask=None):
             "mean_us": float(lat.mean()) / 1e3, "max_us": float(lat.max()) / 1e3}
 
 
-def stall_summary(res, stats):
+def stall_summary(res, stats, watch=None):
     """Where the longest pause of a serving run happened: the host's longest
-    interval between two passes of its admission/completion loop, and the
-    longest interval between two consecutive completions on the device clock.
-    A pause that shows on the host side only was the host thread not running."""
+    interval between two passes of its admission/completion loop, the longest
+    interval between two consecutive completions on the device clock, and
+    (`watch`, a HostPauseWatch) the pauses that a second host thread, which
+    only sleeps 1 ms at a time, saw meanwhile. A pause seen by both host
+    threads at once was the whole host process not running."""
     dev = np.sort(res["device_done_ns"][res["device_done_ns"] > 0].astype(np.int64))
     gap = np.diff(dev)
-    return {"host_max_poll_gap_ms": stats.max_poll_gap_ns / 1e6,
-            "host_max_poll_gap_at_s": stats.max_poll_gap_at_ns / 1e9,
-            "device_max_completion_gap_ms": float(gap.max()) / 1e6 if len(gap) else None,
-            "device_max_completion_gap_at_s": float(dev[int(np.argmax(gap)) + 1] - dev[0]) / 1e9 if len(gap) else None}
+    out = {"host_max_poll_gap_ms": stats.max_poll_gap_ns / 1e6,
+           "host_max_poll_gap_at_s": stats.max_poll_gap_at_ns / 1e9,
+           "device_max_completion_gap_ms": float(gap.max()) / 1e6 if len(gap) else None,
+           "device_max_completion_gap_at_s": float(dev[int(np.argmax(gap)) + 1] - dev[0]) / 1e9 if len(gap) else None}
+    if watch is not None:
+        out.update(watch.summary())
+    return out
+
+
+class HostPauseWatch:
+    """A thread that sleeps 1 ms at a time and records every wake-up later
+    than `over_ms`, with the guest kernel's steal time over the same span."""
+
+    def __init__(self, over_ms=10.0):
+        import threading
+        self.over = over_ms / 1e3
+        self.pauses = []
+        self._stop = threading.Event()
+        self._t0 = time.monotonic()
+        self._steal0 = _steal_ticks()
+        self._th = threading.Thread(target=self._run, daemon=True)
+        self._th.start()
+
+    def _run(self):
+        last = time.monotonic()
+        while not self._stop.is_set():
+            time.sleep(0.001)
+            t = time.monotonic()
+            if t - last > self.over:
+                self.pauses.append((round(last - self._t0, 3), round((t - last) * 1e3, 1)))
+            last = t
+
+    def summary(self):
+        self._stop.set()
+        self._th.join(timeout=1.0)
+        steal = _steal_ticks()
+        tck = os.sysconf("SC_CLK_TCK")
+        return {"second_thread_pause_threshold_ms": self.over * 1e3,
+                "second_thread_pauses_s_ms": self.pauses[:20],
+                "guest_steal_ms": (steal - self._steal0) * 1e3 / tck
+                if steal is not None and self._steal0 is not None else None}
+
+
+def _steal_ticks():
+    """The guest kernel's steal time over all CPUs (/proc/stat), in ticks."""
+    try:
+        with open("/proc/stat") as f:
+            parts = f.readline().split()
+        return int(parts[8]) if parts[0] == "cpu" and len(parts) > 8 else None
+    except (OSError, ValueError):
+        return None
 
 
 def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
@@ -744,6 +797,7 @@ def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
     ss = ServeSetup(h, inst, src_w, tmpl, seed=seed)
     tr = configs.serve_trace(seed, rate=20000.0, duration_s=seconds)
     reqs = ss.requests(tr)
+    watch = HostPauseWatch()
     st, res, stats = h.hicr_serve_run(inst, ss.srv, reqs, 0, int((seconds + 120) * 1e9))
     h.check(st, "serve_run")
     out = {"workload": f"Poisson 20,000 req/s for {seconds:g} s ({len(reqs):,} requests): 70% memcpy batches of "
@@ -757,7 +811,7 @@ def bench_serve(h, inst, seconds=60.0, plain_seconds=1.0, seed=0):
            "max_inflight": int(stats.max_inflight), "arena_high_water_GB": stats.max_region_bytes / 1e9,
            "latency_all": latency_summary(res), "latency_memcpy": latency_summary(res, reqs["kind"] == 0),
            "latency_burst": latency_summary(res, reqs["kind"] == 1),
-           "stalls": stall_summary(res, stats)}
+           "stalls": stall_summary(res, stats, watch)}
     # the plain form on the first plain_seconds of the same trace
     hz = int(plain_seconds * 1e9)
     st, pres, pst = h.hicr_serve_run_plain(inst, ss.srv, reqs, hz, int((plain_seconds + 600) * 1e9))

@@ -262,11 +262,17 @@ hicr_status hicr_set_host_copies(hicr_instance_t inst, int32_t on);
  * batch starts a new one; while it runs it holds one CTA slot of one SM, and
  * device-wide synchronisations (cudaDeviceSynchronize, cudaFree) wait for it
  * to end. This library's cooperative runs (channel streams, ping-pong,
- * serving) and hicr_mem_free end a running server first; channel pushes,
- * digests and the bandwidth probes wait for the copies it holds, so they see
- * them as they would see copies launched on the communication stream. The ops keep the model's semantics: unordered within an epoch,
- * complete at the fence of their tag, counters exact. idle_us = 0 (the
- * default) turns the mode off after the server's pending ops complete.
+ * serving) and hicr_mem_free end a running server first; digests and the
+ * bandwidth probes wait for the copies it holds, so they see them as they
+ * would see copies launched on the communication stream. The ops keep the
+ * model's semantics: unordered within an epoch, complete at the fence of
+ * their tag, counters exact. The channel host calls (hicr_channel_push, peek,
+ * pop, depth; hicr_channels.h) go to the server too while nothing is pending
+ * on the communication stream, after the copies published to it before them;
+ * otherwise they wait for those copies and launch as usual. Either way a
+ * call sees everything issued before it, and returns the same results.
+ * idle_us = 0 (the default) turns the mode off after the server's pending
+ * ops complete.
  * Errors: INVALID (idle_us > 1,000,000 or capturing), DEVICE, TIMEOUT. */
 hicr_status hicr_set_latency_mode(hicr_instance_t inst, uint32_t idle_us);
 

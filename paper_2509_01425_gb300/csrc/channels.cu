@@ -35,260 +35,30 @@
 #include <vector>
 
 #include "../../include/hicr_channels.h"
+#include "channel_calls.cuh"
 #include "channel_host.h"
 
 namespace hicr {
 
 
 // ---------------------------------------------------------------------------
-// Host-call kernels (one CTA, result in the mailbox).
+// Host-call kernels (one CTA, result in the mailbox); the bodies are in
+// channel_calls.cuh, which the latency-mode server shares.
 // ---------------------------------------------------------------------------
-
 __global__ void k_spsc_push_host(SpscView v, const uint8_t* src, unsigned long long k, Mailbox* mb) {
-  __shared__ unsigned long long s_head;
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    const unsigned long long h = ld_rlx(&v.st->head.v), t = ld_acq(&v.st->tail.v);
-    s_ok = (h - t + k <= v.cap);
-    s_head = h;
-  }
-  __syncthreads();
-  if (!s_ok) {
-    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
-    return;
-  }
-  // at most two contiguous runs: up to the ring end, then from its start
-  const unsigned long long first = s_head % v.cap;
-  const unsigned long long run1 = min(k, (unsigned long long)v.cap - first);
-  cta_copy(v.ring + first * v.ts, src, run1 * v.ts);
-  if (k > run1) cta_copy(v.ring, src + run1 * v.ts, (k - run1) * v.ts);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st_rel(&v.st->head.v, s_head + k);
-    mb->v[0] = s_head;
-    mb_post(mb, HICR_OK);
-  }
+  spsc_push_call(v, src, k, mb);
 }
-
-// op 0 = peek(k), 1 = pop(k), 2 = depth
-__global__ void k_spsc_ctl(SpscView v, int op, unsigned long long k, Mailbox* mb) {
-  const unsigned long long h = ld_acq(&v.st->head.v), t = ld_acq(&v.st->tail.v);
-  const unsigned long long depth = h - t;
-  if (op == 2) {
-    mb->v[0] = depth;
-    mb->v[1] = depth * v.ts;
-    mb_post(mb, HICR_OK);
-  } else if (op == 0) {
-    if (k >= depth) {
-      mb_post(mb, HICR_ERR_EMPTY);
-      return;
-    }
-    mb->v[0] = ((t + k) % v.cap) * v.ts;
-    mb->v[1] = v.ts;
-    mb->v[2] = 0;
-    mb->v[3] = t + k;
-    mb_post(mb, HICR_OK);
-  } else {
-    if (k > depth) {
-      mb_post(mb, HICR_ERR_EMPTY);
-      return;
-    }
-    st_rel(&v.st->tail.v, t + k);
-    mb_post(mb, HICR_OK);
-  }
-}
-
+__global__ void k_spsc_ctl(SpscView v, int op, unsigned long long k, Mailbox* mb) { spsc_ctl_call(v, op, k, mb); }
 __global__ void k_mpsc_push_host(MpscView v, unsigned int producer, unsigned int seq, const uint8_t* src,
                                  unsigned long long n, Mailbox* mb) {
-  __shared__ unsigned long long s_start, s_ticket;
-  __shared__ int s_ok;
-  if (threadIdx.x == 0) {
-    const unsigned long long r = round16(n);
-    int ok = 0;
-    for (int attempt = 0; attempt < 1000; ++attempt) {
-      const unsigned long long W = ld_rlx(&v.st->reserve.v);
-      unsigned long long start;
-      const unsigned long long end = mpsc_place(W, &r, 1, v.R, &start);
-      const unsigned long long freed = ld_acq(&v.st->freed.v);
-      const unsigned long long mt = ld_acq(&v.st->msg_tail.v);
-      const unsigned long long t0 = W >> 40;
-      const unsigned long long inflight = (end - freed) & MASK40;
-      const unsigned long long msgs = ((t0 + 1) - mt) & MASK24;
-      if (inflight > v.R || msgs > v.M) break;  // FULL under the placement rule
-      const unsigned long long nw = (((t0 + 1) & MASK24) << 40) | end;
-      if (atomicCAS(&v.st->reserve.v, W, nw) == W) {
-        ok = 1;
-        s_start = start;
-        s_ticket = t0;
-        atomicMax(&v.st->max_bytes.v, inflight);
-        atomicMax(&v.st->max_msgs.v, msgs);
-        break;
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  if (!s_ok) {
-    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
-    return;
-  }
-  cta_copy(v.ring + (s_start & (v.R - 1)), src, n);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    MpscMeta* e = v.meta + (s_ticket & (v.M - 1));
-    e->start = s_start;
-    e->size = (unsigned int)n;
-    e->producer = producer;
-    e->seq = seq;
-    e->flags = 0;
-    st_rel(&e->ready, (s_ticket & MASK24) + 1);
-    mb->v[0] = s_start & (v.R - 1);
-    mb->v[1] = s_ticket;
-    mb_post(mb, HICR_OK);
-  }
+  mpsc_push_call(v, producer, seq, src, n, mb);
 }
-
-// op 0 = peek(k), 1 = pop(k), 2 = depth
-__global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb) {
-  const unsigned long long W = ld_acq(&v.st->reserve.v);
-  const unsigned long long mt = ld_acq(&v.st->msg_tail.v);
-  const unsigned long long freed = ld_acq(&v.st->freed.v);
-  const unsigned long long depth = ((W >> 40) - mt) & MASK24;
-  if (op == 2) {
-    mb->v[0] = depth;
-    mb->v[1] = ((W & MASK40) - freed) & MASK40;
-    mb_post(mb, HICR_OK);
-    return;
-  }
-  if (op == 0) {
-    if (k >= depth) {
-      mb_post(mb, HICR_ERR_EMPTY);
-      return;
-    }
-    const unsigned long long t = mt + k;
-    MpscMeta* e = v.meta + (t & (v.M - 1));
-    if (ld_acq(&e->ready) != (t & MASK24) + 1) {
-      mb_post(mb, HICR_ERR_EMPTY);
-      return;
-    }
-    mb->v[0] = __ldcg(&e->start) & (v.R - 1);
-    mb->v[1] = __ldcg(&e->size);
-    mb->v[2] = __ldcg(&e->producer);
-    mb->v[3] = __ldcg(&e->seq);
-    mb_post(mb, HICR_OK);
-    return;
-  }
-  if (k > depth) {
-    mb_post(mb, HICR_ERR_EMPTY);
-    return;
-  }
-  if (k == 0) {
-    mb_post(mb, HICR_OK);
-    return;
-  }
-  for (unsigned long long i = 0; i < k; ++i) {
-    const unsigned long long t = mt + i;
-    if (ld_acq(&v.meta[t & (v.M - 1)].ready) != (t & MASK24) + 1) {
-      mb_post(mb, HICR_ERR_EMPTY);
-      return;
-    }
-  }
-  const MpscMeta* last = v.meta + ((mt + k - 1) & (v.M - 1));
-  const unsigned long long end = (__ldcg(&last->start) + round16(__ldcg(&last->size))) & MASK40;
-  st_rel(&v.st->freed.v, end);
-  st_rel(&v.st->msg_tail.v, mt + k);
-  mb_post(mb, HICR_OK);
-}
-
+__global__ void k_mpsc_ctl(MpscView v, int op, unsigned long long k, Mailbox* mb) { mpsc_ctl_call(v, op, k, mb); }
 __global__ void k_nl_push_host(NlView v, unsigned int producer, unsigned int seq, const uint8_t* src,
                                unsigned long long n, Mailbox* mb) {
-  __shared__ unsigned long long s_start, s_pub;
-  __shared__ int s_ok;
-  NlState* st = v.st + producer;
-  if (threadIdx.x == 0) {
-    const unsigned long long r = round16(n);
-    unsigned long long start;
-    const unsigned long long end = nl_place(ld_rlx(&st->reserve.v), &r, 1, v.R, &start);
-    const unsigned long long pub = ld_rlx(&st->pub.v);
-    const unsigned long long freed = ld_acq(&st->freed.v), cons = ld_acq(&st->cons.v);
-    s_ok = end - freed <= v.R && pub + 1 - cons <= v.M;
-    s_start = start;
-    s_pub = pub;
-  }
-  __syncthreads();
-  if (!s_ok) {
-    if (threadIdx.x == 0) mb_post(mb, HICR_ERR_FULL);
-    return;
-  }
-  uint8_t* ring = v.ring + (unsigned long long)producer * v.R;
-  cta_copy(ring + (s_start & (v.R - 1)), src, n);
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    NlMeta* e = v.meta + (unsigned long long)producer * v.M + (s_pub & (v.M - 1));
-    e->start = s_start;
-    e->size = (unsigned int)n;
-    e->seq = seq;
-    st_rel(&st->reserve.v, s_start + round16(n));
-    __threadfence();
-    st_rel(&st->pub.v, s_pub + 1);
-    mb->v[0] = s_start & (v.R - 1);
-    mb->v[1] = s_pub;
-    mb_post(mb, HICR_OK);
-  }
+  nl_push_call(v, producer, seq, src, n, mb);
 }
-
-// op 0 = peek(k), 1 = pop(k), 2 = depth; the consumer order is "producers in
-// index order, each producer's messages oldest first". One thread.
-__global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) {
-  unsigned long long msgs = 0, bytes = 0;
-  for (unsigned p = 0; p < v.P; ++p) {
-    const NlState* st = v.st + p;
-    msgs += ld_acq(&st->pub.v) - ld_acq(&st->cons.v);
-    bytes += ld_acq(&st->reserve.v) - ld_acq(&st->freed.v);
-  }
-  if (op == 2) {
-    mb->v[0] = msgs;
-    mb->v[1] = bytes;
-    mb_post(mb, HICR_OK);
-    return;
-  }
-  if (op == 0 ? k >= msgs : k > msgs) {
-    mb_post(mb, HICR_ERR_EMPTY);
-    return;
-  }
-  unsigned long long left = k;
-  for (unsigned p = 0; p < v.P; ++p) {
-    NlState* st = v.st + p;
-    const unsigned long long cons = ld_rlx(&st->cons.v);
-    const unsigned long long d = ld_acq(&st->pub.v) - cons;
-    const NlMeta* m = v.meta + (unsigned long long)p * v.M;
-    if (op == 0) {
-      if (left < d) {
-        const NlMeta* e = m + ((cons + left) & (v.M - 1));
-        mb->v[0] = __ldcg(&e->start) & (v.R - 1);
-        mb->v[1] = __ldcg(&e->size);
-        mb->v[2] = p;
-        mb->v[3] = __ldcg(&e->seq);
-        mb_post(mb, HICR_OK);
-        return;
-      }
-      left -= d;
-    } else {
-      const unsigned long long take = left < d ? left : d;
-      if (take) {
-        const NlMeta* e = m + ((cons + take - 1) & (v.M - 1));
-        st_rel(&st->freed.v, __ldcg(&e->start) + round16(__ldcg(&e->size)));
-        st_rel(&st->cons.v, cons + take);
-        left -= take;
-      }
-      if (!left) break;
-    }
-  }
-  mb_post(mb, HICR_OK);
-}
+__global__ void k_nl_ctl(NlView v, int op, unsigned long long k, Mailbox* mb) { nl_ctl_call(v, op, k, mb); }
 
 // ---------------------------------------------------------------------------
 // Host side.
@@ -484,8 +254,13 @@ hicr_status hicr_channel_destroy(hicr_instance_t h, hicr_channel_t ch) {
   if (!in || in->capturing) return HICR_ERR_INVALID;
   Channel* c = get(in, ch);
   if (!c) return HICR_ERR_INVALID;
+  // a latency-mode server may still hold calls on this channel: end it (it
+  // completes what it took first), so the ring is idle when it is freed
+  hicr_status st = hicr_flush(h);
+  if (st == HICR_OK) st = lat_stop(in);
+  if (st != HICR_OK) return st;
   HICR_CUDA(in, cudaStreamSynchronize(in->comm()));
-  hicr_slot_deregister(h, c->ring_slot);
+  if ((st = hicr_slot_deregister(h, c->ring_slot)) != HICR_OK) return st;
   cudaFree(c->ring);
   delete c;
   in->channels[ch] = nullptr;
@@ -515,41 +290,71 @@ hicr_status hicr_channel_push(hicr_instance_t h, hicr_channel_t ch, uint32_t pro
   Mailbox *mh, *md;
   hicr_status st = hicr_flush(h);
   if (st != HICR_OK) return st;
-  if ((st = lat_drain(in)) != HICR_OK) return st;
-  if ((st = mailbox(in, &mh, &md)) != HICR_OK) return st;
   if (c->kind == 0) {
     if (producer != 0) return HICR_ERR_INVALID;
     if (n > (1ull << 40) / c->token_size) return HICR_ERR_FULL;
     const uint64_t bytes = n * c->token_size;
     if (off > ssize || bytes > ssize - off) return HICR_ERR_BOUNDS;
     if (n > c->capacity) return HICR_ERR_FULL;
-    k_spsc_push_host<<<1, 256, 0, in->comm()>>>(spsc_view(c), (const uint8_t*)sp + off, n, md);
-    st = finish(in, mh);
   } else {
     if (producer >= c->n_producers) return HICR_ERR_INVALID;
     if (off > ssize || n > ssize - off) return HICR_ERR_BOUNDS;
     if (round16(n) > c->ring_bytes || n > 0xffffffffull) return HICR_ERR_TOO_LARGE;
-    if (c->kind == 1)
-      k_mpsc_push_host<<<1, 256, 0, in->comm()>>>(mpsc_view(c), producer, c->seq[producer],
-                                                 (const uint8_t*)sp + off, n, md);
-    else
-      k_nl_push_host<<<1, 256, 0, in->comm()>>>(nl_view(c), producer, c->seq[producer], (const uint8_t*)sp + off, n,
-                                               md);
-    st = finish(in, mh);
-    if (st == HICR_OK) c->seq[producer]++;
   }
-  if (st == HICR_OK) st = record_done(in);
+  // latency mode: the running server takes the call (after the copies
+  // published to it before); otherwise a one-CTA launch on the
+  // communication stream, after the server's copies have drained
+  const bool served = lat_takes_calls(in);
+  if (!served && (st = lat_drain(in)) != HICR_OK) return st;
+  if ((st = mailbox(in, &mh, &md)) != HICR_OK) return st;
+  const uint8_t* src_p = (const uint8_t*)sp + off;
+  const unsigned seq = c->kind == 0 ? 0u : c->seq[producer];
+  if (served) {
+    ChanCall cc{};
+    cc.kind = (unsigned)c->kind;
+    cc.op = -1;
+    cc.producer = producer;
+    cc.seq = seq;
+    cc.src = src_p;
+    cc.k = n;
+    cc.mb = md;
+    if (c->kind == 0) cc.v.s = spsc_view(c);
+    else if (c->kind == 1) cc.v.m = mpsc_view(c);
+    else cc.v.l = nl_view(c);
+    st = lat_channel_call(in, cc, &mh->status);
+  } else {
+    if (c->kind == 0) k_spsc_push_host<<<1, 256, 0, in->comm()>>>(spsc_view(c), src_p, n, md);
+    else if (c->kind == 1) k_mpsc_push_host<<<1, 256, 0, in->comm()>>>(mpsc_view(c), producer, seq, src_p, n, md);
+    else k_nl_push_host<<<1, 256, 0, in->comm()>>>(nl_view(c), producer, seq, src_p, n, md);
+    st = finish(in, mh);
+    if (st == HICR_OK) st = record_done(in);
+  }
+  if (st == HICR_OK && c->kind != 0) c->seq[producer]++;
   return st;
 }
 
 static hicr_status ctl(Instance* in, Channel* c, int op, uint64_t k, Mailbox** out) {
   Mailbox *mh, *md;
-  hicr_status st = mailbox(in, &mh, &md);
-  if (st != HICR_OK) return st;
-  if (c->kind == 0) k_spsc_ctl<<<1, 1, 0, in->comm()>>>(spsc_view(c), op, k, md);
-  else if (c->kind == 1) k_mpsc_ctl<<<1, 1, 0, in->comm()>>>(mpsc_view(c), op, k, md);
-  else k_nl_ctl<<<1, 1, 0, in->comm()>>>(nl_view(c), op, k, md);
-  st = finish(in, mh);
+  const bool served = lat_takes_calls(in);
+  hicr_status st;
+  if (!served && (st = lat_drain(in)) != HICR_OK) return st;
+  if ((st = mailbox(in, &mh, &md)) != HICR_OK) return st;
+  if (served) {
+    ChanCall cc{};
+    cc.kind = (unsigned)c->kind;
+    cc.op = op;
+    cc.k = k;
+    cc.mb = md;
+    if (c->kind == 0) cc.v.s = spsc_view(c);
+    else if (c->kind == 1) cc.v.m = mpsc_view(c);
+    else cc.v.l = nl_view(c);
+    st = lat_channel_call(in, cc, &mh->status);
+  } else {
+    if (c->kind == 0) k_spsc_ctl<<<1, 1, 0, in->comm()>>>(spsc_view(c), op, k, md);
+    else if (c->kind == 1) k_mpsc_ctl<<<1, 1, 0, in->comm()>>>(mpsc_view(c), op, k, md);
+    else k_nl_ctl<<<1, 1, 0, in->comm()>>>(nl_view(c), op, k, md);
+    st = finish(in, mh);
+  }
   *out = mh;
   return st;
 }

@@ -146,9 +146,13 @@ struct GraphRec {
 // the host, done and exit_epoch by the server, stop by the host.
 static constexpr unsigned LAT_RING_OPS = 256;
 struct LatOp {
-  unsigned long long dst, src, n;  // device-usable addresses, bytes
+  unsigned long long dst, src, n;  // copy: device-usable addresses, bytes
   uint32_t dslot, sslot, dtag, stag;
+  uint32_t kind;                   // LAT_COPY, or LAT_CHANNEL: a channel host call
+  uint32_t pad;
+  unsigned long long call[12];     // LAT_CHANNEL: the call (ChanCall, channel_calls.cuh)
 };
+static constexpr uint32_t LAT_COPY = 0, LAT_CHANNEL = 1;
 struct LatRing {
   alignas(128) unsigned long long head;        // ops published
   alignas(128) unsigned long long done;        // ops completed (counters bumped)
@@ -259,6 +263,12 @@ hicr_status lat_stop(Instance* in);
 // flush (a channel push's source, a digest) see those copies as they would
 // with the copies launched on that stream.
 hicr_status lat_drain(Instance* in);
+// Channel host calls in latency mode: whether the server may take one now
+// (latency mode on, nothing pending on the communication stream), and the
+// call itself (published to the server; waits for the status it posts).
+struct ChanCall;
+bool lat_takes_calls(Instance* in);
+hicr_status lat_channel_call(Instance* in, const ChanCall& c, volatile int* status);
 void lat_destroy(Instance* in);
 // memcpy_noalloc.cu: per-device set-up of the allocation-free entry point
 // (device address of its static scratch array, kernels loaded); hicr_init.

@@ -1,6 +1,7 @@
 // Latency mode (hicr_set_latency_mode): small host-validated batches (the
-// ones k_copy_small would take) go to a short-lived persistent server kernel
-// instead of a kernel launch each.
+// ones k_copy_small would take) and the channel host calls (push, peek, pop,
+// depth) go to a short-lived persistent server kernel instead of a kernel
+// launch each.
 //
 // The host writes the ops' descriptors into a ring in mapped page-locked
 // memory and publishes them by advancing `head` (release). One CTA of the
@@ -17,22 +18,35 @@
 // Ordering against the communication stream: the server runs beside it, and
 // that is what the model allows -- ops between two fences are unordered, and
 // a fence waits for the ops of its tag on both (the server's `done` and the
-// stream's completion signals).
+// stream's completion signals). A channel call is synchronous and, like its
+// launched form, must come after everything issued before it: it goes to the
+// server only while the communication stream has nothing pending (the server
+// takes its ring in order, so copies published before it are done first).
 #include <string.h>
 
 #include <atomic>
 #include <thread>
 
+#include "channel_calls.cuh"
 #include "copy.cuh"
 #include "hicr_internal.h"
 
 namespace hicr {
 
+static_assert(sizeof(ChanCall) <= sizeof(((LatOp*)nullptr)->call), "a channel call fits its ring entry");
+
 static constexpr unsigned LAT_THREADS = 512;
+static constexpr unsigned LAT_OP_WORDS = sizeof(LatOp) / 8;
+static_assert(sizeof(LatOp) % 8 == 0 && LAT_OP_WORDS <= LAT_THREADS, "a ring entry is read one word per thread");
 
 __device__ __forceinline__ unsigned long long lat_ld_acq_sys(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long lat_ld_rlx_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ void lat_st_rel_sys(unsigned long long* p, unsigned long long v) {
@@ -103,9 +117,20 @@ __global__ void __launch_bounds__(LAT_THREADS) k_lat_server(LatArgs a) {
     if (ex == 1) break;
     const unsigned long long h = s_head;
     for (unsigned long long t = s_tail; t < h; ++t) {
-      if (threadIdx.x == 0) s_op = r->ops[t % LAT_RING_OPS];
+      // the entry, one word per thread: a single round trip to host memory
+      // (ordered after thread 0's acquire of `head` by the barrier above)
+      if (threadIdx.x < LAT_OP_WORDS)
+        reinterpret_cast<unsigned long long*>(&s_op)[threadIdx.x] =
+            lat_ld_rlx_sys(reinterpret_cast<const unsigned long long*>(&r->ops[t % LAT_RING_OPS]) + threadIdx.x);
       __syncthreads();
-      const LatOp op = s_op;
+      if (s_op.kind == LAT_CHANNEL) {
+        ChanCall c;
+        memcpy(&c, s_op.call, sizeof c);
+        chan_call(c);  // posts its own status to the caller's mailbox
+        __syncthreads();
+        continue;
+      }
+      const LatOp& op = s_op;  // thread 0 rewrites it only after the barrier below
       lat_copy(op);
       // the barrier, then one cumulative fence before the counters
       __syncthreads();
@@ -169,17 +194,43 @@ void lat_destroy(Instance* in) {
   in->lat_ring_dev = nullptr;
 }
 
-// Publish validated ops (at most LAT_RING_OPS in flight) to the server,
-// launching one when the last has announced its exit.
-hicr_status lat_submit(Instance* in, const hicr_op_t* ops, uint64_t count) {
-  LatRing* r = in->lat_ring;
-  volatile unsigned long long* done = &r->done;
-  // room in the ring (bounded wait: a live server drains it)
+// Wait (bounded: a live server drains the ring) until `count` more entries fit.
+static hicr_status lat_room(Instance* in, uint64_t count) {
+  volatile unsigned long long* done = &in->lat_ring->done;
   const uint64_t t0 = now_ns();
   while (in->lat_head + count - *done > LAT_RING_OPS) {
     if (now_ns() - t0 > 10ull * 1000000000ull) return HICR_ERR_TIMEOUT;
     std::this_thread::yield();
   }
+  return HICR_OK;
+}
+
+// Publish the entries written up to lat_head, then launch a server if the
+// last one launched has announced its exit. Publish, full fence, then read
+// the announcement (the server stores its announcement, fences, then reads
+// head): one of the two sees the other's store.
+static hicr_status lat_publish(Instance* in) {
+  LatRing* r = in->lat_ring;
+  __atomic_store_n(&r->head, (unsigned long long)in->lat_head, __ATOMIC_SEQ_CST);
+  __atomic_thread_fence(__ATOMIC_SEQ_CST);
+  if (__atomic_load_n(&r->exit_epoch, __ATOMIC_SEQ_CST) == in->lat_epoch) {
+    LatArgs a;
+    a.ring = in->lat_ring_dev;
+    a.dt = in->dt;
+    a.epoch = ++in->lat_epoch;
+    a.idle_ns = in->lat_idle_ns;
+    k_lat_server<<<1, LAT_THREADS, 0, in->lat_stream>>>(a);
+    HICR_CUDA(in, cudaGetLastError());
+  }
+  return HICR_OK;
+}
+
+// Publish validated ops (at most LAT_RING_OPS in flight) to the server,
+// launching one when the last has announced its exit.
+hicr_status lat_submit(Instance* in, const hicr_op_t* ops, uint64_t count) {
+  LatRing* r = in->lat_ring;
+  hicr_status st = lat_room(in, count);
+  if (st != HICR_OK) return st;
   uint64_t mask[TAG_WORDS] = {};
   for (uint64_t i = 0; i < count; ++i) {
     const HostSlot& d = in->slots[ops[i].dst];
@@ -192,27 +243,61 @@ hicr_status lat_submit(Instance* in, const hicr_op_t* ops, uint64_t count) {
     o.sslot = ops[i].src;
     o.dtag = d.tag;
     o.stag = s.tag;
+    o.kind = LAT_COPY;
     mask[d.tag >> 6] |= 1ull << (d.tag & 63);
     mask[s.tag >> 6] |= 1ull << (s.tag & 63);
   }
   in->lat_head += count;
-  // publish, full fence, then read the last server's exit announcement (the
-  // server stores its announcement, fences, then reads head)
-  __atomic_store_n(&r->head, (unsigned long long)in->lat_head, __ATOMIC_SEQ_CST);
-  __atomic_thread_fence(__ATOMIC_SEQ_CST);
   for (int w = 0; w < TAG_WORDS; ++w)
     for (uint64_t m = mask[w]; m; m &= m - 1) in->tag_lat[w * 64 + __builtin_ctzll(m)] = in->lat_head;
-  // a new server when the last one launched has announced its exit
-  if (__atomic_load_n(&r->exit_epoch, __ATOMIC_SEQ_CST) == in->lat_epoch) {
-    LatArgs a;
-    a.ring = in->lat_ring_dev;
-    a.dt = in->dt;
-    a.epoch = ++in->lat_epoch;
-    a.idle_ns = in->lat_idle_ns;
-    k_lat_server<<<1, LAT_THREADS, 0, in->lat_stream>>>(a);
-    HICR_CUDA(in, cudaGetLastError());
+  return lat_publish(in);
+}
+
+bool lat_takes_calls(Instance* in) {
+  if (!in->lat_idle_ns || !in->lat_ring || in->capturing) return false;
+  if (in->opaque) {
+    // other work was issued on the communication stream: quiet once the done
+    // event (recorded after every launch there) has completed
+    const cudaError_t e = cudaEventQuery(in->done_ev);
+    if (e != cudaSuccess) {
+      if (e != cudaErrorNotReady) (void)cudaGetLastError();
+      return false;
+    }
+    in->opaque = false;
   }
-  return HICR_OK;
+  return *(volatile unsigned long long*)in->sig_mirror >= in->sig_issued;
+}
+
+hicr_status lat_channel_call(Instance* in, const ChanCall& c, volatile int* status) {
+  hicr_status st = lat_room(in, 1);
+  if (st != HICR_OK) return st;
+  LatOp& o = in->lat_ring->ops[in->lat_head % LAT_RING_OPS];
+  o.kind = LAT_CHANNEL;
+  memcpy(o.call, &c, sizeof c);
+  in->lat_head += 1;
+  if ((st = lat_publish(in)) != HICR_OK) return st;
+  // The server posts the status last, behind a system-scope fence. Bounded
+  // wait; a server that ended without posting it (a failed kernel) ends it.
+  const uint64_t t0 = now_ns();
+  for (uint32_t spins = 0;; ++spins) {
+    const int v = *status;
+    if (v != 1) {
+      __atomic_thread_fence(__ATOMIC_ACQUIRE);
+      return (hicr_status)v;
+    }
+    if ((spins & 255) == 255) {
+      const cudaError_t e = cudaStreamQuery(in->lat_stream);
+      if (e != cudaErrorNotReady) {
+        if (*status != 1) continue;
+        if (e != cudaSuccess) return cuda_fail(in, e, "latency-mode server");
+        return HICR_ERR_DEVICE;
+      }
+      const uint64_t dt = now_ns() - t0;
+      if (dt > 60ull * 1000000000ull) return HICR_ERR_TIMEOUT;
+      if (dt > 2000000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (dt > 50000) std::this_thread::yield();
+    }
+  }
 }
 
 // Wait until the server has completed op count `target` (mapped memory).

@@ -13,9 +13,11 @@
  *   spsc_push_pop   hicr_channel_push of one 64-byte token, then
  *                   hicr_channel_pop of it;
  *   dobj_get_fence  hicr_dobj_get of a 16-byte Data Object, then hicr_fence;
- *   memcpy16_fence_latency_mode, dobj_get_fence_latency_mode
- *                   the same two with hicr_set_latency_mode on (a persistent
- *                   server kernel takes the small copies; no launch per call).
+ *   memcpy16_fence_latency_mode, dobj_get_fence_latency_mode,
+ *   spsc_push_pop_latency_mode
+ *                   the same three with hicr_set_latency_mode on (a persistent
+ *                   server kernel takes the small copies and the channel
+ *                   calls; no launch per call).
  * Exit status 0 on success, 1 on any library error (its name is printed).
  */
 #include <stdint.h>
@@ -149,7 +151,17 @@ int main(int argc, char** argv) {
       CHECK(hicr_fence(inst, 0, fence_to));
       if (i >= 0) t[i] = now_ns() - t0;
     }
-    report("dobj_get_fence_latency_mode", t, reps, 1);
+    report("dobj_get_fence_latency_mode", t, reps, 0);
+    hicr_channel_t ch;
+    CHECK(hicr_spsc_create(inst, 64, 1024, &ch));
+    for (int i = -warm; i < reps; ++i) {
+      const uint64_t t0 = now_ns();
+      CHECK(hicr_channel_push(inst, ch, 0, a, 64 * (uint64_t)(i & 1023), 1));
+      CHECK(hicr_channel_pop(inst, ch, 1));
+      if (i >= 0) t[i] = now_ns() - t0;
+    }
+    report("spsc_push_pop_latency_mode", t, reps, 1);
+    CHECK(hicr_channel_destroy(inst, ch));
     CHECK(hicr_set_latency_mode(inst, 0));
     CHECK(hicr_dobj_release(inst, id));
   }

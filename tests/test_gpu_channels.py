@@ -41,17 +41,41 @@ def src_slot(h, inst, data: np.ndarray):
     return s, t
 
 
+def _rewrite_pool(h, inst, rng, s, pool, s2, other):
+    """Overwrite a random range of the source slot by a memcpy from a second
+    slot (a small batch: in latency mode the server takes it) and mirror it in
+    the oracle's copy of the pool. The next push reads the new bytes: a
+    channel call comes after everything issued before it."""
+    n = int(rng.integers(1, min(len(pool), 512) + 1))
+    d = int(rng.integers(0, len(pool) - n + 1))
+    o = int(rng.integers(0, len(other) - n + 1))
+    assert h.hicr_memcpy(inst, s, d, s2, o, n) == 0
+    pool[d:d + n] = other[o:o + n]
+
+
+LATENCY = pytest.mark.parametrize("idle_us", [0, 3000], ids=["launch", "latency_mode"])
+
+
+@LATENCY
 @pytest.mark.parametrize("seed,ts,cap", [(0, 8, 5), (1, 24, 7), (2, 64, 16)])
-def test_spsc_host_calls_match_oracle(h, inst, seed, ts, cap):
+def test_spsc_host_calls_match_oracle(h, inst, seed, ts, cap, idle_us):
+    """Statuses, offsets and token bytes of push / peek / pop / depth match
+    the SPSC oracle; with latency mode on, the calls go to the server kernel
+    and the pool is rewritten by server-side copies between them."""
     rng = np.random.default_rng(seed)
+    assert h.hicr_set_latency_mode(inst, idle_us) == 0
     st, ch = h.hicr_spsc_create(inst, ts, cap)
     assert st == 0
     orc = oc.SpscOracle(ts, cap)
     pool = rng.integers(0, 256, ts * 4 * cap, dtype=np.uint8)
     s, keep = src_slot(h, inst, pool)
+    other = rng.integers(0, 256, 4096, dtype=np.uint8)
+    s2, keep2 = src_slot(h, inst, other)
     for step in range(300):
         r = rng.random()
-        if r < 0.45:
+        if r < 0.08:
+            _rewrite_pool(h, inst, rng, s, pool, s2, other)
+        elif r < 0.45:
             k = int(rng.integers(0, cap + 2))
             off = int(rng.integers(0, len(pool) - k * ts + 1))
             exp = orc.push(pool[off:off + k * ts])
@@ -105,18 +129,24 @@ def test_mpsc_golden_wraparound_through_the_abi(h, inst):
             assert h.hicr_channel_depth(inst, ch)[1:] == (int(f[1]), int(f[2])), f
 
 
+@LATENCY
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_mpsc_host_calls_match_oracle(h, inst, seed):
+def test_mpsc_host_calls_match_oracle(h, inst, seed, idle_us):
     rng = np.random.default_rng(seed)
+    assert h.hicr_set_latency_mode(inst, idle_us) == 0
     P, R, M = 4, 1 << 12, 8
     st, ch = h.hicr_mpsc_create(inst, P, R, M)
     assert st == 0
     orc = oc.MpscOracle(P, R, M)
     pool = rng.integers(0, 256, 1 << 16, dtype=np.uint8)
     s, keep = src_slot(h, inst, pool)
+    other = rng.integers(0, 256, 4096, dtype=np.uint8)
+    s2, keep2 = src_slot(h, inst, other)
     for step in range(400):
         r = rng.random()
-        if r < 0.5:
+        if r < 0.06:
+            _rewrite_pool(h, inst, rng, s, pool, s2, other)
+        elif r < 0.5:
             p = int(rng.integers(0, P))
             n = int(rng.choice([0, 1, 7, 16, 17, 100, 500, 1500, 2100, 4096, 5000]))
             off = int(rng.integers(0, len(pool) - n + 1))
@@ -400,21 +430,27 @@ def test_pingpong_delivers_the_message(h, inst, nbytes, ctas, off):
     assert h.hicr_mem_free(inst, s) == 0
 
 
+@LATENCY
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_nonlocking_host_calls_match_oracle(h, inst, seed):
+def test_nonlocking_host_calls_match_oracle(h, inst, seed, idle_us):
     """Non-locking MPSC (one ring per producer): statuses, offsets within the
     producer's ring, sizes, producers, sequence numbers and payloads match the
     non-locking oracle under random programs that fill and wrap the rings."""
     rng = np.random.default_rng(seed)
+    assert h.hicr_set_latency_mode(inst, idle_us) == 0
     P, R, M = 3, 1 << 10, 4
     st, ch = h.hicr_mpsc_nl_create(inst, P, R, M)
     assert st == 0
     orc = oc.MpscNonLockingOracle(P, R, M)
     pool = rng.integers(0, 256, 1 << 14, dtype=np.uint8)
     s, keep = src_slot(h, inst, pool)
+    other = rng.integers(0, 256, 4096, dtype=np.uint8)
+    s2, keep2 = src_slot(h, inst, other)
     for step in range(400):
         r = rng.random()
-        if r < 0.5:
+        if r < 0.06:
+            _rewrite_pool(h, inst, rng, s, pool, s2, other)
+        elif r < 0.5:
             p = int(rng.integers(0, P))
             n = int(rng.choice([0, 1, 9, 16, 100, 333, 512, 700, 1024, 1100]))
             off = int(rng.integers(0, len(pool) - n + 1))

@@ -185,7 +185,7 @@ def test_c_latency_harness(h, inst):
     d = json.loads(r.stdout)
     print(d, flush=True)
     for k in ("memcpy16_fence", "fence_idle", "exec_await", "spsc_push_pop", "dobj_get_fence",
-              "memcpy16_fence_latency_mode", "dobj_get_fence_latency_mode"):
+              "memcpy16_fence_latency_mode", "dobj_get_fence_latency_mode", "spsc_push_pop_latency_mode"):
         assert 0 < d[k]["p50_us"] <= d[k]["p99_us"] <= d[k]["max_us"]
 
 
