@@ -45,7 +45,10 @@ def _rewrite_pool(h, inst, rng, s, pool, s2, other):
     """Overwrite a random range of the source slot by a memcpy from a second
     slot (a small batch: in latency mode the server takes it) and mirror it in
     the oracle's copy of the pool. The next push reads the new bytes: a
-    channel call comes after everything issued before it."""
+    channel call comes after everything issued before it. The fence first
+    completes the previous rewrite: two copies that write the same bytes in
+    one epoch are unordered (the oracle would apply them in issue order)."""
+    assert h.hicr_fence(inst, 0, 10**10) == 0
     n = int(rng.integers(1, min(len(pool), 512) + 1))
     d = int(rng.integers(0, len(pool) - n + 1))
     o = int(rng.integers(0, len(other) - n + 1))
