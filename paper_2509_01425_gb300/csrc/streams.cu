@@ -55,6 +55,23 @@ __device__ __forceinline__ uint4 words_to_vec(unsigned long long w0, unsigned lo
   return x;
 }
 
+// Load one pass of a copying producer: staged tokens q, q + sstep, ... (mod
+// W) of the batch positions tl, tl + tpi, ... below k, vector column jv.
+// Returns the staged position after the pass.
+__device__ __forceinline__ unsigned long long spsc_load_pass(uint4 (&x)[SPSC_U], const uint8_t* src, unsigned ts,
+                                                             unsigned jv, unsigned long long q,
+                                                             unsigned long long sstep, unsigned long long W,
+                                                             unsigned long long tl, unsigned long long tpi,
+                                                             unsigned long long k) {
+#pragma unroll
+  for (int u = 0; u < SPSC_U; ++u) {
+    if (tl + (unsigned long long)u * tpi < k) x[u] = __ldcg(reinterpret_cast<const uint4*>(src + q * ts) + jv);
+    q += sstep;
+    if (q >= W) q -= W;
+  }
+  return q;
+}
+
 template <bool COPY, bool VERIFY, bool CAPTURE>
 __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   __shared__ int s_stop;
@@ -84,6 +101,13 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
   const unsigned long long sstep = tpi % W;
   unsigned long long cached = base, max_occ = 0, done = 0, mism = 0, dig = 0;
   int stop = 0;
+  // A copying producer's staged tokens do not depend on ring room: each
+  // batch's first pass is loaded before the previous batch is published and
+  // before the room check, so that one L2 round trip per batch overlaps the
+  // hand-off. xp holds the pass to store next.
+  uint4 xp[SPSC_U];
+  if (COPY && producer && fast)
+    spsc_load_pass(xp, src, v.ts, jv, tl0 % W, sstep, W, tl0, tpi, min((unsigned long long)a.batch, a.tokens));
   for (unsigned long long s0 = 0; s0 < a.tokens; s0 += a.batch) {
     const unsigned long long k = min((unsigned long long)a.batch, a.tokens - s0);
     if (tid == 0) {
@@ -116,24 +140,24 @@ __global__ void __launch_bounds__(512) k_spsc_stream(SpscStreamArgs a) {
       // (and staged positions) advance by `step` (`sstep`) without a
       // division per vector
       unsigned long long slot = (base + s0 + tl0) % v.cap;
-      unsigned long long sp = COPY ? (s0 + tl0) % W : 0;
+      // the staged position of this batch's second pass (the first is in xp)
+      unsigned long long sp = COPY ? (s0 + tl0 + (unsigned long long)SPSC_U * tpi) % W : 0;
       for (unsigned long long tl = tl0; tl < k; tl += (unsigned long long)SPSC_U * tpi) {
         if (producer) {
           if (COPY) {
-            uint4 x[SPSC_U];
-            unsigned long long q = sp;
 #pragma unroll
             for (int u = 0; u < SPSC_U; ++u) {
-              if (tl + (unsigned long long)u * tpi < k) x[u] = __ldcg(reinterpret_cast<const uint4*>(src + q * v.ts) + jv);
-              q += sstep;
-              if (q >= W) q -= W;
-            }
-            sp = q;
-#pragma unroll
-            for (int u = 0; u < SPSC_U; ++u) {
-              if (tl + (unsigned long long)u * tpi < k) *(reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv) = x[u];
+              if (tl + (unsigned long long)u * tpi < k) *(reinterpret_cast<uint4*>(v.ring + slot * v.ts) + jv) = xp[u];
               slot += step;
               if (slot >= v.cap) slot -= v.cap;
+            }
+            // then the next pass: of this batch, or the next batch's first
+            const unsigned long long tn = tl + (unsigned long long)SPSC_U * tpi;
+            if (tn < k) {
+              sp = spsc_load_pass(xp, src, v.ts, jv, sp, sstep, W, tn, tpi, k);
+            } else if (s0 + k < a.tokens) {
+              const unsigned long long k2 = min((unsigned long long)a.batch, a.tokens - s0 - k);
+              spsc_load_pass(xp, src, v.ts, jv, (s0 + k + tl0) % W, sstep, W, tl0, tpi, k2);
             }
           } else {
 #pragma unroll
