@@ -302,6 +302,11 @@ inline uint64_t now_ns() {
              std::chrono::steady_clock::now().time_since_epoch())
       .count();
 }
+// Host waits on device progress spin for WAIT_SPIN_NS, then yield the core
+// until WAIT_YIELD_NS, then sleep in short steps. A timed sleep wakes up a
+// timer slack late (tens of microseconds), so the yielding phase covers the
+// waits of the hot path (a fence on an epoch of a few milliseconds).
+static constexpr uint64_t WAIT_SPIN_NS = 50000, WAIT_YIELD_NS = 50000000;
 
 }  // namespace hicr
 

@@ -294,8 +294,8 @@ hicr_status lat_channel_call(Instance* in, const ChanCall& c, volatile int* stat
       }
       const uint64_t dt = now_ns() - t0;
       if (dt > 60ull * 1000000000ull) return HICR_ERR_TIMEOUT;
-      if (dt > 2000000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-      else if (dt > 50000) std::this_thread::yield();
+      if (dt > WAIT_YIELD_NS) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (dt > WAIT_SPIN_NS) std::this_thread::yield();
     }
   }
 }
@@ -317,8 +317,8 @@ hicr_status lat_wait(Instance* in, uint64_t target, uint64_t timeout_ns) {
     if ((spins & 63) == 0) {
       const uint64_t dt = now_ns() - t0;
       if (dt >= timeout_ns) return HICR_ERR_TIMEOUT;
-      if (dt > 2000000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-      else if (dt > 50000) std::this_thread::yield();
+      if (dt > WAIT_YIELD_NS) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (dt > WAIT_SPIN_NS) std::this_thread::yield();
     }
   }
 }

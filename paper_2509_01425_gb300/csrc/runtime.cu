@@ -99,21 +99,21 @@ static hicr_status wait_signal(Instance* in, uint64_t target, uint64_t timeout_n
     if ((spins & 63) == 0) {
       const uint64_t dt = now_ns() - t0;
       if (dt >= timeout_ns) return *m >= target ? HICR_OK : HICR_ERR_TIMEOUT;
-      if (dt > 2000000) std::this_thread::sleep_for(std::chrono::microseconds(20));
-      else if (dt > 50000) std::this_thread::yield();
+      if (dt > WAIT_YIELD_NS) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      else if (dt > WAIT_SPIN_NS) std::this_thread::yield();
     }
   }
 }
 
 hicr_status wait_event(Instance* in, cudaEvent_t ev, uint64_t timeout_ns) {
   const uint64_t t0 = now_ns();
-  uint32_t spins = 0;
   for (;;) {
     cudaError_t e = cudaEventQuery(ev);
     if (e == cudaSuccess) return HICR_OK;
     if (e != cudaErrorNotReady) return cuda_fail(in, e, "cudaEventQuery");
-    if (now_ns() - t0 >= timeout_ns) return HICR_ERR_TIMEOUT;
-    if (++spins > 2000) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    const uint64_t dt = now_ns() - t0;
+    if (dt >= timeout_ns) return HICR_ERR_TIMEOUT;
+    if (dt > WAIT_YIELD_NS) std::this_thread::sleep_for(std::chrono::microseconds(20));
     else std::this_thread::yield();
   }
 }
