@@ -170,8 +170,18 @@ def test_budget_limits_admission_and_everything_completes(h, inst):
     burst = reqs["kind"] == 1
     for i in np.nonzero(burst)[0][:50]:
         assert int(res["digest"][i]) == expected_digest(tmpl, 1, int(reqs["tmpl"][i]))
+    # the device clock at each completion: every request has one, and their
+    # spread fits the host-observed span of the run (first arrival to last
+    # completion seen; the two clocks share no origin, only differences)
+    dev = res["device_done_ns"].astype(np.int64)
+    assert (dev > 0).all()
+    assert dev.max() - dev.min() <= int(stats.wall_ns) + 1_000_000
+    # the host loop's longest pause ends inside the run, after it began
+    assert 0 < stats.max_poll_gap_ns <= stats.max_poll_gap_at_ns
     st, pres, pstats = h.hicr_serve_run_plain(inst, ss.srv, reqs, int(1e12), T)
     assert st == 0 and pstats.completed == len(reqs)
+    assert (pres["device_done_ns"] == 0).all()  # the plain form has no device clock per request
+    assert 0 < pstats.max_poll_gap_ns <= pstats.max_poll_gap_at_ns
     ss.free()
 
 
