@@ -102,6 +102,39 @@ def test_spsc_host_calls_match_oracle(h, inst, seed, ts, cap, idle_us):
     assert h.hicr_channel_depth(inst, ch)[0] == h.HICR_ERR_INVALID
 
 
+def test_latency_mode_push_after_a_stream_copy_reads_its_bytes(h, inst):
+    """In latency mode a channel call goes to the server only while the
+    communication stream is quiet. A 4 MiB memcpy is beyond the server's
+    small-op limit, so the stream runs it; the push issued right after it
+    must come behind it (a launch after the copy) and carry the new bytes."""
+    rng = np.random.default_rng(11)
+    assert h.hicr_set_latency_mode(inst, 3000) == 0
+    ts, cap, n = 64, 64, 4 << 20
+    st, ch = h.hicr_spsc_create(inst, ts, cap)
+    assert st == 0
+    orc = oc.SpscOracle(ts, cap)
+    pool = np.zeros(n, dtype=np.uint8)
+    s, keep = src_slot(h, inst, pool)
+    other = rng.integers(0, 256, n, dtype=np.uint8)
+    s2, keep2 = src_slot(h, inst, other)
+    for rep in range(6):
+        fresh = rng.integers(0, 256, n, dtype=np.uint8)
+        keep2.copy_(torch.from_numpy(fresh))
+        torch.cuda.synchronize()
+        assert h.hicr_memcpy(inst, s, 0, s2, 0, n) == 0
+        off = int(rng.integers(0, n // ts - 8)) * ts
+        assert h.hicr_channel_push(inst, ch, 0, s, off, 8) == orc.push(fresh[off:off + 8 * ts]), rep
+        for j in range(8):
+            gst, info = h.hicr_channel_peek(inst, ch, j)
+            est, einfo = orc.peek(j)
+            assert gst == est == om.OK and info == einfo, (rep, j)
+            assert (ring_bytes(h, inst, ch, info[0], ts) == orc.token(j)).all(), (rep, j)
+        assert h.hicr_channel_pop(inst, ch, 8) == orc.pop(8) == om.OK
+        assert h.hicr_fence(inst, 0, 10**10) == 0
+    assert h.hicr_set_latency_mode(inst, 0) == 0
+    assert h.hicr_channel_destroy(inst, ch) == 0
+
+
 def test_mpsc_golden_wraparound_through_the_abi(h, inst):
     from tests.test_oracle_channels import load_mpsc_golden
     prog = load_mpsc_golden()
