@@ -46,7 +46,11 @@ typedef struct {
   uint32_t n_channels;    /* MPSC channels (one consumer CTA each), >= 1 */
   uint32_t max_msgs;      /* metadata entries per channel (power of two) */
   uint64_t ring_bytes;    /* per channel ring (power of two) */
-  uint32_t chunk_bytes;   /* memcpy work unit (cost bytes, multiple of 1024) */
+  uint32_t chunk_bytes;   /* largest memcpy work unit (cost bytes, multiple of 1024). When a request
+                             is published it is cut into enough units (of at least 16 KiB) to
+                             occupy the worker warps that no published work waits for, so that on
+                             an idle engine it spreads over many warps; with every warp busy its
+                             units are chunk_bytes */
   uint32_t op_cost_bytes; /* per-op charge of the cost model */
   uint32_t verify;        /* 1: never reuse destination regions, so that results
                              can be digested after the run (tests) */

@@ -9,7 +9,9 @@
 //   CTA 0, warp 0   dispatcher: acquires the doorbell, copies each new request
 //                   into the per-request device table, gives it a contiguous range
 //                   of work units (memcpy: one unit per cost chunk of its
-//                   template; burst: one unit per message group) and
+//                   template, cut into enough chunks of SRV_MIN_UNIT to
+//                   chunk_bytes to occupy the idle worker warps; burst: one
+//                   unit per message group) and
 //                   publishes units_pub;
 //   CTAs 1..C       one MPSC consumer per channel (windowed drain as in the
 //                   channel stream kernel); completes burst requests;
@@ -46,6 +48,9 @@ static constexpr unsigned SRV_THREADS = 512;
 static constexpr unsigned SRV_MAX_CH = 64;
 static constexpr int SRV_WIN = 64;
 static constexpr int SRV_PIECE = 512;
+// While worker warps are idle, a memcpy request is cut into enough work units
+// to occupy them, of at least SRV_MIN_UNIT cost bytes (at most chunk_bytes).
+static constexpr unsigned long long SRV_MIN_UNIT = 16ull << 10;
 
 struct SrvReq {
   unsigned long long U;       // first unit
@@ -54,6 +59,7 @@ struct SrvReq {
   unsigned long long done;    // completed chunks / consumed messages
   unsigned long long digest;  // burst digest accumulator
   unsigned int N, need, kind, tmpl;
+  unsigned int unit, pad;     // memcpy: cost bytes per work unit, chosen at dispatch
   unsigned long long gres;    // burst: message groups that have reserved their tickets
   unsigned long long claimed; // units handed out (may pass N by failed claims)
 };
@@ -64,7 +70,8 @@ struct SrvReq {
 static constexpr unsigned SRV_GROUP_MSGS = 8;
 // Workers claim among at most this many of the oldest requests that may have
 // unclaimed units, the one with the fewest unclaimed units first (under
-// overload the requests behind the window wait in order).
+// overload the requests behind the window wait in order; there the units
+// are all chunk_bytes, so fewest units is least work).
 static constexpr unsigned long long SRV_PS_WINDOW = 32;
 static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
 
@@ -93,7 +100,6 @@ struct SrvArgs {
   const unsigned long long* t_opbase;
   const unsigned long long* t_nops;
   const unsigned long long* t_cbase;
-  const unsigned long long* t_chunks;
   const unsigned long long* t_total;
   const unsigned long long* msizes;
   const unsigned long long* moffs;
@@ -162,7 +168,7 @@ __device__ __forceinline__ bool srv_abort(const SrvArgs& a, unsigned long long d
 // line from before the entry was written.
 struct ReqView {
   unsigned long long U, id, dst;
-  unsigned int N, need, kind, tmpl;
+  unsigned int N, need, kind, tmpl, unit;
 };
 __device__ __forceinline__ ReqView load_req(const SrvReq* e) {
   ReqView r;
@@ -173,6 +179,7 @@ __device__ __forceinline__ ReqView load_req(const SrvReq* e) {
   r.need = __ldcg(&e->need);
   r.kind = __ldcg(&e->kind);
   r.tmpl = __ldcg(&e->tmpl);
+  r.unit = __ldcg(&e->unit);
   return r;
 }
 
@@ -188,6 +195,7 @@ __device__ __forceinline__ void srv_complete(const SrvArgs& a, SrvReq* e) {
 __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
   ws_set(a, WS_DISPATCH);
   unsigned long long r = 0, U = 0;
+  const unsigned long long workers = (unsigned long long)(gridDim.x - 1 - a.n_ch) * (SRV_THREADS / 32);
   unsigned long long msgs[SRV_MAX_CH];
   for (unsigned c = 0; c < a.n_ch; ++c) msgs[c] = 0;
   unsigned sleep_ns = 64;
@@ -199,8 +207,24 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
       const unsigned long long w0 = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r));
       const unsigned long long dst = ld_rlx_sys(reinterpret_cast<const unsigned long long*>(a.hdesc + r) + 1);
       const unsigned kind = (unsigned)w0, t = (unsigned)(w0 >> 32);
-      const unsigned long long N = kind == 0 ? a.t_chunks[t] : a.t_ngrp[t];
-      const unsigned long long need = kind == 0 ? a.t_chunks[t] : a.t_nmsg[t];
+      // A memcpy request's work unit: enough units to occupy the worker
+      // warps that no published unit waits for, each between SRV_MIN_UNIT
+      // and chunk_bytes of cost. One warp copies a unit, so on an idle engine
+      // a request spreads over many warps and finishes in about one small
+      // unit's copy; with every warp busy the units are chunk_bytes and the
+      // claims as few as they can be.
+      unsigned long long unit = a.chunk, N, need;
+      if (kind == 0) {
+        const unsigned long long total = a.t_total[t];
+        const unsigned long long backlog = U - min(U, ld_rlx(&a.ctl->claim.v));
+        const unsigned long long idle = workers > backlog ? workers - backlog : 0;
+        const unsigned long long want = max(1ull, idle);
+        unit = min((unsigned long long)a.chunk, max(SRV_MIN_UNIT, (total + want - 1) / want));
+        N = need = (total + unit - 1) / unit;
+      } else {
+        N = a.t_ngrp[t];
+        need = a.t_nmsg[t];
+      }
       e->U = U;
       e->id = r;
       e->dst = dst;
@@ -212,6 +236,7 @@ __device__ void srv_dispatcher(const SrvArgs& a, unsigned long long deadline) {
       e->need = (unsigned)need;
       e->kind = kind;
       e->tmpl = t;
+      e->unit = (unsigned)unit;
       if (kind == 1) msgs[r % a.n_ch] += need;
       if (need == 0) srv_complete(a, e);
       __threadfence();
@@ -247,7 +272,7 @@ __device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   const hicr_op_t* ops = a.tops + a.t_opbase[t];
   const unsigned long long nops = a.t_nops[t];
   const unsigned long long* cstart = a.tcstart + a.t_cbase[t];
-  const unsigned long long chunk = a.chunk, total = a.t_total[t];
+  const unsigned long long chunk = rv.unit, total = a.t_total[t];
   const unsigned long long lo = k * chunk, hi = min(lo + chunk, total);
   const unsigned long long dst = rv.dst;
   for (unsigned long long i = find_op(cstart, nops, lo, lane); i < nops; ++i) {
@@ -736,7 +761,7 @@ struct Server {
   std::vector<MpscView> views;
   // templates (host copies; uploaded lazily)
   std::vector<hicr_op_t> tops;
-  std::vector<unsigned long long> tcstart, t_opbase, t_nops, t_cbase, t_chunks, t_total, t_region;
+  std::vector<unsigned long long> tcstart, t_opbase, t_nops, t_cbase, t_total, t_region;
   std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg, gstart, t_gbase, t_ngrp;
   hicr_slot_t staging = 0;
   bool have_staging = false;
@@ -789,7 +814,7 @@ static char* put(char* p, const std::vector<T>& v, const T** dst) {
 static hicr_status srv_upload(Instance* in, Server* sv) {
   if (sv->uploaded) return HICR_OK;
   if (sv->t_nops.empty()) sv->t_nops.push_back(0), sv->t_opbase.push_back(0), sv->t_cbase.push_back(0),
-      sv->t_chunks.push_back(0), sv->t_total.push_back(0), sv->t_region.push_back(0), sv->tcstart.push_back(0);
+      sv->t_total.push_back(0), sv->t_region.push_back(0), sv->tcstart.push_back(0);
   if (sv->t_nmsg.empty()) sv->t_nmsg.push_back(0), sv->t_mbase.push_back(0), sv->t_gbase.push_back(0),
       sv->t_ngrp.push_back(0);
   if (sv->gstart.empty()) sv->gstart.push_back(0);
@@ -799,7 +824,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
   const size_t bytes = al(sv->tops.size() * sizeof(hicr_op_t)) +
                        8 * (al(sv->tcstart.size() * 8) + al(sv->t_opbase.size() * 8) + al(sv->t_nops.size() * 8) +
-                            al(sv->t_cbase.size() * 8) + al(sv->t_chunks.size() * 8) + al(sv->t_total.size() * 8) +
+                            al(sv->t_cbase.size() * 8) + al(sv->t_total.size() * 8) +
                             al(sv->msizes.size() * 8) + al(sv->moffs.size() * 8) + al(sv->t_mbase.size() * 8) +
                             al(sv->t_nmsg.size() * 8) + al(sv->gstart.size() * 8) + al(sv->t_gbase.size() * 8) +
                             al(sv->t_ngrp.size() * 8) + al(sv->mcap.size() * 8)) / 8;
@@ -822,7 +847,6 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   UP(t_opbase, sv->t_opbase);
   UP(t_nops, sv->t_nops);
   UP(t_cbase, sv->t_cbase);
-  UP(t_chunks, sv->t_chunks);
   UP(t_total, sv->t_total);
   UP(msizes, sv->msizes);
   UP(moffs, sv->moffs);
@@ -953,7 +977,6 @@ hicr_status hicr_serve_add_memcpy_template(hicr_instance_t h, hicr_serve_t s, co
   }
   sv->tcstart.push_back(c);
   sv->t_total.push_back(c);
-  sv->t_chunks.push_back((c + sv->cfg.chunk_bytes - 1) / sv->cfg.chunk_bytes);
   sv->t_region.push_back(region_bytes);
   unsigned long long tb = 0;
   for (uint64_t i = 0; i < count; ++i) tb += ops[i].n;
