@@ -60,20 +60,22 @@ struct SrvReq {
   unsigned long long digest;  // burst digest accumulator
   unsigned int N, need, kind, tmpl;
   unsigned int unit, pad;     // memcpy: cost bytes per work unit, chosen at dispatch
-  unsigned long long gres;    // burst: message groups that have reserved their tickets
+  unsigned long long gres;    // burst: message groups that have reserved their tickets (whole
+                              // reservation: 1 once the burst's reservation is made)
+  unsigned long long wbase;   // burst, whole reservation: the channel's reserve word before it
   unsigned long long claimed; // units handed out (may pass N by failed claims)
 };
 
 // A burst's messages are cut into groups of at most SRV_GROUP_MSGS
 // consecutive messages whose rounded sizes sum to at most SRV_GROUP_BYTES
 // (a larger message is a group of its own); one work unit per group.
-static constexpr unsigned SRV_GROUP_MSGS = 8;
+static constexpr unsigned SRV_GROUP_MSGS = 2;
 // Workers claim among at most this many of the oldest requests that may have
 // unclaimed units, the one with the fewest unclaimed units first (under
 // overload the requests behind the window wait in order; there the units
 // are all chunk_bytes, so fewest units is least work).
 static constexpr unsigned long long SRV_PS_WINDOW = 32;
-static constexpr unsigned long long SRV_GROUP_BYTES = 256ull << 10;
+static constexpr unsigned long long SRV_GROUP_BYTES = 32ull << 10;
 
 struct SrvHostDesc {
   unsigned int kind, tmpl;
@@ -108,6 +110,7 @@ struct SrvArgs {
   const unsigned long long* gstart;   // group starts (message index within the template), ng + 1 per template
   const unsigned long long* t_gbase;  // template's first entry in gstart
   const unsigned long long* t_ngrp;
+  const unsigned long long* t_whole;  // burst template reserves all its messages at once (1) or by groups
   const uint8_t* staging;
   DevTables dt;
   const MpscView* chans;
@@ -297,10 +300,15 @@ __device__ void srv_copy_chunk(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   }
 }
 
-// Push group k of a burst (producer = request index). Lane 0 waits until
-// group k-1 has reserved, reserves the group's tickets and ring bytes with one
-// compare-and-swap and passes the turn on; then the warp copies the messages
-// and publishes their metadata.
+// Push group k of a burst (producer = request index). A burst that takes at
+// most half the ring and half the message slots is reserved whole: group 0's
+// lane 0 places all its messages (the channel's placement rule, from the
+// current reserve word) and takes their tickets and ring bytes with one
+// compare-and-swap; every group then replays the placement from that word to
+// find its messages' positions, so the groups copy side by side. A larger
+// burst reserves group by group: group k waits until group k-1 has reserved,
+// reserves its own messages and passes the turn on. Then the warp copies the
+// group's messages and publishes their metadata.
 __device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, unsigned long long k, unsigned lane,
                                unsigned long long deadline) {
   const unsigned long long id = rv.id;
@@ -315,7 +323,68 @@ __device__ bool srv_push_group(const SrvArgs& a, SrvReq* e, const ReqView& rv, u
   unsigned long long W = 0;
   int stop = 0;
   ws_set(a, WS_RESERVE);
-  if (lane == 0) {
+  if (a.t_whole[t]) {
+    if (lane == 0) {
+      const unsigned long long nmsg = a.t_nmsg[t];
+      if (k == 0) {
+        // place the whole burst and reserve it
+        unsigned long long freed = ld_acq(&v.st->freed.v), mt = ld_acq(&v.st->msg_tail.v);
+        unsigned sleep_ns = 32;
+        for (;;) {
+          W = ld_rlx(&v.st->reserve.v);
+          unsigned long long b = W & MASK40;
+          for (unsigned long long i = 0; i < nmsg; ++i) {
+            const unsigned long long ri = round16(a.msizes[mbase + i]), pos = b & (v.R - 1);
+            if (pos + ri > v.R) b = (b + (v.R - pos)) & MASK40;
+            b = (b + ri) & MASK40;
+          }
+          const unsigned long long t0 = W >> 40;
+          bool room = ((b - freed) & MASK40) <= v.R && (((t0 + nmsg) - mt) & MASK24) <= v.M;
+          if (!room) {
+            freed = ld_acq(&v.st->freed.v);
+            mt = ld_acq(&v.st->msg_tail.v);
+            room = ((b - freed) & MASK40) <= v.R && (((t0 + nmsg) - mt) & MASK24) <= v.M;
+          }
+          if (room && atomicCAS(&v.st->reserve.v, W, (((t0 + nmsg) & MASK24) << 40) | b) == W) break;
+          if (srv_abort(a, deadline)) {
+            stop = 1;
+            break;
+          }
+          if (!room) {
+            __nanosleep(sleep_ns);
+            sleep_ns = min(sleep_ns * 2, 4096u);
+          }
+        }
+        if (!stop) {
+          e->wbase = W;
+          st_rel(&e->gres, 1ull);
+        }
+      } else {
+        unsigned sleep_ns = 32;
+        while (ld_acq(&e->gres) == 0) {  // group 0 has not reserved yet
+          if (srv_abort(a, deadline)) {
+            stop = 1;
+            break;
+          }
+          __nanosleep(sleep_ns);
+          sleep_ns = min(sleep_ns * 2, 256u);
+        }
+        if (!stop) W = __ldcg(&e->wbase);
+      }
+      if (!stop) {
+        // this group's positions: the placement replayed from the burst's word
+        unsigned long long b = W & MASK40;
+        for (unsigned long long i = 0; i < m1; ++i) {
+          const unsigned long long ri = round16(a.msizes[mbase + i]), pos = b & (v.R - 1);
+          if (pos + ri > v.R) b = (b + (v.R - pos)) & MASK40;
+          if (i >= m0) st[i - m0] = b;
+          b = (b + ri) & MASK40;
+        }
+        // the group's first ticket, in the form the copy below expects
+        W = (((W >> 40) + m0) & MASK24) << 40;
+      }
+    }
+  } else if (lane == 0) {
     unsigned sleep_ns = 32;
     while (ld_acq(&e->gres) != k) {  // the previous group's turn
       if (srv_abort(a, deadline)) {
@@ -762,7 +831,7 @@ struct Server {
   // templates (host copies; uploaded lazily)
   std::vector<hicr_op_t> tops;
   std::vector<unsigned long long> tcstart, t_opbase, t_nops, t_cbase, t_total, t_region;
-  std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg, gstart, t_gbase, t_ngrp;
+  std::vector<unsigned long long> msizes, moffs, t_mbase, t_nmsg, gstart, t_gbase, t_ngrp, t_whole;
   hicr_slot_t staging = 0;
   bool have_staging = false;
   bool uploaded = false;
@@ -816,7 +885,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   if (sv->t_nops.empty()) sv->t_nops.push_back(0), sv->t_opbase.push_back(0), sv->t_cbase.push_back(0),
       sv->t_total.push_back(0), sv->t_region.push_back(0), sv->tcstart.push_back(0);
   if (sv->t_nmsg.empty()) sv->t_nmsg.push_back(0), sv->t_mbase.push_back(0), sv->t_gbase.push_back(0),
-      sv->t_ngrp.push_back(0);
+      sv->t_ngrp.push_back(0), sv->t_whole.push_back(0);
   if (sv->gstart.empty()) sv->gstart.push_back(0);
   if (sv->tops.empty()) sv->tops.push_back(hicr_op_t{0, 0, 0, 0, 0});
   if (sv->msizes.empty()) sv->msizes.push_back(0), sv->moffs.push_back(0), sv->mcap.push_back(0);
@@ -827,7 +896,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
                             al(sv->t_cbase.size() * 8) + al(sv->t_total.size() * 8) +
                             al(sv->msizes.size() * 8) + al(sv->moffs.size() * 8) + al(sv->t_mbase.size() * 8) +
                             al(sv->t_nmsg.size() * 8) + al(sv->gstart.size() * 8) + al(sv->t_gbase.size() * 8) +
-                            al(sv->t_ngrp.size() * 8) + al(sv->mcap.size() * 8)) / 8;
+                            al(sv->t_ngrp.size() * 8) + al(sv->t_whole.size() * 8) + al(sv->mcap.size() * 8)) / 8;
   char* d = nullptr;
   HICR_CUDA(in, cudaMalloc(&d, bytes + 4096));
   sv->dev_tmpl = d;
@@ -855,6 +924,7 @@ static hicr_status srv_upload(Instance* in, Server* sv) {
   UP(gstart, sv->gstart);
   UP(t_gbase, sv->t_gbase);
   UP(t_ngrp, sv->t_ngrp);
+  UP(t_whole, sv->t_whole);
   UP(mcap, sv->mcap);
 #undef UP
   sv->uploaded = true;
@@ -1034,6 +1104,11 @@ hicr_status hicr_serve_add_burst_template(hicr_instance_t h, hicr_serve_t s, con
   }
   sv->gstart.push_back(count);
   sv->t_ngrp.push_back(ng);
+  // reserved whole when the burst takes at most half the ring and half the
+  // message slots (so that it fits an emptied channel)
+  uint64_t rb = 0;
+  for (uint64_t i = 0; i < count; ++i) rb += round16(sizes[i]);
+  sv->t_whole.push_back(rb <= sv->cfg.ring_bytes / 2 && count <= sv->cfg.max_msgs / 2 ? 1 : 0);
   *tmpl = t;
   return HICR_OK;
 }

@@ -29,13 +29,13 @@ SEED = 3
 T = 30_000_000_000
 
 
-def small_setup(h, inst, verify=True, budget=512 << 20):
+def small_setup(h, inst, verify=True, budget=512 << 20, ring_bytes=8 << 20):
     src_w = configs.batched(SEED, n_slots=8, total_bytes=64 << 20, slot_lo=1 << 20, slot_hi=16 << 20, n_ops=50,
                             n_hi=64 << 10)
     tmpl = configs.serve_templates(SEED, src_w, n_templates=16, max_ops=48, max_msgs=24, n_hi=256 << 10,
                                    msg_hi=16 << 10)
     assert tmpl.region_bytes.max() <= 16 << 20
-    ss = bench.ServeSetup(h, inst, src_w, tmpl, seed=SEED, budget=budget, n_channels=4, ring_bytes=8 << 20,
+    ss = bench.ServeSetup(h, inst, src_w, tmpl, seed=SEED, budget=budget, n_channels=4, ring_bytes=ring_bytes,
                           max_msgs=1024, chunk_bytes=64 << 10, op_cost_bytes=2048, verify=verify)
     return src_w, tmpl, ss
 
@@ -113,8 +113,17 @@ def _oracle_burst(tmpl, t, ring=8 << 20, max_msgs=1024):
     return np.concatenate(out) if out else np.zeros(0, dtype=np.uint8)
 
 
-def test_mix_delivers_the_oracle_bytes(h, inst):
-    src_w, tmpl, ss = small_setup(h, inst, verify=False, budget=2 << 30)  # room for every kept region
+@pytest.mark.parametrize("ring_bytes", [8 << 20, 32 << 10])
+def test_mix_delivers_the_oracle_bytes(h, inst, ring_bytes):
+    """Every memcpy region and every burst message of a mix, byte for byte.
+    With 8 MiB rings every burst is reserved whole (its groups copy side by
+    side); with 64 KiB rings the bursts above half a ring reserve group by
+    group, and wrap the ring often."""
+    src_w, tmpl, ss = small_setup(h, inst, verify=False, budget=2 << 30, ring_bytes=ring_bytes)  # room for every kept region
+    bb16 = np.array([int(((tmpl.msg_sizes[tmpl.msg_start[t]:tmpl.msg_start[t + 1]].astype(np.int64) + 15) // 16 * 16).sum())
+                     for t in range(16)])
+    if ring_bytes == 32 << 10:
+        assert (bb16 > ring_bytes // 2).any() and (bb16 <= ring_bytes // 2).any()  # both reservation forms
     tr = configs.serve_trace(SEED + 2, rate=200_000.0, duration_s=0.002, n_templates=16)
     reqs = ss.requests(tr)
     burst = reqs["kind"] == 1
