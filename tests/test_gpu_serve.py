@@ -117,7 +117,7 @@ def _oracle_burst(tmpl, t, ring=8 << 20, max_msgs=1024):
 def test_mix_delivers_the_oracle_bytes(h, inst, ring_bytes):
     """Every memcpy region and every burst message of a mix, byte for byte.
     With 8 MiB rings every burst is reserved whole (its groups copy side by
-    side); with 64 KiB rings the bursts above half a ring reserve group by
+    side); with 32 KiB rings the bursts above half a ring reserve group by
     group, and wrap the ring often."""
     src_w, tmpl, ss = small_setup(h, inst, verify=False, budget=2 << 30, ring_bytes=ring_bytes)  # room for every kept region
     bb16 = np.array([int(((tmpl.msg_sizes[tmpl.msg_start[t]:tmpl.msg_start[t + 1]].astype(np.int64) + 15) // 16 * 16).sum())
