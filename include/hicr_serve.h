@@ -14,8 +14,11 @@
  *    device-memory budget minus the channel rings) has room for their region;
  *  - admitted requests are published through a doorbell in mapped host memory;
  *    a dispatcher warp moves them into a device-side request table and cuts
- *    them into work units (memcpy: cost chunks; burst: groups of up to 8
- *    messages); worker warps claim units from the 32 oldest requests that
+ *    them into work units (memcpy: cost chunks, small enough to occupy the
+ *    idle worker warps; burst: groups of up to 2 messages or 32 KiB, whose
+ *    channel tickets and ring bytes the first group reserves for the whole
+ *    burst when it takes at most half the ring); worker warps claim units
+ *    from the 32 oldest requests that
  *    still have unclaimed units, taking the one with the fewest unclaimed
  *    units first (continuous batching with shortest-remaining-first order
  *    inside that window: work of requests admitted at different times
