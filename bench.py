@@ -1234,8 +1234,10 @@ def run_control_small(args):
     wrap-up kernels, and the two stream kernels); two allocation-free batches
     of 10,000 ops (k_plan, k_scan, k_copy); four single memcpys, each
     followed by a fence (k_copy_small); the same four in latency mode with a
-    100 us idle window, 1 ms apart (four k_lat_server launches); and a 1 ms
-    bounded device wait (k_wait_test)."""
+    100 us idle window, 1 ms apart (four k_lat_server launches); four SPSC
+    push + pop pairs in latency mode, 1 ms apart (four more k_lat_server
+    launches, each taking a push and a pop); and a 1 ms bounded device wait
+    (k_wait_test)."""
     import torch
     from paper_2509_01425_gb300 import build
     build.build()
@@ -1291,6 +1293,13 @@ def run_control_small(args):
         h.check(h.hicr_memcpy(inst, b, 41 * MiB + 64 * i, a, 64 * i, 16 << i), "memcpy")
         h.check(h.hicr_fence(inst, 0, 10_000_000_000), "fence")
         time.sleep(0.001)
+    # channel calls in latency mode: one server takes a push and its pop
+    spsc = h.check(h.hicr_spsc_create(inst, 64, 4096), "spsc_create")
+    for i in range(4):
+        h.check(h.hicr_channel_push(inst, spsc, 0, a, 4096 * i, 16), "spsc push")
+        h.check(h.hicr_channel_pop(inst, spsc, 16), "spsc pop")
+        time.sleep(0.001)
+    h.check(h.hicr_channel_destroy(inst, spsc), "destroy")
     h.check(h.hicr_set_latency_mode(inst, 0), "latency mode off")
     st, wst, waited = h.hicr_util_wait_test(inst, 1_000_000)
     h.check(st, "wait_test")
