@@ -188,7 +188,7 @@ hicr_status hicr_spsc_stream(hicr_instance_t inst, const hicr_channel_t* chans, 
 /* Options of hicr_spsc_stream_ex. */
 typedef struct {
   hicr_slot_t src;         /* HBM slot the producers copy tokens from (when src_tokens > 0) */
-  uint32_t reserved;
+  uint32_t flags;          /* HICR_SPSC_DIGEST_ONLY, or 0 */
   uint64_t src_off;        /* byte offset in src of channel 0's staged tokens (16-byte aligned address) */
   uint64_t src_tokens;     /* tokens staged per channel: channel i's at src_off + i * src_tokens *
                               token_size; 0 = the producers write the payload rule instead */
@@ -198,6 +198,11 @@ typedef struct {
   uint64_t capture_stride; /* multiple of 16, >= tokens * token_size */
 } hicr_spsc_stream_opts_t;
 
+/* With producers that write the payload rule: the consumer does not check the
+ * words against the rule (mismatches is 0) and only digests the consumed
+ * stream, as with copy producers. */
+#define HICR_SPSC_DIGEST_ONLY 1u
+
 /* hicr_spsc_stream with two more forms, chosen by `opts`:
  *  - copy producers (src_tokens > 0): a push is what Sec. 4.3 makes it, a
  *    copy from a memory slot into the consumer's ring; token s of the i-th
@@ -206,10 +211,13 @@ typedef struct {
  *    0); it digests the consumed stream as always;
  *  - capture (d_capture != NULL): the consumer also stores every token it
  *    consumed, in consumption order, so that a caller can compare the
- *    delivered stream token by token (tests; it adds a write per token).
+ *    delivered stream token by token (tests; it adds a write per token);
+ *  - digest only (flags HICR_SPSC_DIGEST_ONLY, payload-rule producers): the
+ *    consumer skips the per-word check, so the run measures the channel
+ *    rather than the check; its digest still identifies the stream.
  * All channels must have the same token size when either form is used.
- * Errors: as hicr_spsc_stream, plus INVALID (NULL opts, unaligned or short
- * capture area, unaligned staged tokens), UNSUPPORTED (src not in HBM), BOUNDS
+ * Errors: as hicr_spsc_stream, plus INVALID (NULL opts, unknown flags, unaligned
+ * or short capture area, unaligned staged tokens), UNSUPPORTED (src not in HBM), BOUNDS
  * (staged tokens outside src). */
 hicr_status hicr_spsc_stream_ex(hicr_instance_t inst, const hicr_channel_t* chans, uint32_t n, uint64_t tokens,
                                 uint32_t batch, const hicr_spsc_stream_opts_t* opts, uint64_t timeout_ns,

@@ -1023,8 +1023,10 @@ static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
     ts = c->token_size;
     views[i] = spsc_view(c);
   }
+  if (opts && (opts->flags & ~HICR_SPSC_DIGEST_ONLY)) return HICR_ERR_INVALID;
   const bool copy = opts && opts->src_tokens > 0;
   const bool capture = opts && opts->d_capture != nullptr;
+  const bool verify = !copy && !(opts && (opts->flags & HICR_SPSC_DIGEST_ONLY));
   const uint8_t* src = nullptr;
   if (copy) {
     // the staged tokens of all n channels lie inside the source slot, in HBM,
@@ -1046,7 +1048,9 @@ static hicr_status spsc_stream_run(hicr_instance_t h, const hicr_channel_t* chan
   }
   const void* k;
   if (copy) k = capture ? (const void*)k_spsc_stream<true, false, true> : (const void*)k_spsc_stream<true, false, false>;
-  else k = capture ? (const void*)k_spsc_stream<false, true, true> : (const void*)k_spsc_stream<false, true, false>;
+  else if (verify)
+    k = capture ? (const void*)k_spsc_stream<false, true, true> : (const void*)k_spsc_stream<false, true, false>;
+  else k = capture ? (const void*)k_spsc_stream<false, false, true> : (const void*)k_spsc_stream<false, false, false>;
   // both CTAs of every channel must be resident at once
   int per_sm = 0;
   HICR_CUDA(in, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 512, 0));

@@ -508,8 +508,11 @@ _mpsc_nl_stream_capture = _decl("hicr_mpsc_nl_stream_capture",
 
 
 class hicr_spsc_stream_opts_t(C.Structure):
-    _fields_ = [("src", u32), ("reserved", u32), ("src_off", u64), ("src_tokens", u64), ("d_capture", vp),
+    _fields_ = [("src", u32), ("flags", u32), ("src_off", u64), ("src_tokens", u64), ("d_capture", vp),
                 ("capture_stride", u64)]
+
+
+HICR_SPSC_DIGEST_ONLY = 1
 
 
 _spsc_stream_ex = _decl("hicr_spsc_stream_ex", [H, vp, u32, u64, u32, C.POINTER(hicr_spsc_stream_opts_t), u64, vp])
@@ -610,10 +613,10 @@ def hicr_spsc_stream(inst, chans, tokens, batch, timeout_ns=60_000_000_000):
 
 
 def hicr_spsc_stream_ex(inst, chans, tokens, batch, src=0, src_off=0, src_tokens=0, d_capture=None,
-                        capture_stride=0, timeout_ns=60_000_000_000):
+                        capture_stride=0, timeout_ns=60_000_000_000, flags=0):
     arr = (u32 * len(chans))(*chans)
     res = (hicr_spsc_result_t * len(chans))()
-    o = hicr_spsc_stream_opts_t(src, 0, src_off, src_tokens, _ptr(d_capture), capture_stride)
+    o = hicr_spsc_stream_opts_t(src, flags, src_off, src_tokens, _ptr(d_capture), capture_stride)
     st = _spsc_stream_ex(inst, C.addressof(arr), len(chans), tokens, batch, C.byref(o), timeout_ns, C.addressof(res))
     return st, list(res)
 

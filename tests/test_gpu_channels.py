@@ -233,6 +233,7 @@ def _rule_stream(channel, tokens, ts):
     return splitmix.spsc_token_words(channel, 0, tokens, ts // 8).astype("<u8").view(np.uint8)
 
 
+@pytest.mark.parametrize("digest_only", [False, True], ids=["verify", "digest_only"])
 @pytest.mark.parametrize("n_ch,cap,ts,tokens,batch", [
     (64, 4096, 64, 100_000, 256),
     (8, 16, 64, 1003, 16),
@@ -240,15 +241,17 @@ def _rule_stream(channel, tokens, ts):
     (2, 4096, 128, 70_000, 4096),
     (3, 100, 48, 2_000, 7),          # 3 vectors per token: the general (non-divisible) layout
 ])
-def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch):
+def test_spsc_stream_exact_token_stream(h, inst, n_ch, cap, ts, tokens, batch, digest_only):
     """The consumers' captured streams equal, token by token, the payload-rule
     stream pushed through the SPSC oracle (every channel of the small cases;
     the first and last channel of the 64-channel case, whose other channels
-    are compared with the payload rule's words directly)."""
+    are compared with the payload rule's words directly). Both consumer forms:
+    checking every word against the rule, and digesting only."""
     chans = [h.hicr_spsc_create(inst, ts, cap)[1] for _ in range(n_ch)]
     cap_buf = torch.zeros(n_ch * tokens * ts, dtype=torch.uint8, device="cuda")
     st, res = h.hicr_spsc_stream_ex(inst, chans, tokens, batch, d_capture=cap_buf.data_ptr(),
-                                    capture_stride=tokens * ts)
+                                    capture_stride=tokens * ts,
+                                    flags=h.HICR_SPSC_DIGEST_ONLY if digest_only else 0)
     assert st == 0
     got = cap_buf.cpu().numpy().reshape(n_ch, tokens * ts)
     for i, r in enumerate(res):
@@ -304,6 +307,13 @@ def test_spsc_copy_producers_deliver_the_staged_tokens(h, inst, n_ch, cap, ts, t
         h.HICR_ERR_BOUNDS
     assert h.hicr_spsc_stream_ex(inst, chans, tokens, batch, src=s, src_off=8, src_tokens=staged)[0] == \
         h.HICR_ERR_INVALID
+
+
+def test_spsc_stream_rejects_unknown_flags(h, inst):
+    ch = h.hicr_spsc_create(inst, 64, 64)[1]
+    assert h.hicr_spsc_stream_ex(inst, [ch], 10, 8, flags=2)[0] == h.HICR_ERR_INVALID
+    st, res = h.hicr_spsc_stream_ex(inst, [ch], 10, 8, flags=h.HICR_SPSC_DIGEST_ONLY)
+    assert st == 0 and res[0].popped == 10 and res[0].digest == _spsc_expected_digest(0, 10)
 
 
 def test_spsc_stream_rejects_more_channels_than_can_be_resident(h, inst):
