@@ -650,6 +650,19 @@ def hicr_mpsc_nl_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_
     return st, list(res)
 
 
+def hicr_mpsc_stream_capture(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                             consumer_ctas, d_log, log_stride, d_capture, d_cap_off, timeout_ns=120_000_000_000):
+    return hicr_mpsc_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                            consumer_ctas, d_log, log_stride, timeout_ns, d_capture=d_capture, d_cap_off=d_cap_off)
+
+
+def hicr_mpsc_nl_stream_capture(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                                consumer_ctas, d_log, log_stride, d_capture, d_cap_off, timeout_ns=120_000_000_000):
+    return hicr_mpsc_nl_stream(inst, chans, n_producers, msgs_per_producer, d_sizes, d_src_off, staging, group,
+                               consumer_ctas, d_log, log_stride, timeout_ns, d_capture=d_capture,
+                               d_cap_off=d_cap_off)
+
+
 # ---------------------------------------------------------------------------
 # Serving (include/hicr_serve.h)
 # ---------------------------------------------------------------------------
