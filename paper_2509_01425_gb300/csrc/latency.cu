@@ -87,11 +87,11 @@ __global__ void __launch_bounds__(LAT_THREADS) k_lat_server(LatArgs a) {
       int ex = 0;
       if (h == tail && !announced) {
         const unsigned long long t0 = lat_now();
-        unsigned sleep_ns = 32;
+        // each poll is a round trip to host memory (about a microsecond), so
+        // the pause between polls stays short: it only adds to the latency
         while (h == tail) {
           if (lat_ld_acq_sys(&r->stop) || lat_now() - t0 > a.idle_ns) break;
-          __nanosleep(sleep_ns);
-          sleep_ns = sleep_ns < 256 ? sleep_ns * 2 : 256;
+          __nanosleep(32);
           h = lat_ld_acq_sys(&r->head);
         }
         if (h == tail) {
